@@ -1,0 +1,181 @@
+"""Python face of the plain C oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg; the product path never imports it.
+
+`align(...)` runs one pair; `align_batch(...)` runs many on a thread pool.  Both
+return plain dicts / numpy arrays.  The library is compiled with gcc on first
+use (or by `build()`), next to this file.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+INF = np.iinfo(np.int64).max
+OP_CHARS = {1: "I", 2: "D", 7: "=", 8: "X"}
+STATUS = {0: "OK", 1: "DROPPED", 2: "UNREACHABLE", 3: "EMPTY"}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("mode", C.c_int32), ("affine", C.c_int32), ("gap_open", C.c_int64),
+        ("gap_extend", C.c_int64), ("alphabet", C.c_int32), ("subst", C.POINTER(C.c_int8)),
+        ("use_band", C.c_int32), ("band_literal", C.c_int32), ("band", C.c_int64),
+        ("use_xdrop", C.c_int32), ("xdrop", C.c_int64), ("traceback", C.c_int32),
+        ("order", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("score", C.c_int64), ("q_begin", C.c_int64), ("q_end", C.c_int64),
+        ("r_begin", C.c_int64), ("r_end", C.c_int64), ("status", C.c_int32),
+        ("cells", C.c_int64), ("n_ops", C.c_int64), ("last_k", C.c_int64),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no CUDA)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+        if force or stale:
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC,
+                                   "-lpthread"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_align.restype = C.c_int
+        L.orc_align.argtypes = [C.POINTER(Params), C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                C.POINTER(Result), C.c_void_p, C.c_int64]
+        L.orc_align_batch.restype = C.c_int
+        L.orc_align_batch.argtypes = [C.POINTER(Params), C.c_int64] + [C.c_void_p] * 6 + [
+            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.orc_domain.restype = C.c_int64
+        L.orc_domain.argtypes = [C.POINTER(Params), C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                 C.c_void_p, C.c_void_p, C.c_int64]
+        _lib = L
+    return _lib
+
+
+def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
+                band_literal=False, xdrop=None, traceback=True, order=0, **_ignored):
+    s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
+    a = int(s.shape[0])
+    p = Params()
+    p.mode = 1 if mode in ("local", 1) else 0
+    p.affine = 1 if affine else 0
+    p.gap_open = int(gap_open)
+    p.gap_extend = int(gap_extend)
+    p.alphabet = a
+    p.subst = s.ctypes.data_as(C.POINTER(C.c_int8))
+    p.use_band = 0 if band is None else 1
+    p.band_literal = 1 if band_literal else 0
+    p.band = 0 if band is None else int(band)
+    p.use_xdrop = 0 if xdrop is None else 1
+    p.xdrop = 0 if xdrop is None else (INF if xdrop == INF else int(xdrop))
+    p.traceback = 1 if traceback else 0
+    p.order = int(order)
+    p._keep = s  # keep the table alive
+    return p
+
+
+def _res_dict(r: Result, ops=None):
+    d = dict(score=r.score, q_begin=r.q_begin, q_end=r.q_end, r_begin=r.r_begin,
+             r_end=r.r_end, status=r.status, cells=r.cells, n_ops=r.n_ops, last_k=r.last_k)
+    if ops is not None:
+        d["cigar"] = ops
+    return d
+
+
+def align(q, r, subst, **kw) -> dict:
+    """Align one pair; returns score, coordinates, status, cells and the CIGAR
+    (numpy uint32 BAM ops) when traceback is on."""
+    p = make_params(subst, **kw)
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.uint8))
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.uint8))
+    res = Result()
+    cap = int(q.shape[0] + r.shape[0] + 1)
+    ops = np.zeros(cap, dtype=np.uint32)
+    rc = lib().orc_align(C.byref(p), q.ctypes.data, q.shape[0], r.ctypes.data, r.shape[0],
+                         C.byref(res), ops.ctypes.data, cap)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return _res_dict(res, ops[: res.n_ops].copy() if p.traceback else None)
+
+
+RESULT_DTYPE = np.dtype([("score", np.int64), ("q_begin", np.int64), ("q_end", np.int64),
+                         ("r_begin", np.int64), ("r_end", np.int64), ("status", np.int32),
+                         ("pad", np.int32), ("cells", np.int64), ("n_ops", np.int64),
+                         ("last_k", np.int64)])
+assert RESULT_DTYPE.itemsize == C.sizeof(Result)
+
+
+def align_batch(batch, nthreads: int | None = None, **kw):
+    """Align every pair of a synth.Batch (or anything with the same fields).
+
+    Returns (results, ops, ops_off): a structured array with one row per pair,
+    the concatenated CIGAR ops and where each pair's ops start."""
+    sc = dict(batch.scoring)
+    sc.update(kw)
+    p = make_params(batch.subst, **sc)
+    n = int(batch.q_len.shape[0])
+    res = np.zeros(n, dtype=RESULT_DTYPE)
+    cap = (batch.q_len.astype(np.uint64) + batch.r_len.astype(np.uint64) + 1)
+    off = np.zeros(n, dtype=np.uint64)
+    if n:
+        off[1:] = np.cumsum(cap[:-1])
+    ops = np.zeros(int(cap.sum()) if (p.traceback and n) else 1, dtype=np.uint32)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    q = np.ascontiguousarray(batch.q_seq)
+    r = np.ascontiguousarray(batch.r_seq)
+    qo = np.ascontiguousarray(batch.q_off, dtype=np.uint64)
+    ro = np.ascontiguousarray(batch.r_off, dtype=np.uint64)
+    ql = np.ascontiguousarray(batch.q_len, dtype=np.uint32)
+    rl = np.ascontiguousarray(batch.r_len, dtype=np.uint32)
+    rc = lib().orc_align_batch(C.byref(p), n, q.ctypes.data, qo.ctypes.data, ql.ctypes.data,
+                               r.ctypes.data, ro.ctypes.data, rl.ctypes.data, res.ctypes.data,
+                               ops.ctypes.data if p.traceback else None,
+                               off.ctypes.data, cap.ctypes.data, int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return res, ops, off
+
+
+def domain(q, r, subst, **kw):
+    """Every cell the run evaluated, as an (n, 2) int64 array of (i, j), and an
+    alive (unpruned) flag per cell."""
+    p = make_params(subst, **kw)
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.uint8))
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.uint8))
+    n = lib().orc_domain(C.byref(p), q.ctypes.data, q.shape[0], r.ctypes.data, r.shape[0],
+                         None, None, 0)
+    ij = np.zeros((max(n, 1), 2), dtype=np.int64)
+    alive = np.zeros(max(n, 1), dtype=np.uint8)
+    lib().orc_domain(C.byref(p), q.ctypes.data, q.shape[0], r.ctypes.data, r.shape[0],
+                     ij.ctypes.data, alive.ctypes.data, n)
+    return ij[:n], alive[:n].astype(bool)
+
+
+def cigar_str(ops) -> str:
+    return "".join(f"{int(o) >> 4}{OP_CHARS[int(o) & 15]}" for o in ops)

@@ -1,0 +1,113 @@
+"""Independent checkers used to pin the oracle (test code only).
+
+Nothing here calls the oracle or the CUDA path: these are brute-force path
+enumeration, a textbook two-row Levenshtein distance, and a CIGAR re-scorer.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+OPS = {1: "I", 2: "D", 7: "=", 8: "X"}
+
+
+@functools.lru_cache(maxsize=None)
+def all_paths(M: int, N: int):
+    """Every monotone path (0,0) -> (M,N) with steps 'M' (i+1, j+1), 'H' (j+1)
+    and 'V' (i+1), as tuples.  Their number is the Delannoy number D(M, N)."""
+    if M == 0 and N == 0:
+        return ((),)
+    out = []
+    if M > 0 and N > 0:
+        out += [p + ("M",) for p in all_paths(M - 1, N - 1)]
+    if N > 0:
+        out += [p + ("H",) for p in all_paths(M, N - 1)]
+    if M > 0:
+        out += [p + ("V",) for p in all_paths(M - 1, N)]
+    return tuple(out)
+
+
+def path_score(path, q, r, S, o, e):
+    """Score one path: substitution scores on 'M' steps, and o + L*e for every
+    maximal run of L equal gap steps ('H' runs and 'V' runs are separate gaps)."""
+    i = j = 0
+    sc = 0
+    prev = None
+    for mv in path:
+        if mv == "M":
+            sc += int(S[q[i]][r[j]])
+            i += 1
+            j += 1
+        elif mv == "H":
+            sc -= e + (o if prev != "H" else 0)
+            j += 1
+        else:
+            sc -= e + (o if prev != "V" else 0)
+            i += 1
+        prev = mv
+    return sc
+
+
+def brute_global(q, r, S, o, e):
+    return max(path_score(p, q, r, S, o, e) for p in all_paths(len(q), len(r)))
+
+
+def brute_local(q, r, S, o, e):
+    best = 0  # the empty alignment
+    M, N = len(q), len(r)
+    for i0 in range(M + 1):
+        for i1 in range(i0, M + 1):
+            for j0 in range(N + 1):
+                for j1 in range(j0, N + 1):
+                    if i1 - i0 == 0 and j1 - j0 == 0:
+                        continue
+                    best = max(best, brute_global(q[i0:i1], r[j0:j1], S, o, e))
+    return best
+
+
+def levenshtein(a, b) -> int:
+    """Textbook two-row edit distance (unit substitution / insertion / deletion)."""
+    prev = list(range(len(b) + 1))
+    for i in range(1, len(a) + 1):
+        cur = [i] + [0] * len(b)
+        for j in range(1, len(b) + 1):
+            cur[j] = min(prev[j] + 1, cur[j - 1] + 1, prev[j - 1] + (a[i - 1] != b[j - 1]))
+        prev = cur
+    return prev[-1]
+
+
+def rescore_cigar(ops, q, r, S, o, e, q_begin, r_begin):
+    """Walk a BAM CIGAR over q[q_begin:], r[r_begin:]; return (score, query
+    consumed, reference consumed).  Raises if '=' / 'X' disagree with the codes."""
+    i, j, sc = q_begin, r_begin, 0
+    for op in np.asarray(ops, dtype=np.uint32).tolist():
+        n, c = op >> 4, OPS[op & 15]
+        if n <= 0:
+            raise AssertionError("empty CIGAR op")
+        if c in "=X":
+            for _ in range(n):
+                if (q[i] == r[j]) != (c == "="):
+                    raise AssertionError(f"op {c} at ({i},{j}) disagrees with residues")
+                sc += int(S[q[i]][r[j]])
+                i += 1
+                j += 1
+        elif c == "I":
+            sc -= o + n * e
+            i += n
+        else:
+            sc -= o + n * e
+            j += n
+    return sc, i - q_begin, j - r_begin
+
+
+def cigar_from_str(s: str):
+    code = {"I": 1, "D": 2, "=": 7, "X": 8}
+    out, num = [], ""
+    for ch in s:
+        if ch.isdigit():
+            num += ch
+        else:
+            out.append((int(num) << 4) | code[ch])
+            num = ""
+    return np.array(out, dtype=np.uint32)

@@ -1,0 +1,50 @@
+"""Plants plausible mistakes in copies of the oracle (on the CPU) and checks that
+the pin suite (test_oracle_pins.py) rejects every one of them: a transposed
+operand, a dropped term, a wrong sign, each tie-break flipped, the X-drop rule
+and domain altered, the band edge shifted, the CIGAR op table swapped and the
+cell counter widened."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "transposed_subst": ("c->p->subst[(int)c->q[i - 1] * a + (int)c->r[j - 1]]",
+                         "c->p->subst[(int)c->r[j - 1] * a + (int)c->q[i - 1]]"),
+    "E_open_drops_o": ("out->E = l->H - o - e;", "out->E = l->H - e;"),
+    "F_ext_wrong_sign": ("int64_t ext = u->F - e;", "int64_t ext = u->F + e;"),
+    "E_tie_prefers_ext": ("if (!out->vE || ext > out->E) {", "if (!out->vE || ext >= out->E) {"),
+    "H_tie_E_over_diag": ("if (out->vE && (!out->vH || out->E > out->H))",
+                          "if (out->vE && (!out->vH || out->E >= out->H))"),
+    "H_tie_F_over_E": ("if (out->vF && (!out->vH || out->F > out->H))",
+                       "if (out->vF && (!out->vH || out->F >= out->H))"),
+    "xdrop_running_max": ("    best = nbest;\n", "    if (nbest > best) best = nbest;\n"),
+    "xdrop_non_strict": ("tmp.H >= best - X", "tmp.H > best - X"),
+    "xdrop_domain_no_growth": ("if (lo - 1 > dl) dl = lo - 1;", "if (lo > dl) dl = lo;"),
+    "band_edge_shift": ("c.hi = ((N - M) > 0 ? (N - M) : 0) + p->band;\n    }\n  }\n  memset(res",
+                        "c.hi = ((N - M) > 0 ? (N - M) : 0) + p->band - 1;\n    }\n  }\n  memset(res"),
+    "diag_op_swapped": ("(c->q[i - 1] == c->r[j - 1]) ? ORC_OP_EQ : ORC_OP_X",
+                        "(c->q[i - 1] != c->r[j - 1]) ? ORC_OP_EQ : ORC_OP_X"),
+    "E_emits_I": ("mv[n++] = ORC_OP_D;", "mv[n++] = ORC_OP_I;"),
+    "cells_count_boundary": ("      if (i >= 1 && j >= 1) ++*cells;\n      if (alive)",
+                             "      ++*cells;\n      if (alive)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    a, b = MUTANTS[name]
+    assert src.count(a) >= 1, "mutation site moved; update the mutant"
+    ign = shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*")
+    for d in ("oracle", "tests", "synth"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=ign)
+    (tmp_path / "oracle" / "oracle.c").write_text(src.replace(a, b, 1))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], capture_output=True, text=True, cwd=tmp_path,
+                       timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
