@@ -1,0 +1,346 @@
+"""Benchmark: batched Smith-Waterman protein alignment with CIGAR traceback.
+
+Workload (one step = one filtr_align_batch call over the whole batch): 100,000
+protein pairs, lengths i.i.d. U[100, 1000], query 30-70% identical to the
+reference, seeded 20x20 substitution matrix, affine gaps (open 11, extend 1),
+local alignment, score + end coordinates + CIGAR.  Metric: GCUPS (cells whose
+recurrence was evaluated / second), inputs resident in HBM.
+
+Also reported on the same JSON line: the same call through the host-buffer
+entry point (e2e), the plain one-launch-per-pair form on a sample, the
+roofline of the forward kernel against the measured integer throughput, the
+CPU oracle on a bounded sample, and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "protein-sw-100k"
+METRIC = "GCUPS batched vs plain per-pair launch (bit-exact); serving p50/p99 latency"
+# integer operations per cell in the affine local update with traceback, as the
+# recurrence states them: E (1 add-max), F (1 add-max), H - (o+e) (1 add),
+# diagonal + s (1 add), H (1 three-way max with 0), 4 choice bits (4 compares)
+OPS_PER_CELL = 9
+CPU_SAMPLE_PAIRS = 5000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=100_000)
+    ap.add_argument("--plain-sample", type=int, default=3000)
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.samples)}
+        if not self.samples:
+            return out
+        try:
+            sm = [float(s[1]) for s in self.samples]
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(float(s[2]) for s in self.samples)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            seen = set()
+            for s in self.samples:
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower().startswith("active"):
+                        seen.add(nm)
+            out["reasons"] = sorted(seen)
+            out["power_w_max"] = max(float(s[3]) for s in self.samples)
+        except Exception:
+            pass
+        return out
+
+
+def ncu_traffic():
+    """dram bytes per forward launch from the committed ncu summary, if present."""
+    path = os.path.join(ROOT, "profiles", "k_full_protein_sw.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("dram_bytes_per_cell:"):
+            try:
+                return float(line.split(":")[1].split()[0])
+            except Exception:
+                return None
+    return None
+
+
+def cpu_baseline(batch, sc, npairs):
+    import oracle
+
+    idx = np.arange(min(npairs, batch.n))
+    sub = batch.subset(idx)
+    nth = os.cpu_count() or 1
+    t = time.perf_counter()
+    res, _, _ = oracle.align_batch(sub, nthreads=nth, **sc)
+    dt = time.perf_counter() - t
+    cells = int(res["cells"].sum())
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": nth, "kind": "oracle",
+            "sample": f"first {len(idx)} of the {batch.n} pairs ({cells} cells), {dt:.1f} s"}
+
+
+def run_reference(args):
+    import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    batch = synth.protein_pairs(n=min(args.pairs, max(args.cpu_sample, 1)), seed=2)
+    sc = dict(batch.scoring)
+    times, cells = [], 0
+    per_step = max(1, min(args.cpu_sample // max(args.steps + args.warmup, 1), batch.n))
+    import oracle
+
+    nth = os.cpu_count() or 1
+    for s in range(args.warmup + args.steps):
+        lo = (s * per_step) % batch.n
+        sub = batch.subset(np.arange(lo, min(lo + per_step, batch.n)))
+        t = time.perf_counter()
+        res, _, _ = oracle.align_batch(sub, nthreads=nth, **sc)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append(dt)
+            cells += int(res["cells"].sum())
+    tot = sum(times)
+    v = cells / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / max(len(times), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": per_step,
+                       "note": "CPU oracle (plain C, int64, all host cores) on a bounded sample of the workload"},
+            "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": nth, "kind": "oracle",
+                             "sample": f"{per_step} pairs per step of the {WORKLOAD} workload"},
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2607_06225_gb300 as F
+    import synth
+    from paper_2607_06225_gb300 import build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if not os.path.exists(F._lib.LIB_PATH):
+        B.build()
+    # weak scaling: every rank aligns its own 100k-pair batch (independent problems)
+    batch = synth.protein_pairs(n=args.pairs, seed=2 + 1000 * rank)
+    sc = dict(batch.scoring)
+    params = F.make_params(batch.subst, **sc)
+    ctx = F.Context(local_rank, 64 << 30)
+    db = F.DeviceBatch(batch, dev)
+    out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def step():
+        rc = ctx.align_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(), cig_t.data_ptr(),
+                                 db.cigar_upper, stream=stream.cuda_stream)
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+
+    ctx.set_timing(True)
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    res = F.results_to_numpy(out_t, db.n)
+    cells = int(res["cells"].sum())
+    assert cells == batch.cells_full()
+
+    probe = ctx.probe() if rank == 0 else None
+
+    sampler = ClockSampler(local_rank)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fwd_ms, walk_ms, launches = [], [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        st = ctx.last_stats()  # waits for the step; device-side phase times
+        fwd_ms.append(st["ms_forward"])
+        walk_ms.append(st["ms_walk"])
+        launches.append(st["launches"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        c = torch.tensor([cells], dtype=torch.float64, device=dev)
+        dist.all_reduce(c)
+        total_cells = float(c.item())
+    else:
+        total_cells = float(cells)
+    value = total_cells / (ms * 1e-3) / 1e9
+
+    line = None
+    if rank == 0:
+        # e2e through the host-buffer entry point (pinned host memory)
+        pin = {}
+        for name in ("q_seq", "q_off", "q_len", "r_seq", "r_off", "r_len"):
+            a = np.ascontiguousarray(getattr(batch, name))
+            t = torch.from_numpy(a.view(np.uint8)).pin_memory()
+            pin[name] = (t, a.dtype)
+        hout = torch.empty(db.n * F.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        hcig = torch.empty(db.cigar_upper * 4, dtype=torch.uint8).pin_memory()
+        ptr = [pin[n][0].data_ptr() for n in ("q_seq", "q_off", "q_len", "r_seq", "r_off", "r_len")]
+        e2e_t = []
+        for k in range(2 + args.steps):
+            t0 = time.perf_counter()
+            rc = ctx.align_batch_host_ptr(params, db.n, *ptr, hout.data_ptr(), hcig.data_ptr(), db.cigar_upper)
+            if rc != 0:
+                raise F.FiltrError(rc, F.last_error())
+            if k >= 2:
+                e2e_t.append(time.perf_counter() - t0)
+        hres = hout.numpy().view(F.RESULT_DTYPE)
+        assert np.array_equal(hres, res), "host entry point disagrees with the device entry point"
+        total_ops = int(hres["cigar_off"][-1] + hres["cigar_len"][-1])
+        h2d = sum(int(pin[n][0].numel()) for n in pin)
+        d2h = db.n * F.RESULT_DTYPE.itemsize + total_ops * 4
+        e2e = {"value": cells / (sum(e2e_t) / len(e2e_t)) / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+        # plain one-launch-per-pair form on a sample of the same pairs
+        ns = min(args.plain_sample, batch.n)
+        sub = batch.subset(np.arange(ns))
+        sdb = F.DeviceBatch(sub, dev)
+        sout, scig = F.alloc_outputs(sdb.n, sdb.cigar_upper, dev)
+
+        def timed(plain):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc = ctx.align_batch_ptr(params, sdb.n, *sdb.ptrs(), sout.data_ptr(), scig.data_ptr(),
+                                     sdb.cigar_upper, stream=stream.cuda_stream, plain=plain)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if rc != 0:
+                raise F.FiltrError(rc, F.last_error())
+            return a.elapsed_time(b), F.results_to_numpy(sout, sdb.n)
+
+        timed(False)
+        tb_ms, rb = timed(False)
+        tp_ms, rp = timed(True)
+        assert np.array_equal(rb, rp), "plain and batched results differ"
+        scells = int(rb["cells"].sum())
+
+        fwd = statistics.median(fwd_ms)
+        peak_ops = max(probe["viaddmax"], probe["int_ops"]) if probe else None
+        achieved = cells * OPS_PER_CELL / (fwd * 1e-3) / 1e12
+        traffic_per_cell = ncu_traffic()
+        roof = {"bound": "alu", "kernel": "k_full (forward, all waves)", "achieved": achieved,
+                "peak": peak_ops / 1e12 if peak_ops else None, "unit": "Tops/s",
+                "frac": (achieved / (peak_ops / 1e12)) if peak_ops else None,
+                "ops_per_cell": OPS_PER_CELL,
+                "forward_ms": fwd, "forward_gcups": cells / (fwd * 1e-3) / 1e9,
+                "traffic": (traffic_per_cell * cells / max(1, 1)) if traffic_per_cell else None,
+                "peak_source": "measured int32 add-max throughput (filtr_probe_int_peak)",
+                "probe": probe}
+        line = {
+            "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs": batch.n, "cells_per_step": cells,
+                       "mode": "local affine o=11 e=1, seeded 20x20 matrix, traceback+CIGAR",
+                       "lengths": "U[100,1000] both sides", "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"replica x{world}"},
+            "plain_per_pair": {"pairs": ns, "gcups_plain": scells / (tp_ms * 1e-3) / 1e9,
+                               "gcups_batched_same_pairs": scells / (tb_ms * 1e-3) / 1e9,
+                               "ms_plain": tp_ms, "ms_batched": tb_ms},
+            "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms},
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": int(statistics.median(launches)),
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(batch, sc, args.cpu_sample)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

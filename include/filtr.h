@@ -1,0 +1,242 @@
+/* filtr.h -- C ABI of the GB300 pairwise-alignment library.
+ *
+ * The library evaluates the pairwise sequence-alignment recurrence of
+ * "Compiling Bioinformatics Recurrences" (FILTR): Needleman-Wunsch global and
+ * Smith-Waterman local alignment (Sec. 1, Sec. 2 edit-distance recurrence), with
+ * linear or affine (Gotoh H/E/F, Table 1 "Sequence Alignment") gap costs, exact
+ * integer scores, under the pruning rules of Sec. 7 -- a static band
+ * (Sec. 7.1 prune axis lo <= diag(i,j) <= hi) and X-drop (Sec. 5.2 conditional
+ * definition with the diag_lo / diag_hi domain recurrences, Sec. 7.2) -- and
+ * returns score, end coordinates and the traceback as a SAM/BAM CIGAR.
+ *
+ * Conventions shared by every entry point
+ *   - q is the query (length M, rows i = 1..M), r the reference (length N,
+ *     columns j = 1..N); diag(i,j) = j - i, antidiagonal k = i + j (Sec. 6.2).
+ *   - Residues are small integer codes, one per byte: DNA 0..3 (A C G T),
+ *     protein 0..19.  A code >= the alphabet size is rejected.
+ *   - A gap of length L costs gap_open + L*gap_extend (affine) or L*gap_extend
+ *     (linear).  E is the horizontal gap (consumes the reference, CIGAR 'D'),
+ *     F the vertical gap (consumes the query, CIGAR 'I').
+ *   - Ties: H takes the diagonal, then E, then F; E and F prefer opening over
+ *     extending; a local H of 0 ends the traceback; the best cell is the largest
+ *     H, then the smallest i, then the smallest j.
+ *   - Band: with FILTR_PRUNE_BAND the computed cells satisfy lo <= j-i <= hi
+ *     where lo = min(0, N-M) - band and hi = max(0, N-M) + band (the band is
+ *     widened so it holds both corners); with FILTR_PRUNE_BAND_LITERAL it is
+ *     -band <= j-i <= band exactly, and a global alignment whose corner falls
+ *     outside reports FILTR_ST_UNREACHABLE.
+ *   - X-drop: a cell on antidiagonal k is pruned when H < best(k-1) - xdrop,
+ *     best(k-1) being the largest unpruned H of antidiagonal k-1; antidiagonal
+ *     k+1 covers the diagonals [lo_k - 1, hi_k + 1] spanned by the unpruned
+ *     cells of k; the sweep stops at the first antidiagonal with no unpruned
+ *     cell.  A global alignment that does not reach (M,N) reports
+ *     FILTR_ST_DROPPED with the best unpruned cell as its end.
+ *   - CIGAR ops are BAM uint32 words  (len << 4) | op  with op 7 '=', 8 'X',
+ *     1 'I', 2 'D'.
+ *   - Errors: every function returns a filtr_status; nothing aborts and no
+ *     kernel traps.  filtr_last_error() gives a message for the calling thread.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Device outputs are complete when the stream reaches that point.
+ */
+#ifndef FILTR_H
+#define FILTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FILTR_OK = 0,
+  FILTR_ERR_INVALID = -1,     /* bad argument; nothing was launched */
+  FILTR_ERR_NOMEM = -2,       /* a device or host allocation failed */
+  FILTR_ERR_CUDA = -3,        /* a CUDA call failed (message in filtr_last_error) */
+  FILTR_ERR_TIMEOUT = -4,     /* a bounded device wait or serve wait ran out */
+  FILTR_ERR_BUSY = -5,        /* serve: queue full, or result not ready yet */
+  FILTR_ERR_CIGAR_CAP = -6,   /* cigar buffer too small; results carry the lengths needed */
+  FILTR_ERR_UNSUPPORTED = -7  /* a size or combination this build does not handle */
+} filtr_status;
+
+enum { FILTR_GLOBAL = 0, FILTR_LOCAL = 1 };
+enum { FILTR_ALPHA_DNA = 4, FILTR_ALPHA_PROTEIN = 20 };
+enum { FILTR_PRUNE_BAND = 1u, FILTR_PRUNE_XDROP = 2u, FILTR_PRUNE_BAND_LITERAL = 4u };
+enum { FILTR_PREC_AUTO = 0, FILTR_PREC_I32 = 1, FILTR_PREC_I16X2 = 2 };
+enum { FILTR_XDROP_INF = 0x7fffffff };
+
+/* per-pair outcome in filtr_result.status */
+enum {
+  FILTR_ST_OK = 0,
+  FILTR_ST_DROPPED = 1,     /* X-drop stopped before (M,N) (global) */
+  FILTR_ST_UNREACHABLE = 2, /* literal band excludes (M,N) (global) */
+  FILTR_ST_EMPTY = 3,       /* local best score is 0: empty alignment */
+  FILTR_ST_TOO_WIDE = 4     /* X-drop region wider than the kernel window (see filtr_align_batch) */
+};
+
+typedef struct {
+  int32_t mode;          /* FILTR_GLOBAL or FILTR_LOCAL */
+  int32_t alphabet;      /* FILTR_ALPHA_DNA or FILTR_ALPHA_PROTEIN */
+  int32_t affine;        /* 1: Gotoh H/E/F; 0: linear gap (gap_open ignored) */
+  int32_t gap_open;      /* >= 0 */
+  int32_t gap_extend;    /* >= 0 */
+  const int8_t *subst;   /* HOST pointer: alphabet*alphabet scores, subst[q_code*alphabet + r_code];
+                            copied during the call; need not be symmetric */
+  uint32_t prune;        /* OR of FILTR_PRUNE_* (0 = full matrix) */
+  int32_t band;          /* band half-width >= 0 (used with FILTR_PRUNE_BAND) */
+  int32_t xdrop;         /* X >= 0, or FILTR_XDROP_INF (used with FILTR_PRUNE_XDROP) */
+  int32_t traceback;     /* 0: score and end cell only; 1: also begin cell and CIGAR */
+  int32_t precision;     /* FILTR_PREC_*: a speed choice only; results are identical */
+} filtr_params;
+
+typedef struct {
+  int32_t score;
+  int32_t q_begin, q_end;  /* query residues [q_begin, q_end); q_end = i of the end cell */
+  int32_t r_begin, r_end;  /* reference residues [r_begin, r_end); r_end = j of the end cell */
+  int32_t status;          /* FILTR_ST_* */
+  uint32_t cigar_len;      /* ops of this pair (needed length when the call returned CIGAR_CAP) */
+  uint32_t reserved;
+  uint64_t cigar_off;      /* first op of this pair in the caller's cigar buffer */
+  uint64_t cells;          /* cells (i >= 1, j >= 1) whose recurrence was evaluated, pruned or not */
+} filtr_result;            /* 48 bytes.  Without traceback, q_begin = r_begin = -1 for local
+                              alignments (unknown) and 0 for global ones; cigar_len = 0. */
+
+typedef struct filtr_ctx filtr_ctx;
+typedef struct filtr_server filtr_server;
+
+/* Thread-local message describing the last error of this thread (never NULL). */
+const char *filtr_last_error(void);
+
+/* Library version string. */
+const char *filtr_version(void);
+
+/* Check a parameter block on the host (no device work).  FILTR_OK or
+ * FILTR_ERR_INVALID (negative penalties, unknown mode / alphabet / precision,
+ * negative band or xdrop, NULL subst, a linear gap with a band, ...). */
+filtr_status filtr_params_check(const filtr_params *params);
+
+/* Create a context on `device`.  The context owns its device workspace
+ * (workspace_bytes; 0 picks 8 GiB, capped at half the free device memory),
+ * pinned host staging and streams.  One context serves one host thread at a
+ * time.  *out receives the context or NULL. */
+filtr_status filtr_ctx_create(int device, size_t workspace_bytes, filtr_ctx **out);
+filtr_status filtr_ctx_destroy(filtr_ctx *ctx);
+
+/* Pack step: validate n residue codes at `codes` (DEVICE) against `alphabet`
+ * and write them packed at `packed` (DEVICE, ceil(n*bits/32) uint32 words,
+ * bits = 2 for DNA, 8 for protein; residue t sits at bits [bits*(t % per_word), ...)
+ * of word t / per_word).  *bad_out (DEVICE, one uint32) receives the number of
+ * invalid codes.  Stream ordered; no synchronisation. */
+filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint32_t *packed,
+                        uint32_t *bad_out, void *stream);
+
+/* Align n_pairs independent pairs in one batched call (Sec. 2 recurrence under
+ * the Sec. 7 pruning rules).
+ *   q_seq / r_seq : DEVICE, residue codes, one byte each, pairs concatenated
+ *   q_off / r_off : DEVICE, uint64 start of each pair's sequence
+ *   q_len / r_len : DEVICE, uint32 lengths (0 allowed)
+ *   out           : DEVICE, n_pairs filtr_result
+ *   cigar         : DEVICE, cigar_cap uint32 ops (may be NULL when traceback = 0)
+ * The call reads the lengths back to the host once (a short synchronisation on
+ * `stream`) to plan length buckets, traceback waves and kernel shapes; the rest
+ * is stream ordered.  Pairs of one call share the params.  The CIGARs are laid
+ * out in pair order; if the total exceeds cigar_cap the call returns
+ * FILTR_ERR_CIGAR_CAP after the stream completes and each result carries its
+ * length.  Band and X-drop pairs whose live region outgrows the widest kernel
+ * window (16384 diagonals) get FILTR_ST_TOO_WIDE.  Returns FILTR_ERR_INVALID
+ * before any launch for bad params or codes. */
+filtr_status filtr_align_batch(filtr_ctx *ctx, const filtr_params *params, uint32_t n_pairs,
+                               const uint8_t *q_seq, const uint64_t *q_off, const uint32_t *q_len,
+                               const uint8_t *r_seq, const uint64_t *r_off, const uint32_t *r_len,
+                               filtr_result *out, uint32_t *cigar, uint64_t cigar_cap,
+                               void *stream);
+
+/* Same as filtr_align_batch with every array in HOST memory (pinned memory
+ * gives the fastest copies).  The call copies the inputs to the device, aligns
+ * and copies results and CIGARs back; it returns when they are in host memory. */
+filtr_status filtr_align_batch_host(filtr_ctx *ctx, const filtr_params *params, uint32_t n_pairs,
+                                    const uint8_t *q_seq, const uint64_t *q_off,
+                                    const uint32_t *q_len, const uint8_t *r_seq,
+                                    const uint64_t *r_off, const uint32_t *r_len,
+                                    filtr_result *out, uint32_t *cigar, uint64_t cigar_cap);
+
+/* The same batch, one kernel launch per pair with one warp each (the plain
+ * per-pair form, kept for comparison).  Arguments as filtr_align_batch;
+ * results are identical. */
+filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
+                                     uint32_t n_pairs, const uint8_t *q_seq,
+                                     const uint64_t *q_off, const uint32_t *q_len,
+                                     const uint8_t *r_seq, const uint64_t *r_off,
+                                     const uint32_t *r_len, filtr_result *out, uint32_t *cigar,
+                                     uint64_t cigar_cap, void *stream);
+
+/* Align one long pair with every SM of the device working on it.
+ *   q, r : DEVICE codes (M, N up to 2^31-1);  out : DEVICE, one filtr_result;
+ *   cigar: DEVICE, cigar_cap ops.
+ * X-drop pairs run as one antidiagonal sweep with checkpointed traceback: every
+ * `C`-th antidiagonal's state is kept, and the backward pass recomputes one
+ * segment at a time, so the traceback memory is bounded by the workspace.
+ * Band / full-matrix pairs split the query into row strips, one per CTA, which
+ * hand their boundary rows down through global memory with release/acquire
+ * flags; every wait is bounded and a timeout returns FILTR_ERR_TIMEOUT. */
+filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const uint8_t *q,
+                              uint32_t M, const uint8_t *r, uint32_t N, filtr_result *out,
+                              uint32_t *cigar, uint64_t cigar_cap, void *stream);
+
+/* Per-call statistics.  With timing on, filtr_align_batch records CUDA events
+ * on its stream around each phase; filtr_ctx_last_stats waits for the last
+ * call to finish and returns the device time of each phase (ms), the number of
+ * kernel launches the call made, its traceback waves and its evaluated cells
+ * as planned (the exact counts are in the results). */
+typedef struct {
+  double ms_validate;   /* residue validation kernel */
+  double ms_forward;    /* forward (cell update) kernels, summed over waves */
+  double ms_walk;       /* traceback walks, summed over waves */
+  double ms_place;      /* CIGAR offset scan and compaction */
+  double ms_total;      /* first to last event of the call */
+  uint32_t launches;    /* kernels this library launched for the call */
+  uint32_t waves;
+  uint64_t cells_planned;
+} filtr_stats;
+filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
+filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
+
+/* Measured integer / DPX throughput of this device, used as the cell-update
+ * roofline denominator: out[0] = int32 add/max ops per second (all SMs,
+ * independent chains), out[1] = __viaddmax_s32 per second, out[2] =
+ * __vimax3_s32 per second, out[3] = __viaddmax_s16x2 per second (two lanes per
+ * op), out[4] = the SM clock (Hz) the probe ran at, estimated from clock64(). */
+filtr_status filtr_probe_int_peak(filtr_ctx *ctx, double out[5]);
+
+/* ---- serving: continuous batching of single-pair requests ------------------
+ * Requests are copied into resident device buffers, admitted while their
+ * device memory (sequences + DP workspace + traceback bytes) fits mem_budget,
+ * grouped by kind into micro-batches and launched on up to max_inflight
+ * streams; a micro-batch launches as soon as a stream is free, so requests
+ * that arrive while others run overlap with them on the device.  A worker
+ * thread owned by the server does all device work. */
+filtr_status filtr_serve_create(filtr_ctx *ctx, size_t mem_budget, uint32_t max_inflight,
+                                filtr_server **out);
+/* Queue one pair (HOST pointers, copied before returning).  FILTR_ERR_BUSY if the
+ * request alone exceeds the budget or the host queue is full; *ticket
+ * identifies the request. */
+filtr_status filtr_serve_submit(filtr_server *srv, const filtr_params *params, const uint8_t *q,
+                                uint32_t M, const uint8_t *r, uint32_t N, uint64_t *ticket);
+/* Non-blocking: FILTR_OK and the result (HOST out, cigar up to cap ops, and if
+ * times_ns is not NULL the host monotonic times in ns of submit, launch and
+ * completion), or FILTR_ERR_BUSY if not finished.  A retrieved ticket is
+ * forgotten; FILTR_ERR_INVALID for an unknown ticket; FILTR_ERR_CIGAR_CAP if
+ * cap is too small (out->cigar_len tells the length; the ticket is kept). */
+filtr_status filtr_serve_poll(filtr_server *srv, uint64_t ticket, filtr_result *out,
+                              uint32_t *cigar, uint64_t cap, uint64_t *times_ns);
+/* Blocking variant of poll with a timeout in microseconds (< 0 waits forever);
+ * FILTR_ERR_TIMEOUT when it runs out. */
+filtr_status filtr_serve_wait(filtr_server *srv, uint64_t ticket, int64_t timeout_us,
+                              filtr_result *out, uint32_t *cigar, uint64_t cap,
+                              uint64_t *times_ns);
+filtr_status filtr_serve_destroy(filtr_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FILTR_H */

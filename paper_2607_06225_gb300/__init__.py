@@ -1,0 +1,116 @@
+"""GB300 pairwise alignment (NW / SW, linear and affine gaps, band and X-drop
+pruning, CIGAR traceback) behind the C ABI in include/filtr.h.
+
+This package is the thin Python face of libfiltr.so: it marshals numpy / torch
+buffers into C-ABI calls.  PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._lib import (ALPHA_DNA, ALPHA_PROTEIN, ERR_CIGAR_CAP, ERR_INVALID, ERR_UNSUPPORTED, GLOBAL,
+                   LOCAL, OK, PREC_AUTO, PREC_I16X2, PREC_I32, PRUNE_BAND, PRUNE_BAND_LITERAL,
+                   PRUNE_XDROP, RESULT_DTYPE, ST_DROPPED, ST_EMPTY, ST_OK, ST_TOO_WIDE,
+                   ST_UNREACHABLE, XDROP_INF, Context, FiltrError, Params, check, last_error, lib,
+                   make_params)
+
+__all__ = ["Context", "FiltrError", "Params", "make_params", "DeviceBatch", "align_batch",
+           "align_batch_host", "align_long", "RESULT_DTYPE", "lib", "last_error"]
+
+
+class DeviceBatch:
+    """A batch resident on the device (torch tensors), in the C-ABI layout."""
+
+    def __init__(self, batch, device="cuda"):
+        import torch
+
+        def t(x, dt):
+            return torch.from_numpy(np.ascontiguousarray(x).astype(dt, copy=False)).to(device)
+
+        self.n = int(batch.q_len.shape[0])
+        self.q_seq = t(batch.q_seq if batch.q_seq.size else np.zeros(1, np.uint8), np.uint8)
+        self.r_seq = t(batch.r_seq if batch.r_seq.size else np.zeros(1, np.uint8), np.uint8)
+        self.q_off = t(batch.q_off.view(np.int64), np.int64)
+        self.r_off = t(batch.r_off.view(np.int64), np.int64)
+        self.q_len = t(batch.q_len.view(np.int32), np.int32)
+        self.r_len = t(batch.r_len.view(np.int32), np.int32)
+        self.cigar_upper = int(batch.q_len.astype(np.int64).sum() + batch.r_len.astype(np.int64).sum())
+
+    def ptrs(self):
+        return (self.q_seq.data_ptr(), self.q_off.data_ptr(), self.q_len.data_ptr(),
+                self.r_seq.data_ptr(), self.r_off.data_ptr(), self.r_len.data_ptr())
+
+
+def alloc_outputs(n: int, cigar_cap: int, device="cuda"):
+    import torch
+
+    out = torch.empty(max(n, 1) * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=device)
+    cig = torch.empty(max(cigar_cap, 1), dtype=torch.int32, device=device)
+    return out, cig
+
+
+def results_to_numpy(out_t, n: int):
+    return out_t[: n * RESULT_DTYPE.itemsize].cpu().numpy().view(RESULT_DTYPE).copy()
+
+
+def align_batch(ctx: Context, params: Params, batch, stream=None, plain: bool = False,
+                cigar_cap: int | None = None, device="cuda", raise_on_error=True):
+    """Align a synth.Batch (host numpy) or a DeviceBatch on the device.
+
+    Returns (results structured array, cigar ops uint32 array, status code)."""
+    import torch
+
+    db = batch if isinstance(batch, DeviceBatch) else DeviceBatch(batch, device)
+    cap = db.cigar_upper if cigar_cap is None else int(cigar_cap)
+    out_t, cig_t = alloc_outputs(db.n, cap, device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = ctx.align_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(),
+                             cig_t.data_ptr() if params.traceback else None, cap if params.traceback else 0,
+                             stream=s.cuda_stream, plain=plain)
+    if rc not in (OK, ERR_CIGAR_CAP) and raise_on_error:
+        check(rc, "filtr_align_batch")
+    s.synchronize()
+    res = results_to_numpy(out_t, db.n)
+    cig = cig_t.cpu().numpy().view(np.uint32).copy() if params.traceback else np.zeros(0, np.uint32)
+    return res, cig, rc
+
+
+def align_batch_host(ctx: Context, params: Params, batch, cigar_cap: int | None = None):
+    """Host-buffer entry point: every array in host memory (numpy)."""
+    n = int(batch.q_len.shape[0])
+    cap = int(batch.q_len.astype(np.int64).sum() + batch.r_len.astype(np.int64).sum()) \
+        if cigar_cap is None else int(cigar_cap)
+    out = np.zeros(max(n, 1), dtype=RESULT_DTYPE)
+    cig = np.zeros(max(cap, 1), dtype=np.uint32)
+    arrs = [np.ascontiguousarray(x) for x in (batch.q_seq, batch.q_off, batch.q_len, batch.r_seq,
+                                              batch.r_off, batch.r_len)]
+    rc = ctx.align_batch_host_ptr(params, n, *[a.ctypes.data for a in arrs], out.ctypes.data,
+                                  cig.ctypes.data if params.traceback else None,
+                                  cap if params.traceback else 0)
+    if rc not in (OK, ERR_CIGAR_CAP):
+        check(rc, "filtr_align_batch_host")
+    return out[:n], cig, rc
+
+
+def align_long(ctx: Context, params: Params, q: np.ndarray, r: np.ndarray, device="cuda"):
+    """One long pair with every SM on it; returns (result row, cigar ops, status)."""
+    import torch
+
+    qd = torch.from_numpy(np.ascontiguousarray(q, dtype=np.uint8) if q.size else np.zeros(1, np.uint8)).to(device)
+    rd = torch.from_numpy(np.ascontiguousarray(r, dtype=np.uint8) if r.size else np.zeros(1, np.uint8)).to(device)
+    cap = int(q.shape[0] + r.shape[0] + 1)
+    out_t, cig_t = alloc_outputs(1, cap, device)
+    s = torch.cuda.current_stream()
+    rc = ctx.align_long_ptr(params, qd.data_ptr(), int(q.shape[0]), rd.data_ptr(), int(r.shape[0]),
+                            out_t.data_ptr(), cig_t.data_ptr(), cap, stream=s.cuda_stream)
+    if rc not in (OK, ERR_CIGAR_CAP):
+        check(rc, "filtr_align_long")
+    s.synchronize()
+    res = results_to_numpy(out_t, 1)[0]
+    cig = cig_t.cpu().numpy().view(np.uint32)
+    return res, cig[int(res["cigar_off"]):int(res["cigar_off"]) + int(res["cigar_len"])].copy(), rc
+
+
+def cigar_of(res_row, cig) -> np.ndarray:
+    o, n = int(res_row["cigar_off"]), int(res_row["cigar_len"])
+    return cig[o:o + n]

@@ -1,0 +1,210 @@
+"""ctypes binding of libfiltr.so: the C-ABI names, argument marshalling only.
+
+Every computation happens in the library's CUDA kernels; nothing here falls
+back to the CPU.  If the library has not been built this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfiltr.so")
+
+OK = 0
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_CIGAR_CAP, ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7)
+GLOBAL, LOCAL = 0, 1
+ALPHA_DNA, ALPHA_PROTEIN = 4, 20
+PRUNE_BAND, PRUNE_XDROP, PRUNE_BAND_LITERAL = 1, 2, 4
+PREC_AUTO, PREC_I32, PREC_I16X2 = 0, 1, 2
+XDROP_INF = 0x7FFFFFFF
+ST_OK, ST_DROPPED, ST_UNREACHABLE, ST_EMPTY, ST_TOO_WIDE = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "OK", -1: "ERR_INVALID", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
+                -5: "ERR_BUSY", -6: "ERR_CIGAR_CAP", -7: "ERR_UNSUPPORTED"}
+
+
+class FiltrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("alphabet", C.c_int32), ("affine", C.c_int32),
+                ("gap_open", C.c_int32), ("gap_extend", C.c_int32),
+                ("subst", C.POINTER(C.c_int8)), ("prune", C.c_uint32), ("band", C.c_int32),
+                ("xdrop", C.c_int32), ("traceback", C.c_int32), ("precision", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("score", C.c_int32), ("q_begin", C.c_int32), ("q_end", C.c_int32),
+                ("r_begin", C.c_int32), ("r_end", C.c_int32), ("status", C.c_int32),
+                ("cigar_len", C.c_uint32), ("reserved", C.c_uint32), ("cigar_off", C.c_uint64),
+                ("cells", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ms_validate", C.c_double), ("ms_forward", C.c_double), ("ms_walk", C.c_double),
+                ("ms_place", C.c_double), ("ms_total", C.c_double), ("launches", C.c_uint32),
+                ("waves", C.c_uint32), ("cells_planned", C.c_uint64)]
+
+
+RESULT_DTYPE = np.dtype([("score", np.int32), ("q_begin", np.int32), ("q_end", np.int32),
+                         ("r_begin", np.int32), ("r_end", np.int32), ("status", np.int32),
+                         ("cigar_len", np.uint32), ("reserved", np.uint32),
+                         ("cigar_off", np.uint64), ("cells", np.uint64)])
+assert RESULT_DTYPE.itemsize == C.sizeof(Result) == 48
+
+_lib = None
+_P = C.c_void_p
+_U8P = C.c_void_p
+
+
+def lib():
+    """Load libfiltr.so (built by paper_2607_06225_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfiltr.so is not built; run paper_2607_06225_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        i32 = C.c_int
+        L.filtr_last_error.restype = C.c_char_p
+        L.filtr_version.restype = C.c_char_p
+        L.filtr_params_check.restype = i32
+        L.filtr_params_check.argtypes = [C.POINTER(Params)]
+        L.filtr_ctx_create.restype = i32
+        L.filtr_ctx_create.argtypes = [i32, C.c_size_t, C.POINTER(C.c_void_p)]
+        L.filtr_ctx_destroy.restype = i32
+        L.filtr_ctx_destroy.argtypes = [C.c_void_p]
+        L.filtr_pack.restype = i32
+        L.filtr_pack.argtypes = [_P, C.c_uint64, C.c_int32, _P, _P, _P]
+        batch_args = [C.c_void_p, C.POINTER(Params), C.c_uint32, _P, _P, _P, _P, _P, _P, _P, _P,
+                      C.c_uint64]
+        for name in ("filtr_align_batch", "filtr_align_batch_plain"):
+            f = getattr(L, name)
+            f.restype = i32
+            f.argtypes = batch_args + [_P]
+        L.filtr_align_batch_host.restype = i32
+        L.filtr_align_batch_host.argtypes = batch_args
+        L.filtr_align_long.restype = i32
+        L.filtr_align_long.argtypes = [C.c_void_p, C.POINTER(Params), _P, C.c_uint32, _P,
+                                       C.c_uint32, _P, _P, C.c_uint64, _P]
+        L.filtr_ctx_set_timing.restype = i32
+        L.filtr_ctx_set_timing.argtypes = [C.c_void_p, i32]
+        L.filtr_ctx_last_stats.restype = i32
+        L.filtr_ctx_last_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.filtr_probe_int_peak.restype = i32
+        L.filtr_probe_int_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double * 5)]
+        L.filtr_serve_create.restype = i32
+        L.filtr_serve_create.argtypes = [C.c_void_p, C.c_size_t, C.c_uint32, C.POINTER(C.c_void_p)]
+        L.filtr_serve_submit.restype = i32
+        L.filtr_serve_submit.argtypes = [C.c_void_p, C.POINTER(Params), _P, C.c_uint32, _P,
+                                         C.c_uint32, C.POINTER(C.c_uint64)]
+        L.filtr_serve_poll.restype = i32
+        L.filtr_serve_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(Result), _P, C.c_uint64, _P]
+        L.filtr_serve_wait.restype = i32
+        L.filtr_serve_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(Result), _P,
+                                       C.c_uint64, _P]
+        L.filtr_serve_destroy.restype = i32
+        L.filtr_serve_destroy.argtypes = [C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().filtr_last_error().decode()
+
+
+def check(rc: int, what: str = ""):
+    if rc != OK:
+        raise FiltrError(rc, f"{what}: {last_error()}" if what else last_error())
+    return rc
+
+
+def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
+                band_literal=False, xdrop=None, traceback=False, precision=PREC_AUTO,
+                **_ignored) -> Params:
+    """Build a filtr_params block; the substitution table is kept alive on it."""
+    s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
+    p = Params()
+    p.mode = LOCAL if mode in ("local", LOCAL) else GLOBAL
+    p.alphabet = int(s.shape[0])
+    p.affine = 1 if affine else 0
+    p.gap_open = int(gap_open)
+    p.gap_extend = int(gap_extend)
+    p.subst = s.ctypes.data_as(C.POINTER(C.c_int8))
+    prune = 0
+    if band is not None:
+        prune |= PRUNE_BAND_LITERAL if band_literal else PRUNE_BAND
+    if xdrop is not None:
+        prune |= PRUNE_XDROP
+    p.prune = prune
+    p.band = 0 if band is None else int(band)
+    p.xdrop = 0 if xdrop is None else int(min(int(xdrop), XDROP_INF))
+    p.traceback = 1 if traceback else 0
+    p.precision = int(precision)
+    p._keep = s
+    return p
+
+
+class Context:
+    """One filtr_ctx on one device."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        h = C.c_void_p()
+        check(lib().filtr_ctx_create(int(device), int(workspace_bytes), C.byref(h)),
+              "filtr_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().filtr_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- raw calls: device pointers as ints ---------------------------------
+    def align_batch_ptr(self, params: Params, n: int, q_seq, q_off, q_len, r_seq, r_off, r_len,
+                        out, cigar, cigar_cap: int, stream: int = 0, plain: bool = False) -> int:
+        f = lib().filtr_align_batch_plain if plain else lib().filtr_align_batch
+        return f(self.handle, C.byref(params), int(n), q_seq, q_off, q_len, r_seq, r_off, r_len,
+                 out, cigar, int(cigar_cap), C.c_void_p(int(stream)) if stream else None)
+
+    def align_batch_host_ptr(self, params: Params, n: int, q_seq, q_off, q_len, r_seq, r_off,
+                             r_len, out, cigar, cigar_cap: int) -> int:
+        return lib().filtr_align_batch_host(self.handle, C.byref(params), int(n), q_seq, q_off,
+                                            q_len, r_seq, r_off, r_len, out, cigar, int(cigar_cap))
+
+    def align_long_ptr(self, params: Params, q, M: int, r, N: int, out, cigar, cap: int,
+                       stream: int = 0) -> int:
+        return lib().filtr_align_long(self.handle, C.byref(params), q, int(M), r, int(N), out,
+                                      cigar, int(cap),
+                                      C.c_void_p(int(stream)) if stream else None)
+
+    def set_timing(self, on: bool):
+        check(lib().filtr_ctx_set_timing(self.handle, 1 if on else 0), "filtr_ctx_set_timing")
+
+    def last_stats(self) -> dict:
+        st = Stats()
+        check(lib().filtr_ctx_last_stats(self.handle, C.byref(st)), "filtr_ctx_last_stats")
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def probe(self):
+        arr = (C.c_double * 5)()
+        check(lib().filtr_probe_int_peak(self.handle, C.byref(arr)), "filtr_probe_int_peak")
+        return dict(int_ops=arr[0], viaddmax=arr[1], vimax3=arr[2], viaddmax_s16x2_lanes=arr[3],
+                    sm_hz=arr[4])

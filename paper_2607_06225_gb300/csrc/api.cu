@@ -1,0 +1,651 @@
+// api.cu -- the C ABI (include/filtr.h): contexts, parameter checks, the
+// batched call (plan, wave launches, traceback walk, CIGAR placement), its
+// host-buffer and per-pair-launch variants, packing and the throughput probe.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "filtr_ctx.h"
+#include "plan.h"
+
+namespace filtr {
+
+static thread_local std::string g_err = "no error";
+
+void set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+filtr_status cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return FILTR_ERR_CUDA;
+}
+
+filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
+  if (!p) {
+    set_error("params is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->mode != FILTR_GLOBAL && p->mode != FILTR_LOCAL) {
+    set_error("mode must be FILTR_GLOBAL or FILTR_LOCAL");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->alphabet != FILTR_ALPHA_DNA && p->alphabet != FILTR_ALPHA_PROTEIN) {
+    set_error("alphabet must be 4 (DNA) or 20 (protein)");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->affine != 0 && p->affine != 1) {
+    set_error("affine must be 0 or 1");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->gap_extend < 0 || (p->affine && p->gap_open < 0) || p->gap_extend > (1 << 20) ||
+      (p->affine && p->gap_open > (1 << 20))) {
+    set_error("gap penalties must lie in [0, 2^20]");
+    return FILTR_ERR_INVALID;
+  }
+  if (!p->subst) {
+    set_error("subst is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->prune & ~(uint32_t)(FILTR_PRUNE_BAND | FILTR_PRUNE_XDROP | FILTR_PRUNE_BAND_LITERAL)) {
+    set_error("unknown prune bits 0x%x", p->prune);
+    return FILTR_ERR_INVALID;
+  }
+  const bool band = (p->prune & (FILTR_PRUNE_BAND | FILTR_PRUNE_BAND_LITERAL)) != 0;
+  const bool xd = (p->prune & FILTR_PRUNE_XDROP) != 0;
+  if (band && p->band < 0) {
+    set_error("band must be >= 0");
+    return FILTR_ERR_INVALID;
+  }
+  if (xd && p->xdrop < 0) {
+    set_error("xdrop must be >= 0");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->traceback != 0 && p->traceback != 1) {
+    set_error("traceback must be 0 or 1");
+    return FILTR_ERR_INVALID;
+  }
+  if (p->precision < FILTR_PREC_AUTO || p->precision > FILTR_PREC_I16X2) {
+    set_error("unknown precision");
+    return FILTR_ERR_INVALID;
+  }
+  memset(sp, 0, sizeof *sp);
+  sp->mode = p->mode;
+  sp->affine = p->affine;
+  sp->o = p->affine ? p->gap_open : 0;
+  sp->e = p->gap_extend;
+  sp->alphabet = p->alphabet;
+  sp->use_band = band ? 1 : 0;
+  sp->band_literal = (p->prune & FILTR_PRUNE_BAND_LITERAL) ? 1 : 0;
+  sp->band = band ? p->band : 0;
+  sp->use_xdrop = xd ? 1 : 0;
+  sp->xdrop = xd ? p->xdrop : 0;
+  sp->traceback = p->traceback;
+  for (int t = 0; t < p->alphabet * p->alphabet; ++t) sp->subst[t] = p->subst[t];
+  return FILTR_OK;
+}
+
+// |H| stays below 2^28 so that NEG arithmetic cannot meet finite scores.
+static bool score_range_ok(const ScoreParams &sp, uint64_t max_m, uint64_t max_n) {
+  int smax = 0;
+  for (int t = 0; t < sp.alphabet * sp.alphabet; ++t) smax = std::max(smax, std::abs((int)sp.subst[t]));
+  const double bound = (double)smax * (double)std::min(max_m, max_n) + (double)sp.o +
+                       (double)sp.e * (double)(max_m + max_n) + (double)sp.o * 2.0;
+  return bound < (double)(1 << 28);
+}
+
+// ---- workspace carving ------------------------------------------------------
+struct Carver {
+  char *base;
+  size_t cap, used = 0;
+  template <class T>
+  T *take(size_t count, size_t align = 256) {
+    used = (used + align - 1) / align * align;
+    T *p = reinterpret_cast<T *>(base + used);
+    used += count * sizeof(T);
+    return p;
+  }
+};
+
+int Ctx::full_blocks_per_sm(int R, const ScoreParams &sp) {
+  const auto key = std::make_tuple(R, sp.mode, sp.affine, sp.traceback, sp.use_band, sp.alphabet);
+  auto it = occ_cache.find(key);
+  if (it != occ_cache.end()) return it->second;
+  int nb = full_max_blocks_per_sm(R, sp, sp.alphabet);
+  if (nb < 1) nb = 1;
+  occ_cache[key] = nb;
+  return nb;
+}
+
+cudaEvent_t Ctx::next_event() {
+  if (ev_used == ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ev_pool.push_back(e);
+  }
+  return ev_pool[ev_used++];
+}
+
+void Ctx::span_begin(int phase, cudaStream_t st) {
+  if (!timing) return;
+  Span sp{phase, next_event(), nullptr};
+  if (sp.a) cudaEventRecord(sp.a, st);
+  spans.push_back(sp);
+}
+
+void Ctx::span_end(cudaStream_t st) {
+  if (!timing || spans.empty()) return;
+  spans.back().b = next_event();
+  if (spans.back().b) cudaEventRecord(spans.back().b, st);
+}
+
+bool Ctx::ensure_host(size_t bytes) {
+  if (h_stage_bytes >= bytes) return true;
+  if (h_stage) cudaFreeHost(h_stage);
+  h_stage = nullptr;
+  h_stage_bytes = 0;
+  size_t want = std::max(bytes, (size_t)1 << 20);
+  if (cudaHostAlloc(&h_stage, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h_stage_bytes = want;
+  return true;
+}
+
+// The batched call.  host_* may carry host copies of lengths and offsets
+// (the host-buffer entry point has them); otherwise they are read back.
+filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
+                              const BatchDev &b, filtr_result *out, uint32_t *cigar,
+                              uint64_t cap, cudaStream_t st, bool plain,
+                              const uint32_t *host_ql, const uint32_t *host_rl) {
+  ScoreParams sp;
+  filtr_status rc = to_score_params(params, &sp);
+  if (rc != FILTR_OK) return rc;
+  if (n == 0) return FILTR_OK;
+  if (!b.q_seq || !b.r_seq || !b.q_off || !b.r_off || !b.q_len || !b.r_len || !out) {
+    set_error("a batch pointer is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  if (sp.traceback && !cigar && cap > 0) {
+    set_error("cigar is NULL but cigar_cap > 0");
+    return FILTR_ERR_INVALID;
+  }
+  cudaError_t ce = cudaSetDevice(ctx->device);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
+  if (ctx->done_ev) {
+    ce = cudaEventSynchronize(ctx->done_ev);  // the previous call is finished with the workspace
+    if (ce != cudaSuccess) return cuda_fail(ce, "waiting for the previous call");
+  }
+  ctx->ev_used = 0;
+  ctx->spans.clear();
+  uint32_t launches = 0;
+
+  // 1. lengths back to the host and residue validation (one synchronisation)
+  const size_t lens_bytes = (size_t)n * 4 * 2;
+  if (!ctx->ensure_host(lens_bytes + 64)) {
+    set_error("pinned host allocation of %zu bytes failed", lens_bytes);
+    return FILTR_ERR_NOMEM;
+  }
+  uint32_t *h_ql = reinterpret_cast<uint32_t *>(ctx->h_stage);
+  uint32_t *h_rl = h_ql + n;
+  uint32_t *h_bad = h_rl + n;
+  Carver pre{ctx->ws, ctx->ws_bytes};
+  uint32_t *d_bad = pre.take<uint32_t>(64);
+  ce = cudaMemsetAsync(d_bad, 0, 64 * sizeof(uint32_t), st);
+  ctx->span_begin(Ctx::PH_VALIDATE, st);
+  if (ce == cudaSuccess) ce = launch_validate_pairs(b, n, sp.alphabet, d_bad, st);
+  ctx->span_end(st);
+  ++launches;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_bad, d_bad, 4, cudaMemcpyDeviceToHost, st);
+  if (!host_ql) {
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_ql, b.q_len, n * 4, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_rl, b.r_len, n * 4, cudaMemcpyDeviceToHost, st);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "reading lengths");
+  if (host_ql) {
+    memcpy(h_ql, host_ql, n * 4);
+    memcpy(h_rl, host_rl, n * 4);
+  }
+  if (*h_bad) {
+    set_error("%u residue codes are >= the alphabet size %d", *h_bad, sp.alphabet);
+    return FILTR_ERR_INVALID;
+  }
+
+  // 2. fixed workspace parts, then the plan
+  uint64_t max_m = 0, max_n = 0, stage_words = 0;
+  for (uint32_t p = 0; p < n; ++p) {
+    max_m = std::max<uint64_t>(max_m, h_ql[p]);
+    max_n = std::max<uint64_t>(max_n, h_rl[p]);
+    if (sp.traceback) stage_words += (uint64_t)h_ql[p] + h_rl[p] + 1;
+  }
+  if (max_m >= (1u << 30) || max_n >= (1u << 30)) {
+    set_error("sequence longer than 2^30");
+    return FILTR_ERR_UNSUPPORTED;
+  }
+  if (!score_range_ok(sp, max_m, max_n)) {
+    set_error("scores could exceed 2^28 for these lengths and penalties");
+    return FILTR_ERR_UNSUPPORTED;
+  }
+  const int R_max = 16;
+  const int blocks_per_sm = std::max(ctx->full_blocks_per_sm(8, sp), ctx->full_blocks_per_sm(16, sp));
+  const int grid_max = plain ? 1 : ctx->sms * blocks_per_sm;
+  const uint32_t strip_stride = (uint32_t)(max_n + 2);
+  Carver c{ctx->ws, ctx->ws_bytes};
+  c.take<uint32_t>(64);  // d_bad
+  uint32_t *d_order = c.take<uint32_t>(n);
+  TbLayout *d_tbl = c.take<TbLayout>(n);
+  uint64_t *d_stage_off = c.take<uint64_t>(n);
+  FwdOut *d_fwd = c.take<FwdOut>(n);
+  uint64_t *d_offs = c.take<uint64_t>(n);
+  const size_t n_counters = (size_t)n + 4096;
+  uint32_t *d_counters = c.take<uint32_t>(n_counters);
+  uint64_t *d_total = c.take<uint64_t>(4);
+  int2 *d_strip = c.take<int2>((size_t)grid_max * FULL_WARPS * strip_stride);
+  uint32_t *d_stage = sp.traceback ? c.take<uint32_t>(stage_words) : nullptr;
+  uint32_t *d_tb = c.take<uint32_t>(0);
+  if (c.used > ctx->ws_bytes) {
+    set_error("workspace of %zu bytes is too small for this batch's fixed buffers (%zu bytes)",
+              ctx->ws_bytes, c.used);
+    return FILTR_ERR_NOMEM;
+  }
+  const uint64_t tb_budget = (ctx->ws_bytes - c.used) / 4;
+  (void)R_max;
+
+  Plan P;
+  PlanInput in{&sp, n, h_ql, h_rl, tb_budget, 8};
+  if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
+
+  // 3. upload the plan
+  const uint32_t n_main = (uint32_t)P.order.size();
+  std::vector<uint32_t> order_all = P.order;
+  order_all.insert(order_all.end(), P.trivial.begin(), P.trivial.end());
+  const size_t up_bytes = n * (4 + sizeof(TbLayout) + 8);
+  if (!ctx->ensure_host(up_bytes + 64)) {
+    set_error("pinned host allocation failed");
+    return FILTR_ERR_NOMEM;
+  }
+  char *hs = reinterpret_cast<char *>(ctx->h_stage);
+  memcpy(hs, order_all.data(), n * 4);
+  memcpy(hs + n * 4, P.tbl.data(), n * sizeof(TbLayout));
+  memcpy(hs + n * (4 + sizeof(TbLayout)), P.stage_off.data(), n * 8);
+  ce = cudaMemcpyAsync(d_order, hs, n * 4, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(d_tbl, hs + n * 4, n * sizeof(TbLayout), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(d_stage_off, hs + n * (4 + sizeof(TbLayout)), n * 8, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d_counters, 0, n_counters * 4, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "uploading the plan");
+
+  FullArgs fa;
+  fa.b = b;
+  fa.sp = sp;
+  fa.out = out;
+  fa.fwd = d_fwd;
+  fa.tb = d_tb;
+  fa.tbl = d_tbl;
+  fa.strip_buf = d_strip;
+  fa.strip_stride = strip_stride;
+  WalkArgs wa;
+  wa.b = b;
+  wa.sp = sp;
+  wa.out = out;
+  wa.fwd = d_fwd;
+  wa.tb = d_tb;
+  wa.tbl = d_tbl;
+  wa.stage = d_stage;
+  wa.stage_off = d_stage_off;
+
+  // 4. waves
+  size_t counter_i = 0;
+  for (const Wave &w : P.waves) {
+    ctx->span_begin(Ctx::PH_FORWARD, st);
+    for (const Group &g : w.groups) {
+      const uint32_t cnt = g.end - g.begin;
+      if (g.family == FAM_FULL) {
+        if (plain) {
+          for (uint32_t t = 0; t < cnt; ++t) {
+            fa.order = d_order + g.begin + t;
+            fa.n_order = 1;
+            fa.counter = d_counters + (counter_i++ % n_counters);
+            ce = launch_full(fa, g.R, 1, st);
+            ++launches;
+            if (ce != cudaSuccess) return cuda_fail(ce, "tiled kernel launch");
+            if (sp.traceback) {
+              wa.order = fa.order;
+              wa.n_order = 1;
+              ce = launch_walk(wa, st);
+              ++launches;
+              if (ce != cudaSuccess) return cuda_fail(ce, "walk launch");
+            }
+          }
+        } else {
+          fa.order = d_order + g.begin;
+          fa.n_order = cnt;
+          fa.counter = d_counters + (counter_i++ % n_counters);
+          const int bps = ctx->full_blocks_per_sm(g.R, sp);
+          int grid = std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + FULL_WARPS - 1) / FULL_WARPS);
+          if (grid < 1) grid = 1;
+          ce = launch_full(fa, g.R, grid, st);
+          ++launches;
+          if (ce != cudaSuccess) return cuda_fail(ce, "tiled kernel launch");
+        }
+      } else {
+        set_error("X-drop pruning is not available in this build");
+        return FILTR_ERR_UNSUPPORTED;
+      }
+    }
+    ctx->span_end(st);
+    if (sp.traceback && !plain && w.walk_end > w.walk_begin) {
+      wa.order = d_order + w.walk_begin;
+      wa.n_order = w.walk_end - w.walk_begin;
+      ctx->span_begin(Ctx::PH_WALK, st);
+      ce = launch_walk(wa, st);
+      ctx->span_end(st);
+      ++launches;
+      if (ce != cudaSuccess) return cuda_fail(ce, "walk launch");
+    }
+  }
+  if (!P.trivial.empty()) {
+    ce = launch_trivial(b, sp, d_order + n_main, (uint32_t)P.trivial.size(), out, d_fwd, st);
+    ++launches;
+    if (ce == cudaSuccess && sp.traceback) {
+      wa.order = d_order + n_main;
+      wa.n_order = (uint32_t)P.trivial.size();
+      ce = launch_walk(wa, st);
+      ++launches;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "empty-pair launch");
+  }
+
+  // 5. CIGAR placement
+  if (sp.traceback) {
+    ctx->span_begin(Ctx::PH_PLACE, st);
+    ce = launch_scan_offsets(out, n, d_offs, d_total, st);
+    if (ce == cudaSuccess) ce = launch_compact(wa, n, d_offs, cigar, cap, out, st);
+    ctx->span_end(st);
+    launches += 2;
+    if (ce != cudaSuccess) return cuda_fail(ce, "CIGAR placement");
+    if (cap < P.cigar_upper) {
+      uint64_t *h_total = reinterpret_cast<uint64_t *>(ctx->h_stage);
+      ce = cudaMemcpyAsync(h_total, d_total, 8, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) return cuda_fail(ce, "reading the CIGAR total");
+      if (*h_total > cap) {
+        set_error("CIGARs need %llu ops, cigar_cap is %llu", (unsigned long long)*h_total,
+                  (unsigned long long)cap);
+        ctx->last_launches = launches;
+        return FILTR_ERR_CIGAR_CAP;
+      }
+    }
+  }
+  ctx->last_cells_estimate = P.cells_estimate;
+  ctx->last_waves = (int)P.waves.size();
+  ctx->last_launches = launches;
+  if (!ctx->done_ev) cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
+  if (ctx->done_ev) cudaEventRecord(ctx->done_ev, st);
+  return FILTR_OK;
+}
+
+}  // namespace filtr
+
+using namespace filtr;
+
+extern "C" {
+
+const char *filtr_last_error(void) { return g_err.c_str(); }
+
+const char *filtr_version(void) { return "filtr-gb300 0.1 (sm_103a)"; }
+
+filtr_status filtr_params_check(const filtr_params *params) {
+  ScoreParams sp;
+  return to_score_params(params, &sp);
+}
+
+filtr_status filtr_ctx_create(int device, size_t workspace_bytes, filtr_ctx **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) {
+    set_error("device %d out of range (%d devices)", device, ndev);
+    return FILTR_ERR_INVALID;
+  }
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  Ctx *c = new (std::nothrow) Ctx();
+  if (!c) {
+    set_error("host allocation failed");
+    return FILTR_ERR_NOMEM;
+  }
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  size_t ws = workspace_bytes ? workspace_bytes : ((size_t)8 << 30);
+  if (!workspace_bytes && ws > fr / 2) ws = fr / 2;
+  e = cudaMalloc(&c->ws, ws);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    set_error("cudaMalloc of a %zu-byte workspace failed", ws);
+    return FILTR_ERR_NOMEM;
+  }
+  c->ws_bytes = ws;
+  e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  *out = reinterpret_cast<filtr_ctx *>(c);
+  return FILTR_OK;
+}
+
+filtr_status filtr_ctx_destroy(filtr_ctx *ctx) {
+  if (!ctx) return FILTR_OK;
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->own_stream);
+  if (c->done_ev) {
+    cudaEventSynchronize(c->done_ev);
+    cudaEventDestroy(c->done_ev);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_io) cudaFree(c->d_io);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  cudaStreamDestroy(c->own_stream);
+  delete c;
+  return FILTR_OK;
+}
+
+filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint32_t *packed,
+                        uint32_t *bad_out, void *stream) {
+  if (alphabet != FILTR_ALPHA_DNA && alphabet != FILTR_ALPHA_PROTEIN) {
+    set_error("alphabet must be 4 or 20");
+    return FILTR_ERR_INVALID;
+  }
+  if (n && (!codes || !packed || !bad_out)) {
+    set_error("NULL pointer");
+    return FILTR_ERR_INVALID;
+  }
+  cudaError_t e = launch_pack(codes, n, alphabet, packed, bad_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? FILTR_OK : cuda_fail(e, "pack launch");
+}
+
+filtr_status filtr_align_batch(filtr_ctx *ctx, const filtr_params *params, uint32_t n_pairs,
+                               const uint8_t *q_seq, const uint64_t *q_off, const uint32_t *q_len,
+                               const uint8_t *r_seq, const uint64_t *r_off, const uint32_t *r_len,
+                               filtr_result *out, uint32_t *cigar, uint64_t cigar_cap,
+                               void *stream) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  BatchDev b{q_seq, r_seq, q_off, r_off, q_len, r_len};
+  return align_batch_impl(reinterpret_cast<Ctx *>(ctx), params, n_pairs, b, out, cigar, cigar_cap,
+                          (cudaStream_t)stream, false, nullptr, nullptr);
+}
+
+filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
+                                     uint32_t n_pairs, const uint8_t *q_seq,
+                                     const uint64_t *q_off, const uint32_t *q_len,
+                                     const uint8_t *r_seq, const uint64_t *r_off,
+                                     const uint32_t *r_len, filtr_result *out, uint32_t *cigar,
+                                     uint64_t cigar_cap, void *stream) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  BatchDev b{q_seq, r_seq, q_off, r_off, q_len, r_len};
+  return align_batch_impl(reinterpret_cast<Ctx *>(ctx), params, n_pairs, b, out, cigar, cigar_cap,
+                          (cudaStream_t)stream, true, nullptr, nullptr);
+}
+
+filtr_status filtr_align_batch_host(filtr_ctx *ctx, const filtr_params *params, uint32_t n,
+                                    const uint8_t *q_seq, const uint64_t *q_off,
+                                    const uint32_t *q_len, const uint8_t *r_seq,
+                                    const uint64_t *r_off, const uint32_t *r_len,
+                                    filtr_result *out, uint32_t *cigar, uint64_t cigar_cap) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  if (n == 0) return FILTR_OK;
+  if (!q_seq || !q_off || !q_len || !r_seq || !r_off || !r_len || !out) {
+    set_error("a host pointer is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaSetDevice(c->device);
+  uint64_t qbytes = 0, rbytes = 0;
+  for (uint32_t p = 0; p < n; ++p) {
+    qbytes = std::max<uint64_t>(qbytes, q_off[p] + q_len[p]);
+    rbytes = std::max<uint64_t>(rbytes, r_off[p] + r_len[p]);
+  }
+  const bool tb = params && params->traceback;
+  const uint64_t ccap = tb ? cigar_cap : 0;
+  auto al = [](uint64_t x) { return (x + 255) / 256 * 256; };
+  const uint64_t need = al(qbytes) + al(rbytes) + 2 * al(n * 8ull) + 2 * al(n * 4ull) +
+                        al(n * sizeof(filtr_result)) + al(ccap * 4);
+  if (c->d_io_bytes < need) {
+    if (c->d_io) cudaFree(c->d_io);
+    c->d_io = nullptr;
+    c->d_io_bytes = 0;
+    if (cudaMalloc(&c->d_io, need) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of %llu bytes for host-buffer staging failed",
+                (unsigned long long)need);
+      return FILTR_ERR_NOMEM;
+    }
+    c->d_io_bytes = need;
+  }
+  char *d = reinterpret_cast<char *>(c->d_io);
+  uint8_t *dq = reinterpret_cast<uint8_t *>(d);
+  d += al(qbytes);
+  uint8_t *dr = reinterpret_cast<uint8_t *>(d);
+  d += al(rbytes);
+  uint64_t *dqo = reinterpret_cast<uint64_t *>(d);
+  d += al(n * 8ull);
+  uint64_t *dro = reinterpret_cast<uint64_t *>(d);
+  d += al(n * 8ull);
+  uint32_t *dql = reinterpret_cast<uint32_t *>(d);
+  d += al(n * 4ull);
+  uint32_t *drl = reinterpret_cast<uint32_t *>(d);
+  d += al(n * 4ull);
+  filtr_result *dout = reinterpret_cast<filtr_result *>(d);
+  d += al(n * sizeof(filtr_result));
+  uint32_t *dcig = ccap ? reinterpret_cast<uint32_t *>(d) : nullptr;
+  cudaStream_t st = c->own_stream;
+  cudaError_t e = cudaMemcpyAsync(dq, q_seq, qbytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, r_seq, rbytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dqo, q_off, n * 8ull, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dro, r_off, n * 8ull, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dql, q_len, n * 4ull, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(drl, r_len, n * 4ull, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copies");
+  BatchDev b{dq, dr, dqo, dro, dql, drl};
+  filtr_status rc = align_batch_impl(c, params, n, b, dout, dcig, ccap, st, false, q_len, r_len);
+  if (rc != FILTR_OK && rc != FILTR_ERR_CIGAR_CAP) return rc;
+  e = cudaMemcpyAsync(out, dout, n * sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy of results");
+  if (rc == FILTR_OK && tb && cigar) {
+    uint64_t total = 0;
+    for (uint32_t p = 0; p < n; ++p) total = std::max<uint64_t>(total, out[p].cigar_off + out[p].cigar_len);
+    if (total) {
+      e = cudaMemcpyAsync(cigar, dcig, total * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy of CIGARs");
+    }
+  }
+  return rc;
+}
+
+filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable) {
+  if (!ctx) {
+    set_error("ctx is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  reinterpret_cast<Ctx *>(ctx)->timing = enable != 0;
+  return FILTR_OK;
+}
+
+filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out) {
+  if (!ctx || !out) {
+    set_error("NULL argument");
+    return FILTR_ERR_INVALID;
+  }
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  memset(out, 0, sizeof *out);
+  out->launches = c->last_launches;
+  out->waves = (uint32_t)c->last_waves;
+  out->cells_planned = c->last_cells_estimate;
+  cudaSetDevice(c->device);
+  double *acc[4] = {&out->ms_validate, &out->ms_forward, &out->ms_walk, &out->ms_place};
+  cudaEvent_t first = nullptr, last = nullptr;
+  for (const auto &sp : c->spans) {
+    if (!sp.a || !sp.b) continue;
+    cudaError_t e = cudaEventSynchronize(sp.b);
+    if (e != cudaSuccess) return cuda_fail(e, "timing event");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, sp.a, sp.b);
+    *acc[sp.phase] += ms;
+    if (!first) first = sp.a;
+    last = sp.b;
+  }
+  if (first && last) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, first, last);
+    out->ms_total = ms;
+  }
+  return FILTR_OK;
+}
+
+filtr_status filtr_probe_int_peak(filtr_ctx *ctx, double out[5]) {
+  if (!ctx || !out) {
+    set_error("NULL argument");
+    return FILTR_ERR_INVALID;
+  }
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaSetDevice(c->device);
+  cudaError_t e = run_probe(out);
+  return e == cudaSuccess ? FILTR_OK : cuda_fail(e, "probe");
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// filtr_ctx.h -- the context object behind the opaque filtr_ctx handle.
+#pragma once
+
+#include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <tuple>
+
+#include "filtr_internal.h"
+
+namespace filtr {
+
+struct Ctx {
+  int device = 0;
+  int sms = 0;
+  char *ws = nullptr;         // device workspace (plan, staging, traceback)
+  size_t ws_bytes = 0;
+  void *h_stage = nullptr;    // pinned host staging
+  size_t h_stage_bytes = 0;
+  void *d_io = nullptr;       // device copies for the host-buffer entry point
+  size_t d_io_bytes = 0;
+  cudaStream_t own_stream = nullptr;
+  std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
+  uint64_t last_cells_estimate = 0;
+  int last_waves = 0;
+  uint32_t last_launches = 0;
+  // ordering of successive calls: the next call waits for this event, so the
+  // workspace and the pinned staging are never reused while still in flight
+  cudaEvent_t done_ev = nullptr;
+  // optional per-phase timing
+  bool timing = false;
+  enum Phase { PH_VALIDATE = 0, PH_FORWARD = 1, PH_WALK = 2, PH_PLACE = 3 };
+  struct Span {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Span> spans;
+
+  int full_blocks_per_sm(int R, const ScoreParams &sp);
+  bool ensure_host(size_t bytes);
+  cudaEvent_t next_event();
+  // open / close a timed span on stream st (no-ops when timing is off)
+  void span_begin(int phase, cudaStream_t st);
+  void span_end(cudaStream_t st);
+};
+
+filtr_status to_score_params(const filtr_params *p, ScoreParams *sp);
+filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n, const BatchDev &b,
+                              filtr_result *out, uint32_t *cigar, uint64_t cap, cudaStream_t st,
+                              bool plain, const uint32_t *host_ql, const uint32_t *host_rl);
+
+}  // namespace filtr

@@ -1,0 +1,155 @@
+// filtr_internal.h -- shared definitions of the CUDA path (kernels + host code).
+// Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/filtr.h"
+
+#define FILTR_HD __host__ __device__ __forceinline__
+
+namespace filtr {
+
+// Logical minus infinity of the int32 kernels.  Finite scores stay far above
+// NEG / 2 (|score| < 2^28 is enforced on the host), and a value produced from a
+// NEG input stays far below NEG / 2, so "is it minus infinity" is x < NEG / 2.
+constexpr int32_t NEG = -(1 << 29);
+constexpr int32_t NEG_HALF = NEG / 2;
+constexpr int MAX_ALPHA = 20;
+constexpr int FULL_WARPS = 4;  // warps per CTA of the tiled wavefront kernel
+
+// Band limits on d = j - i (Sec. 7.1 prune axis), widened to hold both corners
+// unless the literal +-B band is asked for.
+FILTR_HD void band_limits(int64_t M, int64_t N, int64_t B, bool literal, int64_t *lo,
+                          int64_t *hi) {
+  if (literal) {
+    *lo = -B;
+    *hi = B;
+  } else {
+    *lo = ((N - M) < 0 ? (N - M) : 0) - B;
+    *hi = ((N - M) > 0 ? (N - M) : 0) + B;
+  }
+}
+
+// Column range [jlo, jhi] (1-based) a row strip [row0 + 1, row0 + H] covers.
+// Unbanded strips cover every column; banded ones only the band's columns.
+FILTR_HD void strip_cols(int64_t row0, int64_t Hs, int64_t M, int64_t N, bool band, int64_t lo,
+                         int64_t hi, int64_t *jlo, int64_t *jhi) {
+  if (!band) {
+    *jlo = 1;
+    *jhi = N;
+    return;
+  }
+  int64_t top = row0 + 1, bot = (row0 + Hs < M) ? row0 + Hs : M;
+  int64_t a = top + lo, b = bot + hi;
+  *jlo = a > 1 ? a : 1;
+  *jhi = b < N ? b : N;
+}
+
+// Traceback words one strip of the tiled kernel writes: one step per column
+// plus 31 pipeline steps, R/8 words per lane per step, 32 lanes.
+FILTR_HD int64_t strip_tb_words(int64_t jlo, int64_t jhi, int R) {
+  int64_t ncol = jhi >= jlo ? (jhi - jlo + 1) : 0;
+  return ncol > 0 ? (ncol + 31) * (R / 8) * 32 : 0;
+}
+
+// Per-pair output of the forward kernels before the traceback walk.
+struct FwdOut {
+  int32_t score;
+  int32_t end_i, end_j;
+  int32_t status;
+};
+
+// Kernel selection for one pair.
+enum Family : uint8_t { FAM_FULL = 0, FAM_XDROP = 1, FAM_TRIVIAL = 2 };
+
+struct PairPlan {
+  uint32_t pair;
+  uint8_t family;
+  uint8_t R;        // rows per lane (tiled kernel) or slots per lane (X-drop kernel)
+  uint8_t warps;    // X-drop kernel: warps per CTA
+  uint8_t pad;
+  uint64_t tb_words;
+  uint64_t cost;    // cell estimate for ordering
+};
+
+// What the traceback walk needs to find a cell's 4 bits.
+struct TbLayout {
+  uint64_t off;      // first word of this pair inside the traceback area
+  uint8_t family;
+  uint8_t R;
+  uint8_t warps;
+  uint8_t valid;     // 1 when this pair has traceback bits
+  int32_t pad;
+};
+
+struct ScoreParams {
+  int32_t mode, affine, o, e;  // o = 0 for linear gaps
+  int32_t alphabet;
+  int32_t use_band, band_literal, band;
+  int32_t use_xdrop, xdrop;
+  int32_t traceback;
+  int8_t subst[MAX_ALPHA * MAX_ALPHA];
+};
+
+struct BatchDev {
+  const uint8_t *q_seq, *r_seq;
+  const uint64_t *q_off, *r_off;
+  const uint32_t *q_len, *r_len;
+};
+
+struct FullArgs {
+  BatchDev b;
+  ScoreParams sp;
+  const uint32_t *order;   // pairs this launch handles, in processing order
+  uint32_t n_order;
+  uint32_t *counter;       // work-queue cursor (zeroed before launch)
+  filtr_result *out;
+  FwdOut *fwd;             // per pair (indexed by pair id)
+  uint32_t *tb;            // traceback area
+  const TbLayout *tbl;     // per pair
+  int2 *strip_buf;         // per resident warp: strip_stride entries
+  uint32_t strip_stride;
+};
+
+struct WalkArgs {
+  BatchDev b;
+  ScoreParams sp;
+  const uint32_t *order;
+  uint32_t n_order;
+  filtr_result *out;
+  const FwdOut *fwd;
+  const uint32_t *tb;
+  const TbLayout *tbl;
+  uint32_t *stage;          // per pair scratch for reversed CIGAR ops
+  const uint64_t *stage_off;
+};
+
+// ---- launches (defined in the .cu files) -----------------------------------
+cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
+int full_smem_bytes(int R, int alphabet);
+int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
+cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s);
+cudaError_t launch_scan_offsets(const filtr_result *out, uint32_t n, uint64_t *offs,
+                                uint64_t *total, cudaStream_t s);
+cudaError_t launch_compact(const WalkArgs &a, uint32_t n, const uint64_t *offs, uint32_t *cigar,
+                           uint64_t cap, filtr_result *out, cudaStream_t s);
+cudaError_t launch_trivial(const BatchDev &b, const ScoreParams &sp, const uint32_t *order,
+                           uint32_t n, filtr_result *out, FwdOut *fwd, cudaStream_t s);
+cudaError_t launch_validate(const uint8_t *codes, uint64_t n, int alphabet, uint32_t *bad,
+                            cudaStream_t s);
+cudaError_t launch_validate_pairs(const BatchDev &b, uint32_t n, int alphabet, uint32_t *bad,
+                                  cudaStream_t s);
+cudaError_t launch_pack(const uint8_t *codes, uint64_t n, int alphabet, uint32_t *packed,
+                        uint32_t *bad, cudaStream_t s);
+cudaError_t run_probe(double out[5]);
+
+// ---- host-side error reporting ---------------------------------------------
+void set_error(const char *fmt, ...);
+filtr_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace filtr

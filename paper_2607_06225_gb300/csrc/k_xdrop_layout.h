@@ -1,0 +1,40 @@
+// k_xdrop_layout.h -- traceback layout of the antidiagonal (X-drop) kernel.
+//
+// Per pair: (M + N + 1) int32 window origins c_k (the column j of slot 0 on
+// antidiagonal k), then for every antidiagonal k a window of WPK words holding
+// one 4-bit nibble per slot (slot p <-> cell (k - c_k - p, c_k + p)).
+#pragma once
+
+#include "filtr_internal.h"
+
+namespace filtr {
+
+FILTR_HD int xd_window_slots(int warps, int S) { return warps * 32 * S; }
+FILTR_HD int xd_words_per_k(int warps, int S) { return xd_window_slots(warps, S) / 8; }
+FILTR_HD uint64_t xd_tb_words(int64_t M, int64_t N, int warps, int S) {
+  return (uint64_t)(M + N + 1) * (uint64_t)(1 + xd_words_per_k(warps, S));
+}
+
+#ifdef __CUDACC__
+struct XdGeom {
+  const int32_t *ck;
+  const uint32_t *tb;
+  int wpk;
+};
+
+__device__ __forceinline__ void xd_geom_init(XdGeom &g, const uint32_t *base, int64_t M, int64_t N,
+                                             const TbLayout &L) {
+  g.ck = reinterpret_cast<const int32_t *>(base);
+  g.tb = base + (M + N + 1);
+  g.wpk = xd_words_per_k(L.warps, L.R);
+}
+
+__device__ __forceinline__ uint32_t xd_bits(const XdGeom &g, int i, int j) {
+  const int64_t k = (int64_t)i + j;
+  const int p = j - __ldg(g.ck + k);
+  const uint32_t w = __ldg(g.tb + k * g.wpk + (p >> 3));
+  return (w >> (4 * (p & 7))) & 15u;
+}
+#endif
+
+}  // namespace filtr

@@ -1,0 +1,54 @@
+// plan.h -- host planner for one batched call: kernel shape per pair, length /
+// cost ordering, traceback waves and the device workspace layout.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "filtr_internal.h"
+
+namespace filtr {
+
+struct Group {          // pairs of one wave that share one kernel instance
+  uint8_t family, R, warps;
+  uint32_t begin, end;  // slice of Plan::order
+};
+
+struct Wave {
+  std::vector<Group> groups;
+  uint32_t walk_begin, walk_end;  // slice of Plan::order whose traceback is walked after this wave
+  uint64_t tb_words;              // traceback words used by this wave
+};
+
+struct Plan {
+  std::vector<uint32_t> order;    // pair ids, grouped per wave and group, cost-descending inside a group
+  std::vector<TbLayout> tbl;      // per pair id
+  std::vector<uint64_t> stage_off;  // per pair id (CIGAR staging, in words)
+  std::vector<Wave> waves;
+  std::vector<uint32_t> trivial;  // pairs with an empty sequence
+  uint64_t stage_words = 0;
+  uint64_t max_n = 0, max_m = 0;
+  uint64_t cigar_upper = 0;       // sum over pairs of M + N: no CIGAR can be longer
+  uint64_t cells_estimate = 0;
+};
+
+struct PlanInput {
+  const ScoreParams *sp;
+  uint32_t n;
+  const uint32_t *q_len, *r_len;  // host copies
+  uint64_t tb_budget_words;       // traceback words one wave may use
+  int xdrop_slots;                // slots per lane of the X-drop kernel
+};
+
+// Rows per lane of the tiled kernel for a query of length M.
+int full_rows_per_lane(uint32_t M);
+// Traceback words of one pair in the tiled kernel.
+uint64_t full_tb_words(uint32_t M, uint32_t N, int R, const ScoreParams &sp);
+// Cell count of one pair under a static band (or the full matrix).
+uint64_t band_cells(uint32_t M, uint32_t N, const ScoreParams &sp);
+
+// Returns false (and sets the error message) if a single pair cannot fit.
+bool make_plan(const PlanInput &in, Plan *out);
+
+}  // namespace filtr

