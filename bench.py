@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=3000)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workspace-gb", type=float, default=64.0)
     return ap.parse_args()
 
 
@@ -196,7 +197,7 @@ def main():
     batch = synth.protein_pairs(n=args.pairs, seed=2 + 1000 * rank)
     sc = dict(batch.scoring)
     params = F.make_params(batch.subst, **sc)
-    ctx = F.Context(local_rank, 64 << 30)
+    ctx = F.Context(local_rank, int(args.workspace_gb * (1 << 30)))
     db = F.DeviceBatch(batch, dev)
     out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
     stream = torch.cuda.current_stream()

@@ -10,6 +10,7 @@
 #include <tuple>
 
 #include "filtr_ctx.h"
+#include "k_xdrop_layout.h"
 #include "plan.h"
 
 namespace filtr {
@@ -223,6 +224,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   }
 
   // 2. fixed workspace parts, then the plan
+  const std::vector<uint32_t> ql(h_ql, h_ql + n), rl(h_rl, h_rl + n);
   uint64_t max_m = 0, max_n = 0, stage_words = 0;
   for (uint32_t p = 0; p < n; ++p) {
     max_m = std::max<uint64_t>(max_m, h_ql[p]);
@@ -251,6 +253,9 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   const size_t n_counters = (size_t)n + 4096;
   uint32_t *d_counters = c.take<uint32_t>(n_counters);
   uint64_t *d_total = c.take<uint64_t>(4);
+  uint32_t *d_ovf = c.take<uint32_t>(n);
+  uint32_t *d_novf = c.take<uint32_t>(4);
+  uint32_t *d_rerun = c.take<uint32_t>(n);
   int2 *d_strip = c.take<int2>((size_t)grid_max * FULL_WARPS * strip_stride);
   uint32_t *d_stage = sp.traceback ? c.take<uint32_t>(stage_words) : nullptr;
   uint32_t *d_tb = c.take<uint32_t>(0);
@@ -270,7 +275,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   const uint32_t n_main = (uint32_t)P.order.size();
   std::vector<uint32_t> order_all = P.order;
   order_all.insert(order_all.end(), P.trivial.begin(), P.trivial.end());
-  const size_t up_bytes = n * (4 + sizeof(TbLayout) + 8);
+  const size_t up_bytes = n * (4 + sizeof(TbLayout) + 8) + 64;
   if (!ctx->ensure_host(up_bytes + 64)) {
     set_error("pinned host allocation failed");
     return FILTR_ERR_NOMEM;
@@ -306,54 +311,132 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   wa.stage = d_stage;
   wa.stage_off = d_stage_off;
 
-  // 4. waves
+  // 4. waves.  X-drop pairs whose live region outgrows their window come back
+  // through the overflow list and are rerun with a wider group (1 -> 4 -> 16
+  // warps) once the wave's walk is done with the traceback area.
   size_t counter_i = 0;
-  for (const Wave &w : P.waves) {
-    ctx->span_begin(Ctx::PH_FORWARD, st);
-    for (const Group &g : w.groups) {
-      const uint32_t cnt = g.end - g.begin;
-      if (g.family == FAM_FULL) {
-        if (plain) {
-          for (uint32_t t = 0; t < cnt; ++t) {
-            fa.order = d_order + g.begin + t;
-            fa.n_order = 1;
-            fa.counter = d_counters + (counter_i++ % n_counters);
-            ce = launch_full(fa, g.R, 1, st);
-            ++launches;
-            if (ce != cudaSuccess) return cuda_fail(ce, "tiled kernel launch");
-            if (sp.traceback) {
-              wa.order = fa.order;
-              wa.n_order = 1;
-              ce = launch_walk(wa, st);
-              ++launches;
-              if (ce != cudaSuccess) return cuda_fail(ce, "walk launch");
-            }
-          }
-        } else {
-          fa.order = d_order + g.begin;
-          fa.n_order = cnt;
+  auto run_group = [&](const uint32_t *d_ord, uint32_t cnt, uint8_t family, int R, int W) -> bool {
+    if (cnt == 0) return true;
+    if (family == FAM_FULL) {
+      if (plain) {
+        for (uint32_t t = 0; t < cnt; ++t) {
+          fa.order = d_ord + t;
+          fa.n_order = 1;
           fa.counter = d_counters + (counter_i++ % n_counters);
-          const int bps = ctx->full_blocks_per_sm(g.R, sp);
-          int grid = std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + FULL_WARPS - 1) / FULL_WARPS);
-          if (grid < 1) grid = 1;
-          ce = launch_full(fa, g.R, grid, st);
+          ce = launch_full(fa, R, 1, st);
           ++launches;
-          if (ce != cudaSuccess) return cuda_fail(ce, "tiled kernel launch");
+          if (ce != cudaSuccess) return false;
+          if (sp.traceback) {
+            wa.order = fa.order;
+            wa.n_order = 1;
+            ce = launch_walk(wa, st);
+            ++launches;
+            if (ce != cudaSuccess) return false;
+          }
         }
-      } else {
-        set_error("X-drop pruning is not available in this build");
-        return FILTR_ERR_UNSUPPORTED;
+        return true;
       }
-    }
-    ctx->span_end(st);
-    if (sp.traceback && !plain && w.walk_end > w.walk_begin) {
-      wa.order = d_order + w.walk_begin;
-      wa.n_order = w.walk_end - w.walk_begin;
-      ctx->span_begin(Ctx::PH_WALK, st);
-      ce = launch_walk(wa, st);
-      ctx->span_end(st);
+      fa.order = d_ord;
+      fa.n_order = cnt;
+      fa.counter = d_counters + (counter_i++ % n_counters);
+      const int bps = ctx->full_blocks_per_sm(R, sp);
+      int grid = (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + FULL_WARPS - 1) / FULL_WARPS);
+      ce = launch_full(fa, R, std::max(grid, 1), st);
       ++launches;
-      if (ce != cudaSuccess) return cuda_fail(ce, "walk launch");
+      return ce == cudaSuccess;
+    }
+    fa.order = d_ord;
+    fa.n_order = cnt;
+    fa.counter = d_counters + (counter_i++ % n_counters);
+    const int ppc = xd_pairs_per_cta(W);
+    const int bps = std::max(1, xd_max_blocks_per_sm(W, sp));
+    int grid = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + ppc - 1) / ppc);
+    ce = launch_xdrop(fa, W, std::max(grid, 1), d_ovf, d_novf, st);
+    ++launches;
+    return ce == cudaSuccess;
+  };
+  auto read_overflow = [&](std::vector<uint32_t> *list) -> bool {
+    uint32_t *h = reinterpret_cast<uint32_t *>(ctx->h_stage);
+    ce = cudaMemcpyAsync(h, d_novf, 4, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return false;
+    const uint32_t k = h[0];
+    list->clear();
+    if (k) {
+      ce = cudaMemcpyAsync(h, d_ovf, k * 4ull, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) return false;
+      list->assign(h, h + k);
+    }
+    return true;
+  };
+  auto walk = [&](const uint32_t *d_ord, uint32_t cnt) -> bool {
+    if (!sp.traceback || plain || cnt == 0) return true;
+    wa.order = d_ord;
+    wa.n_order = cnt;
+    ctx->span_begin(Ctx::PH_WALK, st);
+    ce = launch_walk(wa, st);
+    ctx->span_end(st);
+    ++launches;
+    return ce == cudaSuccess;
+  };
+  std::vector<uint32_t> pending;
+  for (const Wave &w : P.waves) {
+    bool has_xd = false;
+    ctx->span_begin(Ctx::PH_FORWARD, st);
+    for (const Group &g : w.groups) has_xd |= g.family == FAM_XDROP;
+    if (has_xd) {
+      ce = cudaMemsetAsync(d_novf, 0, 4, st);
+      if (ce != cudaSuccess) return cuda_fail(ce, "overflow reset");
+    }
+    for (const Group &g : w.groups)
+      if (!run_group(d_order + g.begin, g.end - g.begin, g.family, g.R, g.warps))
+        return cuda_fail(ce, "forward kernel launch");
+    ctx->span_end(st);
+    std::vector<uint32_t> ovf;
+    if (has_xd && !read_overflow(&ovf)) return cuda_fail(ce, "reading the overflow list");
+    if (!walk(d_order + w.walk_begin, w.walk_end - w.walk_begin)) return cuda_fail(ce, "walk launch");
+    pending.insert(pending.end(), ovf.begin(), ovf.end());
+  }
+  for (int W = 4; W <= 16 && !pending.empty(); W *= 4) {
+    // rerun the pairs that outgrew their window, in sub-waves that fit the budget
+    std::vector<uint32_t> todo;
+    todo.swap(pending);
+    size_t i0 = 0;
+    while (i0 < todo.size()) {
+      size_t i1 = i0;
+      uint64_t used = 0;
+      while (i1 < todo.size()) {
+        const uint32_t p = todo[i1];
+        const uint64_t words = sp.traceback ? xd_tb_words(ql[p], rl[p], W, 8) : 0;
+        if (used + words > tb_budget) break;
+        TbLayout &L = P.tbl[p];
+        L.off = used;
+        L.warps = (uint8_t)W;
+        used += words;
+        ++i1;
+      }
+      if (i1 == i0) {  // a single pair does not fit: it keeps status TOO_WIDE
+        ++i0;
+        continue;
+      }
+      const uint32_t cnt = (uint32_t)(i1 - i0);
+      char *h = reinterpret_cast<char *>(ctx->h_stage);
+      memcpy(h, todo.data() + i0, cnt * 4);
+      memcpy(h + n * 4ull, P.tbl.data(), n * sizeof(TbLayout));
+      ce = cudaMemcpyAsync(d_rerun, h, cnt * 4ull, cudaMemcpyHostToDevice, st);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_tbl, h + n * 4ull, n * sizeof(TbLayout), cudaMemcpyHostToDevice, st);
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(d_novf, 0, 4, st);
+      if (ce != cudaSuccess) return cuda_fail(ce, "rerun upload");
+      ctx->span_begin(Ctx::PH_FORWARD, st);
+      if (!run_group(d_rerun, cnt, FAM_XDROP, 8, W)) return cuda_fail(ce, "rerun launch");
+      ctx->span_end(st);
+      std::vector<uint32_t> ovf;
+      if (!read_overflow(&ovf)) return cuda_fail(ce, "reading the overflow list");
+      if (!walk(d_rerun, cnt)) return cuda_fail(ce, "walk launch");
+      pending.insert(pending.end(), ovf.begin(), ovf.end());
+      i0 = i1;
     }
   }
   if (!P.trivial.empty()) {

@@ -57,6 +57,26 @@ FILTR_HD int64_t strip_tb_words(int64_t jlo, int64_t jhi, int R) {
   return ncol > 0 ? (ncol + 31) * (R / 8) * 32 : 0;
 }
 
+// Traceback bits.  Each cell contributes four bits, pushed most significant
+// first into a 32-bit word by funnel shifts, so after 8 cells cell k sits in
+// bits [4*(7-k), 4*(7-k)+4):
+//   bit 3: E > D              (H came from E unless F wins)
+//   bit 2: F > max(D, E)      (H came from F)
+//   bit 1: E extended          (E_left - e > H_left - (o+e))
+//   bit 0: F extended          (F_up - e > H_up - (o+e))
+// Each bit is the sign of a difference (a - b < 0 <=> b > a); scores are below
+// 2^30 in magnitude, so differences never overflow.
+#ifdef __CUDACC__
+__device__ __forceinline__ void tb_push4(uint32_t &w, int d3, int d2, int d1, int d0) {
+  w = __funnelshift_l((uint32_t)d3, w, 1);
+  w = __funnelshift_l((uint32_t)d2, w, 1);
+  w = __funnelshift_l((uint32_t)d1, w, 1);
+  w = __funnelshift_l((uint32_t)d0, w, 1);
+}
+#endif
+enum : uint32_t { TB_PE = 8u, TB_PF = 4u, TB_EEXT = 2u, TB_FEXT = 1u };
+FILTR_HD uint32_t tb_nibble(uint32_t word, int k) { return (word >> (4 * (7 - (k & 7)))) & 15u; }
+
 // Per-pair output of the forward kernels before the traceback walk.
 struct FwdOut {
   int32_t score;
@@ -133,6 +153,10 @@ struct WalkArgs {
 cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
 int full_smem_bytes(int R, int alphabet);
 int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
+cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
+                         uint32_t *n_overflow, cudaStream_t s);
+int xd_pairs_per_cta(int W);
+int xd_max_blocks_per_sm(int W, const ScoreParams &sp);
 cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s);
 cudaError_t launch_scan_offsets(const filtr_result *out, uint32_t n, uint64_t *offs,
                                 uint64_t *total, cudaStream_t s);

@@ -14,16 +14,21 @@
 // The strip's bottom row (H and F per column) goes to a per-warp global
 // buffer that the next strip's lane 0 reads back.
 //
-// Cell update (affine, Gotoh H/E/F):
-//   E = max(E_left - e, H_left - (o+e))      __viaddmax_s32
-//   F = max(F_up - e, H_up - (o+e))          __viaddmax_s32
-//   H = max(H_diag + s, E, F) [, 0]          __vimax3_s32 / __vimax3_s32_relu
+// Cell update (affine, Gotoh H/E/F), plain int32 add / max:
+//   E = max(E_left - e, H_left - (o+e))
+//   F = max(F_up - e, H_up - (o+e))
+//   H = max(max(H_diag + s, E), F) [, 0]
+// The DPX forms (__viaddmax_s32, __vimax3_s32) compute the same values but
+// issue at half the plain integer rate on sm_103 (filtr_probe_int_peak
+// measures both), so the plain forms are used.
 // Substitution scores come from a per-strip query profile in shared memory
 // (profile[a][row] = s(q_row, a)): one 8- or 16-byte load per lane per step.
 //
-// Traceback nibble per cell: bit0 E > D, bit1 F > max(D, E), bit2 E took the
-// extension, bit3 F took the extension.  Layout per pair: strips in order;
-// per strip, step-major, then word (R/8 per lane), then lane.
+// Traceback: 4 bits per cell, each the sign of a difference shifted into the
+// lane's word (tb_push4, see filtr_internal.h): E > D, F > max(D, E), E took the
+// extension, F took the extension.  Cell k of a word ends in bits
+// [4*(7 - k), 4*(7 - k) + 4).  Layout per pair: strips in order; per strip,
+// step-major, then word (R/8 per lane), then lane.
 #include <climits>
 
 #include "filtr_internal.h"
@@ -44,11 +49,16 @@ struct ProfWord<16> {
   using T = uint4;
 };
 
+// signed byte k of a profile word, sign-extended by one byte permute
 template <int R>
 __device__ __forceinline__ void unpack_scores(const typename ProfWord<R>::T &w, int (&sc)[R]) {
   const uint32_t *u = reinterpret_cast<const uint32_t *>(&w);
 #pragma unroll
-  for (int k = 0; k < R; ++k) sc[k] = (int)(int8_t)((u[k >> 2] >> (8 * (k & 3))) & 0xff);
+  for (int k = 0; k < R; ++k) {
+    const uint32_t b = (uint32_t)(k & 3);
+    const uint32_t sel = b | ((8u | b) << 4) | ((8u | b) << 8) | ((8u | b) << 12);
+    sc[k] = (int)__byte_perm(u[k >> 2], 0u, sel);
+  }
 }
 
 template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND>
@@ -101,11 +111,13 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
 
       // query profile of this strip: prof[a * HS + row] = s(q[row0 + row], a)
       {
+        // rows past M score -128 against everything: their values stay below
+        // the running best of valid rows (see the best-cell tracking below)
         int qc[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
           const int row = top - 1 + k;
-          qc[k] = (row < M) ? (int)q[row] : 0;
+          qc[k] = (row < M) ? (int)q[row] : -1;
         }
         __syncwarp();
         for (int aa = 0; aa < A; ++aa) {
@@ -114,7 +126,11 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
           for (int w = 0; w < R / 4; ++w) {
             uint32_t v = 0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) v |= (uint32_t)(uint8_t)s_sub[qc[4 * w + b] * A + aa] << (8 * b);
+            for (int b = 0; b < 4; ++b) {
+              const int c = qc[4 * w + b];
+              const uint32_t sv = (c >= 0) ? (uint32_t)(uint8_t)s_sub[c * A + aa] : 0x80u;
+              v |= sv << (8 * b);
+            }
             dst[w] = v;
           }
         }
@@ -171,30 +187,28 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
           uint32_t tbw[WPS > 0 ? WPS : 1];
 #pragma unroll
           for (int w = 0; w < WPS; ++w) tbw[w] = 0;
+          int m = 0;  // column max of this lane's cells (local mode)
 #pragma unroll
           for (int k = 0; k < R; ++k) {
             const int Hl = Hc[k];
             const int D = Hdg + sc[k];
             int E, F, H;
-            uint32_t nib = 0;
             if (AFFINE) {
-              const int Hol = Hl - oe, Hou = Hup - oe;
-              E = __viaddmax_s32(Ec[k], -e, Hol);
-              F = __viaddmax_s32(Fup, -e, Hou);
-              H = LOCAL ? __vimax3_s32_relu(D, E, F) : __vimax3_s32(D, E, F);
-              if (TB) {
-                const int DE = max(D, E);
-                nib = (uint32_t)(E > D) | ((uint32_t)(F > DE) << 1) | ((uint32_t)(E > Hol) << 2) |
-                      ((uint32_t)(F > Hou) << 3);
-              }
+              const int Hol = Hl - oe, Eext = Ec[k] - e;
+              const int Hou = Hup - oe, Fext = Fup - e;
+              E = max(Hol, Eext);
+              F = max(Hou, Fext);
+              const int DE = max(D, E);
+              H = max(DE, F);
+              if (LOCAL) H = max(H, 0);
+              if (TB) tb_push4(tbw[k >> 3], D - E, DE - F, Hol - Eext, Hou - Fext);
             } else {
               E = Hl - e;
               F = Hup - e;
-              H = LOCAL ? __vimax3_s32_relu(D, E, F) : __vimax3_s32(D, E, F);
-              if (TB) {
-                const int DE = max(D, E);
-                nib = (uint32_t)(E > D) | ((uint32_t)(F > DE) << 1);
-              }
+              const int DE = max(D, E);
+              H = max(DE, F);
+              if (LOCAL) H = max(H, 0);
+              if (TB) tb_push4(tbw[k >> 3], D - E, DE - F, 0, 0);
             }
             if (BAND) {
               const int dd = j - (top + k);
@@ -204,7 +218,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
                 F = NEG;
               }
             }
-            if (TB) tbw[k >> 3] |= nib << (4 * (k & 7));
+            if (LOCAL) m = max(m, H);
             Hdg = Hl;
             Hc[k] = H;
             Ec[k] = E;
@@ -219,22 +233,23 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
             for (int w = 0; w < WPS; ++w) tbp[tb_base + ((int64_t)t * WPS + w) * 32 + lane] = tbw[w];
           }
           if (lane == 31 && s + 1 < nstrips) sbuf[j] = make_int2(Hup, Fup);
-          if (LOCAL) {
-            int m = NEG;
-            const bool full_rows = (top + R - 1 <= M);
+          // Best cell (local): rows past M never exceed the lane's running best
+          // of valid cells (their diagonal scores are -128 and their gap values
+          // derive from valid cells minus a gap cost), so the unmasked column
+          // max only triggers the masked scan when a valid cell may qualify.
+          if (LOCAL && m > 0 && m >= bestv) {
+            int mv = 0, ii = INT_MAX;
 #pragma unroll
-            for (int k = 0; k < R; ++k)
-              if (full_rows || top + k <= M) m = max(m, Hc[k]);
-            if (m > 0 && m >= bestv) {
-              int ii = INT_MAX;
-#pragma unroll
-              for (int k = R - 1; k >= 0; --k)
-                if (top + k <= M && Hc[k] == m) ii = top + k;
-              if (m > bestv || ii < besti) {
-                bestv = m;
-                besti = ii;
-                bestj = j;
+            for (int k = R - 1; k >= 0; --k)
+              if (top + k <= M && Hc[k] >= mv && Hc[k] > 0) {
+                mv = Hc[k];
+                ii = top + k;
               }
+            // (mv, ii): the largest valid value and, scanning upward, its smallest row
+            if (mv > 0 && (mv > bestv || (mv == bestv && ii < besti))) {
+              bestv = mv;
+              besti = ii;
+              bestj = j;
             }
           }
         }

@@ -33,6 +33,10 @@ __global__ void k_trivial(const BatchDev b, const ScoreParams sp, const uint32_t
     r.q_end = M;
     r.r_end = N;
     r.status = FILTR_ST_OK;
+    if (sp.use_band && sp.band_literal && (N - M > sp.band || M - N > sp.band)) {
+      r.score = 0;  // the literal band misses the corner
+      r.status = FILTR_ST_UNREACHABLE;
+    }
   }
   f.score = r.score;
   f.end_i = r.q_end;

@@ -1,7 +1,7 @@
 // k_tb.cu -- traceback walk, CIGAR offset scan and CIGAR compaction.
 //
 // The walk follows the 4-bit choices the forward kernels stored (one nibble per
-// cell: bit0 E > D, bit1 F > max(D, E), bit2 E extended, bit3 F extended) from
+// cell, see tb_push4 in filtr_internal.h) from
 // the end cell back to the start, tracking the current value so that a local
 // walk stops on the first H of 0 (Smith-Waterman) and emitting run-length BAM
 // ops in reverse into a per-pair staging area.  Global walks that reach row 0
@@ -47,7 +47,7 @@ __device__ __forceinline__ uint32_t full_bits(const uint32_t *tb, FullGeom &g, i
   if (t < 0 || t >= g.nsteps) return 0;  // never taken on a consistent traceback
   const int wps = g.R / 8;
   const uint32_t w = __ldg(tb + g.base + (t * wps + (k >> 3)) * 32 + l);
-  return (w >> (4 * (k & 7))) & 15u;
+  return tb_nibble(w, k);
 }
 
 struct Emitter {
@@ -132,9 +132,9 @@ __global__ void k_walk(const WalkArgs a) {
         break;
       }
       const uint32_t nib = (L.family == FAM_FULL) ? full_bits(tb, g, i, j) : xd_bits(xg, i, j);
-      if (nib & 2u) {
+      if (nib & TB_PF) {
         state = 2;
-      } else if (nib & 1u) {
+      } else if (nib & TB_PE) {
         state = 1;
       } else {
         const int qc = q[i - 1], rc = r[j - 1];
@@ -150,7 +150,7 @@ __global__ void k_walk(const WalkArgs a) {
       }
       const uint32_t nib = (L.family == FAM_FULL) ? full_bits(tb, g, i, j) : xd_bits(xg, i, j);
       em.put(OP_D, 1);
-      if (nib & 4u) {
+      if (nib & TB_EEXT) {
         v += e;
       } else {
         v += oe;
@@ -164,7 +164,7 @@ __global__ void k_walk(const WalkArgs a) {
       }
       const uint32_t nib = (L.family == FAM_FULL) ? full_bits(tb, g, i, j) : xd_bits(xg, i, j);
       em.put(OP_I, 1);
-      if (nib & 8u) {
+      if (nib & TB_FEXT) {
         v += e;
       } else {
         v += oe;

@@ -33,7 +33,7 @@ __device__ __forceinline__ uint32_t xd_bits(const XdGeom &g, int i, int j) {
   const int64_t k = (int64_t)i + j;
   const int p = j - __ldg(g.ck + k);
   const uint32_t w = __ldg(g.tb + k * g.wpk + (p >> 3));
-  return (w >> (4 * (p & 7))) & 15u;
+  return tb_nibble(w, p);
 }
 #endif
 

@@ -87,7 +87,9 @@ bool make_plan(const PlanInput &in, Plan *P) {
       P->stage_off[p] = P->stage_words;
       P->stage_words += (uint64_t)M + N + 1;
     }
-    if (M == 0 || N == 0) {
+    // an empty side leaves no cell to evaluate, except under X-drop, where the
+    // gap cells of row 0 / column 0 are themselves subject to the prune test
+    if ((M == 0 && N == 0) || ((M == 0 || N == 0) && !sp.use_xdrop)) {
       P->trivial.push_back(p);
       if (sp.traceback) P->tbl[p].valid = 0;
       continue;

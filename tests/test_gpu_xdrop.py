@@ -1,0 +1,118 @@
+"""GPU parity of the X-drop antidiagonal kernel against the oracle (bit-exact):
+thresholds from 0 (stops on antidiagonal 1) to infinity (whole matrix), with and
+without a band, global and local, linear and affine, traceback on and off,
+windows that overflow and are rerun with wider groups, and long-read pairs."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import compare, oracle_batch
+
+pytestmark = pytest.mark.gpu
+
+DNA_S = synth.dna_subst(2, -4)
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_06225_gb300 as F
+
+    return F
+
+
+@pytest.fixture(scope="module")
+def ctx(F):
+    c = F.Context(0, 4 << 30)
+    yield c
+    c.close()
+
+
+def run_both(F, ctx, batch, sc):
+    params = F.make_params(batch.subst, **sc)
+    res, cig, rc = F.align_batch(ctx, params, batch)
+    assert rc == 0, F.last_error()
+    ores, oops, ooff = oracle_batch(batch, sc)
+    compare(batch, sc, res, cig, ores, oops, ooff, label=str(sc))
+    return res
+
+
+def mixed_pairs(seed, n=120, lmax=600):
+    qs, rs = synth.random_pairs(n, lmax, lmax, 4, seed=seed, related=0.7)
+    rng = np.random.default_rng(seed)
+    for M, N in [(1, 1), (1, 50), (50, 1), (3, 200), (200, 3), (257, 255)]:
+        qs.append(rng.integers(0, 4, size=M).astype(np.uint8))
+        rs.append(rng.integers(0, 4, size=N).astype(np.uint8))
+    r = rng.integers(0, 4, size=300).astype(np.uint8)
+    qs.append(r.copy())
+    rs.append(r)
+    return synth.pack(qs, rs, 4, DNA_S)
+
+
+@pytest.mark.parametrize("X", [0, 5, 12, 40, 400])
+@pytest.mark.parametrize("tb", [False, True])
+def test_global_affine(F, ctx, X, tb):
+    b = mixed_pairs(100 + X)
+    run_both(F, ctx, b, dict(mode="global", affine=True, gap_open=4, gap_extend=2, xdrop=X,
+                             traceback=tb))
+
+
+@pytest.mark.parametrize("X", [3, 30])
+@pytest.mark.parametrize("mode", ["global", "local"])
+@pytest.mark.parametrize("affine", [False, True])
+def test_modes(F, ctx, X, mode, affine):
+    b = mixed_pairs(7 + X, n=80)
+    run_both(F, ctx, b, dict(mode=mode, affine=affine, gap_open=3 if affine else 0, gap_extend=1,
+                             xdrop=X, traceback=True))
+
+
+@pytest.mark.parametrize("band,literal", [(2, False), (16, False), (16, True), (100, False)])
+def test_band_and_xdrop(F, ctx, band, literal):
+    b = mixed_pairs(31 + band, n=80)
+    run_both(F, ctx, b, dict(mode="global", affine=True, gap_open=4, gap_extend=2, xdrop=60,
+                             band=band, band_literal=literal, traceback=True))
+
+
+def test_protein_xdrop(F, ctx):
+    P = synth.protein_pairs(n=60, lmin=30, lmax=500, seed=21)
+    run_both(F, ctx, P, dict(mode="global", affine=True, gap_open=11, gap_extend=1, xdrop=50,
+                             traceback=True))
+
+
+def test_window_overflow_rerun(F, ctx):
+    """X = infinity keeps every cell: the live region grows to the full
+    antidiagonal, outgrows the 256- and 1024-slot windows and is rerun."""
+    rng = np.random.default_rng(5)
+    qs = [rng.integers(0, 4, size=M).astype(np.uint8) for M in (300, 1500, 2500)]
+    rs = [rng.integers(0, 4, size=N).astype(np.uint8) for N in (280, 1400, 2600)]
+    b = synth.pack(qs, rs, 4, DNA_S)
+    res = run_both(F, ctx, b, dict(mode="global", affine=True, gap_open=4, gap_extend=2,
+                                   xdrop=oracle.INF, traceback=True))
+    full = oracle_batch(b, dict(mode="global", affine=True, gap_open=4, gap_extend=2,
+                                traceback=True))[0]
+    assert np.array_equal(res["score"].astype(np.int64), full["score"])
+
+
+def test_too_wide_reported(F, ctx):
+    """A live region wider than the widest window (4096 cells) is reported, not
+    computed wrongly."""
+    rng = np.random.default_rng(6)
+    q = rng.integers(0, 4, size=5000).astype(np.uint8)
+    r = rng.integers(0, 4, size=5000).astype(np.uint8)
+    b = synth.pack([q], [r], 4, DNA_S)
+    params = F.make_params(DNA_S, mode="global", gap_open=4, gap_extend=2, xdrop=2**31 - 1,
+                           traceback=False)
+    res, _, rc = F.align_batch(ctx, params, b)
+    assert rc == 0 and int(res[0]["status"]) == F.ST_TOO_WIDE
+
+
+def test_long_reads_sampled(F, ctx):
+    """Long noisy reads (band 256 widened to hold both corners, X-drop 400):
+    a 300-pair batch of the long-read model with lengths U[2k, 6k], all pairs
+    checked against the oracle."""
+    b = synth.long_reads(n=300, lmin=2000, lmax=6000, seed=3)
+    run_both(F, ctx, b, dict(b.scoring))
