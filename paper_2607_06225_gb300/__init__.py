@@ -114,3 +114,75 @@ def align_long(ctx: Context, params: Params, q: np.ndarray, r: np.ndarray, devic
 def cigar_of(res_row, cig) -> np.ndarray:
     o, n = int(res_row["cigar_off"]), int(res_row["cigar_len"])
     return cig[o:o + n]
+
+
+class Server:
+    """Continuous-batching server (filtr_serve_*): submit single pairs from any
+    thread, poll or wait for results."""
+
+    def __init__(self, ctx: Context, mem_budget: int, max_inflight: int = 4):
+        import ctypes as C
+
+        h = C.c_void_p()
+        check(lib().filtr_serve_create(ctx.handle, int(mem_budget), int(max_inflight), C.byref(h)),
+              "filtr_serve_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, params: Params, q: np.ndarray, r: np.ndarray) -> int:
+        import ctypes as C
+
+        q = np.ascontiguousarray(q, dtype=np.uint8)
+        r = np.ascontiguousarray(r, dtype=np.uint8)
+        t = C.c_uint64()
+        rc = lib().filtr_serve_submit(self.handle, C.byref(params), q.ctypes.data, int(q.shape[0]),
+                                      r.ctypes.data, int(r.shape[0]), C.byref(t))
+        check(rc, "filtr_serve_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_us: int = -1, cap: int = 1 << 22):
+        """Returns (result row, cigar ops, (t_submit, t_launch, t_done) in ns)."""
+        import ctypes as C
+
+        from ._lib import Result
+
+        res = Result()
+        cig = np.zeros(max(cap, 1), dtype=np.uint32)
+        times = np.zeros(3, dtype=np.uint64)
+        rc = lib().filtr_serve_wait(self.handle, int(ticket), int(timeout_us), C.byref(res),
+                                    cig.ctypes.data, int(cap), times.ctypes.data)
+        check(rc, "filtr_serve_wait")
+        row = np.zeros(1, dtype=RESULT_DTYPE)
+        for k, _ in Result._fields_:
+            row[k] = getattr(res, k)
+        return row[0], cig[: int(res.cigar_len)].copy(), tuple(int(x) for x in times)
+
+    def poll(self, ticket: int, cap: int = 1 << 22):
+        """None while running, else like wait()."""
+        import ctypes as C
+
+        from ._lib import ERR_BUSY, Result
+
+        res = Result()
+        cig = np.zeros(max(cap, 1), dtype=np.uint32)
+        times = np.zeros(3, dtype=np.uint64)
+        rc = lib().filtr_serve_poll(self.handle, int(ticket), C.byref(res), cig.ctypes.data,
+                                    int(cap), times.ctypes.data)
+        if rc == ERR_BUSY:
+            return None
+        check(rc, "filtr_serve_poll")
+        row = np.zeros(1, dtype=RESULT_DTYPE)
+        for k, _ in Result._fields_:
+            row[k] = getattr(res, k)
+        return row[0], cig[: int(res.cigar_len)].copy(), tuple(int(x) for x in times)
+
+    def close(self):
+        if self.handle:
+            lib().filtr_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

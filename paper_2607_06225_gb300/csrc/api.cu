@@ -168,7 +168,8 @@ bool Ctx::ensure_host(size_t bytes) {
 filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
                               const BatchDev &b, filtr_result *out, uint32_t *cigar,
                               uint64_t cap, cudaStream_t st, bool plain,
-                              const uint32_t *host_ql, const uint32_t *host_rl) {
+                              const uint32_t *host_ql, const uint32_t *host_rl,
+                              bool prevalidated) {
   ScoreParams sp;
   filtr_status rc = to_score_params(params, &sp);
   if (rc != FILTR_OK) return rc;
@@ -202,18 +203,21 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   uint32_t *h_bad = h_rl + n;
   Carver pre{ctx->ws, ctx->ws_bytes};
   uint32_t *d_bad = pre.take<uint32_t>(64);
-  ce = cudaMemsetAsync(d_bad, 0, 64 * sizeof(uint32_t), st);
-  ctx->span_begin(Ctx::PH_VALIDATE, st);
-  if (ce == cudaSuccess) ce = launch_validate_pairs(b, n, sp.alphabet, d_bad, st);
-  ctx->span_end(st);
-  ++launches;
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_bad, d_bad, 4, cudaMemcpyDeviceToHost, st);
-  if (!host_ql) {
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_ql, b.q_len, n * 4, cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_rl, b.r_len, n * 4, cudaMemcpyDeviceToHost, st);
+  *h_bad = 0;
+  if (!(prevalidated && host_ql)) {
+    ce = cudaMemsetAsync(d_bad, 0, 64 * sizeof(uint32_t), st);
+    ctx->span_begin(Ctx::PH_VALIDATE, st);
+    if (ce == cudaSuccess) ce = launch_validate_pairs(b, n, sp.alphabet, d_bad, st);
+    ctx->span_end(st);
+    ++launches;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_bad, d_bad, 4, cudaMemcpyDeviceToHost, st);
+    if (!host_ql) {
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_ql, b.q_len, n * 4, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_rl, b.r_len, n * 4, cudaMemcpyDeviceToHost, st);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "reading lengths");
   }
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess) return cuda_fail(ce, "reading lengths");
   if (host_ql) {
     memcpy(h_ql, host_ql, n * 4);
     memcpy(h_rl, host_rl, n * 4);
@@ -241,7 +245,8 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   }
   const int R_max = 16;
   const int blocks_per_sm = std::max(ctx->full_blocks_per_sm(8, sp), ctx->full_blocks_per_sm(16, sp));
-  const int grid_max = plain ? 1 : ctx->sms * blocks_per_sm;
+  const int grid_max = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * blocks_per_sm,
+                                                          ((int64_t)n + FULL_WARPS - 1) / FULL_WARPS);
   const uint32_t strip_stride = (uint32_t)(max_n + 2);
   Carver c{ctx->ws, ctx->ws_bytes};
   c.take<uint32_t>(64);  // d_bad
@@ -501,6 +506,23 @@ filtr_status filtr_ctx_create(int device, size_t workspace_bytes, filtr_ctx **ou
     return FILTR_ERR_INVALID;
   }
   *out = nullptr;
+  Ctx *c = nullptr;
+  filtr_status rc = filtr::ctx_new(device, workspace_bytes, &c);
+  if (rc == FILTR_OK) *out = reinterpret_cast<filtr_ctx *>(c);
+  return rc;
+}
+
+filtr_status filtr_ctx_destroy(filtr_ctx *ctx) {
+  filtr::ctx_delete(reinterpret_cast<Ctx *>(ctx));
+  return FILTR_OK;
+}
+
+}  // extern "C"
+
+namespace filtr {
+
+filtr_status ctx_new(int device, size_t workspace_bytes, Ctx **out) {
+  *out = nullptr;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -535,13 +557,12 @@ filtr_status filtr_ctx_create(int device, size_t workspace_bytes, filtr_ctx **ou
     delete c;
     return cuda_fail(e, "cudaStreamCreate");
   }
-  *out = reinterpret_cast<filtr_ctx *>(c);
+  *out = c;
   return FILTR_OK;
 }
 
-filtr_status filtr_ctx_destroy(filtr_ctx *ctx) {
-  if (!ctx) return FILTR_OK;
-  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+void ctx_delete(Ctx *c) {
+  if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->own_stream);
   if (c->done_ev) {
@@ -554,8 +575,11 @@ filtr_status filtr_ctx_destroy(filtr_ctx *ctx) {
   if (c->h_stage) cudaFreeHost(c->h_stage);
   cudaStreamDestroy(c->own_stream);
   delete c;
-  return FILTR_OK;
 }
+
+}  // namespace filtr
+
+extern "C" {
 
 filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint32_t *packed,
                         uint32_t *bad_out, void *stream) {
@@ -582,7 +606,7 @@ filtr_status filtr_align_batch(filtr_ctx *ctx, const filtr_params *params, uint3
   }
   BatchDev b{q_seq, r_seq, q_off, r_off, q_len, r_len};
   return align_batch_impl(reinterpret_cast<Ctx *>(ctx), params, n_pairs, b, out, cigar, cigar_cap,
-                          (cudaStream_t)stream, false, nullptr, nullptr);
+                          (cudaStream_t)stream, false, nullptr, nullptr, false);
 }
 
 filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
@@ -597,7 +621,7 @@ filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
   }
   BatchDev b{q_seq, r_seq, q_off, r_off, q_len, r_len};
   return align_batch_impl(reinterpret_cast<Ctx *>(ctx), params, n_pairs, b, out, cigar, cigar_cap,
-                          (cudaStream_t)stream, true, nullptr, nullptr);
+                          (cudaStream_t)stream, true, nullptr, nullptr, false);
 }
 
 filtr_status filtr_align_batch_host(filtr_ctx *ctx, const filtr_params *params, uint32_t n,
@@ -663,7 +687,7 @@ filtr_status filtr_align_batch_host(filtr_ctx *ctx, const filtr_params *params, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(drl, r_len, n * 4ull, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copies");
   BatchDev b{dq, dr, dqo, dro, dql, drl};
-  filtr_status rc = align_batch_impl(c, params, n, b, dout, dcig, ccap, st, false, q_len, r_len);
+  filtr_status rc = align_batch_impl(c, params, n, b, dout, dcig, ccap, st, false, q_len, r_len, false);
   if (rc != FILTR_OK && rc != FILTR_ERR_CIGAR_CAP) return rc;
   e = cudaMemcpyAsync(out, dout, n * sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -47,8 +47,13 @@ struct Ctx {
 };
 
 filtr_status to_score_params(const filtr_params *p, ScoreParams *sp);
+// prevalidated: the caller checked every residue code on the host and passes
+// host_ql / host_rl, so the call needs no host synchronisation up front.
 filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n, const BatchDev &b,
                               filtr_result *out, uint32_t *cigar, uint64_t cap, cudaStream_t st,
-                              bool plain, const uint32_t *host_ql, const uint32_t *host_rl);
+                              bool plain, const uint32_t *host_ql, const uint32_t *host_rl,
+                              bool prevalidated);
+filtr_status ctx_new(int device, size_t workspace_bytes, Ctx **out);
+void ctx_delete(Ctx *c);
 
 }  // namespace filtr

@@ -49,15 +49,26 @@ struct ProfWord<16> {
   using T = uint4;
 };
 
-// signed byte k of a profile word, sign-extended by one byte permute
+// Signed byte B of a word, sign-extended by one PTX byte permute: selector
+// nibble B copies byte B, nibbles with the msb set replicate its sign bit.
+// (__byte_perm ignores the selector msb, so it cannot do this.)
+template <int B>
+__device__ __forceinline__ int sext_byte(uint32_t w) {
+  constexpr uint32_t sel = B | ((8u | B) << 4) | ((8u | B) << 8) | ((8u | B) << 12);
+  int r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(w), "n"(sel));
+  return r;
+}
+
 template <int R>
 __device__ __forceinline__ void unpack_scores(const typename ProfWord<R>::T &w, int (&sc)[R]) {
   const uint32_t *u = reinterpret_cast<const uint32_t *>(&w);
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const uint32_t b = (uint32_t)(k & 3);
-    const uint32_t sel = b | ((8u | b) << 4) | ((8u | b) << 8) | ((8u | b) << 12);
-    sc[k] = (int)__byte_perm(u[k >> 2], 0u, sel);
+  for (int k = 0; k < R / 4; ++k) {
+    sc[4 * k + 0] = sext_byte<0>(u[k]);
+    sc[4 * k + 1] = sext_byte<1>(u[k]);
+    sc[4 * k + 2] = sext_byte<2>(u[k]);
+    sc[4 * k + 3] = sext_byte<3>(u[k]);
   }
 }
 
