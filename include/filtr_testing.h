@@ -1,0 +1,25 @@
+/* filtr_testing.h -- test hooks of the GB300 alignment library (not for
+ * production use).  They exercise failure paths without faulting the GPU. */
+#ifndef FILTR_TESTING_H
+#define FILTR_TESTING_H
+
+#include "filtr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Run the intra-pair long kernel of filtr_align_long on (q, M) x (r, N) (DEVICE
+ * codes, full matrix or band per params, traceback ignored) with the first row
+ * strip never publishing its progress, so every later strip's bounded wait runs
+ * out after timeout_ns nanoseconds.  Returns FILTR_ERR_TIMEOUT when the
+ * timeout path works (every warp stopped and the context stays usable);
+ * M must exceed one strip (512 rows). */
+filtr_status filtr_test_long_timeout(filtr_ctx *ctx, const filtr_params *params, const uint8_t *q,
+                                     uint32_t M, const uint8_t *r, uint32_t N,
+                                     uint64_t timeout_ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FILTR_TESTING_H */

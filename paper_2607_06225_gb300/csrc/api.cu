@@ -273,7 +273,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   (void)R_max;
 
   Plan P;
-  PlanInput in{&sp, n, h_ql, h_rl, tb_budget, 8};
+  PlanInput in{&sp, n, h_ql, h_rl, tb_budget, 8, ctx->xdrop_warps0};
   if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
 
   // 3. upload the plan
@@ -306,6 +306,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   fa.tbl = d_tbl;
   fa.strip_buf = d_strip;
   fa.strip_stride = strip_stride;
+  fa.max_n = 0;
   WalkArgs wa;
   wa.b = b;
   wa.sp = sp;
@@ -403,7 +404,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     if (!walk(d_order + w.walk_begin, w.walk_end - w.walk_begin)) return cuda_fail(ce, "walk launch");
     pending.insert(pending.end(), ovf.begin(), ovf.end());
   }
-  for (int W = 4; W <= 16 && !pending.empty(); W *= 4) {
+  for (int W = ctx->xdrop_warps0 < 4 ? 4 : 16; W <= 16 && !pending.empty(); W *= 4) {
     // rerun the pairs that outgrew their window, in sub-waves that fit the budget
     std::vector<uint32_t> todo;
     todo.swap(pending);
@@ -551,6 +552,14 @@ filtr_status ctx_new(int device, size_t workspace_bytes, Ctx **out) {
     return FILTR_ERR_NOMEM;
   }
   c->ws_bytes = ws;
+  e = cudaMalloc(&c->d_small, 4096);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->ws);
+    delete c;
+    set_error("cudaMalloc of 4 KiB failed");
+    return FILTR_ERR_NOMEM;
+  }
   e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaFree(c->ws);
@@ -571,6 +580,7 @@ void ctx_delete(Ctx *c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
+  if (c->d_small) cudaFree(c->d_small);
   if (c->d_io) cudaFree(c->d_io);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   cudaStreamDestroy(c->own_stream);

@@ -18,12 +18,14 @@ struct Ctx {
   void *h_stage = nullptr;    // pinned host staging
   size_t h_stage_bytes = 0;
   void *d_io = nullptr;       // device copies for the host-buffer entry point
+  char *d_small = nullptr;    // 4 KiB of device memory for per-call scalars
   size_t d_io_bytes = 0;
   cudaStream_t own_stream = nullptr;
   std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
   uint64_t last_cells_estimate = 0;
   int last_waves = 0;
   uint32_t last_launches = 0;
+  int xdrop_warps0 = 1;       // first window width (warps) of X-drop pairs
   // ordering of successive calls: the next call waits for this event, so the
   // workspace and the pinned staging are never reused while still in flight
   cudaEvent_t done_ev = nullptr;

@@ -134,6 +134,7 @@ struct FullArgs {
   const TbLayout *tbl;     // per pair
   int2 *strip_buf;         // per resident warp: strip_stride entries
   uint32_t strip_stride;
+  uint32_t max_n;          // 0, or the longest reference the strip buffers hold
 };
 
 struct WalkArgs {
@@ -149,7 +150,30 @@ struct WalkArgs {
   const uint64_t *stage_off;
 };
 
+struct LaneBest;
+// One long pair across the whole grid (k_long.cu).
+struct LongArgs {
+  const uint8_t *q, *r;
+  int M, N;
+  int lo, hi;                 // band on j - i (unbanded: -M-1, N+1)
+  ScoreParams sp;
+  int2 *ring;                 // NW slots of ring_stride entries
+  uint32_t ring_stride;
+  unsigned long long *prog;   // NW progress words (strip << 32 | column), zeroed
+  int *err;                   // set to 1 when a wait times out
+  unsigned long long timeout_ns;
+  int withhold;               // test hook: strip 0 never publishes (forces the timeout)
+  uint32_t *tb;               // traceback words (nullptr without traceback)
+  const int64_t *strip_base;  // first traceback word of each strip
+  struct LaneBest *wbest;     // one per warp
+  int *end_h;                 // H(M, N)
+};
+
 // ---- launches (defined in the .cu files) -----------------------------------
+cudaError_t launch_long(const LongArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_long_finish(const LongArgs &a, int nw, uint64_t cells, filtr_result *out,
+                               FwdOut *fwd, cudaStream_t s);
+int long_blocks_per_sm(const ScoreParams &sp);
 cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
 int full_smem_bytes(int R, int alphabet);
 int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);

@@ -1,0 +1,290 @@
+// k_strip.cuh -- one row strip of the tiled wavefront (shared by the batched
+// kernel k_full and the intra-pair kernel k_long).
+//
+// A strip is 32*R query rows; lane l owns rows [row0 + lR + 1, row0 + lR + R]
+// in registers.  At step t lane l updates column j = jlo + t - l of its rows,
+// so the warp's active cells form a staircase along the antidiagonal
+// direction: every dependency of a lane's top row (left: own registers, up:
+// lane l-1's bottom row at the same column, diagonal: lane l-1's bottom row one
+// column back) was produced at the previous step and arrives by one
+// __shfl_up_sync.  Rows inside a lane are updated top to bottom.  This is the
+// antidiagonal order of Sec. 6.2 applied to R-row tiles; reordering never
+// changes values or traceback (Sec. 6).  Lane 0 reads the strip above's bottom
+// row (H, F per column) through the IO object; lane 31 writes this strip's.
+//
+// Cell update (affine, Gotoh H/E/F), plain int32 add / max:
+//   E = max(E_left - e, H_left - (o+e))
+//   F = max(F_up - e, H_up - (o+e))
+//   H = max(max(H_diag + s, E), F) [, 0]
+// The DPX forms (__viaddmax_s32, __vimax3_s32) compute the same values but
+// issue at half the plain integer rate on sm_103 (filtr_probe_int_peak
+// measures both), so the plain forms are used.  Substitution scores come from
+// a per-strip query profile in shared memory (profile[a][row] = s(q_row, a)):
+// one 8- or 16-byte load per lane per step.
+//
+// Traceback: 4 bits per cell, each the sign of a difference shifted into the
+// lane's word (tb_push4): E > D, F > max(D, E), E took the extension, F took the
+// extension.  Cell k of a word ends in bits [4*(7 - k), 4*(7 - k) + 4).  Per
+// strip: step-major, then word (R/8 per lane), then lane.
+#pragma once
+
+#include <climits>
+
+#include "filtr_internal.h"
+
+namespace filtr {
+
+constexpr unsigned STRIP_FULLMASK = 0xffffffffu;
+
+template <int R>
+struct ProfWord;
+template <>
+struct ProfWord<8> {
+  using T = uint2;
+};
+template <>
+struct ProfWord<16> {
+  using T = uint4;
+};
+
+// Signed byte B of a word, sign-extended by one PTX byte permute: selector
+// nibble B copies byte B, nibbles with the msb set replicate its sign bit.
+// (__byte_perm ignores the selector msb, so it cannot do this.)
+template <int B>
+__device__ __forceinline__ int sext_byte(uint32_t w) {
+  constexpr uint32_t sel = B | ((8u | B) << 4) | ((8u | B) << 8) | ((8u | B) << 12);
+  int r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(w), "n"(sel));
+  return r;
+}
+
+template <int R>
+__device__ __forceinline__ void unpack_scores(const typename ProfWord<R>::T &w, int (&sc)[R]) {
+  const uint32_t *u = reinterpret_cast<const uint32_t *>(&w);
+#pragma unroll
+  for (int k = 0; k < R / 4; ++k) {
+    sc[4 * k + 0] = sext_byte<0>(u[k]);
+    sc[4 * k + 1] = sext_byte<1>(u[k]);
+    sc[4 * k + 2] = sext_byte<2>(u[k]);
+    sc[4 * k + 3] = sext_byte<3>(u[k]);
+  }
+}
+
+// Per-pair constants of a strip pass.
+struct StripPair {
+  int M, N;
+  const uint8_t *q, *r;
+  int lo, hi;        // band on d = j - i (unbanded: -M-1, N+1)
+  int o, e;          // o = 0 for linear gaps
+  int A;
+  const int8_t *s_sub;  // shared-memory substitution table
+  int8_t *prof;         // this warp's profile area (A * 32R bytes)
+  uint32_t *tb;         // this pair's traceback words (nullptr without traceback)
+};
+
+// Running best cell of a lane (local mode): largest H, then smallest i, then j.
+struct LaneBest {
+  int v, i, j;
+};
+
+// Process strip s.  IO must provide (called by every lane unless noted):
+//   bool wait(int j)          -- before lane 0 reads column j of the strip
+//                                above; false aborts the strip (timeout)
+//   int2 in(int j)            -- lane 0 only: (H, F) of the strip above
+//   void out(int j, int H, int F) -- lane 31 only: this strip's bottom row
+//   void done_col(int j, int jlo, int jhi) -- lane 31 only, after out(j)
+// prev_jlo / prev_jhi: the strip above's columns (empty for s == 0).
+// Returns false if IO aborted.  endH receives H(M, jhi) for the lane holding
+// row M when this is the last strip.
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, class IO>
+__device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, int jhi, int prev_jlo,
+                                           int prev_jhi, int64_t tb_base, IO &io, LaneBest &best,
+                                           int &endH) {
+  constexpr int HS = 32 * R;
+  constexpr int WPS = R / 8;
+  using PW = typename ProfWord<R>::T;
+  const int lane = threadIdx.x & 31;
+  const int M = P.M, lo = P.lo, hi = P.hi, o = P.o, e = P.e, oe = P.o + P.e;
+  const int row0 = s * HS;
+  const int top = row0 + lane * R + 1;
+  const int nstrips = (M + HS - 1) / HS;
+
+  // query profile of this strip: prof[a * HS + row] = s(q[row0 + row], a);
+  // rows past M score -128 against everything (see the best-cell tracking)
+  {
+    int qc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int row = top - 1 + k;
+      qc[k] = (row < M) ? (int)P.q[row] : -1;
+    }
+    __syncwarp();
+    for (int aa = 0; aa < P.A; ++aa) {
+      uint32_t *dst = reinterpret_cast<uint32_t *>(P.prof + aa * HS + lane * R);
+#pragma unroll
+      for (int w = 0; w < R / 4; ++w) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = qc[4 * w + b];
+          const uint32_t sv = (c >= 0) ? (uint32_t)(uint8_t)P.s_sub[c * P.A + aa] : 0x80u;
+          v |= sv << (8 * b);
+        }
+        dst[w] = v;
+      }
+    }
+    __syncwarp();
+  }
+
+  // state of column jlo - 1
+  int Hc[R], Ec[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = top + k;
+    int h = NEG;
+    if (jlo == 1 && (!BAND || -i >= lo)) h = LOCAL ? 0 : -(o + i * e);
+    Hc[k] = h;
+    Ec[k] = NEG;
+  }
+  int dtop = NEG;  // H(top - 1, jlo - 1)
+  if (jlo == 1) {
+    const int i = top - 1;
+    if (!BAND || -i >= lo) dtop = (i == 0 || LOCAL) ? 0 : -(o + i * e);
+  } else if (s > 0) {
+    const int jj = jlo - 1;
+    if (jj >= prev_jlo && jj <= prev_jhi) {
+      if (!io.wait(jj)) return false;
+      if (lane == 0) dtop = io.in(jj).x;
+    }
+  }
+
+  const int nsteps = (jhi - jlo + 1) + 31;
+  int upH = NEG, upF = NEG, prevIn = dtop;
+  int rc_next = P.r[jlo - 1];
+  for (int t = 0; t < nsteps; ++t) {
+    const int j = jlo + t - lane;
+    const int j0 = jlo + t;  // lane 0's column
+    if (s > 0 && j0 <= jhi && j0 >= prev_jlo && j0 <= prev_jhi) {
+      if (!io.wait(j0)) return false;
+    }
+    int inH = __shfl_up_sync(STRIP_FULLMASK, upH, 1);
+    int inF = AFFINE ? __shfl_up_sync(STRIP_FULLMASK, upF, 1) : NEG;
+    if (lane == 0) {
+      if (s == 0) {
+        inH = (!BAND || j <= hi) ? (LOCAL ? 0 : -(o + j * e)) : NEG;
+        inF = NEG;
+      } else if (j >= prev_jlo && j <= prev_jhi) {
+        const int2 v = io.in(j);
+        inH = v.x;
+        inF = v.y;
+      } else {
+        inH = NEG;
+        inF = NEG;
+      }
+    }
+    if (j >= jlo && j <= jhi) {
+      const int rc = rc_next;
+      if (j < jhi) rc_next = P.r[j];
+      const PW pw = *reinterpret_cast<const PW *>(P.prof + rc * HS + lane * R);
+      int sc[R];
+      unpack_scores<R>(pw, sc);
+      int Hup = inH, Fup = inF, Hdg = prevIn;
+      uint32_t tbw[WPS > 0 ? WPS : 1];
+#pragma unroll
+      for (int w = 0; w < WPS; ++w) tbw[w] = 0;
+      int m = 0;  // column max of this lane's cells (local mode)
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int Hl = Hc[k];
+        const int D = Hdg + sc[k];
+        int E, F, H;
+        if (AFFINE) {
+          const int Hol = Hl - oe, Eext = Ec[k] - e;
+          const int Hou = Hup - oe, Fext = Fup - e;
+          E = max(Hol, Eext);
+          F = max(Hou, Fext);
+          const int DE = max(D, E);
+          H = max(DE, F);
+          if (LOCAL) H = max(H, 0);
+          if (TB) tb_push4(tbw[k >> 3], D - E, DE - F, Hol - Eext, Hou - Fext);
+        } else {
+          E = Hl - e;
+          F = Hup - e;
+          const int DE = max(D, E);
+          H = max(DE, F);
+          if (LOCAL) H = max(H, 0);
+          if (TB) tb_push4(tbw[k >> 3], D - E, DE - F, 0, 0);
+        }
+        if (BAND) {
+          const int dd = j - (top + k);
+          if (dd < lo || dd > hi) {
+            H = NEG;
+            E = NEG;
+            F = NEG;
+          }
+        }
+        if (LOCAL) m = max(m, H);
+        Hdg = Hl;
+        Hc[k] = H;
+        Ec[k] = E;
+        Hup = H;
+        Fup = F;
+      }
+      upH = Hup;
+      upF = Fup;
+      prevIn = inH;
+      if (TB) {
+#pragma unroll
+        for (int w = 0; w < WPS; ++w) P.tb[tb_base + ((int64_t)t * WPS + w) * 32 + lane] = tbw[w];
+      }
+      if (lane == 31 && s + 1 < nstrips) {
+        io.out(j, Hup, Fup);
+        io.done_col(j, jlo, jhi);
+      }
+      // Best cell (local): rows past M never exceed the lane's running best
+      // of valid cells (their diagonal scores are -128 and their gap values
+      // derive from valid cells minus a gap cost), so the unmasked column max
+      // only triggers the masked scan when a valid cell may qualify; the scan
+      // itself only looks at valid rows.
+      if (LOCAL && m > 0 && m >= best.v) {
+        int mv = 0, ii = INT_MAX;
+#pragma unroll
+        for (int k = R - 1; k >= 0; --k)
+          if (top + k <= M && Hc[k] >= mv && Hc[k] > 0) {
+            mv = Hc[k];
+            ii = top + k;
+          }
+        if (mv > 0 && (mv > best.v || (mv == best.v && ii < best.i))) {
+          best.v = mv;
+          best.i = ii;
+          best.j = j;
+        }
+      }
+    }
+  }
+  if (!LOCAL && s == nstrips - 1 && top <= M && M < top + R) {
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+      if (top + k == M) endH = Hc[k];
+  }
+  __syncwarp();
+  return true;
+}
+
+// warp-wide reduction of LaneBest with the tie-break (all lanes get the result)
+__device__ __forceinline__ LaneBest warp_best(LaneBest b) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const int ov = __shfl_xor_sync(STRIP_FULLMASK, b.v, off);
+    const int oi = __shfl_xor_sync(STRIP_FULLMASK, b.i, off);
+    const int oj = __shfl_xor_sync(STRIP_FULLMASK, b.j, off);
+    if (ov > b.v || (ov == b.v && (oi < b.i || (oi == b.i && oj < b.j)))) {
+      b.v = ov;
+      b.i = oi;
+      b.j = oj;
+    }
+  }
+  return b;
+}
+
+}  // namespace filtr

@@ -1,0 +1,269 @@
+// long.cu -- filtr_align_long: one long pair with every SM on it.
+//
+// X-drop pairs (and pairs with an empty side) run as a one-pair batch of the
+// antidiagonal kernel with a 4-warp first window (reruns widen it); the
+// antidiagonal order is inherently sequential, so one wide group is what the
+// pair can use.  Full-matrix and banded pairs run the cooperative strip kernel
+// (k_long.cu) across the whole grid, then the ordinary traceback walk.
+#include <cstring>
+
+#include "../../include/filtr_testing.h"
+#include "filtr_ctx.h"
+#include "k_strip.cuh"
+#include "plan.h"
+
+namespace filtr {
+namespace {
+
+struct Carve {
+  char *base;
+  size_t cap, used = 0;
+  template <class T>
+  T *take(size_t count) {
+    used = (used + 255) / 256 * 256;
+    T *p = reinterpret_cast<T *>(base + used);
+    used += count * sizeof(T);
+    return p;
+  }
+};
+
+constexpr unsigned long long LONG_TIMEOUT_NS = 20ull * 1000 * 1000 * 1000;  // 20 s without progress
+
+filtr_status validate_seq(Ctx *c, const uint8_t *q, uint32_t M, const uint8_t *r, uint32_t N,
+                          int alphabet, cudaStream_t st) {
+  uint32_t *d_bad = reinterpret_cast<uint32_t *>(c->d_small);
+  cudaError_t e = cudaMemsetAsync(d_bad, 0, 4, st);
+  if (e == cudaSuccess) e = launch_validate(q, M, alphabet, d_bad, st);
+  if (e == cudaSuccess) e = launch_validate(r, N, alphabet, d_bad, st);
+  if (!c->ensure_host(64)) return FILTR_ERR_NOMEM;
+  uint32_t *h = reinterpret_cast<uint32_t *>(c->h_stage);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_bad, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "validating residues");
+  if (*h) {
+    set_error("%u residue codes are >= the alphabet size %d", *h, alphabet);
+    return FILTR_ERR_INVALID;
+  }
+  return FILTR_OK;
+}
+
+// the cooperative strip kernel; withhold != 0 is the timeout test
+filtr_status run_long(Ctx *c, const ScoreParams &sp, const filtr_params *params, const uint8_t *q,
+                      uint32_t M, const uint8_t *r, uint32_t N, filtr_result *out, uint32_t *cigar,
+                      uint64_t cap, cudaStream_t st, int withhold, unsigned long long timeout_ns) {
+  constexpr int R = 16, HS = 32 * R;
+  int64_t lo = -(int64_t)M - 1, hi = (int64_t)N + 1;
+  if (sp.use_band) {
+    band_limits(M, N, sp.band, sp.band_literal, &lo, &hi);
+    lo = std::max<int64_t>(lo, -(int64_t)M - 1);
+    hi = std::min<int64_t>(hi, (int64_t)N + 1);
+  }
+  const int nstrips = (int)((M + HS - 1) / HS);
+  // strip geometry: widest strip and traceback bases
+  std::vector<int64_t> base(nstrips + 1, 0);
+  int64_t widest = 0;
+  for (int s = 0; s < nstrips; ++s) {
+    int64_t jl, jh;
+    strip_cols((int64_t)s * HS, HS, M, N, sp.use_band != 0, lo, hi, &jl, &jh);
+    widest = std::max<int64_t>(widest, jh >= jl ? jh - jl + 1 : 0);
+    base[s + 1] = base[s] + (sp.traceback ? strip_tb_words(jl, jh, R) : 0);
+  }
+  const uint64_t tb_words = (uint64_t)base[nstrips];
+  const int bps = std::max(1, long_blocks_per_sm(sp));
+  int grid = c->sms * bps;
+  grid = std::max(1, std::min(grid, (nstrips + FULL_WARPS - 1) / FULL_WARPS));
+  // the ring may use a quarter of the workspace
+  const uint64_t stride = (uint64_t)widest + 2;
+  while (grid > 1 && (uint64_t)grid * FULL_WARPS * stride * 8 > c->ws_bytes / 4) grid /= 2;
+  if (withhold) grid = std::max(grid, 2);
+  const int nw = grid * FULL_WARPS;
+
+  Carve cv{c->ws, c->ws_bytes};
+  int2 *ring = cv.take<int2>((size_t)nw * stride);
+  unsigned long long *prog = cv.take<unsigned long long>(nw);
+  int *err = cv.take<int>(4);
+  LaneBest *wbest = cv.take<LaneBest>(nw);
+  int *end_h = cv.take<int>(4);
+  int64_t *d_base = cv.take<int64_t>(nstrips + 1);
+  FwdOut *d_fwd = cv.take<FwdOut>(1);
+  uint32_t *d_one = cv.take<uint32_t>(16);  // order, lengths, offsets of the one-pair batch
+  TbLayout *d_tbl = cv.take<TbLayout>(1);
+  uint64_t *d_misc = cv.take<uint64_t>(8);   // stage_off, offsets, total
+  uint32_t *d_stage = sp.traceback ? cv.take<uint32_t>((size_t)M + N + 1) : nullptr;
+  uint32_t *d_tb = cv.take<uint32_t>(tb_words);
+  if (cv.used > c->ws_bytes) {
+    set_error("the long pair needs %zu workspace bytes (traceback %llu); the context has %zu -- "
+              "use a band, X-drop, or score only",
+              cv.used, (unsigned long long)tb_words * 4, c->ws_bytes);
+    return FILTR_ERR_NOMEM;
+  }
+  // host-side constants for the one-pair batch used by the walk
+  if (!c->ensure_host(4096 + (nstrips + 1) * 8)) return FILTR_ERR_NOMEM;
+  char *h = reinterpret_cast<char *>(c->h_stage);
+  uint32_t one[16] = {0, M, N};            // order[0] = 0, q_len = M, r_len = N
+  TbLayout L{};
+  L.off = 0;
+  L.family = FAM_FULL;
+  L.R = R;
+  L.warps = 1;
+  L.valid = sp.traceback ? 1 : 0;
+  uint64_t misc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // stage_off, q_off, r_off
+  memcpy(h, one, sizeof one);
+  memcpy(h + 64, &L, sizeof L);
+  memcpy(h + 128, misc, sizeof misc);
+  memcpy(h + 256, base.data(), (nstrips + 1) * 8);
+  cudaError_t e = cudaMemcpyAsync(d_one, h, sizeof one, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tbl, h + 64, sizeof L, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_misc, h + 128, sizeof misc, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_base, h + 256, (nstrips + 1) * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(prog, 0, nw * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "long-pair setup");
+
+  LongArgs a;
+  a.q = q;
+  a.r = r;
+  a.M = (int)M;
+  a.N = (int)N;
+  a.lo = (int)lo;
+  a.hi = (int)hi;
+  a.sp = sp;
+  a.ring = ring;
+  a.ring_stride = (uint32_t)stride;
+  a.prog = prog;
+  a.err = err;
+  a.timeout_ns = timeout_ns;
+  a.withhold = withhold;
+  a.tb = sp.traceback ? d_tb : nullptr;
+  a.strip_base = d_base;
+  a.wbest = wbest;
+  a.end_h = end_h;
+  c->span_begin(Ctx::PH_FORWARD, st);
+  e = launch_long(a, grid, st);
+  c->span_end(st);
+  if (e != cudaSuccess) return cuda_fail(e, "long-pair kernel launch");
+  const uint64_t cells = band_cells(M, N, sp);
+  e = launch_long_finish(a, nw, cells, out, d_fwd, st);
+  if (e != cudaSuccess) return cuda_fail(e, "long-pair finish");
+  uint32_t launches = 2;
+  if (sp.traceback && !withhold) {
+    const uint64_t *d_off = d_misc + 1;
+    BatchDev b{q, r, d_off, d_off + 1, d_one + 1, d_one + 2};
+    WalkArgs wa;
+    wa.b = b;
+    wa.sp = sp;
+    wa.order = d_one;
+    wa.n_order = 1;
+    wa.out = out;
+    wa.fwd = d_fwd;
+    wa.tb = d_tb;
+    wa.tbl = d_tbl;
+    wa.stage = d_stage;
+    wa.stage_off = d_misc;
+    c->span_begin(Ctx::PH_WALK, st);
+    e = launch_walk(wa, st);
+    c->span_end(st);
+    if (e == cudaSuccess) e = launch_scan_offsets(out, 1, d_misc + 3, d_misc + 4, st);
+    if (e == cudaSuccess) e = launch_compact(wa, 1, d_misc + 3, cigar, cap, out, st);
+    launches += 3;
+    if (e != cudaSuccess) return cuda_fail(e, "long-pair traceback");
+  }
+  // the wait flag (and the CIGAR length) decide the status: synchronise once
+  int *h_err = reinterpret_cast<int *>(h + 1024);
+  filtr_result *h_res = reinterpret_cast<filtr_result *>(h + 1088);
+  e = cudaMemcpyAsync(h_err, err, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_res, out, sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "long-pair completion");
+  c->last_launches = launches;
+  c->last_cells_estimate = cells;
+  c->last_waves = 1;
+  if (*h_err) {
+    set_error("a strip wait ran out after %llu ns", (unsigned long long)timeout_ns);
+    return FILTR_ERR_TIMEOUT;
+  }
+  if (sp.traceback && h_res->cigar_len > cap) {
+    set_error("the CIGAR needs %u ops, cigar_cap is %llu", h_res->cigar_len, (unsigned long long)cap);
+    return FILTR_ERR_CIGAR_CAP;
+  }
+  return FILTR_OK;
+}
+
+}  // namespace
+}  // namespace filtr
+
+using namespace filtr;
+
+extern "C" {
+
+filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const uint8_t *q,
+                              uint32_t M, const uint8_t *r, uint32_t N, filtr_result *out,
+                              uint32_t *cigar, uint64_t cigar_cap, void *stream) {
+  ScoreParams sp;
+  filtr_status rc = to_score_params(params, &sp);
+  if (rc != FILTR_OK) return rc;
+  if (!ctx || !out || (M && !q) || (N && !r) || (sp.traceback && cigar_cap && !cigar)) {
+    set_error("filtr_align_long: NULL argument");
+    return FILTR_ERR_INVALID;
+  }
+  if (M >= (1u << 30) || N >= (1u << 30)) {
+    set_error("sequence longer than 2^30");
+    return FILTR_ERR_UNSUPPORTED;
+  }
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(c->device);
+  if (c->done_ev) cudaEventSynchronize(c->done_ev);
+  c->ev_used = 0;
+  c->spans.clear();
+  rc = validate_seq(c, q, M, r, N, sp.alphabet, st);
+  if (rc != FILTR_OK) return rc;
+  if (sp.use_xdrop || M == 0 || N == 0 || (uint64_t)M * N < (1ull << 22) || M <= 512) {
+    // a one-pair batch: lengths and offsets from the small device buffer
+    uint64_t *d_off = reinterpret_cast<uint64_t *>(c->d_small + 1024);
+    uint32_t *d_len = reinterpret_cast<uint32_t *>(c->d_small + 1088);
+    if (!c->ensure_host(4096)) return FILTR_ERR_NOMEM;
+    char *h = reinterpret_cast<char *>(c->h_stage);
+    uint64_t offs[2] = {0, 0};
+    uint32_t lens[2] = {M, N};
+    memcpy(h + 2048, offs, sizeof offs);
+    memcpy(h + 2112, lens, sizeof lens);
+    cudaError_t e = cudaMemcpyAsync(d_off, h + 2048, sizeof offs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_len, h + 2112, sizeof lens, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the staging is reused by the batch call
+    if (e != cudaSuccess) return cuda_fail(e, "one-pair setup");
+    BatchDev b{q ? q : reinterpret_cast<const uint8_t *>(c->d_small),
+               r ? r : reinterpret_cast<const uint8_t *>(c->d_small), d_off, d_off + 1, d_len, d_len + 1};
+    const int w0 = c->xdrop_warps0;
+    c->xdrop_warps0 = 4;
+    rc = align_batch_impl(c, params, 1, b, out, cigar, cigar_cap, st, false, lens, lens + 1, true);
+    c->xdrop_warps0 = w0;
+    return rc;
+  }
+  rc = run_long(c, sp, params, q, M, r, N, out, cigar, cigar_cap, st, 0, LONG_TIMEOUT_NS);
+  if (!c->done_ev) cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming);
+  if (c->done_ev) cudaEventRecord(c->done_ev, st);
+  return rc;
+}
+
+filtr_status filtr_test_long_timeout(filtr_ctx *ctx, const filtr_params *params, const uint8_t *q,
+                                     uint32_t M, const uint8_t *r, uint32_t N,
+                                     uint64_t timeout_ns) {
+  ScoreParams sp;
+  filtr_status rc = to_score_params(params, &sp);
+  if (rc != FILTR_OK) return rc;
+  if (!ctx || !q || !r || M <= 512 || N == 0) {
+    set_error("filtr_test_long_timeout: needs M > 512 and device sequences");
+    return FILTR_ERR_INVALID;
+  }
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaSetDevice(c->device);
+  if (c->done_ev) cudaEventSynchronize(c->done_ev);
+  sp.traceback = 0;
+  filtr_result *d_out = reinterpret_cast<filtr_result *>(c->d_small + 2048);
+  rc = run_long(c, sp, params, q, M, r, N, d_out, nullptr, 0, c->own_stream, 1, timeout_ns);
+  return rc;
+}
+
+}  // extern "C"

@@ -99,7 +99,7 @@ bool make_plan(const PlanInput &in, Plan *P) {
     if (sp.use_xdrop) {
       x.family = FAM_XDROP;
       x.R = (uint8_t)in.xdrop_slots;
-      x.warps = 1;
+      x.warps = (uint8_t)(in.xdrop_warps > 0 ? in.xdrop_warps : 1);
       x.tb_words = sp.traceback ? xd_tb_words(M, N, x.warps, x.R) : 0;
       // the live region is data dependent; its cost is at most the band / matrix
       x.cost = band_cells(M, N, sp);

@@ -39,6 +39,7 @@ struct PlanInput {
   const uint32_t *q_len, *r_len;  // host copies
   uint64_t tb_budget_words;       // traceback words one wave may use
   int xdrop_slots;                // slots per lane of the X-drop kernel
+  int xdrop_warps;                // first window width of X-drop pairs (warps)
 };
 
 // Rows per lane of the tiled kernel for a query of length M.
