@@ -19,6 +19,11 @@ filtr_status filtr_test_long_timeout(filtr_ctx *ctx, const filtr_params *params,
                                      uint32_t M, const uint8_t *r, uint32_t N,
                                      uint64_t timeout_ns);
 
+/* Make filtr_align_long use the checkpointed X-drop traceback (state of every
+ * `interval`-th antidiagonal kept, segments recomputed backwards) even when
+ * the whole traceback would fit; interval 0 restores the automatic choice. */
+filtr_status filtr_test_set_checkpoint(filtr_ctx *ctx, int32_t interval);
+
 #ifdef __cplusplus
 }
 #endif

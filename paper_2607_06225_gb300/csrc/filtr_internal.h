@@ -135,6 +135,7 @@ struct FullArgs {
   int2 *strip_buf;         // per resident warp: strip_stride entries
   uint32_t strip_stride;
   uint32_t max_n;          // 0, or the longest reference the strip buffers hold
+  const struct XdCkpt *ck; // X-drop kernel: checkpoint mode (nullptr = normal)
 };
 
 struct WalkArgs {
@@ -180,6 +181,9 @@ int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
 cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
                          uint32_t *n_overflow, cudaStream_t s);
 int xd_pairs_per_cta(int W);
+struct WalkState;
+cudaError_t launch_walk_segment(const WalkArgs &a, const uint32_t *seg_tb, const int32_t *seg_ck,
+                                int k_start, int wpk, WalkState *st, cudaStream_t s);
 int xd_max_blocks_per_sm(int W, const ScoreParams &sp);
 cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s);
 cudaError_t launch_scan_offsets(const filtr_result *out, uint32_t n, uint64_t *offs,

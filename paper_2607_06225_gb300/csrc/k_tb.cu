@@ -180,6 +180,109 @@ __global__ void k_walk(const WalkArgs a) {
   res->cigar_len = em.n;
 }
 
+// Resumable walk over one recomputed segment (antidiagonals (k_start, k_end])
+// of a checkpointed X-drop traceback; one thread.  Stops when the walk leaves
+// the segment (the next, earlier segment continues from the saved state) or
+// when the alignment's start is reached.
+__global__ void k_walk_segment(const WalkArgs a, const uint32_t *seg_tb, const int32_t *seg_ck,
+                               int k_start, int wpk, WalkState *ws) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  WalkState w = *ws;
+  if (w.done) return;
+  const uint32_t p = a.order[0];
+  const uint8_t *q = a.b.q_seq + a.b.q_off[p];
+  const uint8_t *r = a.b.r_seq + a.b.r_off[p];
+  const bool local = a.sp.mode == FILTR_LOCAL;
+  const int A = a.sp.alphabet, e = a.sp.e, oe = a.sp.o + a.sp.e;
+  Emitter em{a.stage + a.stage_off[p], w.n, w.cur, w.run};
+  int i = w.i, j = w.j, v = w.v, state = w.state;
+  bool done = false;
+  auto bits = [&](int ii, int jj) -> uint32_t {
+    const int64_t row = (int64_t)ii + jj - k_start - 1;
+    const int pp = jj - seg_ck[row];
+    return tb_nibble(seg_tb[row * wpk + (pp >> 3)], pp);
+  };
+  for (;;) {
+    if (state == 0) {
+      if ((i == 0 && j == 0) || (local && v == 0)) {
+        done = true;
+        break;
+      }
+      if (i == 0) {
+        em.put(OP_D, (uint32_t)j);
+        j = 0;
+        done = true;
+        break;
+      }
+      if (j == 0) {
+        em.put(OP_I, (uint32_t)i);
+        i = 0;
+        done = true;
+        break;
+      }
+    }
+    if (i + j <= k_start) break;  // the cell belongs to an earlier segment
+    if (state == 0) {
+      const uint32_t nib = bits(i, j);
+      if (nib & TB_PF) {
+        state = 2;
+      } else if (nib & TB_PE) {
+        state = 1;
+      } else {
+        const int qc = q[i - 1], rc = r[j - 1];
+        em.put(qc == rc ? OP_EQ : OP_X, 1);
+        v -= a.sp.subst[qc * A + rc];
+        --i;
+        --j;
+      }
+    } else if (state == 1) {
+      if (j == 0) {
+        state = 0;
+        continue;
+      }
+      const uint32_t nib = bits(i, j);
+      em.put(OP_D, 1);
+      if (nib & TB_EEXT) {
+        v += e;
+      } else {
+        v += oe;
+        state = 0;
+      }
+      --j;
+    } else {
+      if (i == 0) {
+        state = 0;
+        continue;
+      }
+      const uint32_t nib = bits(i, j);
+      em.put(OP_I, 1);
+      if (nib & TB_FEXT) {
+        v += e;
+      } else {
+        v += oe;
+        state = 0;
+      }
+      --i;
+    }
+  }
+  if (done) {
+    em.flush();
+    filtr_result *res = a.out + p;
+    res->q_begin = i;
+    res->r_begin = j;
+    res->cigar_len = em.n;
+  }
+  w.i = i;
+  w.j = j;
+  w.v = v;
+  w.state = state;
+  w.done = done ? 1 : 0;
+  w.n = em.n;
+  w.cur = em.cur;
+  w.run = em.run;
+  *ws = w;
+}
+
 // Exclusive scan of cigar_len (pair order) into offs; *total = sum.  One CTA.
 __global__ void k_scan(const filtr_result *out, uint32_t n, uint64_t *offs, uint64_t *total) {
   __shared__ uint64_t part[1024];
@@ -236,6 +339,12 @@ __global__ void k_compact(const WalkArgs a, uint32_t n, const uint64_t *offs, ui
 cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s) {
   if (a.n_order == 0) return cudaSuccess;
   k_walk<<<(a.n_order + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_segment(const WalkArgs &a, const uint32_t *seg_tb, const int32_t *seg_ck,
+                                int k_start, int wpk, WalkState *st, cudaStream_t s) {
+  k_walk_segment<<<1, 32, 0, s>>>(a, seg_tb, seg_ck, k_start, wpk, st);
   return cudaGetLastError();
 }
 

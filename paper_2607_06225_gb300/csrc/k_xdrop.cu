@@ -161,11 +161,18 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     if (a.sp.use_band) band_limits(M, N, a.sp.band, a.sp.band_literal, &blo, &bhi);
     const int band_lo = (int)max(blo, -(int64_t)M), band_hi = (int)min(bhi, (int64_t)N);
 
+    const XdCkpt *ck = a.ck;
+    const int ckmode = ck ? ck->mode : 0;
     uint32_t *tbp = nullptr;
     int32_t *ckp = nullptr;
     if (TB) {
-      ckp = reinterpret_cast<int32_t *>(a.tb + a.tbl[p].off);
-      tbp = a.tb + a.tbl[p].off + (uint64_t)(M + N + 1);
+      if (ckmode == 2) {  // rows indexed by k - k_start - 1
+        ckp = ck->seg_ck;
+        tbp = ck->seg_tb;
+      } else {
+        ckp = reinterpret_cast<int32_t *>(a.tb + a.tbl[p].off);
+        tbp = a.tb + a.tbl[p].off + (uint64_t)(M + N + 1);
+      }
     }
 
     // ---- antidiagonal 0: the cell (0, 0) ---------------------------------------
@@ -193,15 +200,38 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     int cornerH = INT_MIN;  // set by the thread owning (M, N) on antidiagonal M + N
     // residue codes of this thread's slots at the current origin: q[i-1], r[j-1]
     uint32_t qw[2] = {0, 0}, rw[2] = {0, 0};
-    if (TB && tid == 0) ckp[0] = 0;
+    if (TB && tid == 0 && ckmode != 2) ckp[0] = 0;
+    int k_first = 1, k_last = M + N;
+    if (ckmode == 2) {
+      // resume from the checkpoint of antidiagonal k_start
+      k_first = ck->k_start + 1;
+      k_last = min(ck->k_end, M + N);
+      if (ck->k_start > 0) {
+        const int32_t *rec = ck->buf + (int64_t)(ck->k_start / ck->C) * xd_ckpt_ints(W);
+        c = rec[0];
+        dprev = rec[1];
+        best = rec[2];
+        lo = rec[3];
+        hi = rec[4];
+        const int32_t *mine = rec + 8 + tid * (4 * XS);
+#pragma unroll
+        for (int s = 0; s < XS; ++s) {
+          H1[s] = mine[s];
+          E1[s] = mine[XS + s];
+          F1[s] = mine[2 * XS + s];
+          H2[s] = mine[3 * XS + s];
+        }
+      }
+    }
     if (W > 1) {
-      if (lane == 0) sh.first[0][warp] = Edge{H1[0], E1[0], F1[0], H2[0]};
-      if (lane == 31) sh.last[0][warp] = Edge{H1[XS - 1], E1[XS - 1], F1[XS - 1], H2[XS - 1]};
+      const int b0 = (k_first - 1) & 1;
+      if (lane == 0) sh.first[b0][warp] = Edge{H1[0], E1[0], F1[0], H2[0]};
+      if (lane == 31) sh.last[b0][warp] = Edge{H1[XS - 1], E1[XS - 1], F1[XS - 1], H2[XS - 1]};
       __syncthreads();
     }
 
-    int k = 1;
-    for (; k <= M + N; ++k) {
+    int k = k_first;
+    for (; k <= k_last; ++k) {
       // ---- candidate range of antidiagonal k, as columns [jA, jB] --------------
       int dl = lo - 1, dh = hi + 1;
       dl = max(dl, band_lo);
@@ -219,7 +249,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       // residue codes at the new origin: slot p <-> (i, j) = (k - cn - p, cn + p)
       // delta 1: j + 1 for every slot (r shifts down), i same
       // delta 0: i + 1 for every slot (q shifts up), j same
-      if (k == 1) {
+      if (k == k_first) {
         // first fill: load directly
         uint32_t w0 = 0, w1 = 0, v0 = 0, v1 = 0;
 #pragma unroll
@@ -304,8 +334,9 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         F1[s] = Fn[s];
       }
       if (TB) {
-        tbp[(uint64_t)k * (WIN / 8) + tid] = nibs;
-        if (tid == 0) ckp[k] = cn;
+        const int64_t row = (ckmode == 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
+        tbp[row * (WIN / 8) + tid] = nibs;
+        if (tid == 0) ckp[row] = cn;
       }
       // this thread's best cell on k (largest slot among equal maxima = smallest i)
       if (tbs >= 0) {
@@ -363,6 +394,26 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       lo = 2 * (cn + glo) - k;
       hi = 2 * (cn + ghi) - k;
       if (k == M + N) corner = true;
+      if (ckmode == 1 && (k % ck->C) == 0) {
+        // checkpoint: window state after antidiagonal k
+        int32_t *rec = ck->buf + (int64_t)(k / ck->C) * xd_ckpt_ints(W);
+        if (tid == 0) {
+          rec[0] = c;
+          rec[1] = dprev;
+          rec[2] = best;
+          rec[3] = lo;
+          rec[4] = hi;
+          rec[5] = 1;
+        }
+        int32_t *mine = rec + 8 + tid * (4 * XS);
+#pragma unroll
+        for (int s = 0; s < XS; ++s) {
+          mine[s] = H1[s];
+          mine[XS + s] = E1[s];
+          mine[2 * XS + s] = F1[s];
+          mine[3 * XS + s] = H2[s];
+        }
+      }
     }
     const int last_k = (k > M + N) ? M + N : k;
     (void)last_k;
@@ -412,7 +463,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       }
       cornerH = ch;
     }
-    if (tid == 0) {
+    if (tid == 0 && ckmode != 2) {
       int score = 0, ei = 0, ej = 0;
       if (status == FILTR_ST_TOO_WIDE) {
         const uint32_t slot = atomicAdd(n_overflow, 1u);

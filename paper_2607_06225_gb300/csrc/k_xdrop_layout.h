@@ -15,6 +15,27 @@ FILTR_HD uint64_t xd_tb_words(int64_t M, int64_t N, int warps, int S) {
   return (uint64_t)(M + N + 1) * (uint64_t)(1 + xd_words_per_k(warps, S));
 }
 
+// Checkpointed traceback (filtr_align_long when the whole traceback does not
+// fit): mode 1 sweeps forward without traceback and stores the window state of
+// every C-th antidiagonal; mode 2 resumes from the checkpoint of k_start and
+// recomputes antidiagonals (k_start, k_end] with traceback into a segment
+// buffer, which a resumable walk then consumes backwards.
+struct XdCkpt {
+  int mode;            // 1 forward with checkpoints, 2 resume one segment
+  int C;               // checkpoint interval in antidiagonals
+  int32_t *buf;        // checkpoints, xd_ckpt_ints(W) ints each, indexed by k / C
+  int k_start, k_end;  // mode 2
+  uint32_t *seg_tb;    // mode 2: (k_end - k_start) rows of WIN/8 words
+  int32_t *seg_ck;     // mode 2: window origin of each recomputed antidiagonal
+};
+FILTR_HD int64_t xd_ckpt_ints(int warps) { return 8 + (int64_t)xd_window_slots(warps, 8) * 4; }
+
+// Resumable walk over checkpointed segments (one thread).
+struct WalkState {
+  int i, j, v, state, done, cur;
+  uint32_t n, run;
+};
+
 #ifdef __CUDACC__
 struct XdGeom {
   const int32_t *ck;

@@ -114,3 +114,26 @@ def test_strip_wait_timeout_and_recovery(F, ctx):
     # the context (and the GPU) stay usable
     check_pair(F, ctx, q, r, DNA_S, dict(mode="global", affine=True, gap_open=4, gap_extend=2,
                                          traceback=True))
+
+
+@pytest.mark.parametrize("interval", [7, 64, 1000])
+def test_checkpointed_traceback(F, ctx, interval):
+    """Forcing the checkpointed X-drop traceback (state kept every `interval`
+    antidiagonals, segments recomputed backwards) gives the oracle's result,
+    including pairs that end DROPPED and local alignments."""
+    cases = []
+    b = synth.long_pair(length=6000, seg=150, seed=11, xdrop=120)
+    cases.append((b.pair(0), b.subst, dict(b.scoring)))
+    rng = np.random.default_rng(12)
+    r = rng.integers(0, 4, 3000).astype(np.uint8)
+    q = np.concatenate([r[:1500], rng.integers(0, 4, 900).astype(np.uint8)])
+    cases.append(((q, r), DNA_S, dict(mode="global", affine=True, gap_open=4, gap_extend=2, xdrop=30,
+                                       traceback=True)))
+    cases.append(((q, r), DNA_S, dict(mode="local", affine=True, gap_open=4, gap_extend=2, xdrop=60,
+                                       traceback=True)))
+    assert F.lib().filtr_test_set_checkpoint(ctx.handle, interval) == 0
+    try:
+        for (qq, rr), S, sc in cases:
+            check_pair(F, ctx, qq, rr, S, sc)
+    finally:
+        F.lib().filtr_test_set_checkpoint(ctx.handle, 0)
