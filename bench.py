@@ -44,11 +44,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--pairs", type=int, default=100_000)
+    ap.add_argument("--workload", default="protein-sw-100k",
+                    choices=["protein-sw-100k", "short-dna-1k", "long-reads-10k", "long-pair-1m"])
+    ap.add_argument("--pairs", type=int, default=0, help="0: the workload's own size")
     ap.add_argument("--plain-sample", type=int, default=3000)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workspace-gb", type=float, default=64.0)
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -118,6 +123,74 @@ def ncu_traffic():
             except Exception:
                 return None
     return None
+
+
+SERVE_KINDS = {
+    "sw_protein": dict(mode="local", affine=True, gap_open=11, gap_extend=1, traceback=True),
+    "band_dna": dict(mode="global", affine=True, gap_open=4, gap_extend=2, band=256, traceback=True),
+    "xdrop_dna": dict(mode="global", affine=True, gap_open=4, gap_extend=2, xdrop=400, traceback=True),
+}
+
+
+def reduce_over_ranks(ms: float, cells: float, dist, device) -> tuple:
+    """Whole-job timing for N replicas: the step time is the slowest rank's and
+    the work is every rank's cells (weak scaling: each rank aligns its own
+    batch; no data moves between ranks)."""
+    import torch
+
+    if dist is None:
+        return ms, cells
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([cells], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), float(c.item())
+
+
+def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lanes: int, seed: int = 4):
+    """Serving mix at a fixed offered load: first the burst capacity of the mix
+    (every request submitted at once), then Poisson arrivals at `load_frac` of
+    that capacity for `seconds`; latency = completion - submission."""
+    import synth
+
+    srv = F.Server(ctx, int(budget_gb * (1 << 30)), max_inflight=lanes)
+    psub = synth.protein_subst(np.random.default_rng(2))
+    params = {k: F.make_params(psub if k == "sw_protein" else synth.dna_subst(2, -4), **v)
+              for k, v in SERVE_KINDS.items()}
+
+    def run(reqs, paced):
+        t0 = time.perf_counter()
+        tickets = []
+        for rq in reqs:
+            if paced:
+                delay = rq.t_arrival - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(srv.submit(params[rq.kind], rq.q, rq.r))
+        lat, cells = [], 0
+        for t in tickets:
+            res, _, times = srv.wait(t)
+            lat.append((times[2] - times[0]) * 1e-6)
+            cells += int(res["cells"])
+        return time.perf_counter() - t0, lat, cells
+
+    burst, _ = synth.serve_mix(400, rate_hz=1e9, seed=seed + 100)
+    wall, _, cells = run(burst, paced=False)
+    capacity = cells / wall  # cells per second for this mix
+    mean_cells = cells / len(burst)
+    rate = load_frac * capacity / mean_cells
+    n = max(50, int(rate * seconds))
+    reqs, _ = synth.serve_mix(n, rate_hz=rate, seed=seed)
+    wall, lat, cells = run(reqs, paced=True)
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": n, "offered_rate_hz": rate, "load_frac_of_capacity": load_frac,
+            "offered_gcups": rate * mean_cells / 1e9, "capacity_gcups": capacity / 1e9,
+            "achieved_gcups": cells / wall / 1e9, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "mix": "40% SW protein / 40% band-256 NW DNA / 20% X-drop-400 DNA, log-normal lengths "
+                   "(median 2000, sigma 1, clipped 100-100000), traceback on",
+            "budget_gb": budget_gb, "lanes": lanes}
 
 
 def cpu_baseline(batch, sc, npairs):
@@ -193,8 +266,17 @@ def main():
     dev = torch.device("cuda", local_rank)
     if not os.path.exists(F._lib.LIB_PATH):
         B.build()
-    # weak scaling: every rank aligns its own 100k-pair batch (independent problems)
-    batch = synth.protein_pairs(n=args.pairs, seed=2 + 1000 * rank)
+    # weak scaling: every rank aligns its own batch (independent problems)
+    wl = args.workload
+    seed_off = 1000 * rank
+    if wl == "protein-sw-100k":
+        batch = synth.protein_pairs(n=args.pairs or 100_000, seed=2 + seed_off)
+    elif wl == "short-dna-1k":
+        batch = synth.short_dna_pairs(n=args.pairs or 1000, seed=1 + seed_off)
+    elif wl == "long-reads-10k":
+        batch = synth.long_reads(n=args.pairs or 10_000, seed=3 + seed_off)
+    else:
+        batch = synth.long_pair(seed=5 + seed_off)
     sc = dict(batch.scoring)
     params = F.make_params(batch.subst, **sc)
     ctx = F.Context(local_rank, int(args.workspace_gb * (1 << 30)))
@@ -202,10 +284,18 @@ def main():
     out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    is_long = wl == "long-pair-1m"
+    tb_on = bool(sc.get("traceback"))
 
     def step():
-        rc = ctx.align_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(), cig_t.data_ptr(),
-                                 db.cigar_upper, stream=stream.cuda_stream)
+        if is_long:
+            rc = ctx.align_long_ptr(params, db.q_seq.data_ptr(), int(batch.q_len[0]),
+                                    db.r_seq.data_ptr(), int(batch.r_len[0]), out_t.data_ptr(),
+                                    cig_t.data_ptr(), db.cigar_upper, stream=stream.cuda_stream)
+        else:
+            rc = ctx.align_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(),
+                                     cig_t.data_ptr() if tb_on else None,
+                                     db.cigar_upper if tb_on else 0, stream=stream.cuda_stream)
         if rc != 0:
             raise F.FiltrError(rc, F.last_error())
 
@@ -215,7 +305,8 @@ def main():
     torch.cuda.synchronize()
     res = F.results_to_numpy(out_t, db.n)
     cells = int(res["cells"].sum())
-    assert cells == batch.cells_full()
+    if wl in ("protein-sw-100k", "short-dna-1k"):
+        assert cells == batch.cells_full()
 
     probe = ctx.probe() if rank == 0 else None
 
@@ -241,15 +332,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([cells], dtype=torch.float64, device=dev)
-        dist.all_reduce(c)
-        total_cells = float(c.item())
-    else:
-        total_cells = float(cells)
+    ms, total_cells = reduce_over_ranks(ms, float(cells), dist, dev)
     value = total_cells / (ms * 1e-3) / 1e9
 
     line = None
@@ -334,6 +417,8 @@ def main():
             "clocks": clocks,
             "wall_s_timed": wall,
         }
+        if not args.no_serve:
+            line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(batch, sc, args.cpu_sample)
         print(json.dumps(line), flush=True)

@@ -10,7 +10,6 @@
 #include "plan.h"
 
 #include <algorithm>
-#include <cmath>
 
 #include "k_xdrop_layout.h"
 
@@ -20,8 +19,9 @@ int full_rows_per_lane(uint32_t M) { return M <= 256 ? 8 : 16; }
 
 uint64_t full_tb_words(uint32_t M, uint32_t N, int R, const ScoreParams &sp) {
   const int64_t HS = 32 * R;
-  int64_t lo = -(int64_t)M - 1, hi = (int64_t)N + 1;
   const bool band = sp.use_band != 0;
+  if (!band) return (uint64_t)((M + HS - 1) / HS) * (uint64_t)strip_tb_words(1, N, R);
+  int64_t lo = -(int64_t)M - 1, hi = (int64_t)N + 1;
   if (band) band_limits(M, N, sp.band, sp.band_literal, &lo, &hi);
   uint64_t w = 0;
   const int64_t ns = (M + HS - 1) / HS;
@@ -55,18 +55,19 @@ uint64_t band_cells(uint32_t M, uint32_t N, const ScoreParams &sp) {
   return c;
 }
 
+// half-octave buckets: 2 * floor(log2(cost)) + the next bit
 static int cost_bucket(uint64_t cost) {
-  if (cost == 0) return 0;
-  int b = 0;
-  double x = (double)cost;
-  b = (int)std::floor(std::log2(x) * 2.0);  // half-octave buckets
-  return std::min(63, std::max(0, b));
+  if (cost < 2) return 0;
+  const int lg = 63 - __builtin_clzll(cost);
+  const int b = 2 * lg + (int)((cost >> (lg - 1)) & 1);
+  return b < 63 ? b : 63;
 }
 
 bool make_plan(const PlanInput &in, Plan *P) {
   const ScoreParams &sp = *in.sp;
   const uint32_t n = in.n;
   P->order.clear();
+  P->order.reserve(n);
   P->tbl.assign(n, TbLayout{});
   P->stage_off.assign(n, 0);
   P->waves.clear();
@@ -76,12 +77,18 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->cigar_upper = 0;
   P->cells_estimate = 0;
 
-  std::vector<PairPlan> pp;
-  pp.reserve(n);
+  // per pair: kernel shape key, cost bucket, traceback words (flat arrays)
+  // shape keys: 0..2 tiled kernel with R = 16, 8 (ordered so wide shapes launch
+  // first); 3 the X-drop kernel
+  std::vector<uint8_t> bucket(n), shape(n);
+  std::vector<uint64_t> words(n);
+  std::vector<uint32_t> cnt(64, 0);
+  const int xw = in.xdrop_warps > 0 ? in.xdrop_warps : 1;
+  uint32_t live = 0;
   for (uint32_t p = 0; p < n; ++p) {
     const uint32_t M = in.q_len[p], N = in.r_len[p];
-    P->max_n = std::max<uint64_t>(P->max_n, N);
-    P->max_m = std::max<uint64_t>(P->max_m, M);
+    if (N > P->max_n) P->max_n = N;
+    if (M > P->max_m) P->max_m = M;
     P->cigar_upper += (uint64_t)M + N;
     if (sp.traceback) {
       P->stage_off[p] = P->stage_words;
@@ -91,83 +98,81 @@ bool make_plan(const PlanInput &in, Plan *P) {
     // gap cells of row 0 / column 0 are themselves subject to the prune test
     if ((M == 0 && N == 0) || ((M == 0 || N == 0) && !sp.use_xdrop)) {
       P->trivial.push_back(p);
-      if (sp.traceback) P->tbl[p].valid = 0;
+      shape[p] = 255;
       continue;
     }
-    PairPlan x{};
-    x.pair = p;
+    const uint64_t cost = band_cells(M, N, sp);
+    P->cells_estimate += cost;
+    uint64_t w = 0;
     if (sp.use_xdrop) {
-      x.family = FAM_XDROP;
-      x.R = (uint8_t)in.xdrop_slots;
-      x.warps = (uint8_t)(in.xdrop_warps > 0 ? in.xdrop_warps : 1);
-      x.tb_words = sp.traceback ? xd_tb_words(M, N, x.warps, x.R) : 0;
-      // the live region is data dependent; its cost is at most the band / matrix
-      x.cost = band_cells(M, N, sp);
+      shape[p] = 3;
+      if (sp.traceback) w = xd_tb_words(M, N, xw, in.xdrop_slots);
     } else {
-      x.family = FAM_FULL;
-      x.R = (uint8_t)full_rows_per_lane(M);
-      x.warps = 1;
-      x.tb_words = sp.traceback ? full_tb_words(M, N, x.R, sp) : 0;
-      x.cost = band_cells(M, N, sp);
+      const int R = full_rows_per_lane(M);
+      shape[p] = (R == 16) ? 0 : 1;
+      if (sp.traceback) w = full_tb_words(M, N, R, sp);
     }
-    P->cells_estimate += x.cost;
-    if (sp.traceback && x.tb_words > in.tb_budget_words) {
+    if (sp.traceback && w > in.tb_budget_words) {
       set_error("pair %u needs %llu traceback bytes, more than the workspace allows", p,
-                (unsigned long long)(x.tb_words * 4));
+                (unsigned long long)(w * 4));
       return false;
     }
-    pp.push_back(x);
+    words[p] = w;
+    bucket[p] = (uint8_t)(63 - cost_bucket(cost));
+    cnt[bucket[p]]++;
+    ++live;
   }
 
-  // counting sort, most expensive bucket first
-  std::vector<uint32_t> cnt(64, 0);
-  for (auto &x : pp) cnt[63 - cost_bucket(x.cost)]++;
+  // counting sort of pair ids, most expensive bucket first
   std::vector<uint32_t> start(64, 0);
   for (int b = 1; b < 64; ++b) start[b] = start[b - 1] + cnt[b - 1];
-  std::vector<PairPlan> sorted(pp.size());
-  for (auto &x : pp) sorted[start[63 - cost_bucket(x.cost)]++] = x;
+  std::vector<uint32_t> sorted(live);
+  for (uint32_t p = 0; p < n; ++p)
+    if (shape[p] != 255) sorted[start[bucket[p]]++] = p;
 
-  // waves
+  // waves: cut the cost order where the traceback budget is used up, then
+  // group each wave by kernel shape (stable counting sort over 4 keys)
   const uint64_t budget = sp.traceback ? in.tb_budget_words : ~0ull;
   size_t i = 0;
   while (i < sorted.size()) {
     size_t j = i;
     uint64_t used = 0;
-    while (j < sorted.size() && used + sorted[j].tb_words <= budget) used += sorted[j++].tb_words;
-    // group the slice [i, j) by kernel shape, stable (keeps the cost order)
+    uint32_t kc[4] = {0, 0, 0, 0};
+    while (j < sorted.size() && used + words[sorted[j]] <= budget) {
+      used += words[sorted[j]];
+      kc[shape[sorted[j]]]++;
+      ++j;
+    }
     Wave w;
     w.tb_words = used;
-    std::vector<PairPlan> slice(sorted.begin() + i, sorted.begin() + j);
-    std::stable_sort(slice.begin(), slice.end(), [](const PairPlan &a, const PairPlan &b) {
-      if (a.family != b.family) return a.family < b.family;
-      if (a.R != b.R) return a.R > b.R;
-      return a.warps > b.warps;
-    });
     const uint32_t wave_begin = (uint32_t)P->order.size();
+    uint32_t ks[4];
+    ks[0] = wave_begin;
+    for (int k = 1; k < 4; ++k) ks[k] = ks[k - 1] + kc[k - 1];
+    P->order.resize(wave_begin + (j - i));
+    uint32_t kpos[4] = {ks[0], ks[1], ks[2], ks[3]};
+    for (size_t t = i; t < j; ++t) P->order[kpos[shape[sorted[t]]]++] = sorted[t];
+    // traceback offsets in wave order, per-pair layout, groups
     uint64_t off = 0;
-    size_t g0 = 0;
-    for (size_t t = 0; t < slice.size(); ++t) {
-      const PairPlan &x = slice[t];
-      TbLayout &L = P->tbl[x.pair];
-      L.off = off;
-      L.family = x.family;
-      L.R = x.R;
-      L.warps = x.warps;
-      L.valid = sp.traceback ? 1 : 0;
-      off += x.tb_words;
-      P->order.push_back(x.pair);
-      const bool last = (t + 1 == slice.size());
-      if (last || slice[t + 1].family != x.family || slice[t + 1].R != x.R ||
-          slice[t + 1].warps != x.warps) {
-        Group g;
-        g.family = x.family;
-        g.R = x.R;
-        g.warps = x.warps;
-        g.begin = wave_begin + (uint32_t)g0;
-        g.end = wave_begin + (uint32_t)(t + 1);
-        w.groups.push_back(g);
-        g0 = t + 1;
+    for (int k = 0; k < 4; ++k) {
+      if (!kc[k]) continue;
+      Group g;
+      g.family = (k == 3) ? FAM_XDROP : FAM_FULL;
+      g.R = (k == 3) ? (uint8_t)in.xdrop_slots : (k == 0 ? 16 : 8);
+      g.warps = (k == 3) ? (uint8_t)xw : 1;
+      g.begin = ks[k];
+      g.end = ks[k] + kc[k];
+      for (uint32_t t = g.begin; t < g.end; ++t) {
+        const uint32_t p = P->order[t];
+        TbLayout &L = P->tbl[p];
+        L.off = off;
+        L.family = g.family;
+        L.R = g.R;
+        L.warps = g.warps;
+        L.valid = sp.traceback ? 1 : 0;
+        off += words[p];
       }
+      w.groups.push_back(g);
     }
     w.walk_begin = wave_begin;
     w.walk_end = (uint32_t)P->order.size();
