@@ -170,6 +170,39 @@ filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
                                      const uint32_t *r_len, filtr_result *out, uint32_t *cigar,
                                      uint64_t cigar_cap, void *stream);
 
+/* Score-only batched alignment that allocates nothing (the paper has no
+ * counterpart; this is a deployment variant).  Some callers cannot call
+ * cudaMalloc -- code inside a host framework that owns all device memory and
+ * forbids further allocation, or latency-critical paths that cannot afford
+ * cudaMalloc's implicit device-wide synchronisation.  This entry point needs
+ * no context and calls no cudaMalloc, cudaFree or allocating library routine:
+ * its scratch (a work-queue counter and one strip buffer per resident warp) is
+ * a fixed 32 MiB device array inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   params        : traceback must be 0; full matrix or band (no X-drop)
+ *   q_seq .. r_len: DEVICE, as filtr_align_batch;  out: DEVICE, n_pairs results
+ *   max_query_len / max_ref_len: the longest query / reference of the batch;
+ *                   the strip buffers are sized by max_ref_len, so the batch
+ *                   runs on fewer warps as it grows, and it is rejected with
+ *                   FILTR_ERR_UNSUPPORTED beyond 1,048,566 reference residues (or when
+ *                   scores could reach 2^28); a pair longer than the limits it
+ *                   was given gets status FILTR_ST_TOO_WIDE.
+ * Results equal filtr_align_batch's (score, end coordinates, status, cells;
+ * q_begin / r_begin as without traceback).  The call validates residue codes
+ * and waits for that check on `stream` (FILTR_ERR_INVALID for a bad code),
+ * then returns with the alignment queued on `stream`.  The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array and clears its counters first: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. */
+filtr_status filtr_align_batch_noalloc(const filtr_params *params, uint32_t n_pairs,
+                                       const uint8_t *q_seq, const uint64_t *q_off,
+                                       const uint32_t *q_len, const uint8_t *r_seq,
+                                       const uint64_t *r_off, const uint32_t *r_len,
+                                       uint32_t max_query_len, uint32_t max_ref_len,
+                                       filtr_result *out, void *stream);
+
 /* Align one long pair with every SM of the device working on it.
  *   q, r : DEVICE codes (M, N up to 2^31-1);  out : DEVICE, one filtr_result;
  *   cigar: DEVICE, cigar_cap ops.

@@ -87,6 +87,9 @@ def lib():
             f = getattr(L, name)
             f.restype = i32
             f.argtypes = batch_args + [_P]
+        L.filtr_align_batch_noalloc.restype = i32
+        L.filtr_align_batch_noalloc.argtypes = [C.POINTER(Params), C.c_uint32, _P, _P, _P, _P, _P,
+                                                _P, C.c_uint32, C.c_uint32, _P, _P]
         L.filtr_align_batch_host.restype = i32
         L.filtr_align_batch_host.argtypes = batch_args
         L.filtr_align_long.restype = i32

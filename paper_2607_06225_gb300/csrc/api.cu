@@ -307,6 +307,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   fa.strip_buf = d_strip;
   fa.strip_stride = strip_stride;
   fa.max_n = 0;
+  fa.max_m = 0;
   fa.ck = nullptr;
   WalkArgs wa;
   wa.b = b;

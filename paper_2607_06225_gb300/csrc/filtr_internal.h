@@ -135,6 +135,7 @@ struct FullArgs {
   int2 *strip_buf;         // per resident warp: strip_stride entries
   uint32_t strip_stride;
   uint32_t max_n;          // 0, or the longest reference the strip buffers hold
+  uint32_t max_m;          // 0, or the longest query accepted
   const struct XdCkpt *ck; // X-drop kernel: checkpoint mode (nullptr = normal)
 };
 

@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
     P.prof = smem + 512 + wib * (A * HS);
     P.tb = TB ? a.tb + a.tbl[p].off : nullptr;
     const int M = P.M, N = P.N;
-    if (a.max_n && (uint32_t)N > a.max_n) {  // only the fixed-scratch entry point sets max_n
+    if ((a.max_n && (uint32_t)N > a.max_n) || (a.max_m && (uint32_t)M > a.max_m)) {
+      // only the fixed-scratch entry point sets these limits
       if (lane == 0) {
         filtr_result res{};
         res.status = FILTR_ST_TOO_WIDE;

@@ -252,6 +252,7 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
     fa.strip_buf = nullptr;
     fa.strip_stride = 0;
     fa.max_n = 0;
+    fa.max_m = 0;
     fa.ck = d_ck;
     c->span_begin(Ctx::PH_FORWARD, st);
     e = launch_xdrop(fa, W, 1, d_ovf, d_ovf + 1, st);
