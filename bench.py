@@ -30,6 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "protein-sw-100k"
+WORKLOAD_DESC = {
+    "protein-sw-100k": "local affine o=11 e=1, seeded 20x20 matrix, traceback+CIGAR, lengths U[100,1000]",
+    "short-dna-1k": "global affine +2/-4 o=4 e=2, score only, 1000 pairs of 128 bp at 5% error",
+    "long-reads-10k": "global affine DNA, band 256 (widened) + X-drop 400, traceback+CIGAR, "
+                      "10k reads U[10k,50k] at 6/3/1% ins/del/sub",
+    "long-pair-1m": "global affine DNA, X-drop 1000, checkpointed traceback, 1 Mbp at 1% + 5 kb insertion",
+}
 METRIC = "GCUPS batched vs plain per-pair launch (bit-exact); serving p50/p99 latency"
 # integer operations per cell in the affine local update with traceback, as the
 # recurrence states them: E (1 add-max), F (1 add-max), H - (o+e) (1 add),
@@ -112,17 +119,25 @@ class ClockSampler:
 
 
 def ncu_traffic():
-    """dram bytes per forward launch from the committed ncu summary, if present."""
+    """DRAM bytes per cell of the forward kernel from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+
     path = os.path.join(ROOT, "profiles", "k_full_protein_sw.md")
-    if not os.path.exists(path):
+    src = os.path.join(ROOT, "paper_2607_06225_gb300", "csrc", "k_strip.cuh")
+    if not os.path.exists(path) or not os.path.exists(src):
         return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha, per_cell = None, None
     for line in open(path):
-        if line.startswith("dram_bytes_per_cell:"):
+        if line.startswith("source_sha:"):
+            sha = line.split(":")[1].strip()
+        if "dram_bytes_per_cell:" in line:
             try:
-                return float(line.split(":")[1].split()[0])
+                per_cell = float(line.split("dram_bytes_per_cell:")[1].split()[0].strip("|"))
             except Exception:
-                return None
-    return None
+                per_cell = None
+    return per_cell if sha == cur else None
 
 
 SERVE_KINDS = {
@@ -243,6 +258,111 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def host_entry_e2e(F, ctx, params, batch, db, res, cells, steps, tb_on):
+    """The same call through the host-buffer entry point (pinned host memory):
+    host-to-device copies of the inputs and device-to-host copies of results
+    and CIGARs are inside the timed region."""
+    import torch
+
+    pin = {}
+    for name in ("q_seq", "q_off", "q_len", "r_seq", "r_off", "r_len"):
+        a = np.ascontiguousarray(getattr(batch, name))
+        pin[name] = torch.from_numpy(a.view(np.uint8)).pin_memory()
+    hout = torch.empty(db.n * F.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    hcig = torch.empty(max(db.cigar_upper, 1) * 4, dtype=torch.uint8).pin_memory()
+    ptr = [pin[n].data_ptr() for n in ("q_seq", "q_off", "q_len", "r_seq", "r_off", "r_len")]
+    e2e_t = []
+    for k in range(2 + steps):
+        t0 = time.perf_counter()
+        rc = ctx.align_batch_host_ptr(params, db.n, *ptr, hout.data_ptr(),
+                                      hcig.data_ptr() if tb_on else None,
+                                      db.cigar_upper if tb_on else 0)
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+        if k >= 2:
+            e2e_t.append(time.perf_counter() - t0)
+    hres = hout.numpy().view(F.RESULT_DTYPE)
+    assert np.array_equal(hres, res), "host entry point disagrees with the device entry point"
+    total_ops = int(hres["cigar_off"][-1] + hres["cigar_len"][-1]) if tb_on else 0
+    h2d = sum(int(pin[n].numel()) for n in pin)
+    d2h = db.n * F.RESULT_DTYPE.itemsize + total_ops * 4
+    return {"value": cells / (sum(e2e_t) / len(e2e_t)) / 1e9, "unit": "GCUPS",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def long_pair_e2e(F, ctx, params, batch, steps, res, stream, dev):
+    """The long pair end to end: pinned host codes copied in, filtr_align_long,
+    the result and CIGAR copied back."""
+    import torch
+
+    q, r = batch.pair(0)
+    hq = torch.from_numpy(np.ascontiguousarray(q)).pin_memory()
+    hr = torch.from_numpy(np.ascontiguousarray(r)).pin_memory()
+    dq = torch.empty_like(hq, device=dev)
+    dr = torch.empty_like(hr, device=dev)
+    cap = len(q) + len(r) + 1
+    dout = torch.empty(F.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    dcig = torch.empty(cap, dtype=torch.int32, device=dev)
+    hout = torch.empty(F.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    hcig = torch.empty(cap, dtype=torch.int32).pin_memory()
+    times = []
+    for k in range(1 + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dq.copy_(hq, non_blocking=True)
+        dr.copy_(hr, non_blocking=True)
+        rc = ctx.align_long_ptr(params, dq.data_ptr(), len(q), dr.data_ptr(), len(r),
+                                dout.data_ptr(), dcig.data_ptr(), cap, stream=stream.cuda_stream)
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+        hout.copy_(dout, non_blocking=True)
+        n_ops = int(res[0]["cigar_len"])
+        hcig[:n_ops].copy_(dcig[:n_ops], non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= 1:
+            times.append(time.perf_counter() - t0)
+    got = hout.numpy().view(F.RESULT_DTYPE)
+    assert np.array_equal(got, res), "end-to-end long pair disagrees"
+    cells = int(res[0]["cells"])
+    return {"value": cells / (sum(times) / len(times)) / 1e9, "unit": "GCUPS",
+            "h2d_bytes_per_step": len(q) + len(r),
+            "d2h_bytes_per_step": F.RESULT_DTYPE.itemsize + 4 * int(res[0]["cigar_len"])}
+
+
+def plain_per_pair(F, ctx, params, batch, nsample, stream, dev, tb_on):
+    """The plain form: one kernel launch per pair, on a sample of the same pairs,
+    timed beside the batched call on that sample; results must agree."""
+    import torch
+
+    ns = min(nsample, batch.n)
+    sub = batch.subset(np.arange(ns))
+    sdb = F.DeviceBatch(sub, dev)
+    sout, scig = F.alloc_outputs(sdb.n, sdb.cigar_upper, dev)
+
+    def timed(plain):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc = ctx.align_batch_ptr(params, sdb.n, *sdb.ptrs(), sout.data_ptr(),
+                                 scig.data_ptr() if tb_on else None,
+                                 sdb.cigar_upper if tb_on else 0, stream=stream.cuda_stream,
+                                 plain=plain)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+        return a.elapsed_time(b), F.results_to_numpy(sout, sdb.n)
+
+    timed(False)
+    tb_ms, rb = timed(False)
+    tp_ms, rp = timed(True)
+    assert np.array_equal(rb, rp), "plain and batched results differ"
+    scells = int(rb["cells"].sum())
+    return {"pairs": ns, "gcups_plain": scells / (tp_ms * 1e-3) / 1e9,
+            "gcups_batched_same_pairs": scells / (tb_ms * 1e-3) / 1e9,
+            "ms_plain": tp_ms, "ms_batched": tb_ms}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -337,65 +457,25 @@ def main():
 
     line = None
     if rank == 0:
-        # e2e through the host-buffer entry point (pinned host memory)
-        pin = {}
-        for name in ("q_seq", "q_off", "q_len", "r_seq", "r_off", "r_len"):
-            a = np.ascontiguousarray(getattr(batch, name))
-            t = torch.from_numpy(a.view(np.uint8)).pin_memory()
-            pin[name] = (t, a.dtype)
-        hout = torch.empty(db.n * F.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
-        hcig = torch.empty(db.cigar_upper * 4, dtype=torch.uint8).pin_memory()
-        ptr = [pin[n][0].data_ptr() for n in ("q_seq", "q_off", "q_len", "r_seq", "r_off", "r_len")]
-        e2e_t = []
-        for k in range(2 + args.steps):
-            t0 = time.perf_counter()
-            rc = ctx.align_batch_host_ptr(params, db.n, *ptr, hout.data_ptr(), hcig.data_ptr(), db.cigar_upper)
-            if rc != 0:
-                raise F.FiltrError(rc, F.last_error())
-            if k >= 2:
-                e2e_t.append(time.perf_counter() - t0)
-        hres = hout.numpy().view(F.RESULT_DTYPE)
-        assert np.array_equal(hres, res), "host entry point disagrees with the device entry point"
-        total_ops = int(hres["cigar_off"][-1] + hres["cigar_len"][-1])
-        h2d = sum(int(pin[n][0].numel()) for n in pin)
-        d2h = db.n * F.RESULT_DTYPE.itemsize + total_ops * 4
-        e2e = {"value": cells / (sum(e2e_t) / len(e2e_t)) / 1e9, "unit": "GCUPS",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-
-        # plain one-launch-per-pair form on a sample of the same pairs
-        ns = min(args.plain_sample, batch.n)
-        sub = batch.subset(np.arange(ns))
-        sdb = F.DeviceBatch(sub, dev)
-        sout, scig = F.alloc_outputs(sdb.n, sdb.cigar_upper, dev)
-
-        def timed(plain):
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            rc = ctx.align_batch_ptr(params, sdb.n, *sdb.ptrs(), sout.data_ptr(), scig.data_ptr(),
-                                     sdb.cigar_upper, stream=stream.cuda_stream, plain=plain)
-            b.record(stream)
-            torch.cuda.synchronize()
-            if rc != 0:
-                raise F.FiltrError(rc, F.last_error())
-            return a.elapsed_time(b), F.results_to_numpy(sout, sdb.n)
-
-        timed(False)
-        tb_ms, rb = timed(False)
-        tp_ms, rp = timed(True)
-        assert np.array_equal(rb, rp), "plain and batched results differ"
-        scells = int(rb["cells"].sum())
-
+        if is_long:
+            e2e, plain = long_pair_e2e(F, ctx, params, batch, args.steps, res, stream, dev), None
+        else:
+            e2e = host_entry_e2e(F, ctx, params, batch, db, res, cells, args.steps, tb_on)
+            plain = plain_per_pair(F, ctx, params, batch, args.plain_sample, stream, dev, tb_on)
         fwd = statistics.median(fwd_ms)
         peak_ops = max(probe["viaddmax"], probe["int_ops"]) if probe else None
         achieved = cells * OPS_PER_CELL / (fwd * 1e-3) / 1e12
         traffic_per_cell = ncu_traffic()
-        roof = {"bound": "alu", "kernel": "k_full (forward, all waves)", "achieved": achieved,
+        kern = "k_xdrop (antidiagonal sweep)" if wl in ("long-reads-10k", "long-pair-1m") else \
+            "k_full (forward, all waves)"
+        roof = {"bound": "alu", "kernel": kern, "achieved": achieved,
                 "peak": peak_ops / 1e12 if peak_ops else None, "unit": "Tops/s",
                 "frac": (achieved / (peak_ops / 1e12)) if peak_ops else None,
                 "ops_per_cell": OPS_PER_CELL,
                 "forward_ms": fwd, "forward_gcups": cells / (fwd * 1e-3) / 1e9,
-                "traffic": (traffic_per_cell * cells / max(1, 1)) if traffic_per_cell else None,
+                "traffic": (traffic_per_cell * cells) if traffic_per_cell else None,
+                "traffic_unit": "DRAM bytes per step (ncu dram__bytes_read+write per cell x cells)",
+                "algorithmic_bytes": 0.5 * cells,
                 "peak_source": "measured int32 add-max throughput (filtr_probe_int_peak)",
                 "probe": probe}
         line = {
@@ -403,13 +483,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs": batch.n, "cells_per_step": cells,
-                       "mode": "local affine o=11 e=1, seeded 20x20 matrix, traceback+CIGAR",
-                       "lengths": "U[100,1000] both sides", "l2": "flushed between timed steps (512 MB write)",
+            "config": {"workload": wl, "pairs": batch.n, "cells_per_step": cells,
+                       "mode": WORKLOAD_DESC[wl],
+                       "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replica x{world}"},
-            "plain_per_pair": {"pairs": ns, "gcups_plain": scells / (tp_ms * 1e-3) / 1e9,
-                               "gcups_batched_same_pairs": scells / (tb_ms * 1e-3) / 1e9,
-                               "ms_plain": tp_ms, "ms_batched": tb_ms},
+            "plain_per_pair": plain,
             "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms},
             "roofline": roof,
             "e2e": e2e,
@@ -417,9 +495,9 @@ def main():
             "clocks": clocks,
             "wall_s_timed": wall,
         }
-        if not args.no_serve:
+        if not args.no_serve and wl == "protein-sw-100k":
             line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and not is_long:
             line["cpu_baseline"] = cpu_baseline(batch, sc, args.cpu_sample)
         print(json.dumps(line), flush=True)
     if dist:

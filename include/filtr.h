@@ -71,7 +71,8 @@ enum {
   FILTR_ST_DROPPED = 1,     /* X-drop stopped before (M,N) (global) */
   FILTR_ST_UNREACHABLE = 2, /* literal band excludes (M,N) (global) */
   FILTR_ST_EMPTY = 3,       /* local best score is 0: empty alignment */
-  FILTR_ST_TOO_WIDE = 4     /* X-drop region wider than the kernel window (see filtr_align_batch) */
+  FILTR_ST_TOO_WIDE = 4,    /* X-drop region wider than the kernel window (see filtr_align_batch) */
+  FILTR_ST_TIMEOUT = 5      /* a bounded wait of the intra-pair kernel ran out (no result) */
 };
 
 typedef struct {
@@ -143,7 +144,7 @@ filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint
  * out in pair order; if the total exceeds cigar_cap the call returns
  * FILTR_ERR_CIGAR_CAP after the stream completes and each result carries its
  * length.  Band and X-drop pairs whose live region outgrows the widest kernel
- * window (16384 diagonals) get FILTR_ST_TOO_WIDE.  Returns FILTR_ERR_INVALID
+ * window (8192 cells on one antidiagonal) get FILTR_ST_TOO_WIDE.  Returns FILTR_ERR_INVALID
  * before any launch for bad params or codes. */
 filtr_status filtr_align_batch(filtr_ctx *ctx, const filtr_params *params, uint32_t n_pairs,
                                const uint8_t *q_seq, const uint64_t *q_off, const uint32_t *q_len,

@@ -243,8 +243,8 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     set_error("scores could exceed 2^28 for these lengths and penalties");
     return FILTR_ERR_UNSUPPORTED;
   }
-  const int R_max = 16;
-  const int blocks_per_sm = std::max(ctx->full_blocks_per_sm(8, sp), ctx->full_blocks_per_sm(16, sp));
+  int blocks_per_sm = 1;
+  for (int R : {8, 16, 24, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->full_blocks_per_sm(R, sp));
   const int grid_max = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * blocks_per_sm,
                                                           ((int64_t)n + FULL_WARPS - 1) / FULL_WARPS);
   const uint32_t strip_stride = (uint32_t)(max_n + 2);
@@ -270,7 +270,6 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     return FILTR_ERR_NOMEM;
   }
   const uint64_t tb_budget = (ctx->ws_bytes - c.used) / 4;
-  (void)R_max;
 
   Plan P;
   PlanInput in{&sp, n, h_ql, h_rl, tb_budget, 8, ctx->xdrop_warps0};
@@ -353,12 +352,30 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       ++launches;
       return ce == cudaSuccess;
     }
+    if (plain) {
+      for (uint32_t t = 0; t < cnt; ++t) {
+        fa.order = d_ord + t;
+        fa.n_order = 1;
+        fa.counter = d_counters + (counter_i++ % n_counters);
+        ce = launch_xdrop(fa, W, 1, d_ovf, d_novf, st);
+        ++launches;
+        if (ce != cudaSuccess) return false;
+        if (sp.traceback) {  // a pair that outgrew its window is skipped by the walk
+          wa.order = fa.order;
+          wa.n_order = 1;
+          ce = launch_walk(wa, st);
+          ++launches;
+          if (ce != cudaSuccess) return false;
+        }
+      }
+      return true;
+    }
     fa.order = d_ord;
     fa.n_order = cnt;
     fa.counter = d_counters + (counter_i++ % n_counters);
     const int ppc = xd_pairs_per_cta(W);
     const int bps = std::max(1, xd_max_blocks_per_sm(W, sp));
-    int grid = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + ppc - 1) / ppc);
+    int grid = (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + ppc - 1) / ppc);
     ce = launch_xdrop(fa, W, std::max(grid, 1), d_ovf, d_novf, st);
     ++launches;
     return ce == cudaSuccess;
@@ -406,7 +423,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     if (!walk(d_order + w.walk_begin, w.walk_end - w.walk_begin)) return cuda_fail(ce, "walk launch");
     pending.insert(pending.end(), ovf.begin(), ovf.end());
   }
-  for (int W = ctx->xdrop_warps0 < 4 ? 4 : 16; W <= 16 && !pending.empty(); W *= 4) {
+  static const int kWider[] = {4, 16, 32};
+  for (int wi = 0; wi < 3 && !pending.empty(); ++wi) {
+    const int W = kWider[wi];
+    if (W <= ctx->xdrop_warps0) continue;
     // rerun the pairs that outgrew their window, in sub-waves that fit the budget
     std::vector<uint32_t> todo;
     todo.swap(pending);

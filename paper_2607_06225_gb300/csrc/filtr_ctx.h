@@ -57,6 +57,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n, 
                               bool plain, const uint32_t *host_ql, const uint32_t *host_rl,
                               bool prevalidated);
 filtr_status ctx_new(int device, size_t workspace_bytes, Ctx **out);
+// one long full-matrix / banded pair across the grid, not waited for
+filtr_status long_pair_async(Ctx *c, const ScoreParams &sp, const filtr_params *params,
+                             const uint8_t *q, uint32_t M, const uint8_t *r, uint32_t N,
+                             filtr_result *out, uint32_t *cigar, uint64_t cap, cudaStream_t st);
 void ctx_delete(Ctx *c);
 
 }  // namespace filtr

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_long(const LongArgs a) {
   P.r = a.r;
   P.lo = a.lo;
   P.hi = a.hi;
+  P.one = (a.sp.alphabet > 0) ? 1 : 0;  // 1, unknown to the compiler
   P.o = a.sp.o;
   P.e = a.sp.e;
   P.A = A;
@@ -175,6 +176,13 @@ __global__ void k_long_finish(const LongArgs a, int nw, uint64_t cells, filtr_re
   filtr_result res{};
   res.cells = cells;
   const bool local = a.sp.mode == FILTR_LOCAL;
+  if (*(volatile int *)a.err) {
+    res.status = FILTR_ST_TIMEOUT;
+    *out = res;
+    FwdOut f{0, 0, 0, FILTR_ST_TIMEOUT};
+    *fwd = f;
+    return;
+  }
   if (local) {
     if (b.v > 0) {
       res.score = b.v;

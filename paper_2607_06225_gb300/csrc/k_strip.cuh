@@ -46,6 +46,20 @@ template <>
 struct ProfWord<16> {
   using T = uint4;
 };
+struct alignas(8) Prof24 {
+  uint2 a, b, c;
+};
+template <>
+struct ProfWord<24> {
+  using T = Prof24;
+};
+struct alignas(16) Prof32 {
+  uint4 a, b;
+};
+template <>
+struct ProfWord<32> {
+  using T = Prof32;
+};
 
 // Signed byte B of a word, sign-extended by one PTX byte permute: selector
 // nibble B copies byte B, nibbles with the msb set replicate its sign bit.
@@ -70,8 +84,21 @@ __device__ __forceinline__ void unpack_scores(const typename ProfWord<R>::T &w, 
   }
 }
 
+// a + b * one with `one` == 1 held in a register the compiler cannot fold:
+// the add issues as an integer multiply-add on the FMA pipe, leaving the ALU
+// pipe to the max, funnel-shift and byte-permute work of the cell update (the
+// two pipes issue in parallel; the kernel is otherwise ALU-pipe bound).
+__device__ __forceinline__ int fadd(int a, int b, int one) {
+  int r;
+  asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(r) : "r"(b), "r"(one), "r"(a));
+  return r;
+}
+// a - b the same way (mone == -1)
+__device__ __forceinline__ int fsub(int a, int b, int mone) { return fadd(a, b, mone); }
+
 // Per-pair constants of a strip pass.
 struct StripPair {
+  int one;           // 1, computed at run time (see fadd)
   int M, N;
   const uint8_t *q, *r;
   int lo, hi;        // band on d = j - i (unbanded: -M-1, N+1)
@@ -104,7 +131,8 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
   constexpr int WPS = R / 8;
   using PW = typename ProfWord<R>::T;
   const int lane = threadIdx.x & 31;
-  const int M = P.M, lo = P.lo, hi = P.hi, o = P.o, e = P.e, oe = P.o + P.e;
+  const int M = P.M, lo = P.lo, hi = P.hi, o = P.o, e = P.e;
+  const int one = P.one, mone = -P.one, me = -P.e, moe = -(P.o + P.e);
   const int row0 = s * HS;
   const int top = row0 + lane * R + 1;
   const int nstrips = (M + HS - 1) / HS;
@@ -196,24 +224,26 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int Hl = Hc[k];
-        const int D = Hdg + sc[k];
+        const int D = fadd(Hdg, sc[k], one);
         int E, F, H;
         if (AFFINE) {
-          const int Hol = Hl - oe, Eext = Ec[k] - e;
-          const int Hou = Hup - oe, Fext = Fup - e;
+          const int Hol = fadd(Hl, moe, one), Eext = fadd(Ec[k], me, one);
+          const int Hou = fadd(Hup, moe, one), Fext = fadd(Fup, me, one);
           E = max(Hol, Eext);
           F = max(Hou, Fext);
           const int DE = max(D, E);
           H = max(DE, F);
           if (LOCAL) H = max(H, 0);
-          if (TB) tb_push4(tbw[k >> 3], D - E, DE - F, Hol - Eext, Hou - Fext);
+          if (TB)
+            tb_push4(tbw[k >> 3], fsub(D, E, mone), fsub(DE, F, mone), fsub(Hol, Eext, mone),
+                     fsub(Hou, Fext, mone));
         } else {
-          E = Hl - e;
-          F = Hup - e;
+          E = fadd(Hl, me, one);
+          F = fadd(Hup, me, one);
           const int DE = max(D, E);
           H = max(DE, F);
           if (LOCAL) H = max(H, 0);
-          if (TB) tb_push4(tbw[k >> 3], D - E, DE - F, 0, 0);
+          if (TB) tb_push4(tbw[k >> 3], fsub(D, E, mone), fsub(DE, F, mone), 0, 0);
         }
         if (BAND) {
           const int dd = j - (top + k);

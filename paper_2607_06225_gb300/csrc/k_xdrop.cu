@@ -311,7 +311,16 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       uint32_t nibs = 0;
       int tmax = INT_MIN, tlo = INT_MAX, thi = INT_MIN, tbs = -1;
       const int doff = delta + dprev - 1;
-      if (delta == 1) {
+      // a warp whose slots all lie outside the candidate range only clears its state
+      const bool wact = __any_sync(FULLMASK, vB >= 0 && vA < XS);
+      if (!wact) {
+#pragma unroll
+        for (int s = 0; s < XS; ++s) {
+          Hn[s] = NEG;
+          En[s] = NEG;
+          Fn[s] = NEG;
+        }
+      } else if (delta == 1) {
         if (doff == 0)
           xd_cells<W, LOCAL, AFFINE, TB, 1, 0>(H1, E1, F1, H2, Hn, En, Fn, pv, nx, qw, rw, s_sub, A,
                                               o, e, vA, vB, thr, nibs, tmax, tlo, thi, tbs);
@@ -557,6 +566,7 @@ int xd_max_blocks_per_sm(int W, const ScoreParams &sp) {
     case 4: return occ_w<4>(sp);
     case 8: return occ_w<8>(sp);
     case 16: return occ_w<16>(sp);
+    case 32: return occ_w<32>(sp);
     default: return 0;
   }
 }
@@ -569,6 +579,7 @@ cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
     case 4: return dispatch_w<4>(a, grid, overflow, n_overflow, s);
     case 8: return dispatch_w<8>(a, grid, overflow, n_overflow, s);
     case 16: return dispatch_w<16>(a, grid, overflow, n_overflow, s);
+    case 32: return dispatch_w<32>(a, grid, overflow, n_overflow, s);
     default: return cudaErrorInvalidValue;
   }
 }

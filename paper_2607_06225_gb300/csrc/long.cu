@@ -51,7 +51,8 @@ filtr_status validate_seq(Ctx *c, const uint8_t *q, uint32_t M, const uint8_t *r
 // the cooperative strip kernel; withhold != 0 is the timeout test
 filtr_status run_long(Ctx *c, const ScoreParams &sp, const filtr_params *params, const uint8_t *q,
                       uint32_t M, const uint8_t *r, uint32_t N, filtr_result *out, uint32_t *cigar,
-                      uint64_t cap, cudaStream_t st, int withhold, unsigned long long timeout_ns) {
+                      uint64_t cap, cudaStream_t st, int withhold, unsigned long long timeout_ns,
+                      bool sync = true) {
   constexpr int R = 16, HS = 32 * R;
   int64_t lo = -(int64_t)M - 1, hi = (int64_t)N + 1;
   if (sp.use_band) {
@@ -170,6 +171,10 @@ filtr_status run_long(Ctx *c, const ScoreParams &sp, const filtr_params *params,
     launches += 3;
     if (e != cudaSuccess) return cuda_fail(e, "long-pair traceback");
   }
+  c->last_launches = launches;
+  c->last_cells_estimate = band_cells(M, N, sp);
+  c->last_waves = 1;
+  if (!sync) return FILTR_OK;  // the result's status reports a timeout
   // the wait flag (and the CIGAR length) decide the status: synchronise once
   int *h_err = reinterpret_cast<int *>(h + 1024);
   filtr_result *h_res = reinterpret_cast<filtr_result *>(h + 1088);
@@ -177,9 +182,6 @@ filtr_status run_long(Ctx *c, const ScoreParams &sp, const filtr_params *params,
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_res, out, sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "long-pair completion");
-  c->last_launches = launches;
-  c->last_cells_estimate = cells;
-  c->last_waves = 1;
   if (*h_err) {
     set_error("a strip wait ran out after %llu ns", (unsigned long long)timeout_ns);
     return FILTR_ERR_TIMEOUT;
@@ -199,7 +201,9 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   (void)params;
   const int64_t K = (int64_t)M + N;
   const int64_t nseg = K / C + 1;
-  for (int W = 4; W <= 16; W *= 4) {
+  static const int kWidths[] = {4, 16, 32};
+  for (int wi = 0; wi < 3; ++wi) {
+    const int W = kWidths[wi];
     const int wpk = xd_words_per_k(W, 8);
     Carve cv{c->ws, c->ws_bytes};
     int32_t *ck_buf = cv.take<int32_t>((size_t)(K / C + 1) * xd_ckpt_ints(W));
@@ -262,7 +266,7 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward sweep");
     const FwdOut f = *hf;
-    if (f.status == FILTR_ST_TOO_WIDE && W < 16) continue;
+    if (f.status == FILTR_ST_TOO_WIDE && W < 32) continue;
     if (!sp.traceback || (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED)) return FILTR_OK;
     // backward: one segment at a time, from the end cell's antidiagonal down to 0
     WalkState w0{f.end_i, f.end_j, f.score, 0, 0, -1, 0, 0};
@@ -323,6 +327,22 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
 }
 
 }  // namespace
+
+// One long full-matrix / banded pair on the whole GPU without waiting for it
+// (the serving loop's path for large requests).
+filtr_status long_pair_async(Ctx *c, const ScoreParams &sp, const filtr_params *params,
+                             const uint8_t *q, uint32_t M, const uint8_t *r, uint32_t N,
+                             filtr_result *out, uint32_t *cigar, uint64_t cap, cudaStream_t st) {
+  if (c->done_ev) cudaEventSynchronize(c->done_ev);
+  c->ev_used = 0;
+  c->spans.clear();
+  const filtr_status rc =
+      run_long(c, sp, params, q, M, r, N, out, cigar, cap, st, 0, LONG_TIMEOUT_NS, false);
+  if (!c->done_ev) cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming);
+  if (c->done_ev) cudaEventRecord(c->done_ev, st);
+  return rc;
+}
+
 }  // namespace filtr
 
 using namespace filtr;
@@ -353,7 +373,7 @@ filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const 
   if (rc != FILTR_OK) return rc;
   if (sp.use_xdrop && M && N &&
       (c->ckpt_interval > 0 ||
-       4 * xd_tb_words(M, N, 4, 8) > c->ws_bytes / 2)) {  // the whole traceback would not fit
+       4 * xd_tb_words(M, N, 32, 8) > c->ws_bytes / 2)) {  // the widest traceback would not fit
     const int C = c->ckpt_interval > 0 ? c->ckpt_interval : 4096;
     rc = run_xdrop_ckpt(c, sp, params, q, M, r, N, out, cigar, cigar_cap, st, C);
     if (!c->done_ev) cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming);

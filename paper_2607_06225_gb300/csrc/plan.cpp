@@ -15,7 +15,22 @@
 
 namespace filtr {
 
-int full_rows_per_lane(uint32_t M) { return M <= 256 ? 8 : 16; }
+// Rows per lane: the tile height 32R whose padded work, strips x (N + 31 steps)
+// x (R + 2) (two cell-equivalents of per-step overhead), is smallest.
+int full_rows_per_lane(uint32_t M, uint32_t N) {
+  static const int Rs[4] = {32, 24, 16, 8};
+  int best = 8;
+  uint64_t best_cost = ~0ull;
+  for (int R : Rs) {
+    const uint64_t strips = (M + 32u * R - 1) / (32u * R);
+    const uint64_t cost = strips * ((uint64_t)N + 31) * (uint64_t)(R + 2);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = R;
+    }
+  }
+  return best;
+}
 
 uint64_t full_tb_words(uint32_t M, uint32_t N, int R, const ScoreParams &sp) {
   const int64_t HS = 32 * R;
@@ -78,8 +93,8 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->cells_estimate = 0;
 
   // per pair: kernel shape key, cost bucket, traceback words (flat arrays)
-  // shape keys: 0..2 tiled kernel with R = 16, 8 (ordered so wide shapes launch
-  // first); 3 the X-drop kernel
+  // shape keys: 0..3 the tiled kernel with R = 32, 24, 16, 8 (wide tiles
+  // launch first); 4 the X-drop kernel
   std::vector<uint8_t> bucket(n), shape(n);
   std::vector<uint64_t> words(n);
   std::vector<uint32_t> cnt(64, 0);
@@ -105,11 +120,11 @@ bool make_plan(const PlanInput &in, Plan *P) {
     P->cells_estimate += cost;
     uint64_t w = 0;
     if (sp.use_xdrop) {
-      shape[p] = 3;
+      shape[p] = 4;
       if (sp.traceback) w = xd_tb_words(M, N, xw, in.xdrop_slots);
     } else {
-      const int R = full_rows_per_lane(M);
-      shape[p] = (R == 16) ? 0 : 1;
+      const int R = full_rows_per_lane(M, N);
+      shape[p] = (uint8_t)(R == 32 ? 0 : R == 24 ? 1 : R == 16 ? 2 : 3);
       if (sp.traceback) w = full_tb_words(M, N, R, sp);
     }
     if (sp.traceback && w > in.tb_budget_words) {
@@ -131,13 +146,13 @@ bool make_plan(const PlanInput &in, Plan *P) {
     if (shape[p] != 255) sorted[start[bucket[p]]++] = p;
 
   // waves: cut the cost order where the traceback budget is used up, then
-  // group each wave by kernel shape (stable counting sort over 4 keys)
+  // group each wave by kernel shape (stable counting sort over 5 keys)
   const uint64_t budget = sp.traceback ? in.tb_budget_words : ~0ull;
   size_t i = 0;
   while (i < sorted.size()) {
     size_t j = i;
     uint64_t used = 0;
-    uint32_t kc[4] = {0, 0, 0, 0};
+    uint32_t kc[5] = {0, 0, 0, 0, 0};
     while (j < sorted.size() && used + words[sorted[j]] <= budget) {
       used += words[sorted[j]];
       kc[shape[sorted[j]]]++;
@@ -146,20 +161,21 @@ bool make_plan(const PlanInput &in, Plan *P) {
     Wave w;
     w.tb_words = used;
     const uint32_t wave_begin = (uint32_t)P->order.size();
-    uint32_t ks[4];
+    uint32_t ks[5];
     ks[0] = wave_begin;
-    for (int k = 1; k < 4; ++k) ks[k] = ks[k - 1] + kc[k - 1];
+    for (int k = 1; k < 5; ++k) ks[k] = ks[k - 1] + kc[k - 1];
     P->order.resize(wave_begin + (j - i));
-    uint32_t kpos[4] = {ks[0], ks[1], ks[2], ks[3]};
+    uint32_t kpos[5] = {ks[0], ks[1], ks[2], ks[3], ks[4]};
     for (size_t t = i; t < j; ++t) P->order[kpos[shape[sorted[t]]]++] = sorted[t];
     // traceback offsets in wave order, per-pair layout, groups
     uint64_t off = 0;
-    for (int k = 0; k < 4; ++k) {
+    static const uint8_t kR[4] = {32, 24, 16, 8};
+    for (int k = 0; k < 5; ++k) {
       if (!kc[k]) continue;
       Group g;
-      g.family = (k == 3) ? FAM_XDROP : FAM_FULL;
-      g.R = (k == 3) ? (uint8_t)in.xdrop_slots : (k == 0 ? 16 : 8);
-      g.warps = (k == 3) ? (uint8_t)xw : 1;
+      g.family = (k == 4) ? FAM_XDROP : FAM_FULL;
+      g.R = (k == 4) ? (uint8_t)in.xdrop_slots : kR[k];
+      g.warps = (k == 4) ? (uint8_t)xw : 1;
       g.begin = ks[k];
       g.end = ks[k] + kc[k];
       for (uint32_t t = g.begin; t < g.end; ++t) {

@@ -42,8 +42,8 @@ struct PlanInput {
   int xdrop_warps;                // first window width of X-drop pairs (warps)
 };
 
-// Rows per lane of the tiled kernel for a query of length M.
-int full_rows_per_lane(uint32_t M);
+// Rows per lane of the tiled kernel for an M x N pair.
+int full_rows_per_lane(uint32_t M, uint32_t N);
 // Traceback words of one pair in the tiled kernel.
 uint64_t full_tb_words(uint32_t M, uint32_t N, int R, const ScoreParams &sp);
 // Cell count of one pair under a static band (or the full matrix).

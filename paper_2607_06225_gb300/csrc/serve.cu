@@ -41,6 +41,7 @@ struct Req {
   int8_t subst[MAX_ALPHA * MAX_ALPHA];
   std::vector<uint8_t> q, r;
   uint64_t bytes = 0;   // lane memory this request needs
+  uint64_t io = 0;      // of which in the lane's I/O buffer
   uint64_t cells = 0;
   bool big = false;     // cost class
   uint64_t t_submit = 0, t_launch = 0, t_done = 0;
@@ -78,6 +79,7 @@ struct Server {
   uint64_t next_ticket = 1;
   bool stop = false;
   size_t lane_capacity = 0;   // bytes a micro-batch may use on one lane
+  size_t lane_io = 0;         // of which in the lane's I/O buffer
   size_t max_queue = 1 << 20;
   filtr_status fatal = FILTR_OK;
   std::string fatal_msg;
@@ -94,7 +96,7 @@ uint64_t request_bytes(const ScoreParams &sp, uint32_t M, uint32_t N) {
     if (sp.use_xdrop)
       b += 4 * xd_tb_words(M, N, 4, 8);  // room for one widened rerun
     else if (M && N)
-      b += 4 * full_tb_words(M, N, full_rows_per_lane(M), sp);
+      b += 4 * full_tb_words(M, N, full_rows_per_lane(M, N), sp);
   }
   b += 64ull * 1024 + 16ull * (N + 2) * 64;  // per-call fixed parts and strip buffers, generous
   return b;
@@ -159,8 +161,16 @@ filtr_status launch_batch(Server *S, Lane &L) {
              reinterpret_cast<uint32_t *>(L.d_io + o_ql), reinterpret_cast<uint32_t *>(L.d_io + o_rl)};
   filtr_result *dres = reinterpret_cast<filtr_result *>(L.d_io + o_res);
   uint32_t *dcig = reinterpret_cast<uint32_t *>(L.d_io + o_cig);
-  filtr_status rc = align_batch_impl(L.ctx, &B[0]->p, n, b, dres, B[0]->sp.traceback ? dcig : nullptr,
-                                     B[0]->sp.traceback ? ops + 1 : 0, st, false, ql, rl, true);
+  filtr_status rc;
+  if (n == 1 && B[0]->big && !B[0]->sp.use_xdrop && B[0]->q.size() > 512 && !B[0]->r.empty()) {
+    // a large request: every SM on it (intra-pair strips) instead of one warp
+    rc = long_pair_async(L.ctx, B[0]->sp, &B[0]->p, b.q_seq, (uint32_t)B[0]->q.size(), b.r_seq,
+                         (uint32_t)B[0]->r.size(), dres, B[0]->sp.traceback ? dcig : nullptr,
+                         B[0]->sp.traceback ? ops + 1 : 0, st);
+  } else {
+    rc = align_batch_impl(L.ctx, &B[0]->p, n, b, dres, B[0]->sp.traceback ? dcig : nullptr,
+                          B[0]->sp.traceback ? ops + 1 : 0, st, false, ql, rl, true);
+  }
   if (rc != FILTR_OK) return rc;
   e = cudaMemcpyAsync(h + o_res, L.d_io + o_res, sizeof(filtr_result) * n, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && B[0]->sp.traceback)
@@ -223,13 +233,16 @@ void worker_main(Server *S) {
     for (Lane &L : S->lanes) {
       if (L.busy || S->queue.empty() || S->stop) continue;
       Req *head = S->queue.front();
-      uint64_t used = 0;
+      uint64_t used = 0, used_io = 0;
       std::vector<Req *> pick;
       for (auto it = S->queue.begin(); it != S->queue.end();) {
         Req *r = *it;
-        if (same_params(head, r) && (pick.empty() || used + r->bytes <= S->lane_capacity) &&
+        if (same_params(head, r) &&
+            (pick.empty() ||
+             (used + r->bytes <= S->lane_capacity && used_io + r->io <= S->lane_io)) &&
             pick.size() < 65536) {
           used += r->bytes;
+          used_io += r->io;
           pick.push_back(r);
           it = S->queue.erase(it);
           if (r->big) break;  // big requests run alone
@@ -312,15 +325,18 @@ filtr_status filtr_serve_create(filtr_ctx *ctx, size_t mem_budget, uint32_t max_
   if (!S) return FILTR_ERR_NOMEM;
   S->parent = parent;
   S->budget = mem_budget;
+  // per lane: a small I/O buffer (codes, results, CIGARs) and a workspace for
+  // the traceback; one request may use most of a lane, a micro-batch as much
   const size_t per_lane = mem_budget / max_inflight;
-  const size_t io = std::max<size_t>(per_lane / 4, 1 << 20);
-  const size_t ws = per_lane - std::min(per_lane / 4, per_lane / 2);
-  if (ws < (64u << 20)) {
+  const size_t io = std::max<size_t>(per_lane / 16, 16u << 20);
+  if (per_lane < io + (64u << 20)) {
     delete S;
     set_error("serve_create: budget too small (%zu bytes per lane)", per_lane);
     return FILTR_ERR_INVALID;
   }
-  S->lane_capacity = std::min(io, ws) / 2;
+  const size_t ws = per_lane - io;
+  S->lane_capacity = ws / 10 * 8;
+  S->lane_io = io - 4096;
   S->lanes.resize(max_inflight);
   cudaSetDevice(parent->device);
   for (Lane &L : S->lanes) {
@@ -380,10 +396,12 @@ filtr_status filtr_serve_submit(filtr_server *srv, const filtr_params *params, c
   R->q.assign(q, q + M);
   R->r.assign(r, r + N);
   R->bytes = request_bytes(R->sp, M, N);
+  R->io = 256 * 8 + 2ull * (M + N) + 4ull * (M + N + 1) + 64;
   R->cells = band_cells(M, N, R->sp);
   R->big = R->cells > BIG_CELLS;
   std::lock_guard<std::mutex> lk(S->mu);
-  if (R->bytes > S->lane_capacity || S->queue.size() >= S->max_queue || S->stop) {
+  if (R->bytes > S->lane_capacity || R->io > S->lane_io || S->queue.size() >= S->max_queue ||
+      S->stop) {
     delete R;
     set_error("serve_submit: request exceeds the lane budget or the queue is full");
     return FILTR_ERR_BUSY;

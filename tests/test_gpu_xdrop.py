@@ -85,10 +85,11 @@ def test_protein_xdrop(F, ctx):
 
 def test_window_overflow_rerun(F, ctx):
     """X = infinity keeps every cell: the live region grows to the full
-    antidiagonal, outgrows the 256- and 1024-slot windows and is rerun."""
+    antidiagonal, outgrows the 256-, 1024- and 4096-slot windows and is rerun
+    with wider groups."""
     rng = np.random.default_rng(5)
-    qs = [rng.integers(0, 4, size=M).astype(np.uint8) for M in (300, 1500, 2500)]
-    rs = [rng.integers(0, 4, size=N).astype(np.uint8) for N in (280, 1400, 2600)]
+    qs = [rng.integers(0, 4, size=M).astype(np.uint8) for M in (300, 1500, 2500, 5200)]
+    rs = [rng.integers(0, 4, size=N).astype(np.uint8) for N in (280, 1400, 2600, 5000)]
     b = synth.pack(qs, rs, 4, DNA_S)
     res = run_both(F, ctx, b, dict(mode="global", affine=True, gap_open=4, gap_extend=2,
                                    xdrop=oracle.INF, traceback=True))
@@ -98,11 +99,11 @@ def test_window_overflow_rerun(F, ctx):
 
 
 def test_too_wide_reported(F, ctx):
-    """A live region wider than the widest window (4096 cells) is reported, not
+    """A live region wider than the widest window (8192 cells) is reported, not
     computed wrongly."""
     rng = np.random.default_rng(6)
-    q = rng.integers(0, 4, size=5000).astype(np.uint8)
-    r = rng.integers(0, 4, size=5000).astype(np.uint8)
+    q = rng.integers(0, 4, size=9000).astype(np.uint8)
+    r = rng.integers(0, 4, size=9000).astype(np.uint8)
     b = synth.pack([q], [r], 4, DNA_S)
     params = F.make_params(DNA_S, mode="global", gap_open=4, gap_extend=2, xdrop=2**31 - 1,
                            traceback=False)
@@ -116,3 +117,18 @@ def test_long_reads_sampled(F, ctx):
     checked against the oracle."""
     b = synth.long_reads(n=300, lmin=2000, lmax=6000, seed=3)
     run_both(F, ctx, b, dict(b.scoring))
+
+
+def test_plain_equals_batched_xdrop(F, ctx):
+    """One launch (and one walk) per pair gives the batched call's results,
+    including pairs that outgrow the one-warp window and are rerun wider."""
+    b = synth.long_reads(n=12, lmin=1500, lmax=3000, seed=13)
+    params = F.make_params(b.subst, **b.scoring)
+    r1, c1, rc1 = F.align_batch(ctx, params, b)
+    r2, c2, rc2 = F.align_batch(ctx, params, b, plain=True)
+    assert rc1 == 0 and rc2 == 0, F.last_error()
+    assert np.array_equal(r1, r2)
+    used = int((r1["cigar_off"] + r1["cigar_len"]).max())
+    assert np.array_equal(c1[:used], c2[:used])
+    ores, oops, ooff = oracle_batch(b, dict(b.scoring))
+    compare(b, dict(b.scoring), r1, c1, ores, oops, ooff, label="plain")
