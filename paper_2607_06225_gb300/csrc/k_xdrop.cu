@@ -140,10 +140,14 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       __syncthreads();
   };
 
+  bool first_item = true;
   for (;;) {
     // ---- next pair --------------------------------------------------------------
     uint32_t t0 = 0;
-    if (W == 1) {
+    if (a.ck) {  // checkpointed sweep: one pair, taken once by group 0
+      t0 = (first_item && grp == 0) ? 0u : a.n_order;
+      first_item = false;
+    } else if (W == 1) {
       if (lane == 0) t0 = atomicAdd(a.counter, 1u);
       t0 = __shfl_sync(FULLMASK, t0, 0);
     } else {
@@ -163,6 +167,15 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
 
     const XdCkpt *ck = a.ck;
     const int ckmode = ck ? ck->mode : 0;
+    const int seg = ck ? ck->k_start / ck->C : 0;
+    if (ckmode == 3) {
+      // another launch did this segment, the sweep has finished, or the state
+      // to resume does not fit this window (every thread reads the same words)
+      bool skip = ck->flags[0] != 0 || ck->flags[1 + seg] != 0;
+      if (!skip && ck->k_start > 0)
+        skip = ck->buf[(int64_t)seg * xd_ckpt_stride() + XCK_USED] > WIN;
+      if (skip) break;
+    }
     uint32_t *tbp = nullptr;
     int32_t *ckp = nullptr;
     if (TB) {
@@ -202,27 +215,38 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     uint32_t qw[2] = {0, 0}, rw[2] = {0, 0};
     if (TB && tid == 0 && ckmode != 2) ckp[0] = 0;
     int k_first = 1, k_last = M + N;
-    if (ckmode == 2) {
+    if (ckmode >= 2) {
       // resume from the checkpoint of antidiagonal k_start
       k_first = ck->k_start + 1;
       k_last = min(ck->k_end, M + N);
       if (ck->k_start > 0) {
-        const int32_t *rec = ck->buf + (int64_t)(ck->k_start / ck->C) * xd_ckpt_ints(W);
-        c = rec[0];
-        dprev = rec[1];
-        best = rec[2];
-        lo = rec[3];
-        hi = rec[4];
-        const int32_t *mine = rec + 8 + tid * (4 * XS);
+        const int32_t *rec = ck->buf + (int64_t)seg * xd_ckpt_stride();
+        c = rec[XCK_ORIGIN];
+        dprev = rec[XCK_DPREV];
+        best = rec[XCK_BEST];
+        lo = rec[XCK_LO];
+        hi = rec[XCK_HI];
+        const int wwin = rec[XCK_WIN];  // slots beyond the writer's window are NEG
+        const int32_t *mine = rec + XCK_HDR + tid * (4 * XS);
 #pragma unroll
         for (int s = 0; s < XS; ++s) {
-          H1[s] = mine[s];
-          E1[s] = mine[XS + s];
-          F1[s] = mine[2 * XS + s];
-          H2[s] = mine[3 * XS + s];
+          const bool in = tid * XS + s < wwin;
+          H1[s] = in ? mine[s] : NEG;
+          E1[s] = in ? mine[XS + s] : NEG;
+          F1[s] = in ? mine[2 * XS + s] : NEG;
+          H2[s] = in ? mine[3 * XS + s] : NEG;
+        }
+        if (ckmode == 3) {  // the best cell and the cell count so far
+          if (tid == 0) {
+            bv = rec[XCK_BV];
+            bi = rec[XCK_BI];
+            bj = rec[XCK_BJ];
+          }
+          cells = (uint64_t)(uint32_t)rec[XCK_CELLS_LO] | ((uint64_t)(uint32_t)rec[XCK_CELLS_HI] << 32);
         }
       }
     }
+    bool ended = false;  // the sweep stopped (empty antidiagonal or k = M + N)
     if (W > 1) {
       const int b0 = (k_first - 1) & 1;
       if (lane == 0) sh.first[b0][warp] = Edge{H1[0], E1[0], F1[0], H2[0]};
@@ -239,7 +263,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       // parity of k; d = 2j - k
       const int jA = max(max(0, k - M), (k + dl + 1) >> 1);  // ceil((k+dl)/2)
       const int jB = min(min(N, k), (k + dh) >> 1);           // floor((k+dh)/2)
-      if (jA > jB) break;  // empty domain: nothing alive on k
+      if (jA > jB) {  // empty domain: nothing alive on k
+        ended = true;
+        break;
+      }
       const int cn = min(jA, c + 1);
       const int delta = cn - c;
       if (jB - cn + 1 > WIN) {
@@ -397,35 +424,17 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       dprev = delta;
       if (glo == INT_MAX) {  // nothing alive on k: the sweep ends here
         if (k == M + N) corner = false;
+        ended = true;
         break;
       }
       best = gmax;
       lo = 2 * (cn + glo) - k;
       hi = 2 * (cn + ghi) - k;
       if (k == M + N) corner = true;
-      if (ckmode == 1 && (k % ck->C) == 0) {
-        // checkpoint: window state after antidiagonal k
-        int32_t *rec = ck->buf + (int64_t)(k / ck->C) * xd_ckpt_ints(W);
-        if (tid == 0) {
-          rec[0] = c;
-          rec[1] = dprev;
-          rec[2] = best;
-          rec[3] = lo;
-          rec[4] = hi;
-          rec[5] = 1;
-        }
-        int32_t *mine = rec + 8 + tid * (4 * XS);
-#pragma unroll
-        for (int s = 0; s < XS; ++s) {
-          mine[s] = H1[s];
-          mine[XS + s] = E1[s];
-          mine[2 * XS + s] = F1[s];
-          mine[3 * XS + s] = H2[s];
-        }
-      }
     }
-    const int last_k = (k > M + N) ? M + N : k;
-    (void)last_k;
+    if (k > k_last && k_last == M + N) ended = true;
+    // a window too narrow for this segment leaves it to the next, wider launch
+    if (ckmode == 3 && status == FILTR_ST_TOO_WIDE && W < XD_MAX_WARPS) break;
 
     // ---- result -------------------------------------------------------------------
     // group-wide best cell (largest H, then smallest i, then smallest j)
@@ -472,7 +481,51 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       }
       cornerH = ch;
     }
+    if (ckmode == 3 && !ended && status == FILTR_ST_OK) {
+      // segment done, sweep not finished: store the window state after k_end
+      int32_t *rec = ck->buf + (int64_t)(ck->k_end / ck->C) * xd_ckpt_stride();
+      int used = 0;  // one past the last slot holding a value other than NEG
+#pragma unroll
+      for (int s = 0; s < XS; ++s)
+        if (H1[s] != NEG || E1[s] != NEG || F1[s] != NEG || H2[s] != NEG) used = tid * XS + s + 1;
+      used = __reduce_max_sync(FULLMASK, used);
+      if (W > 1) {
+        __syncthreads();
+        if (lane == 0) sh.red[0][warp][0] = used;
+        __syncthreads();
+        for (int w = 0; w < W; ++w) used = max(used, sh.red[0][w][0]);
+      }
+      int32_t *mine = rec + XCK_HDR + tid * (4 * XS);
+#pragma unroll
+      for (int s = 0; s < XS; ++s) {
+        mine[s] = H1[s];
+        mine[XS + s] = E1[s];
+        mine[2 * XS + s] = F1[s];
+        mine[3 * XS + s] = H2[s];
+      }
+      if (tid == 0) {
+        rec[XCK_ORIGIN] = c;
+        rec[XCK_DPREV] = dprev;
+        rec[XCK_BEST] = best;
+        rec[XCK_LO] = lo;
+        rec[XCK_HI] = hi;
+        rec[XCK_USED] = used;
+        rec[XCK_WIN] = WIN;
+        rec[XCK_BV] = bv;
+        rec[XCK_BI] = bi;
+        rec[XCK_BJ] = bj;
+        rec[XCK_CELLS_LO] = (int32_t)(uint32_t)cells;
+        rec[XCK_CELLS_HI] = (int32_t)(uint32_t)(cells >> 32);
+        ck->flags[1 + seg] = W;
+      }
+      gsync();
+      continue;
+    }
     if (tid == 0 && ckmode != 2) {
+      if (ckmode == 3) {  // the sweep ends in this segment (or outgrew the widest window)
+        ck->flags[0] = 1;
+        if (status != FILTR_ST_TOO_WIDE) ck->flags[1 + seg] = W;
+      }
       int score = 0, ei = 0, ej = 0;
       if (status == FILTR_ST_TOO_WIDE) {
         const uint32_t slot = atomicAdd(n_overflow, 1u);

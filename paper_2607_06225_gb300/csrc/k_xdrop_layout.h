@@ -15,20 +15,34 @@ FILTR_HD uint64_t xd_tb_words(int64_t M, int64_t N, int warps, int S) {
   return (uint64_t)(M + N + 1) * (uint64_t)(1 + xd_words_per_k(warps, S));
 }
 
-// Checkpointed traceback (filtr_align_long when the whole traceback does not
-// fit): mode 1 sweeps forward without traceback and stores the window state of
-// every C-th antidiagonal; mode 2 resumes from the checkpoint of k_start and
-// recomputes antidiagonals (k_start, k_end] with traceback into a segment
-// buffer, which a resumable walk then consumes backwards.
+// Checkpointed sweep of one long pair (filtr_align_long).  The antidiagonals
+// are cut into segments (s*C, (s+1)*C].  Mode 3 sweeps one segment forward
+// without traceback, resuming from the checkpoint of its first antidiagonal,
+// and stores the window state after its last one; the host launches it once
+// per group width (1, 2, 4, ... warps) and each launch does nothing if the
+// segment is already done, the sweep has finished, or the checkpointed state
+// does not fit its window -- so every segment runs at the narrowest width
+// that holds it.  Mode 2 resumes from the checkpoint of k_start and recomputes
+// (k_start, k_end] with traceback into a segment buffer, which a resumable
+// walk then consumes backwards.
 struct XdCkpt {
-  int mode;            // 1 forward with checkpoints, 2 resume one segment
+  int mode;            // 3 forward segment, 2 recompute one segment with traceback
   int C;               // checkpoint interval in antidiagonals
-  int32_t *buf;        // checkpoints, xd_ckpt_ints(W) ints each, indexed by k / C
-  int k_start, k_end;  // mode 2
+  int32_t *buf;        // checkpoints, xd_ckpt_stride() ints each, indexed by k / C
+  int k_start, k_end;  // the segment (k_start, k_end]
   uint32_t *seg_tb;    // mode 2: (k_end - k_start) rows of WIN/8 words
   int32_t *seg_ck;     // mode 2: window origin of each recomputed antidiagonal
+  int32_t *flags;      // mode 3: [0] sweep finished, [1 + s] width that completed segment s
 };
-FILTR_HD int64_t xd_ckpt_ints(int warps) { return 8 + (int64_t)xd_window_slots(warps, 8) * 4; }
+// checkpoint record: a header, then H, E, F of antidiagonal k and H of k - 1
+// for every slot of the widest window (thread t's 4*S values at 16 + t*4*S);
+// slots at or beyond the writer's window read as NEG
+enum : int {
+  XCK_ORIGIN = 0, XCK_DPREV, XCK_BEST, XCK_LO, XCK_HI, XCK_USED, XCK_WIN,
+  XCK_BV, XCK_BI, XCK_BJ, XCK_CELLS_LO, XCK_CELLS_HI, XCK_HDR = 16
+};
+constexpr int XD_MAX_WARPS = 32;
+FILTR_HD int64_t xd_ckpt_stride() { return XCK_HDR + (int64_t)xd_window_slots(XD_MAX_WARPS, 8) * 4; }
 
 // Resumable walk over checkpointed segments (one thread).
 struct WalkState {

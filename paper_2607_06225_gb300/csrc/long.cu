@@ -5,7 +5,9 @@
 // antidiagonal order is inherently sequential, so one wide group is what the
 // pair can use.  Full-matrix and banded pairs run the cooperative strip kernel
 // (k_long.cu) across the whole grid, then the ordinary traceback walk.
+#include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "../../include/filtr_testing.h"
 #include "filtr_ctx.h"
@@ -14,6 +16,10 @@
 #include "plan.h"
 
 namespace filtr {
+
+// X-drop pairs with more antidiagonals than this run as a segmented sweep, each
+// segment at the narrowest group width that holds its live region
+constexpr int64_t XD_SEGMENTED_SWEEP = 1 << 16;
 namespace {
 
 struct Carve {
@@ -200,128 +206,149 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
                             int C) {
   (void)params;
   const int64_t K = (int64_t)M + N;
-  const int64_t nseg = K / C + 1;
-  static const int kWidths[] = {4, 16, 32};
-  for (int wi = 0; wi < 3; ++wi) {
-    const int W = kWidths[wi];
-    const int wpk = xd_words_per_k(W, 8);
-    Carve cv{c->ws, c->ws_bytes};
-    int32_t *ck_buf = cv.take<int32_t>((size_t)(K / C + 1) * xd_ckpt_ints(W));
-    uint32_t *seg_tb = cv.take<uint32_t>((size_t)C * wpk);
-    int32_t *seg_ck = cv.take<int32_t>(C);
-    XdCkpt *d_ck = cv.take<XdCkpt>(nseg + 1);
-    WalkState *d_ws = cv.take<WalkState>(1);
-    FwdOut *d_fwd = cv.take<FwdOut>(1);
-    uint32_t *d_one = cv.take<uint32_t>(16);   // order, lengths, counters
-    TbLayout *d_tbl = cv.take<TbLayout>(1);
-    uint64_t *d_misc = cv.take<uint64_t>(8);   // stage_off, offsets, CIGAR offset
-    uint32_t *d_ovf = cv.take<uint32_t>(4);
-    uint32_t *d_stage = sp.traceback ? cv.take<uint32_t>((size_t)M + N + 1) : nullptr;
-    if (cv.used > c->ws_bytes) {
-      set_error("checkpointed traceback needs %zu workspace bytes; the context has %zu", cv.used,
-                c->ws_bytes);
-      return FILTR_ERR_NOMEM;
+  const int64_t nseg = (K + C - 1) / C;
+  static const int kLadder[] = {1, 2, 4, 8, 16, XD_MAX_WARPS};
+  Carve cv{c->ws, c->ws_bytes};
+  int32_t *ck_buf = cv.take<int32_t>((size_t)(nseg + 1) * xd_ckpt_stride());
+  uint32_t *seg_tb =
+      sp.traceback ? cv.take<uint32_t>((size_t)C * xd_words_per_k(XD_MAX_WARPS, 8)) : nullptr;
+  int32_t *seg_ck = sp.traceback ? cv.take<int32_t>(C) : nullptr;
+  XdCkpt *d_ck = cv.take<XdCkpt>(2 * nseg + 1);
+  int32_t *d_flags = cv.take<int32_t>(nseg + 1);
+  WalkState *d_ws = cv.take<WalkState>(1);
+  FwdOut *d_fwd = cv.take<FwdOut>(1);
+  uint32_t *d_one = cv.take<uint32_t>(16);   // order, lengths
+  TbLayout *d_tbl = cv.take<TbLayout>(1);
+  uint64_t *d_misc = cv.take<uint64_t>(8);   // stage_off, offsets, CIGAR offset
+  uint32_t *d_ovf = cv.take<uint32_t>(4);
+  uint32_t *d_stage = sp.traceback ? cv.take<uint32_t>((size_t)M + N + 1) : nullptr;
+  if (cv.used > c->ws_bytes) {
+    set_error("checkpointed traceback needs %zu workspace bytes; the context has %zu", cv.used,
+              c->ws_bytes);
+    return FILTR_ERR_NOMEM;
+  }
+  // host staging: the one-pair batch, the segment descriptors, the flags
+  const size_t desc_off = 4096;
+  const size_t flags_off = desc_off + (size_t)(2 * nseg + 1) * sizeof(XdCkpt);
+  if (!c->ensure_host(flags_off + (size_t)(nseg + 1) * 4 + 64)) return FILTR_ERR_NOMEM;
+  char *h = reinterpret_cast<char *>(c->h_stage);
+  uint32_t one[16] = {0, M, N};  // order, q_len, r_len
+  TbLayout L{};
+  uint64_t misc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  memcpy(h, one, sizeof one);
+  memcpy(h + 64, &L, sizeof L);
+  memcpy(h + 128, misc, sizeof misc);
+  XdCkpt *hk = reinterpret_cast<XdCkpt *>(h + desc_off);
+  for (int64_t sgi = 0; sgi < nseg; ++sgi)
+    hk[sgi] = XdCkpt{3, C, ck_buf, (int)(sgi * C), (int)std::min<int64_t>((sgi + 1) * C, K),
+                     nullptr, nullptr, d_flags};
+  cudaError_t e = cudaMemcpyAsync(d_one, h, sizeof one, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tbl, h + 64, sizeof L, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_misc, h + 128, sizeof misc, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_ck, hk, nseg * sizeof(XdCkpt), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, (nseg + 1) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_ovf, 0, 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpoint setup");
+  const uint64_t *d_off = d_misc + 1;
+  BatchDev b{q, r, d_off, d_off + 1, d_one + 1, d_one + 2};
+  FullArgs fa;
+  fa.b = b;
+  fa.sp = sp;
+  fa.sp.traceback = 0;  // the forward sweep keeps checkpoints, not traceback bits
+  fa.order = d_one;
+  fa.n_order = 1;
+  fa.counter = nullptr;  // unused with checkpoints
+  fa.out = out;
+  fa.fwd = d_fwd;
+  fa.tb = nullptr;
+  fa.tbl = d_tbl;
+  fa.strip_buf = nullptr;
+  fa.strip_stride = 0;
+  fa.max_n = 0;
+  fa.max_m = 0;
+  // forward: every segment is offered to each width in turn; the narrowest
+  // window that holds it does the work, the other launches return at once
+  uint32_t launches = 0;
+  c->span_begin(Ctx::PH_FORWARD, st);
+  for (int64_t sgi = 0; sgi < nseg && e == cudaSuccess; ++sgi) {
+    fa.ck = d_ck + sgi;
+    for (int W : kLadder) {
+      e = launch_xdrop(fa, W, 1, d_ovf, d_ovf + 1, st);
+      ++launches;
+      if (e != cudaSuccess) break;
     }
-    // host staging: the one-pair batch, the segment descriptors, the walk state
-    const size_t hbytes = 4096 + (size_t)(nseg + 1) * sizeof(XdCkpt);
-    if (!c->ensure_host(hbytes)) return FILTR_ERR_NOMEM;
-    char *h = reinterpret_cast<char *>(c->h_stage);
-    uint32_t one[16] = {0, M, N, 0, 0};          // order, q_len, r_len, counters (zero)
-    TbLayout L{};
-    uint64_t misc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    memcpy(h, one, sizeof one);
-    memcpy(h + 64, &L, sizeof L);
-    memcpy(h + 128, misc, sizeof misc);
-    XdCkpt *hk = reinterpret_cast<XdCkpt *>(h + 4096);
-    hk[0] = XdCkpt{1, C, ck_buf, 0, 0, nullptr, nullptr};
-    cudaError_t e = cudaMemcpyAsync(d_one, h, sizeof one, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tbl, h + 64, sizeof L, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_misc, h + 128, sizeof misc, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ck, hk, sizeof(XdCkpt), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_ovf, 0, 16, st);
-    if (e != cudaSuccess) return cuda_fail(e, "checkpoint setup");
-    const uint64_t *d_off = d_misc + 1;
-    BatchDev b{q, r, d_off, d_off + 1, d_one + 1, d_one + 2};
-    FullArgs fa;
-    fa.b = b;
-    fa.sp = sp;
-    fa.sp.traceback = 0;  // the forward sweep keeps checkpoints, not traceback bits
-    fa.order = d_one;
-    fa.n_order = 1;
-    fa.counter = d_one + 3;
-    fa.out = out;
-    fa.fwd = d_fwd;
-    fa.tb = nullptr;
-    fa.tbl = d_tbl;
-    fa.strip_buf = nullptr;
-    fa.strip_stride = 0;
-    fa.max_n = 0;
-    fa.max_m = 0;
-    fa.ck = d_ck;
-    c->span_begin(Ctx::PH_FORWARD, st);
-    e = launch_xdrop(fa, W, 1, d_ovf, d_ovf + 1, st);
-    c->span_end(st);
-    FwdOut *hf = reinterpret_cast<FwdOut *>(h + 256);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hf, d_fwd, sizeof(FwdOut), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward sweep");
-    const FwdOut f = *hf;
-    if (f.status == FILTR_ST_TOO_WIDE && W < 32) continue;
-    if (!sp.traceback || (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED)) return FILTR_OK;
-    // backward: one segment at a time, from the end cell's antidiagonal down to 0
-    WalkState w0{f.end_i, f.end_j, f.score, 0, 0, -1, 0, 0};
-    WalkState *hw = reinterpret_cast<WalkState *>(h + 512);
-    *hw = w0;
-    const int64_t ke = (int64_t)f.end_i + f.end_j;
-    int64_t nsegs = 0;
-    for (int64_t khi = ke; khi > 0;) {
-      const int64_t klo = ((khi - 1) / C) * C;
-      hk[1 + nsegs++] = XdCkpt{2, C, ck_buf, (int)klo, (int)khi, seg_tb, seg_ck};
-      khi = klo;
+  }
+  c->span_end(st);
+  FwdOut *hf = reinterpret_cast<FwdOut *>(h + 256);
+  int32_t *hflags = reinterpret_cast<int32_t *>(h + flags_off);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hf, d_fwd, sizeof(FwdOut), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hflags, d_flags, (nseg + 1) * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward sweep");
+  const FwdOut f = *hf;
+  c->last_launches = launches;
+  if (!sp.traceback || (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED)) return FILTR_OK;
+  // backward: one segment at a time, from the end cell's antidiagonal down to
+  // 0, each recomputed at the width that completed it going forward
+  WalkState w0{f.end_i, f.end_j, f.score, 0, 0, -1, 0, 0};
+  WalkState *hw = reinterpret_cast<WalkState *>(h + 512);
+  *hw = w0;
+  const int64_t ke = (int64_t)f.end_i + f.end_j;
+  XdCkpt *hb = hk + nseg;
+  std::vector<int> seg_w;
+  int64_t nb = 0;
+  for (int64_t khi = ke; khi > 0;) {
+    const int64_t klo = ((khi - 1) / C) * C;
+    const int W = hflags[1 + klo / C];
+    if (W <= 0) {
+      set_error("checkpointed sweep: segment at antidiagonal %lld has no width", (long long)klo);
+      return FILTR_ERR_CUDA;
     }
-    e = cudaMemcpyAsync(d_ws, hw, sizeof(WalkState), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && nsegs)
-      e = cudaMemcpyAsync(d_ck + 1, hk + 1, nsegs * sizeof(XdCkpt), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "segment setup");
-    FullArgs ra = fa;
-    ra.sp = sp;  // traceback on
-    ra.out = reinterpret_cast<filtr_result *>(c->d_small + 3072);  // mode 2 writes no result
-    WalkArgs wa;
-    wa.b = b;
-    wa.sp = sp;
-    wa.order = d_one;
-    wa.n_order = 1;
-    wa.out = out;
-    wa.fwd = d_fwd;
-    wa.tb = nullptr;
-    wa.tbl = d_tbl;
-    wa.stage = d_stage;
-    wa.stage_off = d_misc;
-    uint32_t launches = 1;
-    for (int64_t sgi = 0; sgi < nsegs; ++sgi) {
-      ra.ck = d_ck + 1 + sgi;
-      ra.counter = d_one + 4 + (sgi & 7);
-      e = cudaMemsetAsync(ra.counter, 0, 4, st);
-      if (e == cudaSuccess) e = launch_xdrop(ra, W, 1, d_ovf, d_ovf + 1, st);
-      if (e == cudaSuccess)
-        e = launch_walk_segment(wa, seg_tb, seg_ck, hk[1 + sgi].k_start, wpk, d_ws, st);
-      launches += 2;
-      if (e != cudaSuccess) return cuda_fail(e, "segment recompute");
-    }
-    uint64_t *d_offs = d_misc + 4;
-    e = cudaMemsetAsync(d_offs, 0, 8, st);
-    if (e == cudaSuccess) e = launch_compact(wa, 1, d_offs, cigar, cap, out, st);
-    filtr_result *hr = reinterpret_cast<filtr_result *>(h + 1024);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hr, out, sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "checkpointed traceback");
-    c->last_launches = launches + 1;
-    c->last_waves = (int)nsegs;
-    if (hr->cigar_len > cap) {
-      set_error("the CIGAR needs %u ops, cigar_cap is %llu", hr->cigar_len, (unsigned long long)cap);
-      return FILTR_ERR_CIGAR_CAP;
-    }
-    return FILTR_OK;
+    hb[nb++] = XdCkpt{2, C, ck_buf, (int)klo, (int)khi, seg_tb, seg_ck, d_flags};
+    seg_w.push_back(W);
+    khi = klo;
+  }
+  e = cudaMemcpyAsync(d_ws, hw, sizeof(WalkState), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nb)
+    e = cudaMemcpyAsync(d_ck + nseg, hb, nb * sizeof(XdCkpt), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "segment setup");
+  FullArgs ra = fa;
+  ra.sp = sp;  // traceback on
+  ra.out = reinterpret_cast<filtr_result *>(c->d_small + 3072);  // mode 2 writes no result
+  WalkArgs wa;
+  wa.b = b;
+  wa.sp = sp;
+  wa.order = d_one;
+  wa.n_order = 1;
+  wa.out = out;
+  wa.fwd = d_fwd;
+  wa.tb = nullptr;
+  wa.tbl = d_tbl;
+  wa.stage = d_stage;
+  wa.stage_off = d_misc;
+  for (int64_t sgi = 0; sgi < nb; ++sgi) {
+    ra.ck = d_ck + nseg + sgi;
+    e = launch_xdrop(ra, seg_w[sgi], 1, d_ovf, d_ovf + 1, st);
+    if (e == cudaSuccess)
+      e = launch_walk_segment(wa, seg_tb, seg_ck, hb[sgi].k_start, xd_words_per_k(seg_w[sgi], 8),
+                              d_ws, st);
+    launches += 2;
+    if (e != cudaSuccess) return cuda_fail(e, "segment recompute");
+  }
+  uint64_t *d_offs = d_misc + 4;
+  e = cudaMemsetAsync(d_offs, 0, 8, st);
+  if (e == cudaSuccess) e = launch_compact(wa, 1, d_offs, cigar, cap, out, st);
+  filtr_result *hr = reinterpret_cast<filtr_result *>(h + 1024);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hr, out, sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "checkpointed traceback");
+  c->last_launches = launches + 1;
+  c->last_waves = (int)nb;
+  if (hr->cigar_len > cap) {
+    set_error("the CIGAR needs %u ops, cigar_cap is %llu", hr->cigar_len, (unsigned long long)cap);
+    return FILTR_ERR_CIGAR_CAP;
   }
   return FILTR_OK;
 }
@@ -372,7 +399,7 @@ filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const 
   rc = validate_seq(c, q, M, r, N, sp.alphabet, st);
   if (rc != FILTR_OK) return rc;
   if (sp.use_xdrop && M && N &&
-      (c->ckpt_interval > 0 ||
+      (c->ckpt_interval > 0 || (int64_t)M + N > XD_SEGMENTED_SWEEP ||
        4 * xd_tb_words(M, N, 32, 8) > c->ws_bytes / 2)) {  // the widest traceback would not fit
     const int C = c->ckpt_interval > 0 ? c->ckpt_interval : 4096;
     rc = run_xdrop_ckpt(c, sp, params, q, M, r, N, out, cigar, cigar_cap, st, C);
