@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--precision", default="auto", choices=["auto", "i32", "i16x2"],
+                    help="cell width of the tiled kernels (results are identical)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plan with the built-in shape costs instead of timed ones")
     return ap.parse_args()
 
 
@@ -398,7 +402,8 @@ def main():
     else:
         batch = synth.long_pair(seed=5 + seed_off)
     sc = dict(batch.scoring)
-    params = F.make_params(batch.subst, **sc)
+    prec = {"auto": F.PREC_AUTO, "i32": F.PREC_I32, "i16x2": F.PREC_I16X2}[args.precision]
+    params = F.make_params(batch.subst, **dict(sc, precision=prec))
     ctx = F.Context(local_rank, int(args.workspace_gb * (1 << 30)))
     db = F.DeviceBatch(batch, dev)
     out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
@@ -419,6 +424,9 @@ def main():
         if rc != 0:
             raise F.FiltrError(rc, F.last_error())
 
+    tune = None
+    if not args.no_autotune and not sc.get("xdrop"):
+        tune = ctx.autotune(params)  # one-time setup, outside every timed region
     ctx.set_timing(True)
     for _ in range(max(args.warmup, 1)):
         step()
@@ -447,6 +455,7 @@ def main():
         fwd_ms.append(st["ms_forward"])
         walk_ms.append(st["ms_walk"])
         launches.append(st["launches"])
+        packed = st.get("pairs_i16x2", 0)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
@@ -485,10 +494,12 @@ def main():
             "data": "synthetic",
             "config": {"workload": wl, "pairs": batch.n, "cells_per_step": cells,
                        "mode": WORKLOAD_DESC[wl],
+                       "precision": args.precision, "pairs_i16x2": packed,
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replica x{world}"},
             "plain_per_pair": plain,
             "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms},
+            "autotune_ns_per_warp_step": tune,
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": int(statistics.median(launches)),

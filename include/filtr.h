@@ -145,7 +145,18 @@ filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint
  * FILTR_ERR_CIGAR_CAP after the stream completes and each result carries its
  * length.  Band and X-drop pairs whose live region outgrows the widest kernel
  * window (8192 cells on one antidiagonal) get FILTR_ST_TOO_WIDE.  Returns FILTR_ERR_INVALID
- * before any launch for bad params or codes. */
+ * before any launch for bad params or codes, FILTR_ERR_UNSUPPORTED when scores
+ * could reach 2^28 in magnitude (largest |substitution score| x shorter side +
+ * 3 x open + extend x (longest query + longest reference)) or, for local
+ * alignments, largest |substitution score| x shorter side reaches 2^26.
+ * params->precision picks the cell width of unbanded, non-X-drop pairs:
+ * FILTR_PREC_I16X2 runs every pair whose score range provably fits 15 bits
+ * (substitution scores in [-64, 63] and a bound, for its lengths, on every
+ * value the recurrence forms) two cells per 32-bit register, FILTR_PREC_I32
+ * never does, and
+ * FILTR_PREC_AUTO picks per pair by cost (measured ones after filtr_autotune).
+ * No pair is ever computed in a width it could overflow, so results do not
+ * depend on the choice. */
 filtr_status filtr_align_batch(filtr_ctx *ctx, const filtr_params *params, uint32_t n_pairs,
                                const uint8_t *q_seq, const uint64_t *q_off, const uint32_t *q_len,
                                const uint8_t *r_seq, const uint64_t *r_off, const uint32_t *r_len,
@@ -231,9 +242,35 @@ typedef struct {
   uint32_t launches;    /* kernels this library launched for the call */
   uint32_t waves;
   uint64_t cells_planned;
+  uint32_t pairs_i16x2; /* pairs that ran in the int16x2 tiled kernel */
+  uint32_t reserved;
 } filtr_stats;
 filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
+
+/* Autotuning of the tiled kernel shapes (the paper leaves autotuning to
+ * future work, Sec. 12).  Times every tiled shape -- the int32 tile with 32,
+ * 24, 16 or 8 rows per lane and, where the parameters allow it, the int16x2
+ * tile with 32 or 16 -- on calibration batches that fill every resident warp
+ * slot of the device three times (pairs of one full strip of query rows by 512
+ * reference residues, random codes), and keeps in ctx the device time per warp
+ * step of each shape for this recurrence kind (mode, gap model, traceback,
+ * alphabet, band).  Later filtr_align_batch calls of the same kind give each
+ * pair the shape whose predicted time, strips x (N + fill steps) x that cost,
+ * is smallest.  Results never change: the shapes are bit-exact alternatives.
+ *   out: optional; rows_per_lane / packed describe the six shapes, and
+ *        ns_per_warp_step is 0 for shapes not timed (not allowed for these
+ *        parameters, or too large for the workspace).
+ * Synchronous (waits for the context's previous call); uses the workspace.
+ * Errors: FILTR_ERR_INVALID (NULL ctx, bad params, X-drop parameters, which
+ * use the antidiagonal kernel only), FILTR_ERR_NOMEM (the workspace holds no
+ * calibration batch), FILTR_ERR_CUDA. */
+typedef struct {
+  int32_t rows_per_lane[6];
+  int32_t packed[6];
+  double ns_per_warp_step[6];
+} filtr_tune_report;
+filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params, filtr_tune_report *out);
 
 /* Measured integer / DPX throughput of this device, used as the cell-update
  * roofline denominator: out[0] = int32 add/max ops per second (all SMs,

@@ -49,7 +49,13 @@ class Result(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("ms_validate", C.c_double), ("ms_forward", C.c_double), ("ms_walk", C.c_double),
                 ("ms_place", C.c_double), ("ms_total", C.c_double), ("launches", C.c_uint32),
-                ("waves", C.c_uint32), ("cells_planned", C.c_uint64)]
+                ("waves", C.c_uint32), ("cells_planned", C.c_uint64),
+                ("pairs_i16x2", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("rows_per_lane", C.c_int32 * 6), ("packed", C.c_int32 * 6),
+                ("ns_per_warp_step", C.c_double * 6)]
 
 
 RESULT_DTYPE = np.dtype([("score", np.int32), ("q_begin", np.int32), ("q_end", np.int32),
@@ -99,6 +105,8 @@ def lib():
         L.filtr_ctx_set_timing.argtypes = [C.c_void_p, i32]
         L.filtr_ctx_last_stats.restype = i32
         L.filtr_ctx_last_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.filtr_autotune.restype = i32
+        L.filtr_autotune.argtypes = [C.c_void_p, C.POINTER(Params), C.POINTER(TuneReport)]
         L.filtr_probe_int_peak.restype = i32
         L.filtr_probe_int_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double * 5)]
         L.filtr_test_long_timeout.restype = i32
@@ -210,6 +218,18 @@ class Context:
         st = Stats()
         check(lib().filtr_ctx_last_stats(self.handle, C.byref(st)), "filtr_ctx_last_stats")
         return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def autotune(self, params) -> dict:
+        """Time the tiled kernel shapes for this recurrence kind (filtr_autotune);
+        returns {"i32 R=32": ns per warp step, ...} for the shapes timed."""
+        rep = TuneReport()
+        check(lib().filtr_autotune(self.handle, C.byref(params), C.byref(rep)), "filtr_autotune")
+        out = {}
+        for k in range(6):
+            if rep.ns_per_warp_step[k] > 0:
+                kind = "i16x2" if rep.packed[k] else "i32"
+                out[f"{kind} R={rep.rows_per_lane[k]}"] = rep.ns_per_warp_step[k]
+        return out
 
     def probe(self):
         arr = (C.c_double * 5)()

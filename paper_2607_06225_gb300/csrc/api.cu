@@ -91,18 +91,17 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
   sp->use_xdrop = xd ? 1 : 0;
   sp->xdrop = xd ? p->xdrop : 0;
   sp->traceback = p->traceback;
-  for (int t = 0; t < p->alphabet * p->alphabet; ++t) sp->subst[t] = p->subst[t];
+  sp->precision = p->precision;
+  sp->smin = 127;
+  sp->smax = -128;
+  for (int t = 0; t < p->alphabet * p->alphabet; ++t) {
+    sp->subst[t] = p->subst[t];
+    sp->smin = std::min(sp->smin, (int32_t)p->subst[t]);
+    sp->smax = std::max(sp->smax, (int32_t)p->subst[t]);
+  }
   return FILTR_OK;
 }
 
-// |H| stays below 2^28 so that NEG arithmetic cannot meet finite scores.
-static bool score_range_ok(const ScoreParams &sp, uint64_t max_m, uint64_t max_n) {
-  int smax = 0;
-  for (int t = 0; t < sp.alphabet * sp.alphabet; ++t) smax = std::max(smax, std::abs((int)sp.subst[t]));
-  const double bound = (double)smax * (double)std::min(max_m, max_n) + (double)sp.o +
-                       (double)sp.e * (double)(max_m + max_n) + (double)sp.o * 2.0;
-  return bound < (double)(1 << 28);
-}
 
 // ---- workspace carving ------------------------------------------------------
 struct Carver {
@@ -122,6 +121,16 @@ int Ctx::full_blocks_per_sm(int R, const ScoreParams &sp) {
   auto it = occ_cache.find(key);
   if (it != occ_cache.end()) return it->second;
   int nb = full_max_blocks_per_sm(R, sp, sp.alphabet);
+  if (nb < 1) nb = 1;
+  occ_cache[key] = nb;
+  return nb;
+}
+
+int Ctx::pack_blocks_per_sm(int R, const ScoreParams &sp) {
+  const auto key = std::make_tuple(R | 0x100, sp.mode, sp.affine, sp.traceback, 0, sp.alphabet);
+  auto it = occ_cache.find(key);
+  if (it != occ_cache.end()) return it->second;
+  int nb = pack_max_blocks_per_sm(R, sp);
   if (nb < 1) nb = 1;
   occ_cache[key] = nb;
   return nb;
@@ -240,11 +249,13 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     return FILTR_ERR_UNSUPPORTED;
   }
   if (!score_range_ok(sp, max_m, max_n)) {
-    set_error("scores could exceed 2^28 for these lengths and penalties");
+    set_error("scores could exceed 2^28 (2^26 for local alignments) for these lengths and penalties");
     return FILTR_ERR_UNSUPPORTED;
   }
   int blocks_per_sm = 1;
   for (int R : {8, 16, 24, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->full_blocks_per_sm(R, sp));
+  if (!sp.use_band && !sp.use_xdrop && sp.precision != FILTR_PREC_I32)
+    for (int R : {16, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->pack_blocks_per_sm(R, sp));
   const int grid_max = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * blocks_per_sm,
                                                           ((int64_t)n + FULL_WARPS - 1) / FULL_WARPS);
   const uint32_t strip_stride = (uint32_t)(max_n + 2);
@@ -273,6 +284,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
 
   Plan P;
   PlanInput in{&sp, n, h_ql, h_rl, tb_budget, 8, ctx->xdrop_warps0};
+  in.shape_cost = ctx->tuned_costs(sp);
   if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
 
   // 3. upload the plan
@@ -324,13 +336,14 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   size_t counter_i = 0;
   auto run_group = [&](const uint32_t *d_ord, uint32_t cnt, uint8_t family, int R, int W) -> bool {
     if (cnt == 0) return true;
-    if (family == FAM_FULL) {
+    if (family == FAM_FULL || family == FAM_PACK) {
+      const bool pk = family == FAM_PACK;
       if (plain) {
         for (uint32_t t = 0; t < cnt; ++t) {
           fa.order = d_ord + t;
           fa.n_order = 1;
           fa.counter = d_counters + (counter_i++ % n_counters);
-          ce = launch_full(fa, R, 1, st);
+          ce = pk ? launch_pack(fa, R, 1, st) : launch_full(fa, R, 1, st);
           ++launches;
           if (ce != cudaSuccess) return false;
           if (sp.traceback) {
@@ -346,9 +359,9 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       fa.order = d_ord;
       fa.n_order = cnt;
       fa.counter = d_counters + (counter_i++ % n_counters);
-      const int bps = ctx->full_blocks_per_sm(R, sp);
+      const int bps = pk ? ctx->pack_blocks_per_sm(R, sp) : ctx->full_blocks_per_sm(R, sp);
       int grid = (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + FULL_WARPS - 1) / FULL_WARPS);
-      ce = launch_full(fa, R, std::max(grid, 1), st);
+      ce = pk ? launch_pack(fa, R, std::max(grid, 1), st) : launch_full(fa, R, std::max(grid, 1), st);
       ++launches;
       return ce == cudaSuccess;
     }
@@ -501,6 +514,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     }
   }
   ctx->last_cells_estimate = P.cells_estimate;
+  ctx->last_pairs_packed = 0;
+  for (const Wave &w : P.waves)
+    for (const Group &g : w.groups)
+      if (g.family == FAM_PACK) ctx->last_pairs_packed += g.end - g.begin;
   ctx->last_waves = (int)P.waves.size();
   ctx->last_launches = launches;
   if (!ctx->done_ev) cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
@@ -755,6 +772,7 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out) {
   out->launches = c->last_launches;
   out->waves = (uint32_t)c->last_waves;
   out->cells_planned = c->last_cells_estimate;
+  out->pairs_i16x2 = c->last_pairs_packed;
   cudaSetDevice(c->device);
   double *acc[4] = {&out->ms_validate, &out->ms_forward, &out->ms_walk, &out->ms_place};
   cudaEvent_t first = nullptr, last = nullptr;

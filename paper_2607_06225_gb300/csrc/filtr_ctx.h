@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "filtr_internal.h"
+#include "plan.h"
 
 namespace filtr {
 
@@ -23,6 +24,7 @@ struct Ctx {
   cudaStream_t own_stream = nullptr;
   std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
   uint64_t last_cells_estimate = 0;
+  uint32_t last_pairs_packed = 0;
   int last_waves = 0;
   uint32_t last_launches = 0;
   int xdrop_warps0 = 1;       // first window width (warps) of X-drop pairs
@@ -41,7 +43,19 @@ struct Ctx {
   size_t ev_used = 0;
   std::vector<Span> spans;
 
+  // measured shape costs (filtr_autotune), per recurrence kind
+  using TuneKey = std::tuple<int, int, int, int, int>;  // mode, affine, traceback, alphabet, band
+  std::map<TuneKey, std::vector<ShapeCost>> tuned;
+  static TuneKey tune_key(const ScoreParams &sp) {
+    return TuneKey(sp.mode, sp.affine, sp.traceback, sp.alphabet, sp.use_band);
+  }
+  const ShapeCost *tuned_costs(const ScoreParams &sp) const {
+    auto it = tuned.find(tune_key(sp));
+    return it == tuned.end() ? nullptr : it->second.data();
+  }
+
   int full_blocks_per_sm(int R, const ScoreParams &sp);
+  int pack_blocks_per_sm(int R, const ScoreParams &sp);
   bool ensure_host(size_t bytes);
   cudaEvent_t next_event();
   // open / close a timed span on stream st (no-ops when timing is off)

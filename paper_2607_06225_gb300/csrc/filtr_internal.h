@@ -85,7 +85,7 @@ struct FwdOut {
 };
 
 // Kernel selection for one pair.
-enum Family : uint8_t { FAM_FULL = 0, FAM_XDROP = 1, FAM_TRIVIAL = 2 };
+enum Family : uint8_t { FAM_FULL = 0, FAM_XDROP = 1, FAM_TRIVIAL = 2, FAM_PACK = 3 };
 
 struct PairPlan {
   uint32_t pair;
@@ -113,8 +113,53 @@ struct ScoreParams {
   int32_t use_band, band_literal, band;
   int32_t use_xdrop, xdrop;
   int32_t traceback;
+  int32_t precision;           // FILTR_PREC_*
+  int32_t smin, smax;          // smallest / largest substitution score
   int8_t subst[MAX_ALPHA * MAX_ALPHA];
 };
+
+// Score range of a batch whose longest query / reference are max_m / max_n:
+// |H| stays below 2^28 so that NEG arithmetic never meets finite scores, and
+// local scores stay below 2^26 so that the tiled kernels' best-cell keys
+// (H * 32 + row) fit in 31 bits.
+inline bool score_range_ok(const ScoreParams &sp, uint64_t max_m, uint64_t max_n) {
+  int smax = 0;
+  for (int t = 0; t < sp.alphabet * sp.alphabet; ++t) {
+    const int v = sp.subst[t] < 0 ? -sp.subst[t] : sp.subst[t];
+    smax = v > smax ? v : smax;
+  }
+  const double shorter = (double)(max_m < max_n ? max_m : max_n);
+  const double bound = (double)smax * shorter + 3.0 * (double)sp.o +
+                       (double)sp.e * (double)(max_m + max_n);
+  if (bound >= (double)(1 << 28)) return false;
+  return sp.mode != FILTR_LOCAL || (double)smax * shorter < (double)(1 << 26);
+}
+
+// ---- packed 16-bit cells (two per 32-bit register) ---------------------------
+// A value v is held as the unsigned 16-bit v + B.  B is chosen per pair so that
+// every quantity the recurrence forms (H, E, F, the diagonal candidate and the
+// gap candidates) lies in [0, 0x8000): then sums never carry or borrow across
+// the halves, unsigned max is signed max, and A - B + 0x7fff leaves [A > B] in
+// bit 15 of each half.  Returns B, or -1 when the pair's bound does not fit
+// (the pair then runs in int32).  Unbanded alignments only; substitution
+// scores must lie in [-64, 63] (the profile holds s + 64 in 7 bits).
+FILTR_HD int pack_bias(int mode, int o, int e, int smin, int smax, int64_t M, int64_t N) {
+  if (smin < -64 || smax > 63) return -1;
+  const int64_t oe = (int64_t)o + e;
+  // lowest value any formed quantity can take:
+  //   local:  H >= 0, E, F >= -(o+e), extensions a further -e, diagonal >= smin
+  //   global: H(i,j) >= -(2o + e(i+j)) (a gap down the first column, then one
+  //           along row i), then the same offsets
+  int64_t low = oe + e + 64;
+  if (mode != FILTR_LOCAL) low += 2 * (int64_t)o + (int64_t)e * (M + N);
+  const int64_t B = low + e + 2;
+  const int64_t high = (int64_t)(smax > 0 ? smax : 0) * ((M < N ? M : N) + 1) + 2;
+  if (B + high >= 0x7ff0) return -1;
+  return (int)B;
+}
+FILTR_HD uint64_t pack_strip_tb_words(int64_t jlo, int64_t jhi, int R) {
+  return jhi >= jlo ? (uint64_t)((jhi - jlo + 1) + 63) * (uint64_t)(R / 8) * 32u : 0;
+}
 
 struct BatchDev {
   const uint8_t *q_seq, *r_seq;
@@ -179,6 +224,8 @@ int long_blocks_per_sm(const ScoreParams &sp);
 cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
 int full_smem_bytes(int R, int alphabet);
 int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
+cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);  // R = 16, 32
+int pack_max_blocks_per_sm(int R, const ScoreParams &sp);
 cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
                          uint32_t *n_overflow, cudaStream_t s);
 int xd_pairs_per_cta(int W);

@@ -95,6 +95,12 @@ __device__ __forceinline__ int fadd(int a, int b, int one) {
 }
 // a - b the same way (mone == -1)
 __device__ __forceinline__ int fsub(int a, int b, int mone) { return fadd(a, b, mone); }
+// a * b + c on the FMA pipe
+__device__ __forceinline__ int fmad(int a, int b, int c) {
+  int r;
+  asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
 
 // Per-pair constants of a strip pass.
 struct StripPair {
@@ -189,6 +195,15 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
   const int nsteps = (jhi - jlo + 1) + 31;
   int upH = NEG, upF = NEG, prevIn = dtop;
   int rc_next = P.r[jlo - 1];
+  // Best cell (local), without a per-step scan: each cell's key is
+  // H * 32 + (31 - its row in the lane), so the largest key is the largest H
+  // and, among equal H, the smallest i; a lane keeps its best key and takes a
+  // step's largest key only if strictly greater, so among equal keys (same
+  // cell row, later column) the smallest j stays.  A cell of an earlier strip
+  // beats an equal H here: the key starts at best.v * 32 + 31.  Keys need
+  // H < 2^26 (the host rejects local pairs whose bound reaches it).
+  int bestkey = best.v * 32 + 31;
+  const int k32 = 32 * P.one;
   for (int t = 0; t < nsteps; ++t) {
     const int j = jlo + t - lane;
     const int j0 = jlo + t;  // lane 0's column
@@ -220,7 +235,7 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
       uint32_t tbw[WPS > 0 ? WPS : 1];
 #pragma unroll
       for (int w = 0; w < WPS; ++w) tbw[w] = 0;
-      int m = 0;  // column max of this lane's cells (local mode)
+      int mkey = 0;  // largest key of this lane's cells in this column (local mode)
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int Hl = Hc[k];
@@ -253,7 +268,7 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
             F = NEG;
           }
         }
-        if (LOCAL) m = max(m, H);
+        if (LOCAL) mkey = max(mkey, fmad(BAND ? max(H, 0) : H, k32, 31 - k));
         Hdg = Hl;
         Hc[k] = H;
         Ec[k] = E;
@@ -271,24 +286,13 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
         io.out(j, Hup, Fup);
         io.done_col(j, jlo, jhi);
       }
-      // Best cell (local): rows past M never exceed the lane's running best
-      // of valid cells (their diagonal scores are -128 and their gap values
-      // derive from valid cells minus a gap cost), so the unmasked column max
-      // only triggers the masked scan when a valid cell may qualify; the scan
-      // itself only looks at valid rows.
-      if (LOCAL && m > 0 && m >= best.v) {
-        int mv = 0, ii = INT_MAX;
-#pragma unroll
-        for (int k = R - 1; k >= 0; --k)
-          if (top + k <= M && Hc[k] >= mv && Hc[k] > 0) {
-            mv = Hc[k];
-            ii = top + k;
-          }
-        if (mv > 0 && (mv > best.v || (mv == best.v && ii < best.i))) {
-          best.v = mv;
-          best.i = ii;
-          best.j = j;
-        }
+      // rows past M stay below a valid cell of their lane already seen, so
+      // they never win; lanes wholly past M keep no best
+      if (LOCAL && top <= M && mkey > bestkey) {
+        bestkey = mkey;
+        best.v = mkey >> 5;
+        best.i = top + 31 - (mkey & 31);
+        best.j = j;
       }
     }
   }

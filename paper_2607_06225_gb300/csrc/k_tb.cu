@@ -50,6 +50,28 @@ __device__ __forceinline__ uint32_t full_bits(const uint32_t *tb, FullGeom &g, i
   return tb_nibble(w, k);
 }
 
+// The int16x2 tiled kernel's layout (unbanded): every strip has N + 63 steps
+// of R/8 words per lane; the high half of a lane's rows runs one step behind.
+struct PackGeom {
+  int R;
+  int64_t strip_words;
+};
+
+__device__ __forceinline__ uint32_t pack_bits(const uint32_t *tb, const PackGeom &g, int i, int j) {
+  const int HS = 32 * g.R, P = g.R >> 1;
+  const int s = (i - 1) / HS;
+  const int rho = (i - 1) - s * HS;
+  const int l = rho / g.R, kk = rho - l * g.R;
+  const int h = kk >= P ? 1 : 0, k = kk - h * P;
+  const int64_t t = (int64_t)j - 1 + 2 * l + h;
+  const int wps = g.R / 8;
+  const uint32_t w =
+      __ldg(tb + s * g.strip_words + (t * wps + h * (P / 8) + (k >> 3)) * 32 + l);
+  const int c = k & 7;
+  return (((w >> c) & 1u) << 3) | (((w >> (8 + c)) & 1u) << 2) | (((w >> (16 + c)) & 1u) << 1) |
+         ((w >> (24 + c)) & 1u);
+}
+
 struct Emitter {
   uint32_t *st;
   uint32_t n;
@@ -89,6 +111,7 @@ __global__ void k_walk(const WalkArgs a) {
 
   FullGeom g;
   XdGeom xg;
+  PackGeom pg{L.R, (int64_t)pack_strip_tb_words(1, N, L.R)};
   if (L.family == FAM_FULL && L.valid) {
     g.R = L.R;
     g.HS = 32 * L.R;
@@ -131,7 +154,9 @@ __global__ void k_walk(const WalkArgs a) {
         i = 0;
         break;
       }
-      const uint32_t nib = (L.family == FAM_FULL) ? full_bits(tb, g, i, j) : xd_bits(xg, i, j);
+      const uint32_t nib = (L.family == FAM_FULL)   ? full_bits(tb, g, i, j)
+                                 : (L.family == FAM_PACK) ? pack_bits(tb, pg, i, j)
+                                                          : xd_bits(xg, i, j);
       if (nib & TB_PF) {
         state = 2;
       } else if (nib & TB_PE) {
@@ -148,7 +173,9 @@ __global__ void k_walk(const WalkArgs a) {
         state = 0;
         continue;
       }
-      const uint32_t nib = (L.family == FAM_FULL) ? full_bits(tb, g, i, j) : xd_bits(xg, i, j);
+      const uint32_t nib = (L.family == FAM_FULL)   ? full_bits(tb, g, i, j)
+                                 : (L.family == FAM_PACK) ? pack_bits(tb, pg, i, j)
+                                                          : xd_bits(xg, i, j);
       em.put(OP_D, 1);
       if (nib & TB_EEXT) {
         v += e;
@@ -162,7 +189,9 @@ __global__ void k_walk(const WalkArgs a) {
         state = 0;
         continue;
       }
-      const uint32_t nib = (L.family == FAM_FULL) ? full_bits(tb, g, i, j) : xd_bits(xg, i, j);
+      const uint32_t nib = (L.family == FAM_FULL)   ? full_bits(tb, g, i, j)
+                                 : (L.family == FAM_PACK) ? pack_bits(tb, pg, i, j)
+                                                          : xd_bits(xg, i, j);
       em.put(OP_I, 1);
       if (nib & TB_FEXT) {
         v += e;

@@ -396,6 +396,10 @@ filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const 
   if (c->done_ev) cudaEventSynchronize(c->done_ev);
   c->ev_used = 0;
   c->spans.clear();
+  if (!score_range_ok(sp, M, N)) {
+    set_error("scores could exceed 2^28 (2^26 for local alignments) for these lengths and penalties");
+    return FILTR_ERR_UNSUPPORTED;
+  }
   rc = validate_seq(c, q, M, r, N, sp.alphabet, st);
   if (rc != FILTR_OK) return rc;
   if (sp.use_xdrop && M && N &&

@@ -97,12 +97,8 @@ filtr_status filtr_align_batch_noalloc(const filtr_params *params, uint32_t n_pa
               (size_t)((NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / (FULL_WARPS * sizeof(int2)) - 2));
     return FILTR_ERR_UNSUPPORTED;
   }
-  int smax = 0;
-  for (int t = 0; t < sp.alphabet * sp.alphabet; ++t) smax = std::max(smax, std::abs((int)sp.subst[t]));
-  const double bound = (double)smax * std::min(max_query_len, max_ref_len) + 3.0 * sp.o +
-                       (double)sp.e * ((double)max_query_len + max_ref_len);
-  if (bound >= (double)(1 << 28)) {
-    set_error("scores could exceed 2^28 for these lengths and penalties");
+  if (!score_range_ok(sp, max_query_len, max_ref_len)) {
+    set_error("scores could exceed 2^28 (2^26 for local alignments) for these lengths and penalties");
     return FILTR_ERR_UNSUPPORTED;
   }
   void *scratch = nullptr;

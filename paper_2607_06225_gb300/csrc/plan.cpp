@@ -15,6 +15,20 @@
 
 namespace filtr {
 
+// Kernel shapes of the unbanded / banded tiled path and their cost model:
+// a shape costs strips x (N + fill) steps x (per_row x rows + per_step) per
+// lane, with the coefficients in issue-slot units (defaults from the measured
+// instruction mix; filtr_autotune replaces them with timed values).
+const ShapeCost kDefaultShapeCost[SHAPE_TILED] = {
+    {32, 31, 16.0f, 30.0f, false}, {24, 31, 16.0f, 30.0f, false}, {16, 31, 16.0f, 30.0f, false},
+    {8, 31, 16.0f, 30.0f, false},  {32, 63, 6.5f, 40.0f, true},   {16, 63, 6.5f, 40.0f, true}};
+
+double shape_cost(const ShapeCost &c, uint32_t M, uint32_t N) {
+  const uint64_t hs = 32u * c.R;
+  const uint64_t strips = (M + hs - 1) / hs;
+  return (double)strips * (double)(N + c.fill) * ((double)c.per_row * c.R + c.per_step);
+}
+
 // Rows per lane: the tile height 32R whose padded work, strips x (N + 31 steps)
 // x (R + 2) (two cell-equivalents of per-step overhead), is smallest.
 int full_rows_per_lane(uint32_t M, uint32_t N) {
@@ -93,8 +107,10 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->cells_estimate = 0;
 
   // per pair: kernel shape key, cost bucket, traceback words (flat arrays)
-  // shape keys: 0..3 the tiled kernel with R = 32, 24, 16, 8 (wide tiles
-  // launch first); 4 the X-drop kernel
+  // shape keys: 0..3 the int32 tiled kernel with R = 32, 24, 16, 8; 4, 5 the
+  // int16x2 tiled kernel with R = 32, 16; 6 the X-drop kernel
+  const ShapeCost *costs = in.shape_cost ? in.shape_cost : kDefaultShapeCost;
+  const bool pack_ok = !sp.use_band && !sp.use_xdrop && sp.precision != FILTR_PREC_I32;
   std::vector<uint8_t> bucket(n), shape(n);
   std::vector<uint64_t> words(n);
   std::vector<uint32_t> cnt(64, 0);
@@ -120,12 +136,30 @@ bool make_plan(const PlanInput &in, Plan *P) {
     P->cells_estimate += cost;
     uint64_t w = 0;
     if (sp.use_xdrop) {
-      shape[p] = 4;
+      shape[p] = SHAPE_XDROP;
       if (sp.traceback) w = xd_tb_words(M, N, xw, in.xdrop_slots);
     } else {
-      const int R = full_rows_per_lane(M, N);
-      shape[p] = (uint8_t)(R == 32 ? 0 : R == 24 ? 1 : R == 16 ? 2 : 3);
-      if (sp.traceback) w = full_tb_words(M, N, R, sp);
+      // cheapest eligible shape; FILTR_PREC_I16X2 takes the packed kernel
+      // whenever the pair's score range fits it
+      const bool packable =
+          pack_ok && pack_bias(sp.mode, sp.o, sp.e, sp.smin, sp.smax, M, N) >= 0;
+      int best = -1;
+      double bc = 0;
+      for (int k = 0; k < SHAPE_TILED; ++k) {
+        if (costs[k].packed && !packable) continue;
+        if (sp.use_band && costs[k].packed) continue;
+        if (packable && sp.precision == FILTR_PREC_I16X2 && !costs[k].packed) continue;
+        const double c = shape_cost(costs[k], M, N);
+        if (best < 0 || c < bc) {
+          best = k;
+          bc = c;
+        }
+      }
+      shape[p] = (uint8_t)best;
+      const ShapeCost &sc = costs[best];
+      if (sp.traceback)
+        w = sc.packed ? (uint64_t)((M + 32u * sc.R - 1) / (32u * sc.R)) * pack_strip_tb_words(1, N, sc.R)
+                      : full_tb_words(M, N, sc.R, sp);
     }
     if (sp.traceback && w > in.tb_budget_words) {
       set_error("pair %u needs %llu traceback bytes, more than the workspace allows", p,
@@ -146,13 +180,13 @@ bool make_plan(const PlanInput &in, Plan *P) {
     if (shape[p] != 255) sorted[start[bucket[p]]++] = p;
 
   // waves: cut the cost order where the traceback budget is used up, then
-  // group each wave by kernel shape (stable counting sort over 5 keys)
+  // group each wave by kernel shape (stable counting sort over the keys)
   const uint64_t budget = sp.traceback ? in.tb_budget_words : ~0ull;
   size_t i = 0;
   while (i < sorted.size()) {
     size_t j = i;
     uint64_t used = 0;
-    uint32_t kc[5] = {0, 0, 0, 0, 0};
+    uint32_t kc[SHAPE_KEYS] = {};
     while (j < sorted.size() && used + words[sorted[j]] <= budget) {
       used += words[sorted[j]];
       kc[shape[sorted[j]]]++;
@@ -161,21 +195,26 @@ bool make_plan(const PlanInput &in, Plan *P) {
     Wave w;
     w.tb_words = used;
     const uint32_t wave_begin = (uint32_t)P->order.size();
-    uint32_t ks[5];
+    uint32_t ks[SHAPE_KEYS], kpos[SHAPE_KEYS];
     ks[0] = wave_begin;
-    for (int k = 1; k < 5; ++k) ks[k] = ks[k - 1] + kc[k - 1];
+    for (int k = 1; k < SHAPE_KEYS; ++k) ks[k] = ks[k - 1] + kc[k - 1];
     P->order.resize(wave_begin + (j - i));
-    uint32_t kpos[5] = {ks[0], ks[1], ks[2], ks[3], ks[4]};
+    for (int k = 0; k < SHAPE_KEYS; ++k) kpos[k] = ks[k];
     for (size_t t = i; t < j; ++t) P->order[kpos[shape[sorted[t]]]++] = sorted[t];
     // traceback offsets in wave order, per-pair layout, groups
     uint64_t off = 0;
-    static const uint8_t kR[4] = {32, 24, 16, 8};
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < SHAPE_KEYS; ++k) {
       if (!kc[k]) continue;
       Group g;
-      g.family = (k == 4) ? FAM_XDROP : FAM_FULL;
-      g.R = (k == 4) ? (uint8_t)in.xdrop_slots : kR[k];
-      g.warps = (k == 4) ? (uint8_t)xw : 1;
+      if (k == SHAPE_XDROP) {
+        g.family = FAM_XDROP;
+        g.R = (uint8_t)in.xdrop_slots;
+        g.warps = (uint8_t)xw;
+      } else {
+        g.family = costs[k].packed ? FAM_PACK : FAM_FULL;
+        g.R = (uint8_t)costs[k].R;
+        g.warps = 1;
+      }
       g.begin = ks[k];
       g.end = ks[k] + kc[k];
       for (uint32_t t = g.begin; t < g.end; ++t) {

@@ -33,6 +33,17 @@ struct Plan {
   uint64_t cells_estimate = 0;
 };
 
+// Tiled kernel shapes (int32 R = 32, 24, 16, 8; int16x2 R = 32, 16), then X-drop.
+enum : int { SHAPE_TILED = 6, SHAPE_XDROP = 6, SHAPE_KEYS = 7 };
+struct ShapeCost {
+  int R, fill;        // rows per lane; fill steps per strip (staircase)
+  float per_row;      // cost of one row (int32) or one packed register pair of rows / 2
+  float per_step;     // per-step overhead of a lane
+  bool packed;
+};
+extern const ShapeCost kDefaultShapeCost[SHAPE_TILED];
+double shape_cost(const ShapeCost &c, uint32_t M, uint32_t N);
+
 struct PlanInput {
   const ScoreParams *sp;
   uint32_t n;
@@ -40,6 +51,7 @@ struct PlanInput {
   uint64_t tb_budget_words;       // traceback words one wave may use
   int xdrop_slots;                // slots per lane of the X-drop kernel
   int xdrop_warps;                // first window width of X-drop pairs (warps)
+  const ShapeCost *shape_cost = nullptr;  // nullptr: kDefaultShapeCost
 };
 
 // Rows per lane of the tiled kernel for an M x N pair.

@@ -1,0 +1,224 @@
+// tune.cu -- filtr_autotune: measured costs of the tiled kernel shapes.
+//
+// The planner gives each pair the tiled shape (int32 tile with R = 32, 24, 16
+// or 8 rows per lane, or the int16x2 tile with R = 32 or 16) whose predicted
+// time, strips x (N + fill steps) x cost-per-warp-step, is smallest.  The
+// built-in costs come from instruction counts; this entry point replaces them
+// with the device time per warp step measured on this GPU for one recurrence
+// kind: each shape runs a batch that fills every resident warp slot three
+// times over with pairs of one full strip (32R query rows) by 512 reference
+// residues of random codes, and the cost is the launch's duration divided by
+// the warp steps it executed.  Shapes are bit-exact alternatives, so tuning
+// changes speed only.
+#include <cstring>
+#include <vector>
+
+#include "filtr_ctx.h"
+
+namespace filtr {
+namespace {
+
+constexpr int TUNE_N = 512;
+constexpr int TUNE_ROUNDS = 3;
+
+struct TuneCarve {
+  char *base;
+  size_t cap, used = 0;
+  template <class T>
+  T *take(size_t count) {
+    used = (used + 255) / 256 * 256;
+    T *p = reinterpret_cast<T *>(base + used);
+    used += count * sizeof(T);
+    return p;
+  }
+};
+
+uint64_t splitmix(uint64_t &s) {
+  uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Time one shape; returns ns per warp step, or a negative value if the
+// workspace cannot hold a batch that fills the device once.
+double time_shape(Ctx *c, const ScoreParams &sp, const ShapeCost &shape, cudaStream_t st,
+                  filtr_status *rc) {
+  *rc = FILTR_OK;
+  const int R = shape.R, M = 32 * R, N = TUNE_N;
+  const int bps = shape.packed ? c->pack_blocks_per_sm(R, sp) : c->full_blocks_per_sm(R, sp);
+  const int grid = c->sms * bps;
+  const int64_t slots = (int64_t)grid * FULL_WARPS;
+  uint64_t tbw = 0;
+  if (sp.traceback)
+    tbw = shape.packed ? pack_strip_tb_words(1, N, R) : full_tb_words(M, N, R, sp);
+  auto bytes_for = [&](int64_t B) {
+    return (size_t)B * (M + N) + (size_t)B * (16 + 8 + sizeof(filtr_result) + sizeof(FwdOut) +
+                                              sizeof(TbLayout)) +
+           (size_t)slots * (N + 2) * sizeof(int2) + (size_t)B * tbw * 4 + 64 * 256;
+  };
+  int64_t B = slots * TUNE_ROUNDS;
+  while (B > slots && bytes_for(B) > c->ws_bytes) B -= slots;
+  if (bytes_for(B) > c->ws_bytes) return -1.0;
+
+  TuneCarve cv{c->ws, c->ws_bytes};
+  uint8_t *d_codes = cv.take<uint8_t>((size_t)B * (M + N));
+  uint64_t *d_off = cv.take<uint64_t>(2 * B);
+  uint32_t *d_len = cv.take<uint32_t>(2 * B);
+  filtr_result *d_out = cv.take<filtr_result>(B);
+  FwdOut *d_fwd = cv.take<FwdOut>(B);
+  TbLayout *d_tbl = cv.take<TbLayout>(B);
+  uint32_t *d_counter = cv.take<uint32_t>(64);
+  int2 *d_strip = cv.take<int2>((size_t)slots * (N + 2));
+  uint32_t *d_tb = sp.traceback ? cv.take<uint32_t>((size_t)B * tbw) : nullptr;
+
+  // random codes, offsets (queries first, then references), lengths, layouts
+  std::vector<uint8_t> codes((size_t)B * (M + N));
+  uint64_t seed = 0x5eed0001ull + (uint64_t)R * 131 + (shape.packed ? 7 : 0);
+  for (size_t i = 0; i < codes.size(); i += 8) {
+    uint64_t v = splitmix(seed);
+    for (size_t b = 0; b < 8 && i + b < codes.size(); ++b)
+      codes[i + b] = (uint8_t)(((v >> (8 * b)) & 0xffu) % (uint64_t)sp.alphabet);
+  }
+  std::vector<uint64_t> offs(2 * B);
+  std::vector<uint32_t> lens(2 * B);
+  std::vector<TbLayout> tbl(B);
+  for (int64_t p = 0; p < B; ++p) {
+    offs[p] = (uint64_t)p * M;
+    offs[B + p] = (uint64_t)B * M + (uint64_t)p * N;
+    lens[p] = (uint32_t)M;
+    lens[B + p] = (uint32_t)N;
+    tbl[p] = TbLayout{};
+    tbl[p].off = (uint64_t)p * tbw;
+    tbl[p].family = shape.packed ? FAM_PACK : FAM_FULL;
+    tbl[p].R = (uint8_t)R;
+    tbl[p].warps = 1;
+    tbl[p].valid = sp.traceback ? 1 : 0;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_codes, codes.data(), codes.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_off, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_len, lens.data(), lens.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tbl, tbl.data(), tbl.size() * sizeof(TbLayout), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(e, "autotune upload");
+    return -1.0;
+  }
+  FullArgs fa{};
+  fa.b = BatchDev{d_codes, d_codes, d_off, d_off + B, d_len, d_len + B};
+  fa.sp = sp;
+  fa.order = nullptr;
+  fa.n_order = (uint32_t)B;
+  fa.out = d_out;
+  fa.fwd = d_fwd;
+  fa.tb = d_tb;
+  fa.tbl = d_tbl;
+  fa.strip_buf = d_strip;
+  fa.strip_stride = N + 2;
+  fa.max_n = 0;
+  fa.max_m = 0;
+  fa.ck = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = -1.0f;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // one warm-up, two timed
+    fa.counter = d_counter + 4 * rep;
+    e = cudaMemsetAsync(fa.counter, 0, 4, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess)
+      e = shape.packed ? launch_pack(fa, R, grid, st) : launch_full(fa, R, grid, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best_ms < 0 || ms < best_ms)) best_ms = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(e, "autotune launch");
+    return -1.0;
+  }
+  const double warp_steps = (double)B * (double)(N + shape.fill);
+  return (double)best_ms * 1e6 / warp_steps;
+}
+
+}  // namespace
+}  // namespace filtr
+
+using namespace filtr;
+
+extern "C" filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params,
+                                       filtr_tune_report *out) {
+  ScoreParams sp;
+  filtr_status rc = to_score_params(params, &sp);
+  if (rc != FILTR_OK) return rc;
+  if (!ctx) {
+    set_error("filtr_autotune: ctx is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  if (sp.use_xdrop) {
+    set_error("filtr_autotune: X-drop parameters have no tiled shapes to tune");
+    return FILTR_ERR_INVALID;
+  }
+  Ctx *c = reinterpret_cast<Ctx *>(ctx);
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (c->done_ev) {
+    e = cudaEventSynchronize(c->done_ev);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous call");
+  }
+  cudaStream_t st = nullptr;
+  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  std::vector<ShapeCost> tab(kDefaultShapeCost, kDefaultShapeCost + SHAPE_TILED);
+  if (out) memset(out, 0, sizeof *out);
+  double ns_k[SHAPE_TILED] = {};
+  bool any = false;
+  for (int k = 0; k < SHAPE_TILED; ++k) {
+    ShapeCost &s = tab[k];
+    if (out) {
+      out->rows_per_lane[k] = s.R;
+      out->packed[k] = s.packed ? 1 : 0;
+    }
+    const bool can_pack = !sp.use_band && sp.precision != FILTR_PREC_I32 &&
+                          pack_bias(sp.mode, sp.o, sp.e, sp.smin, sp.smax, 32 * s.R, TUNE_N) >= 0;
+    if (s.packed && !can_pack) continue;  // the planner never picks it for this kind
+    filtr_status trc = FILTR_OK;
+    const double ns = time_shape(c, sp, s, st, &trc);
+    if (trc != FILTR_OK) {
+      cudaStreamDestroy(st);
+      return trc;
+    }
+    if (ns <= 0) continue;  // keeps the built-in estimate
+    s.per_row = 0.0f;
+    s.per_step = (float)ns;
+    ns_k[k] = ns;
+    any = true;
+    if (out) out->ns_per_warp_step[k] = ns;
+  }
+  cudaStreamDestroy(st);
+  if (!any) {
+    set_error("filtr_autotune: the workspace cannot hold one calibration batch");
+    return FILTR_ERR_NOMEM;
+  }
+  // untimed shapes keep the model's cost scaled to the timed ones
+  double scale_num = 0, scale_den = 0;
+  for (int k = 0; k < SHAPE_TILED; ++k)
+    if (ns_k[k] > 0) {
+      const ShapeCost &d = kDefaultShapeCost[k];
+      scale_num += ns_k[k];
+      scale_den += d.per_row * d.R + d.per_step;
+    }
+  for (int k = 0; k < SHAPE_TILED; ++k)
+    if (ns_k[k] <= 0) {  // not timed
+      const double model = tab[k].per_row * tab[k].R + tab[k].per_step;
+      tab[k].per_row = 0.0f;
+      tab[k].per_step = (float)(scale_den > 0 ? model * scale_num / scale_den : model);
+    }
+  c->tuned[Ctx::tune_key(sp)] = tab;
+  return FILTR_OK;
+}
