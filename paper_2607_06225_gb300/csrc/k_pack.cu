@@ -214,7 +214,7 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
     uint32_t Hmup = fadd2(Hup, MOE, one);
     const bool edge = !(t >= 63 && t <= N - 1);  // warp-uniform
     const uint32_t KM = (actL ? 0x0000ffffu : 0u) | (actH ? 0xffff0000u : 0u);
-    uint32_t m = 0;
+    uint32_t m = 0, hprevk = 0;
     uint32_t accA = 0, accB = 0;
     uint32_t tbw[2 * G > 0 ? 2 * G : 1];
 
@@ -268,16 +268,21 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
         Hdg = Hc[k];
         Hmup = Hmn;
         Fup = F;
+        const uint32_t Hk = EDGE ? (H & KM) : H;  // inactive halves count as 0
+        if (LOCAL) {  // two registers fold into the step's max at once
+          if (k & 1)
+            m = __vimax3_u16x2(m, hprevk, Hk);
+          else
+            hprevk = Hk;
+        }
         if constexpr (EDGE) {
           Hc[k] = select_bits(KM, H, Hc[k]);
           if (AFFINE) Ec[k] = select_bits(KM, E, Ec[k]);
           Hm[k] = select_bits(KM, Hmn, Hm[k]);
-          if (LOCAL) m = max2(m, H & KM);
         } else {
           Hc[k] = H;
           if (AFFINE) Ec[k] = E;
           Hm[k] = Hmn;
-          if (LOCAL) m = max2(m, H);
         }
       }
     };

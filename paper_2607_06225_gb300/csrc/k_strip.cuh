@@ -235,7 +235,7 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
       uint32_t tbw[WPS > 0 ? WPS : 1];
 #pragma unroll
       for (int w = 0; w < WPS; ++w) tbw[w] = 0;
-      int mkey = 0;  // largest key of this lane's cells in this column (local mode)
+      int mkey = 0, kprev = 0;  // largest key of this lane's cells in this column (local mode)
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int Hl = Hc[k];
@@ -247,8 +247,7 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
           E = max(Hol, Eext);
           F = max(Hou, Fext);
           const int DE = max(D, E);
-          H = max(DE, F);
-          if (LOCAL) H = max(H, 0);
+          H = LOCAL ? __vimax3_s32(DE, F, 0) : max(DE, F);  // DPX: one ALU slot
           if (TB)
             tb_push4(tbw[k >> 3], fsub(D, E, mone), fsub(DE, F, mone), fsub(Hol, Eext, mone),
                      fsub(Hou, Fext, mone));
@@ -256,8 +255,7 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
           E = fadd(Hl, me, one);
           F = fadd(Hup, me, one);
           const int DE = max(D, E);
-          H = max(DE, F);
-          if (LOCAL) H = max(H, 0);
+          H = LOCAL ? __vimax3_s32(DE, F, 0) : max(DE, F);
           if (TB) tb_push4(tbw[k >> 3], fsub(D, E, mone), fsub(DE, F, mone), 0, 0);
         }
         if (BAND) {
@@ -268,7 +266,13 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
             F = NEG;
           }
         }
-        if (LOCAL) mkey = max(mkey, fmad(BAND ? max(H, 0) : H, k32, 31 - k));
+        if (LOCAL) {  // keys of two rows fold into the column's max at once
+          const int key = fmad(BAND ? max(H, 0) : H, k32, 31 - k);
+          if (k & 1)
+            mkey = __vimax3_s32(mkey, kprev, key);
+          else
+            kprev = key;
+        }
         Hdg = Hl;
         Hc[k] = H;
         Ec[k] = E;
