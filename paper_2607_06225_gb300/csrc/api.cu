@@ -376,7 +376,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
         if (sp.traceback) {  // a pair that outgrew its window is skipped by the walk
           wa.order = fa.order;
           wa.n_order = 1;
-          ce = launch_walk(wa, st);
+          ce = launch_walk_xd(wa, st);
           ++launches;
           if (ce != cudaSuccess) return false;
         }
@@ -413,7 +413,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     wa.order = d_ord;
     wa.n_order = cnt;
     ctx->span_begin(Ctx::PH_WALK, st);
-    ce = launch_walk(wa, st);
+    ce = sp.use_xdrop ? launch_walk_xd(wa, st) : launch_walk(wa, st);
     ctx->span_end(st);
     ++launches;
     return ce == cudaSuccess;

@@ -209,107 +209,213 @@ __global__ void k_walk(const WalkArgs a) {
   res->cigar_len = em.n;
 }
 
+// ---- warp walks over the antidiagonal (X-drop) layout ------------------------
+// The walk itself is serial, and one thread per pair spends it waiting on two
+// dependent loads per step (the window origin c_k, then the traceback word).
+// A warp prefetches instead: from the current cell (i0, j0) on antidiagonal
+// k0, lane L loads c of antidiagonal k0 - L and the words holding the slots a
+// path from (i0, j0) can reach there -- every step lowers i + j by 1 or 2 and
+// j by at most 1, so on k0 - L the path's column lies in [j0 - L, j0]: at most
+// 32 slots, 5 words.  Lane 0 then walks through shared memory until the path
+// leaves the 32 cached antidiagonals, and the warp refills.
+
+constexpr int XW = 5;  // cached words per antidiagonal
+
+struct WalkCore {
+  const uint8_t *q, *r;
+  const int8_t *subst;
+  int A, e, oe;
+  bool local;
+  int i, j, v, state;
+  Emitter em;
+};
+
+// Walks until the alignment's start is reached (returns true), or until the
+// current cell's antidiagonal is <= k_stop or < k_low (returns false, state
+// kept); the steps are those of k_walk.
+template <class Bits>
+__device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t k_stop,
+                                         int64_t k_low) {
+  for (;;) {
+    if (w.state == 0) {
+      if ((w.i == 0 && w.j == 0) || (w.local && w.v == 0)) return true;
+      if (w.i == 0) {
+        w.em.put(OP_D, (uint32_t)w.j);
+        w.j = 0;
+        return true;
+      }
+      if (w.j == 0) {
+        w.em.put(OP_I, (uint32_t)w.i);
+        w.i = 0;
+        return true;
+      }
+    }
+    const int64_t k = (int64_t)w.i + w.j;
+    if (k <= k_stop || k < k_low) return false;
+    if (w.state == 0) {
+      const uint32_t nib = bits(w.i, w.j);
+      if (nib & TB_PF) {
+        w.state = 2;
+      } else if (nib & TB_PE) {
+        w.state = 1;
+      } else {
+        const int qc = w.q[w.i - 1], rc = w.r[w.j - 1];
+        w.em.put(qc == rc ? OP_EQ : OP_X, 1);
+        w.v -= w.subst[qc * w.A + rc];
+        --w.i;
+        --w.j;
+      }
+    } else if (w.state == 1) {
+      if (w.j == 0) {
+        w.state = 0;
+        continue;
+      }
+      const uint32_t nib = bits(w.i, w.j);
+      w.em.put(OP_D, 1);
+      if (nib & TB_EEXT) {
+        w.v += w.e;
+      } else {
+        w.v += w.oe;
+        w.state = 0;
+      }
+      --w.j;
+    } else {
+      if (w.i == 0) {
+        w.state = 0;
+        continue;
+      }
+      const uint32_t nib = bits(w.i, w.j);
+      w.em.put(OP_I, 1);
+      if (nib & TB_FEXT) {
+        w.v += w.e;
+      } else {
+        w.v += w.oe;
+        w.state = 0;
+      }
+      --w.i;
+    }
+  }
+}
+
+struct XdCache {
+  uint32_t w[32 * XW];
+  int32_t c[32], b[32];
+};
+
+// All lanes: cache antidiagonals k0 - lane (those > k_min) around column j0.
+// Row of antidiagonal k in ck / tb: k - row_off.
+__device__ __forceinline__ void xd_fill(XdCache &C, const int32_t *ck, const uint32_t *tb, int wpk,
+                                        int64_t row_off, int64_t k0, int j0, int64_t k_min) {
+  const int lane = threadIdx.x & 31;
+  const int64_t kk = k0 - lane;
+  if (kk > k_min) {
+    const int64_t row = kk - row_off;
+    const int c = __ldg(ck + row);
+    const int plo = max(j0 - lane - c, 0), phi = j0 - c;
+    const int w0 = plo >> 3, w1 = min(phi >> 3, wpk - 1);
+#pragma unroll
+    for (int x = 0; x < XW; ++x)
+      if (w0 + x <= w1) C.w[lane * XW + x] = __ldg(tb + row * wpk + w0 + x);
+    C.c[lane] = c;
+    C.b[lane] = w0;
+  }
+  __syncwarp();
+}
+
+struct XdCacheBits {
+  const XdCache *C;
+  int64_t k0;
+  __device__ uint32_t operator()(int ii, int jj) const {
+    const int L = (int)(k0 - ((int64_t)ii + jj));
+    const int p = jj - C->c[L];
+    return tb_nibble(C->w[L * XW + (p >> 3) - C->b[L]], p);
+  }
+};
+
+// One warp per pair of a batched X-drop call (4 pairs per 128-thread block).
+__global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
+  __shared__ XdCache cache[4];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t t = blockIdx.x * 4 + wib;
+  if (t >= a.n_order) return;
+  const uint32_t p = a.order[t];
+  const FwdOut f = a.fwd[p];
+  const TbLayout L = a.tbl[p];
+  if (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED) {
+    if (lane == 0) a.out[p].cigar_len = 0;
+    return;
+  }
+  const int M = (int)a.b.q_len[p], N = (int)a.b.r_len[p];
+  const uint32_t *base = a.tb + L.off;
+  const int32_t *ck = reinterpret_cast<const int32_t *>(base);
+  const uint32_t *tbw = base + ((int64_t)M + N + 1);
+  const int wpk = xd_words_per_k(L.warps, L.R);
+  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
+             a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
+             Emitter{a.stage + a.stage_off[p], 0, -1, 0}};
+  XdCache &C = cache[wib];
+  bool done = false;
+  for (;;) {
+    const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
+    if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
+    const int64_t k0 = (int64_t)i0 + j0;
+    xd_fill(C, ck, tbw, wpk, 0, k0, j0, 0);
+    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    w.em.flush();
+    filtr_result *res = a.out + p;
+    res->q_begin = w.i;
+    res->r_begin = w.j;
+    res->cigar_len = w.em.n;
+  }
+}
+
 // Resumable walk over one recomputed segment (antidiagonals (k_start, k_end])
-// of a checkpointed X-drop traceback; one thread.  Stops when the walk leaves
+// of a checkpointed X-drop traceback; one warp.  Stops when the walk leaves
 // the segment (the next, earlier segment continues from the saved state) or
 // when the alignment's start is reached.
-__global__ void k_walk_segment(const WalkArgs a, const uint32_t *seg_tb, const int32_t *seg_ck,
-                               int k_start, int wpk, WalkState *ws) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  WalkState w = *ws;
-  if (w.done) return;
+__global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int32_t *seg_ck,
+                            int k_start, int wpk, WalkState *ws) {
+  __shared__ XdCache C;
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const WalkState st = *ws;
+  if (st.done) return;
   const uint32_t p = a.order[0];
-  const uint8_t *q = a.b.q_seq + a.b.q_off[p];
-  const uint8_t *r = a.b.r_seq + a.b.r_off[p];
-  const bool local = a.sp.mode == FILTR_LOCAL;
-  const int A = a.sp.alphabet, e = a.sp.e, oe = a.sp.o + a.sp.e;
-  Emitter em{a.stage + a.stage_off[p], w.n, w.cur, w.run};
-  int i = w.i, j = w.j, v = w.v, state = w.state;
+  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
+             a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, st.i, st.j, st.v, st.state,
+             Emitter{a.stage + a.stage_off[p], st.n, st.cur, st.run}};
   bool done = false;
-  auto bits = [&](int ii, int jj) -> uint32_t {
-    const int64_t row = (int64_t)ii + jj - k_start - 1;
-    const int pp = jj - seg_ck[row];
-    return tb_nibble(seg_tb[row * wpk + (pp >> 3)], pp);
-  };
   for (;;) {
-    if (state == 0) {
-      if ((i == 0 && j == 0) || (local && v == 0)) {
-        done = true;
-        break;
-      }
-      if (i == 0) {
-        em.put(OP_D, (uint32_t)j);
-        j = 0;
-        done = true;
-        break;
-      }
-      if (j == 0) {
-        em.put(OP_I, (uint32_t)i);
-        i = 0;
-        done = true;
-        break;
-      }
-    }
-    if (i + j <= k_start) break;  // the cell belongs to an earlier segment
-    if (state == 0) {
-      const uint32_t nib = bits(i, j);
-      if (nib & TB_PF) {
-        state = 2;
-      } else if (nib & TB_PE) {
-        state = 1;
-      } else {
-        const int qc = q[i - 1], rc = r[j - 1];
-        em.put(qc == rc ? OP_EQ : OP_X, 1);
-        v -= a.sp.subst[qc * A + rc];
-        --i;
-        --j;
-      }
-    } else if (state == 1) {
-      if (j == 0) {
-        state = 0;
-        continue;
-      }
-      const uint32_t nib = bits(i, j);
-      em.put(OP_D, 1);
-      if (nib & TB_EEXT) {
-        v += e;
-      } else {
-        v += oe;
-        state = 0;
-      }
-      --j;
-    } else {
-      if (i == 0) {
-        state = 0;
-        continue;
-      }
-      const uint32_t nib = bits(i, j);
-      em.put(OP_I, 1);
-      if (nib & TB_FEXT) {
-        v += e;
-      } else {
-        v += oe;
-        state = 0;
-      }
-      --i;
-    }
+    const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
+    const bool d = __shfl_sync(0xffffffffu, (int)done, 0) != 0;
+    const int64_t k0 = (int64_t)i0 + j0;
+    if (d || k0 <= k_start) break;
+    xd_fill(C, seg_ck, seg_tb, wpk, (int64_t)k_start + 1, k0, j0, k_start);
+    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, k_start, k0 - 31);
+    __syncwarp();
   }
-  if (done) {
-    em.flush();
-    filtr_result *res = a.out + p;
-    res->q_begin = i;
-    res->r_begin = j;
-    res->cigar_len = em.n;
+  if (lane == 0) {
+    if (done) {
+      w.em.flush();
+      filtr_result *res = a.out + p;
+      res->q_begin = w.i;
+      res->r_begin = w.j;
+      res->cigar_len = w.em.n;
+    }
+    WalkState o;
+    o.i = w.i;
+    o.j = w.j;
+    o.v = w.v;
+    o.state = w.state;
+    o.done = done ? 1 : 0;
+    o.n = w.em.n;
+    o.cur = w.em.cur;
+    o.run = w.em.run;
+    *ws = o;
   }
-  w.i = i;
-  w.j = j;
-  w.v = v;
-  w.state = state;
-  w.done = done ? 1 : 0;
-  w.n = em.n;
-  w.cur = em.cur;
-  w.run = em.run;
-  *ws = w;
 }
 
 // Exclusive scan of cigar_len (pair order) into offs; *total = sum.  One CTA.
@@ -371,9 +477,15 @@ cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_walk_xd(const WalkArgs &a, cudaStream_t s) {
+  if (a.n_order == 0) return cudaSuccess;
+  k_walk_xdw<<<(a.n_order + 3) / 4, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_walk_segment(const WalkArgs &a, const uint32_t *seg_tb, const int32_t *seg_ck,
                                 int k_start, int wpk, WalkState *st, cudaStream_t s) {
-  k_walk_segment<<<1, 32, 0, s>>>(a, seg_tb, seg_ck, k_start, wpk, st);
+  k_walk_segw<<<1, 32, 0, s>>>(a, seg_tb, seg_ck, k_start, wpk, st);
   return cudaGetLastError();
 }
 
