@@ -24,6 +24,12 @@ filtr_status filtr_test_long_timeout(filtr_ctx *ctx, const filtr_params *params,
  * the whole traceback would fit; interval 0 restores the automatic choice. */
 filtr_status filtr_test_set_checkpoint(filtr_ctx *ctx, int32_t interval);
 
+/* With on != 0, the checkpointed X-drop traceback skips its single pass (every
+ * segment's traceback kept in the workspace and walked once) and takes the
+ * path it otherwise falls back to when that pool runs out: a forward sweep
+ * without traceback, then each segment recomputed backwards and walked. */
+filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ struct Ctx {
   uint32_t last_launches = 0;
   int xdrop_warps0 = 1;       // first window width (warps) of X-drop pairs
   int ckpt_interval = 0;      // > 0: filtr_align_long always checkpoints X-drop tracebacks
+  bool ckpt_recompute = false;  // checkpointed traceback: recompute segments, no single pass
   // ordering of successive calls: the next call waits for this event, so the
   // workspace and the pinned staging are never reused while still in flight
   cudaEvent_t done_ev = nullptr;

@@ -235,6 +235,8 @@ cudaError_t launch_walk_segment(const WalkArgs &a, const uint32_t *seg_tb, const
 int xd_max_blocks_per_sm(int W, const ScoreParams &sp);
 cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s);
 cudaError_t launch_walk_xd(const WalkArgs &a, cudaStream_t s);  // X-drop pairs, a warp each
+cudaError_t launch_walk_pool(const WalkArgs &a, const uint32_t *pool, const int32_t *seg_ck_all,
+                             const uint64_t *seg_off, const int32_t *seg_w, int C, cudaStream_t s);
 cudaError_t launch_scan_offsets(const filtr_result *out, uint32_t n, uint64_t *offs,
                                 uint64_t *total, cudaStream_t s);
 cudaError_t launch_compact(const WalkArgs &a, uint32_t n, const uint64_t *offs, uint32_t *cigar,

@@ -302,20 +302,48 @@ struct XdCache {
   int32_t c[32], b[32];
 };
 
+// Where antidiagonal k's window origin and traceback row live.
+struct XdRows {  // one pair's own layout or a recomputed segment: row = k - row_off
+  const int32_t *ck;
+  const uint32_t *tb;
+  int wpk;
+  int64_t row_off;
+  __device__ void at(int64_t k, int &c, const uint32_t *&row, int &w) const {
+    const int64_t i = k - row_off;
+    c = __ldg(ck + i);
+    row = tb + i * wpk;
+    w = wpk;
+  }
+};
+struct XdPoolRows {  // single-pass segmented sweep: segment s = (k - 1) / C
+  const uint32_t *pool;
+  const int32_t *seg_ck_all;
+  const uint64_t *seg_off;
+  const int32_t *seg_w;
+  int C;
+  __device__ void at(int64_t k, int &c, const uint32_t *&row, int &w) const {
+    const int64_t s = (k - 1) / C, i = k - 1 - s * C;
+    w = xd_words_per_k(__ldg(seg_w + s), 8);
+    c = __ldg(seg_ck_all + s * C + i);
+    row = pool + __ldg(seg_off + s) + i * w;
+  }
+};
+
 // All lanes: cache antidiagonals k0 - lane (those > k_min) around column j0.
-// Row of antidiagonal k in ck / tb: k - row_off.
-__device__ __forceinline__ void xd_fill(XdCache &C, const int32_t *ck, const uint32_t *tb, int wpk,
-                                        int64_t row_off, int64_t k0, int j0, int64_t k_min) {
+template <class Rows>
+__device__ __forceinline__ void xd_fill(XdCache &C, const Rows &rows, int64_t k0, int j0,
+                                        int64_t k_min) {
   const int lane = threadIdx.x & 31;
   const int64_t kk = k0 - lane;
   if (kk > k_min) {
-    const int64_t row = kk - row_off;
-    const int c = __ldg(ck + row);
+    int c, wpk;
+    const uint32_t *row;
+    rows.at(kk, c, row, wpk);
     const int plo = max(j0 - lane - c, 0), phi = j0 - c;
     const int w0 = plo >> 3, w1 = min(phi >> 3, wpk - 1);
 #pragma unroll
     for (int x = 0; x < XW; ++x)
-      if (w0 + x <= w1) C.w[lane * XW + x] = __ldg(tb + row * wpk + w0 + x);
+      if (w0 + x <= w1) C.w[lane * XW + x] = __ldg(row + w0 + x);
     C.c[lane] = c;
     C.b[lane] = w0;
   }
@@ -359,7 +387,7 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
     const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
     if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
     const int64_t k0 = (int64_t)i0 + j0;
-    xd_fill(C, ck, tbw, wpk, 0, k0, j0, 0);
+    xd_fill(C, XdRows{ck, tbw, wpk, 0}, k0, j0, 0);
     if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31);
     __syncwarp();
   }
@@ -393,7 +421,7 @@ __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int3
     const bool d = __shfl_sync(0xffffffffu, (int)done, 0) != 0;
     const int64_t k0 = (int64_t)i0 + j0;
     if (d || k0 <= k_start) break;
-    xd_fill(C, seg_ck, seg_tb, wpk, (int64_t)k_start + 1, k0, j0, k_start);
+    xd_fill(C, XdRows{seg_ck, seg_tb, wpk, (int64_t)k_start + 1}, k0, j0, k_start);
     if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, k_start, k0 - 31);
     __syncwarp();
   }
@@ -415,6 +443,38 @@ __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int3
     o.cur = w.em.cur;
     o.run = w.em.run;
     *ws = o;
+  }
+}
+
+// The whole traceback of a single-pass segmented sweep; one warp.
+__global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
+  __shared__ XdCache C;
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const uint32_t p = a.order[0];
+  const FwdOut f = a.fwd[p];
+  if (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED) {
+    if (lane == 0) a.out[p].cigar_len = 0;
+    return;
+  }
+  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
+             a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
+             Emitter{a.stage + a.stage_off[p], 0, -1, 0}};
+  bool done = false;
+  for (;;) {
+    const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
+    if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
+    const int64_t k0 = (int64_t)i0 + j0;
+    xd_fill(C, rows, k0, j0, 0);
+    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    w.em.flush();
+    filtr_result *res = a.out + p;
+    res->q_begin = w.i;
+    res->r_begin = w.j;
+    res->cigar_len = w.em.n;
   }
 }
 
@@ -480,6 +540,12 @@ cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s) {
 cudaError_t launch_walk_xd(const WalkArgs &a, cudaStream_t s) {
   if (a.n_order == 0) return cudaSuccess;
   k_walk_xdw<<<(a.n_order + 3) / 4, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_pool(const WalkArgs &a, const uint32_t *pool, const int32_t *seg_ck_all,
+                             const uint64_t *seg_off, const int32_t *seg_w, int C, cudaStream_t s) {
+  k_walk_poolw<<<1, 32, 0, s>>>(a, XdPoolRows{pool, seg_ck_all, seg_off, seg_w, C});
   return cudaGetLastError();
 }
 

@@ -43,6 +43,7 @@ struct alignas(16) XdShared {
   Edge first[2][W];      // slot 0 of the warp (lane 0) after each antidiagonal
   Edge last[2][W];       // slot 31*S + S-1 of the warp (lane 31)
   uint32_t pair;         // work item of the group
+  unsigned long long rsv;  // traceback rows reserved by the group (checkpointed sweep)
 };
 
 __device__ __forceinline__ int code_at(const uint32_t (&w)[2], int s) {
@@ -178,10 +179,28 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     }
     uint32_t *tbp = nullptr;
     int32_t *ckp = nullptr;
+    unsigned long long rsv = 0;
     if (TB) {
       if (ckmode == 2) {  // rows indexed by k - k_start - 1
         ckp = ck->seg_ck;
         tbp = ck->seg_tb;
+      } else if (ckmode == 3) {  // rows from the pool, indexed by k - k_start - 1
+        const unsigned long long need = (unsigned long long)ck->C * (WIN / 8);
+        if (W == 1) {
+          if (lane == 0) rsv = atomicAdd(ck->pool_next, need);
+          rsv = __shfl_sync(FULLMASK, rsv, 0);
+        } else {
+          if (threadIdx.x == 0) sh.rsv = atomicAdd(ck->pool_next, need);
+          __syncthreads();
+          rsv = sh.rsv;
+          __syncthreads();
+        }
+        if (rsv + need > ck->pool_words) {  // every thread sees the same rsv
+          if (tid == 0) ck->flags[0] = 2;
+          break;
+        }
+        ckp = ck->seg_ck_all + (int64_t)seg * ck->C;
+        tbp = ck->pool + rsv;
       } else {
         ckp = reinterpret_cast<int32_t *>(a.tb + a.tbl[p].off);
         tbp = a.tb + a.tbl[p].off + (uint64_t)(M + N + 1);
@@ -213,7 +232,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     int cornerH = INT_MIN;  // set by the thread owning (M, N) on antidiagonal M + N
     // residue codes of this thread's slots at the current origin: q[i-1], r[j-1]
     uint32_t qw[2] = {0, 0}, rw[2] = {0, 0};
-    if (TB && tid == 0 && ckmode != 2) ckp[0] = 0;
+    if (TB && tid == 0 && ckmode == 0) ckp[0] = 0;
     int k_first = 1, k_last = M + N;
     if (ckmode >= 2) {
       // resume from the checkpoint of antidiagonal k_start
@@ -370,7 +389,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         F1[s] = Fn[s];
       }
       if (TB) {
-        const int64_t row = (ckmode == 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
+        const int64_t row = (ckmode >= 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
         tbp[row * (WIN / 8) + tid] = nibs;
         if (tid == 0) ckp[row] = cn;
       }
@@ -516,6 +535,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         rec[XCK_BJ] = bj;
         rec[XCK_CELLS_LO] = (int32_t)(uint32_t)cells;
         rec[XCK_CELLS_HI] = (int32_t)(uint32_t)(cells >> 32);
+        if (TB) {
+          ck->seg_off[seg] = rsv;
+          ck->seg_w[seg] = W;
+        }
         ck->flags[1 + seg] = W;
       }
       gsync();
@@ -523,6 +546,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     }
     if (tid == 0 && ckmode != 2) {
       if (ckmode == 3) {  // the sweep ends in this segment (or outgrew the widest window)
+        if (TB && status != FILTR_ST_TOO_WIDE) {
+          ck->seg_off[seg] = rsv;
+          ck->seg_w[seg] = W;
+        }
         ck->flags[0] = 1;
         if (status != FILTR_ST_TOO_WIDE) ck->flags[1 + seg] = W;
       }

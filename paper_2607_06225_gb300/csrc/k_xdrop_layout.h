@@ -32,7 +32,17 @@ struct XdCkpt {
   int k_start, k_end;  // the segment (k_start, k_end]
   uint32_t *seg_tb;    // mode 2: (k_end - k_start) rows of WIN/8 words
   int32_t *seg_ck;     // mode 2: window origin of each recomputed antidiagonal
-  int32_t *flags;      // mode 3: [0] sweep finished, [1 + s] width that completed segment s
+  int32_t *flags;      // mode 3: [0] sweep finished (2: traceback pool exhausted),
+                       //         [1 + s] width that completed segment s
+  // mode 3 with traceback (single pass): each attempt at a segment reserves
+  // C rows of its window's words from the pool; the attempt that completes
+  // the segment records where they are and at which width
+  uint32_t *pool;
+  uint64_t pool_words;
+  unsigned long long *pool_next;
+  int32_t *seg_ck_all;  // window origin of every antidiagonal, C per segment
+  uint64_t *seg_off;    // per segment: first pool word of its rows
+  int32_t *seg_w;       // per segment: its width in warps
 };
 // checkpoint record: a header, then H, E, F of antidiagonal k and H of k - 1
 // for every slot of the widest window (thread t's 4*S values at 16 + t*4*S);

@@ -210,9 +210,11 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   static const int kLadder[] = {1, 2, 4, 8, 16, XD_MAX_WARPS};
   Carve cv{c->ws, c->ws_bytes};
   int32_t *ck_buf = cv.take<int32_t>((size_t)(nseg + 1) * xd_ckpt_stride());
-  uint32_t *seg_tb =
-      sp.traceback ? cv.take<uint32_t>((size_t)C * xd_words_per_k(XD_MAX_WARPS, 8)) : nullptr;
-  int32_t *seg_ck = sp.traceback ? cv.take<int32_t>(C) : nullptr;
+  const bool single = sp.traceback && !c->ckpt_recompute;
+  uint32_t *seg_tb = (sp.traceback && !single)
+                         ? cv.take<uint32_t>((size_t)C * xd_words_per_k(XD_MAX_WARPS, 8))
+                         : nullptr;
+  int32_t *seg_ck = (sp.traceback && !single) ? cv.take<int32_t>(C) : nullptr;
   XdCkpt *d_ck = cv.take<XdCkpt>(2 * nseg + 1);
   int32_t *d_flags = cv.take<int32_t>(nseg + 1);
   WalkState *d_ws = cv.take<WalkState>(1);
@@ -222,10 +224,23 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   uint64_t *d_misc = cv.take<uint64_t>(8);   // stage_off, offsets, CIGAR offset
   uint32_t *d_ovf = cv.take<uint32_t>(4);
   uint32_t *d_stage = sp.traceback ? cv.take<uint32_t>((size_t)M + N + 1) : nullptr;
+  // single pass: every segment's traceback rows kept in a pool (the rest of
+  // the workspace), walked once at the end; if the pool runs out the sweep
+  // stops and runs again without traceback, with the segments recomputed
+  int32_t *seg_ck_all = single ? cv.take<int32_t>((size_t)nseg * C) : nullptr;
+  uint64_t *seg_off = single ? cv.take<uint64_t>(nseg) : nullptr;
+  int32_t *seg_wd = single ? cv.take<int32_t>(nseg) : nullptr;
+  unsigned long long *pool_next = single ? cv.take<unsigned long long>(4) : nullptr;
   if (cv.used > c->ws_bytes) {
     set_error("checkpointed traceback needs %zu workspace bytes; the context has %zu", cv.used,
               c->ws_bytes);
     return FILTR_ERR_NOMEM;
+  }
+  uint32_t *pool = nullptr;
+  uint64_t pool_words = 0;
+  if (single) {
+    pool = cv.take<uint32_t>(0);
+    pool_words = cv.used < c->ws_bytes ? (c->ws_bytes - cv.used) / 4 : 0;
   }
   // host staging: the one-pair batch, the segment descriptors, the flags
   const size_t desc_off = 4096;
@@ -240,9 +255,11 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   memcpy(h + 128, misc, sizeof misc);
   XdCkpt *hk = reinterpret_cast<XdCkpt *>(h + desc_off);
   for (int64_t sgi = 0; sgi < nseg; ++sgi)
-    hk[sgi] = XdCkpt{3, C, ck_buf, (int)(sgi * C), (int)std::min<int64_t>((sgi + 1) * C, K),
-                     nullptr, nullptr, d_flags};
+    hk[sgi] = XdCkpt{3,      C,          ck_buf,    (int)(sgi * C),
+                     (int)std::min<int64_t>((sgi + 1) * C, K), nullptr, nullptr, d_flags,
+                     pool,   pool_words, pool_next, seg_ck_all, seg_off, seg_wd};
   cudaError_t e = cudaMemcpyAsync(d_one, h, sizeof one, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && single) e = cudaMemsetAsync(pool_next, 0, 8, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_tbl, h + 64, sizeof L, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_misc, h + 128, sizeof misc, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -255,7 +272,7 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   FullArgs fa;
   fa.b = b;
   fa.sp = sp;
-  fa.sp.traceback = 0;  // the forward sweep keeps checkpoints, not traceback bits
+  fa.sp.traceback = single ? 1 : 0;  // else the forward sweep keeps checkpoints only
   fa.order = d_one;
   fa.n_order = 1;
   fa.counter = nullptr;  // unused with checkpoints
@@ -289,7 +306,44 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward sweep");
   const FwdOut f = *hf;
   c->last_launches = launches;
+  if (single && hflags[0] == 2) {  // the pool ran out: recompute the segments instead
+    const bool saved = c->ckpt_recompute;
+    c->ckpt_recompute = true;
+    const filtr_status rc = run_xdrop_ckpt(c, sp, params, q, M, r, N, out, cigar, cap, st, C);
+    c->ckpt_recompute = saved;
+    return rc;
+  }
   if (!sp.traceback || (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED)) return FILTR_OK;
+  WalkArgs wp;
+  wp.b = b;
+  wp.sp = sp;
+  wp.order = d_one;
+  wp.n_order = 1;
+  wp.out = out;
+  wp.fwd = d_fwd;
+  wp.tb = nullptr;
+  wp.tbl = d_tbl;
+  wp.stage = d_stage;
+  wp.stage_off = d_misc;
+  if (single) {  // one walk over the kept traceback
+    c->span_begin(Ctx::PH_WALK, st);
+    e = launch_walk_pool(wp, pool, seg_ck_all, seg_off, seg_wd, C, st);
+    c->span_end(st);
+    uint64_t *d_offs = d_misc + 4;
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_offs, 0, 8, st);
+    if (e == cudaSuccess) e = launch_compact(wp, 1, d_offs, cigar, cap, out, st);
+    filtr_result *hr = reinterpret_cast<filtr_result *>(h + 1024);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr, out, sizeof(filtr_result), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "single-pass traceback");
+    c->last_launches = launches + 2;
+    c->last_waves = 1;
+    if (hr->cigar_len > cap) {
+      set_error("the CIGAR needs %u ops, cigar_cap is %llu", hr->cigar_len, (unsigned long long)cap);
+      return FILTR_ERR_CIGAR_CAP;
+    }
+    return FILTR_OK;
+  }
   // backward: one segment at a time, from the end cell's antidiagonal down to
   // 0, each recomputed at the width that completed it going forward
   WalkState w0{f.end_i, f.end_j, f.score, 0, 0, -1, 0, 0};
@@ -445,6 +499,15 @@ filtr_status filtr_test_set_checkpoint(filtr_ctx *ctx, int32_t interval) {
     return FILTR_ERR_INVALID;
   }
   reinterpret_cast<Ctx *>(ctx)->ckpt_interval = interval;
+  return FILTR_OK;
+}
+
+filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on) {
+  if (!ctx) {
+    set_error("filtr_test_force_recompute: ctx is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  reinterpret_cast<Ctx *>(ctx)->ckpt_recompute = on != 0;
   return FILTR_OK;
 }
 

@@ -117,10 +117,12 @@ def test_strip_wait_timeout_and_recovery(F, ctx):
 
 
 @pytest.mark.parametrize("interval", [7, 64, 1000])
-def test_checkpointed_traceback(F, ctx, interval):
-    """Forcing the checkpointed X-drop traceback (state kept every `interval`
-    antidiagonals, segments recomputed backwards) gives the oracle's result,
-    including pairs that end DROPPED and local alignments."""
+@pytest.mark.parametrize("recompute", [False, True])
+def test_checkpointed_traceback(F, ctx, interval, recompute):
+    """Forcing the segmented X-drop sweep (state kept every `interval`
+    antidiagonals) gives the oracle's result, including pairs that end DROPPED
+    and local alignments, both in its single pass (every segment's traceback
+    kept and walked once) and with the segments recomputed backwards."""
     cases = []
     b = synth.long_pair(length=6000, seg=150, seed=11, xdrop=120)
     cases.append((b.pair(0), b.subst, dict(b.scoring)))
@@ -132,8 +134,30 @@ def test_checkpointed_traceback(F, ctx, interval):
     cases.append(((q, r), DNA_S, dict(mode="local", affine=True, gap_open=4, gap_extend=2, xdrop=60,
                                        traceback=True)))
     assert F.lib().filtr_test_set_checkpoint(ctx.handle, interval) == 0
+    assert F.lib().filtr_test_force_recompute(ctx.handle, int(recompute)) == 0
     try:
         for (qq, rr), S, sc in cases:
             check_pair(F, ctx, qq, rr, S, sc)
     finally:
         F.lib().filtr_test_set_checkpoint(ctx.handle, 0)
+        F.lib().filtr_test_force_recompute(ctx.handle, 0)
+
+
+def test_traceback_pool_exhausted_falls_back(F, ctx):
+    """A context too small to keep a ~200 kb X-drop pair's whole traceback runs
+    out of pool in the single pass and falls back to recomputing the segments;
+    the result equals the single pass's in a large context."""
+    b = synth.long_pair(length=200_000, seg=1000, seed=17, xdrop=400)
+    q, r = b.pair(0)
+    params = F.make_params(b.subst, **b.scoring)
+    big, cig_big, rc = F.align_long(ctx, params, q, r)
+    assert rc == 0, F.last_error()
+    small = F.Context(0, 40 << 20)
+    try:
+        res, cig, rc = F.align_long(small, params, q, r)
+        assert rc == 0, F.last_error()
+    finally:
+        small.close()
+    assert np.array_equal(res, big)
+    assert np.array_equal(cig, cig_big)
+    assert int(res["status"]) in (0, 1)
