@@ -249,7 +249,7 @@ filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
 
 /* Autotuning of the tiled kernel shapes (the paper leaves autotuning to
- * future work, Sec. 12).  Times every tiled shape -- the int32 tile with 32,
+ * future work, Sec. 11).  Times every tiled shape -- the int32 tile with 32,
  * 24, 16 or 8 rows per lane and, where the parameters allow it, the int16x2
  * tile with 32 or 16 -- on calibration batches that fill every resident warp
  * slot of the device three times (pairs of one full strip of query rows by 512

@@ -34,7 +34,7 @@ class Params(C.Structure):
         ("gap_extend", C.c_int64), ("alphabet", C.c_int32), ("subst", C.POINTER(C.c_int8)),
         ("use_band", C.c_int32), ("band_literal", C.c_int32), ("band", C.c_int64),
         ("use_xdrop", C.c_int32), ("xdrop", C.c_int64), ("traceback", C.c_int32),
-        ("order", C.c_int32),
+        ("order", C.c_int32), ("zdrop", C.c_int32),
     ]
 
 
@@ -78,7 +78,7 @@ def lib():
 
 
 def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
-                band_literal=False, xdrop=None, traceback=True, order=0, **_ignored):
+                band_literal=False, xdrop=None, zdrop=None, traceback=True, order=0, **_ignored):
     s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
     a = int(s.shape[0])
     p = Params()
@@ -91,8 +91,12 @@ def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, ban
     p.use_band = 0 if band is None else 1
     p.band_literal = 1 if band_literal else 0
     p.band = 0 if band is None else int(band)
-    p.use_xdrop = 0 if xdrop is None else 1
-    p.xdrop = 0 if xdrop is None else (INF if xdrop == INF else int(xdrop))
+    if xdrop is not None and zdrop is not None:
+        raise ValueError("xdrop and zdrop are exclusive")
+    thr = xdrop if zdrop is None else zdrop
+    p.use_xdrop = 0 if thr is None else 1
+    p.xdrop = 0 if thr is None else (INF if thr == INF else int(thr))
+    p.zdrop = 0 if zdrop is None else 1
     p.traceback = 1 if traceback else 0
     p.order = int(order)
     p._keep = s  # keep the table alive

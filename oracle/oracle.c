@@ -254,8 +254,10 @@ static int run_static(ctx_t *c, int64_t *cells) {
  * (0,0), never pruned.  For k >= 1 the candidate diagonals are
  * [lo_{k-1} - 1, hi_{k-1} + 1] (same parity as k) inside the matrix and the
  * band; a cell is pruned (H = E = F = invalid) when its H is invalid or
- * H < best_{k-1} - X.  The sweep stops after the first antidiagonal without an
- * unpruned cell. */
+ * H < best_{k-1} - X.  Z-drop (zdrop = 1, Z = xdrop) prunes when
+ * best_{k-1} - H > Z + |d - dbest_{k-1}|, dbest_{k-1} the diagonal of
+ * antidiagonal k-1's best cell (ties: smallest i, i.e. largest d).  The sweep
+ * stops after the first antidiagonal without an unpruned cell. */
 static int run_xdrop(ctx_t *c, int64_t *cells, int64_t *last_k) {
   const int64_t X = c->p->xdrop;
   const int no_thresh = (X == INT64_MAX);
@@ -267,7 +269,8 @@ static int run_xdrop(ctx_t *c, int64_t *cells, int64_t *last_k) {
   eval_cell(c, 0, 0, &tmp, &ch);
   *o = tmp;
   o->alive = 1;
-  int64_t best = 0, lo = 0, hi = 0;
+  int64_t best = 0, lo = 0, hi = 0, dbest = 0;
+  const int zdrop = c->p->zdrop != 0;
   *cells = 0;
   *last_k = 0;
   for (int64_t k = 1; k <= K; ++k) {
@@ -278,18 +281,22 @@ static int run_xdrop(ctx_t *c, int64_t *cells, int64_t *last_k) {
     if (store_push(&c->st, k, dl, dh)) return -1;
     *last_k = k;
     int any = 0;
-    int64_t nbest = 0, nlo = 0, nhi = 0;
+    int64_t nbest = 0, nlo = 0, nhi = 0, ndbest = 0;
     for (int64_t d = dl; d <= dh; d += 2) {
       int64_t i = (k - d) / 2, j = (k + d) / 2;
       cell_t *x = get(c, i, j);
       eval_cell(c, i, j, &tmp, &ch);
-      int alive = tmp.vH && (no_thresh || tmp.H >= best - X);
+      const int64_t dist = zdrop ? (d > dbest ? d - dbest : dbest - d) : 0;
+      int alive = tmp.vH && (no_thresh || tmp.H >= best - X - dist);
       if (!alive) memset(&tmp, 0, sizeof tmp);
       *x = tmp;
       x->alive = (uint8_t)alive;
       if (i >= 1 && j >= 1) ++*cells;
       if (alive) {
-        if (!any || tmp.H > nbest) nbest = tmp.H;
+        if (!any || tmp.H > nbest || (tmp.H == nbest && d > ndbest)) {
+          nbest = tmp.H;
+          ndbest = d;
+        }
         if (!any || d < nlo) nlo = d;
         if (!any || d > nhi) nhi = d;
         any = 1;
@@ -297,6 +304,7 @@ static int run_xdrop(ctx_t *c, int64_t *cells, int64_t *last_k) {
     }
     if (!any) break;
     best = nbest;
+    dbest = ndbest;
     lo = nlo;
     hi = nhi;
   }

@@ -19,6 +19,10 @@
  *     antidiagonal k is pruned when H < best(k-1) - X, best(k-1) being the
  *     largest unpruned H on antidiagonal k-1; the next antidiagonal covers the
  *     diagonals [lo_k - 1, hi_k + 1] of the unpruned cells of k;
+ *   - Z-drop (Sec. 9.3's pruning condition): as X-drop, but a cell on antidiagonal
+ *     k is pruned when best(k-1) - H > Z + |diag(i,j) - diag_best(k-1)|,
+ *     diag_best(k-1) being the diagonal of antidiagonal k-1's best cell (the
+ *     largest H; among equal H the smallest i, i.e. the largest diagonal);
  *   - traceback with fixed tie-breaks, emitted as a SAM/BAM CIGAR.
  * Parity of the tie-break order and of the X-drop domain reading is pinned only
  * by hand-worked examples (the paper does not fix them).
@@ -45,6 +49,7 @@ typedef struct {
   int64_t xdrop;       /* X >= 0; INT64_MAX means no threshold */
   int32_t traceback;   /* 1: emit CIGAR and begin coordinates */
   int32_t order;       /* evaluation order for unpruned / banded runs: 0 row-major, 1 antidiagonal */
+  int32_t zdrop;       /* with use_xdrop: 1 = Z-drop with Z = xdrop (distance term added) */
 } orc_params;
 
 typedef struct {

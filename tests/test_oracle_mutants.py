@@ -1,8 +1,9 @@
 """Plants plausible mistakes in copies of the oracle (on the CPU) and checks that
 the pin suite (test_oracle_pins.py) rejects every one of them: a transposed
 operand, a dropped term, a wrong sign, each tie-break flipped, the X-drop rule
-and domain altered, the band edge shifted, the CIGAR op table swapped and the
-cell counter widened."""
+and domain altered, the Z-drop distance term dropped, signed or anchored, its
+best-diagonal tie flipped, the band edge shifted, the CIGAR op table swapped and
+the cell counter widened."""
 import os
 import shutil
 import subprocess
@@ -30,6 +31,11 @@ MUTANTS = {
     "diag_op_swapped": ("(c->q[i - 1] == c->r[j - 1]) ? ORC_OP_EQ : ORC_OP_X",
                         "(c->q[i - 1] != c->r[j - 1]) ? ORC_OP_EQ : ORC_OP_X"),
     "E_emits_I": ("mv[n++] = ORC_OP_D;", "mv[n++] = ORC_OP_I;"),
+    "zdrop_no_distance": ("const int64_t dist = zdrop ? (d > dbest ? d - dbest : dbest - d) : 0;",
+                          "const int64_t dist = 0;"),
+    "zdrop_signed_distance": ("(d > dbest ? d - dbest : dbest - d)", "(d - dbest)"),
+    "zdrop_tie_smallest_i_flipped": ("(tmp.H == nbest && d > ndbest)", "(tmp.H == nbest && d < ndbest)"),
+    "zdrop_best_diagonal_frozen": ("    dbest = ndbest;\n", "\n"),
     "cells_count_boundary": ("      if (i >= 1 && j >= 1) ++*cells;\n      if (alive)",
                              "      ++*cells;\n      if (alive)"),
 }

@@ -170,6 +170,21 @@ def test_xdrop_infinite_equals_unpruned(mode, oracle_lib):
         assert np.array_equal(x["cigar"], full["cigar"])
 
 
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_zdrop_infinite_equals_unpruned(mode, oracle_lib):
+    """Sec. 9.3 Z-drop with Z = infinity prunes nothing: the unpruned result."""
+    rng = np.random.default_rng(19)
+    for _ in range(25):
+        M, N = int(rng.integers(0, 25)), int(rng.integers(0, 25))
+        q = rng.integers(0, 4, size=M).astype(np.uint8)
+        r = rng.integers(0, 4, size=N).astype(np.uint8)
+        full = oracle.align(q, r, DNA_S, mode=mode, gap_open=4, gap_extend=2)
+        z = oracle.align(q, r, DNA_S, mode=mode, gap_open=4, gap_extend=2, zdrop=oracle.INF)
+        for key in ("score", "q_begin", "q_end", "r_begin", "r_end", "status", "cells"):
+            assert z[key] == full[key]
+        assert np.array_equal(z["cigar"], full["cigar"])
+
+
 @pytest.mark.parametrize("band", [None, 3])
 @pytest.mark.parametrize("mode", ["global", "local"])
 def test_schedule_invariance(mode, band, oracle_lib):
@@ -213,7 +228,7 @@ def test_hand_worked(case, oracle_lib):
     S = np.full((4, 4), case["mismatch"], np.int8)
     np.fill_diagonal(S, case["match"])
     kw = dict(mode=case["mode"], affine=case["affine"], gap_open=case["gap_open"],
-              gap_extend=case["gap_extend"], xdrop=case.get("xdrop"))
+              gap_extend=case["gap_extend"], xdrop=case.get("xdrop"), zdrop=case.get("zdrop"))
     res = oracle.align(q, r, S, **kw)
     assert res["score"] == case["score"]
     assert res["status"] == case["status"]
