@@ -31,6 +31,9 @@
  *     cells of k; the sweep stops at the first antidiagonal with no unpruned
  *     cell.  A global alignment that does not reach (M,N) reports
  *     FILTR_ST_DROPPED with the best unpruned cell as its end.
+ *   - Z-drop (Sec. 9.3): as X-drop, with a cell pruned when
+ *     best(k-1) - H > xdrop + |(j - i) - d_best(k-1)|, d_best(k-1) the diagonal
+ *     of antidiagonal k-1's best cell (largest H, then smallest i).
  *   - CIGAR ops are BAM uint32 words  (len << 4) | op  with op 7 '=', 8 'X',
  *     1 'I', 2 'D'.
  *   - Errors: every function returns a filtr_status; nothing aborts and no
@@ -61,7 +64,8 @@ typedef enum {
 
 enum { FILTR_GLOBAL = 0, FILTR_LOCAL = 1 };
 enum { FILTR_ALPHA_DNA = 4, FILTR_ALPHA_PROTEIN = 20 };
-enum { FILTR_PRUNE_BAND = 1u, FILTR_PRUNE_XDROP = 2u, FILTR_PRUNE_BAND_LITERAL = 4u };
+enum { FILTR_PRUNE_BAND = 1u, FILTR_PRUNE_XDROP = 2u, FILTR_PRUNE_BAND_LITERAL = 4u,
+       FILTR_PRUNE_ZDROP = 8u };  /* XDROP and ZDROP exclude each other */
 enum { FILTR_PREC_AUTO = 0, FILTR_PREC_I32 = 1, FILTR_PREC_I16X2 = 2 };
 enum { FILTR_XDROP_INF = 0x7fffffff };
 
@@ -85,7 +89,7 @@ typedef struct {
                             copied during the call; need not be symmetric */
   uint32_t prune;        /* OR of FILTR_PRUNE_* (0 = full matrix) */
   int32_t band;          /* band half-width >= 0 (used with FILTR_PRUNE_BAND) */
-  int32_t xdrop;         /* X >= 0, or FILTR_XDROP_INF (used with FILTR_PRUNE_XDROP) */
+  int32_t xdrop;         /* X (or Z) >= 0, or FILTR_XDROP_INF (with FILTR_PRUNE_XDROP / ZDROP) */
   int32_t traceback;     /* 0: score and end cell only; 1: also begin cell and CIGAR */
   int32_t precision;     /* FILTR_PREC_*: a speed choice only; results are identical */
 } filtr_params;

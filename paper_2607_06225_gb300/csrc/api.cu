@@ -57,12 +57,18 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
     set_error("subst is NULL");
     return FILTR_ERR_INVALID;
   }
-  if (p->prune & ~(uint32_t)(FILTR_PRUNE_BAND | FILTR_PRUNE_XDROP | FILTR_PRUNE_BAND_LITERAL)) {
+  if (p->prune & ~(uint32_t)(FILTR_PRUNE_BAND | FILTR_PRUNE_XDROP | FILTR_PRUNE_BAND_LITERAL |
+                             FILTR_PRUNE_ZDROP)) {
     set_error("unknown prune bits 0x%x", p->prune);
     return FILTR_ERR_INVALID;
   }
   const bool band = (p->prune & (FILTR_PRUNE_BAND | FILTR_PRUNE_BAND_LITERAL)) != 0;
-  const bool xd = (p->prune & FILTR_PRUNE_XDROP) != 0;
+  const bool zd = (p->prune & FILTR_PRUNE_ZDROP) != 0;
+  const bool xd = (p->prune & FILTR_PRUNE_XDROP) != 0 || zd;
+  if (zd && (p->prune & FILTR_PRUNE_XDROP)) {
+    set_error("FILTR_PRUNE_XDROP and FILTR_PRUNE_ZDROP exclude each other");
+    return FILTR_ERR_INVALID;
+  }
   if (band && p->band < 0) {
     set_error("band must be >= 0");
     return FILTR_ERR_INVALID;
@@ -89,6 +95,7 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
   sp->band_literal = (p->prune & FILTR_PRUNE_BAND_LITERAL) ? 1 : 0;
   sp->band = band ? p->band : 0;
   sp->use_xdrop = xd ? 1 : 0;
+  sp->zdrop = zd ? 1 : 0;
   sp->xdrop = xd ? p->xdrop : 0;
   sp->traceback = p->traceback;
   sp->precision = p->precision;

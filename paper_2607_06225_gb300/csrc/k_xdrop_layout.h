@@ -49,7 +49,7 @@ struct XdCkpt {
 // slots at or beyond the writer's window read as NEG
 enum : int {
   XCK_ORIGIN = 0, XCK_DPREV, XCK_BEST, XCK_LO, XCK_HI, XCK_USED, XCK_WIN,
-  XCK_BV, XCK_BI, XCK_BJ, XCK_CELLS_LO, XCK_CELLS_HI, XCK_HDR = 16
+  XCK_BV, XCK_BI, XCK_BJ, XCK_CELLS_LO, XCK_CELLS_HI, XCK_DBEST, XCK_HDR = 16
 };
 constexpr int XD_MAX_WARPS = 32;
 FILTR_HD int64_t xd_ckpt_stride() { return XCK_HDR + (int64_t)xd_window_slots(XD_MAX_WARPS, 8) * 4; }

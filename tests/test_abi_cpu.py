@@ -49,7 +49,7 @@ def test_params_check(L):
     ok = L.make_params(S, gap_open=4, gap_extend=2)
     assert L.lib().filtr_params_check(C.byref(ok)) == L.OK
     for bad in [dict(gap_open=-1), dict(gap_extend=-2), dict(band=-3), dict(xdrop=-1),
-                dict(precision=7)]:
+                dict(zdrop=-1), dict(precision=7)]:
         p = L.make_params(S, **{**dict(gap_open=4, gap_extend=2), **bad})
         assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID, bad
     p = L.make_params(np.zeros((5, 5), np.int8))
@@ -61,6 +61,13 @@ def test_params_check(L):
     p.subst = C.POINTER(C.c_int8)()
     assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
     assert L.lib().filtr_params_check(None) == L.ERR_INVALID
+    # X-drop and Z-drop exclude each other
+    with pytest.raises(ValueError):
+        L.make_params(S, xdrop=3, zdrop=3)
+    p = L.make_params(S, zdrop=3)
+    assert L.lib().filtr_params_check(C.byref(p)) == L.OK
+    p.prune |= L.PRUNE_XDROP
+    assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
 
 
 def test_ctx_create_without_gpu_fails_cleanly(L):
