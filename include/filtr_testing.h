@@ -30,6 +30,11 @@ filtr_status filtr_test_set_checkpoint(filtr_ctx *ctx, int32_t interval);
  * without traceback, then each segment recomputed backwards and walked. */
 filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on);
 
+/* Group width (1, 2, 4, 8, 16 or 32 warps) at which filtr_align_batch first
+ * runs X-drop / Z-drop pairs (those that outgrow it are rerun wider); 0
+ * restores the default.  Results do not depend on it. */
+filtr_status filtr_test_set_first_width(filtr_ctx *ctx, int32_t warps);
+
 #ifdef __cplusplus
 }
 #endif

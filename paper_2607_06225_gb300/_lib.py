@@ -116,6 +116,8 @@ def lib():
         L.filtr_test_set_checkpoint.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_test_force_recompute.restype = i32
         L.filtr_test_force_recompute.argtypes = [C.c_void_p, C.c_int32]
+        L.filtr_test_set_first_width.restype = i32
+        L.filtr_test_set_first_width.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_serve_create.restype = i32
         L.filtr_serve_create.argtypes = [C.c_void_p, C.c_size_t, C.c_uint32, C.POINTER(C.c_void_p)]
         L.filtr_serve_submit.restype = i32

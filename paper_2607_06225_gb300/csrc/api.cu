@@ -443,10 +443,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     if (!walk(d_order + w.walk_begin, w.walk_end - w.walk_begin)) return cuda_fail(ce, "walk launch");
     pending.insert(pending.end(), ovf.begin(), ovf.end());
   }
-  static const int kWider[] = {4, 16, 32};
-  for (int wi = 0; wi < 3 && !pending.empty(); ++wi) {
+  static const int kWider[] = {2, 4, 8, 16, 32};
+  for (int wi = 0; wi < 5 && !pending.empty(); ++wi) {
     const int W = kWider[wi];
-    if (W <= ctx->xdrop_warps0) continue;
+    if (W <= P.xdrop_w0) continue;
     // rerun the pairs that outgrew their window, in sub-waves that fit the budget
     std::vector<uint32_t> todo;
     todo.swap(pending);

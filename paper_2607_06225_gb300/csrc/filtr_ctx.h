@@ -27,7 +27,7 @@ struct Ctx {
   uint32_t last_pairs_packed = 0;
   int last_waves = 0;
   uint32_t last_launches = 0;
-  int xdrop_warps0 = 1;       // first window width (warps) of X-drop pairs
+  int xdrop_warps0 = 0;       // first window width (warps) of X-drop pairs, 0: estimated
   int ckpt_interval = 0;      // > 0: filtr_align_long always checkpoints X-drop tracebacks
   bool ckpt_recompute = false;  // checkpointed traceback: recompute segments, no single pass
   // ordering of successive calls: the next call waits for this event, so the

@@ -502,6 +502,16 @@ filtr_status filtr_test_set_checkpoint(filtr_ctx *ctx, int32_t interval) {
   return FILTR_OK;
 }
 
+filtr_status filtr_test_set_first_width(filtr_ctx *ctx, int32_t warps) {
+  if (!ctx || (warps != 0 && warps != 1 && warps != 2 && warps != 4 && warps != 8 && warps != 16 &&
+               warps != 32)) {
+    set_error("filtr_test_set_first_width: bad arguments");
+    return FILTR_ERR_INVALID;
+  }
+  reinterpret_cast<Ctx *>(ctx)->xdrop_warps0 = warps;
+  return FILTR_OK;
+}
+
 filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on) {
   if (!ctx) {
     set_error("filtr_test_force_recompute: ctx is NULL");

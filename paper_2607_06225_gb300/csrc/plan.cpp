@@ -84,6 +84,37 @@ uint64_t band_cells(uint32_t M, uint32_t N, const ScoreParams &sp) {
   return c;
 }
 
+// X-drop / Z-drop live region: a cell delta places off the best cell along an
+// antidiagonal sits 2*delta diagonals away, which takes gaps costing about
+// o + 2*delta*e.  X-drop keeps it while that stays within X, so about
+// (X - o) / e cells live; Z-drop adds one per diagonal of distance to the
+// threshold, so about (Z - o) / (e - 1) (no bound when e <= 1).  The band and
+// the matrix cap both.  The first group is the narrowest whose window holds the
+// estimate; pairs that outgrow it are rerun wider, so a low estimate costs a
+// partial pass, a high one a wider (slower) sweep.
+int xdrop_first_width(const ScoreParams &sp, uint32_t n, const uint32_t *q_len,
+                      const uint32_t *r_len, int slots) {
+  const double X = (double)sp.xdrop, o = (double)sp.o, e = (double)sp.e;
+  double est = 1e18;
+  if (sp.xdrop < FILTR_XDROP_INF) {
+    if (!sp.zdrop && e > 0) est = std::max(1.0, (X - o) / e);
+    if (sp.zdrop && e > 1) est = std::max(1.0, (X - o) / (e - 1));
+  }
+  double cap = 0;
+  for (uint32_t p = 0; p < n; ++p) {
+    double c = (double)std::min(q_len[p], r_len[p]) + 1;
+    if (sp.use_band) {
+      int64_t lo, hi;
+      band_limits(q_len[p], r_len[p], sp.band, sp.band_literal, &lo, &hi);
+      c = std::min(c, (double)(hi - lo) / 2 + 1);
+    }
+    cap = std::max(cap, c);
+  }
+  est = std::min(est, cap);
+  for (int W : {1, 2, 4, 8, 16}) if ((double)W * 32 * slots >= est) return W;
+  return 32;
+}
+
 // half-octave buckets: 2 * floor(log2(cost)) + the next bit
 static int cost_bucket(uint64_t cost) {
   if (cost < 2) return 0;
@@ -114,7 +145,10 @@ bool make_plan(const PlanInput &in, Plan *P) {
   std::vector<uint8_t> bucket(n), shape(n);
   std::vector<uint64_t> words(n);
   std::vector<uint32_t> cnt(64, 0);
-  const int xw = in.xdrop_warps > 0 ? in.xdrop_warps : 1;
+  const int xw = in.xdrop_warps > 0
+                     ? in.xdrop_warps
+                     : (sp.use_xdrop ? xdrop_first_width(sp, n, in.q_len, in.r_len, in.xdrop_slots) : 1);
+  P->xdrop_w0 = xw;
   uint32_t live = 0;
   for (uint32_t p = 0; p < n; ++p) {
     const uint32_t M = in.q_len[p], N = in.r_len[p];

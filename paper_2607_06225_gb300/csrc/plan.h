@@ -30,6 +30,7 @@ struct Plan {
   uint64_t stage_words = 0;
   uint64_t max_n = 0, max_m = 0;
   uint64_t cigar_upper = 0;       // sum over pairs of M + N: no CIGAR can be longer
+  int xdrop_w0 = 1;               // group width X-drop / Z-drop pairs first run at
   uint64_t cells_estimate = 0;
 };
 
@@ -50,9 +51,14 @@ struct PlanInput {
   const uint32_t *q_len, *r_len;  // host copies
   uint64_t tb_budget_words;       // traceback words one wave may use
   int xdrop_slots;                // slots per lane of the X-drop kernel
-  int xdrop_warps;                // first window width of X-drop pairs (warps)
+  int xdrop_warps;                // first window width of X-drop pairs (warps), 0: estimated
   const ShapeCost *shape_cost = nullptr;  // nullptr: kDefaultShapeCost
 };
+
+// First group width (warps) for X-drop / Z-drop pairs, from the expected width
+// of their live region (see plan.cpp).
+int xdrop_first_width(const ScoreParams &sp, uint32_t n, const uint32_t *q_len,
+                      const uint32_t *r_len, int slots);
 
 // Rows per lane of the tiled kernel for an M x N pair.
 int full_rows_per_lane(uint32_t M, uint32_t N);
