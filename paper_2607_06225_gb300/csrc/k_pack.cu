@@ -64,6 +64,12 @@ __device__ __forceinline__ uint32_t fadd2(uint32_t a, uint32_t b, uint32_t one) 
   asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(b), "r"(one), "r"(a));
   return r;
 }
+// a * b + c on the FMA pipe (low 32 bits)
+__device__ __forceinline__ uint32_t fmad32(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
 // acc | (p & (0x01010101 << c)), c a compile-time constant after unrolling
 __device__ __forceinline__ uint32_t plane_or(uint32_t acc, uint32_t p, int c) {
   return acc | (p & (0x01010101u << c));
@@ -172,10 +178,8 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
   uint32_t prevS = h0(row0) << 16;  // H(row0, 0), the first diagonal
   uint32_t outH = Hc[P - 1], outF = NEG2, Flast = NEG2, hprev = Hc[P - 1];
   const int nsteps = N + 63;
-  // rows of the lane inside the matrix, as bit masks over each half's registers
-  const int nvalid = min(max(M - top + 1, 0), R);
-  const uint32_t lo_valid = nvalid >= P ? (1u << P) - 1u : (1u << nvalid) - 1u;
-  const uint32_t hi_valid = nvalid > P ? (1u << (nvalid - P)) - 1u : 0u;
+  // best-cell key of the lane so far: a later strip needs a strictly larger H
+  uint32_t bestkey = ((uint32_t)(best.v + B) << 16) | 31u;
   int rc_lo = PP.r[0], rc_hi = rc_lo;
   int rc_next = PP.r[min(max(1 - 2 * lane, 1), N) - 1];
 
@@ -214,7 +218,7 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
     uint32_t Hmup = fadd2(Hup, MOE, one);
     const bool edge = !(t >= 63 && t <= N - 1);  // warp-uniform
     const uint32_t KM = (actL ? 0x0000ffffu : 0u) | (actH ? 0xffff0000u : 0u);
-    uint32_t m = 0, hprevk = 0;
+    uint32_t mkey = 0;  // largest best-cell key of this step (local mode)
     uint32_t accA = 0, accB = 0;
     uint32_t tbw[2 * G > 0 ? 2 * G : 1];
 
@@ -270,10 +274,11 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
         Fup = F;
         const uint32_t Hk = EDGE ? (H & KM) : H;  // inactive halves count as 0
         if (LOCAL) {  // two registers fold into the step's max at once
-          if (k & 1)
-            m = __vimax3_u16x2(m, hprevk, Hk);
-          else
-            hprevk = Hk;
+          // 32-bit keys: the half's biased H above a tag 31 - row, so the
+          // largest key is the largest H and, among equal H, the smallest i
+          const uint32_t key_lo = fmad32(Hk, 65536u, 31u - k);
+          const uint32_t key_hi = (Hk & 0xffff0000u) | (31u - (P + k));
+          mkey = __vimax3_u32(mkey, key_lo, key_hi);
         }
         if constexpr (EDGE) {
           Hc[k] = select_bits(KM, H, Hc[k]);
@@ -299,29 +304,16 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
     }
     if (lane == 31 && actH && s + 1 < nstrips)
       buf[cH] = make_int2((int)(Hc[P - 1] >> 16), (int)(Fup >> 16));
-    // best cell (local): a step whose largest value reaches the lane's best
-    // looks up the first row holding it (bit k: low half of register k = row
-    // k, bit 16 + k: high half = row P + k) and keeps it under the full
-    // tie-break.  Rows past M stay below a valid cell of their lane already
-    // seen; lanes wholly past M keep no best.
-    if (LOCAL && top <= M) {
-      const uint32_t mmv = max(m & 0xffffu, m >> 16);
-      const int mm = (int)mmv - B;
-      if (mm > 0 && mm >= best.v) {
-        const uint32_t MMP = mmv * 65537u;
-        uint32_t eq = 0;
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-          const uint32_t ne = (Hc[k] ^ MMP) + K7F;  // bits 15 / 31: half differs
-          eq |= (~ne >> (15 - k)) & (0x00010001u << k);
-        }
-        const uint32_t lo = eq & (actL ? lo_valid : 0u);
-        const uint32_t hi = (eq >> 16) & (actH ? hi_valid : 0u);
-        if (lo)
-          best_put(best, mm, top + __ffs(lo) - 1, cL);
-        else if (hi)
-          best_put(best, mm, top + P + __ffs(hi) - 1, cH);
-      }
+    // best cell (local): a lane takes the step's largest key only if strictly
+    // above its best key (equal keys: the same row at a later column, whose
+    // smaller j already stands).  Rows past M stay below a valid cell of their
+    // lane already seen; lanes wholly past M keep no best.
+    if (LOCAL && top <= M && mkey > bestkey) {
+      bestkey = mkey;
+      const int row = 31 - (int)(mkey & 0xffffu);
+      best.v = (int)(mkey >> 16) - B;
+      best.i = top + row;
+      best.j = row < P ? cL : cH;
     }
   }
   if (!LOCAL && s == nstrips - 1 && top <= M && M < top + R) {
