@@ -255,14 +255,14 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
 /* Autotuning of the tiled kernel shapes (the paper leaves autotuning to
  * future work, Sec. 11).  Times every tiled shape -- the int32 tile with 32,
  * 24, 16 or 8 rows per lane and, where the parameters allow it, the int16x2
- * tile with 32 or 16 -- on calibration batches that fill every resident warp
+ * tile with the same heights -- on calibration batches that fill every resident warp
  * slot of the device three times (pairs of one full strip of query rows by 512
  * reference residues, random codes), and keeps in ctx the device time per warp
  * step of each shape for this recurrence kind (mode, gap model, traceback,
  * alphabet, band).  Later filtr_align_batch calls of the same kind give each
  * pair the shape whose predicted time, strips x (N + fill steps) x that cost,
  * is smallest.  Results never change: the shapes are bit-exact alternatives.
- *   out: optional; rows_per_lane / packed describe the six shapes, and
+ *   out: optional; rows_per_lane / packed describe the eight shapes, and
  *        ns_per_warp_step is 0 for shapes not timed (not allowed for these
  *        parameters, or too large for the workspace).
  * Synchronous (waits for the context's previous call); uses the workspace.
@@ -270,9 +270,9 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
  * use the antidiagonal kernel only), FILTR_ERR_NOMEM (the workspace holds no
  * calibration batch), FILTR_ERR_CUDA. */
 typedef struct {
-  int32_t rows_per_lane[6];
-  int32_t packed[6];
-  double ns_per_warp_step[6];
+  int32_t rows_per_lane[8];
+  int32_t packed[8];
+  double ns_per_warp_step[8];
 } filtr_tune_report;
 filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params, filtr_tune_report *out);
 

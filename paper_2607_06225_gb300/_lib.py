@@ -54,8 +54,8 @@ class Stats(C.Structure):
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("rows_per_lane", C.c_int32 * 6), ("packed", C.c_int32 * 6),
-                ("ns_per_warp_step", C.c_double * 6)]
+    _fields_ = [("rows_per_lane", C.c_int32 * 8), ("packed", C.c_int32 * 8),
+                ("ns_per_warp_step", C.c_double * 8)]
 
 
 RESULT_DTYPE = np.dtype([("score", np.int32), ("q_begin", np.int32), ("q_end", np.int32),
@@ -234,7 +234,7 @@ class Context:
         rep = TuneReport()
         check(lib().filtr_autotune(self.handle, C.byref(params), C.byref(rep)), "filtr_autotune")
         out = {}
-        for k in range(6):
+        for k in range(8):
             if rep.ns_per_warp_step[k] > 0:
                 kind = "i16x2" if rep.packed[k] else "i32"
                 out[f"{kind} R={rep.rows_per_lane[k]}"] = rep.ns_per_warp_step[k]

@@ -158,8 +158,11 @@ FILTR_HD int pack_bias(int mode, int o, int e, int smin, int smax, int64_t M, in
   if (B + high >= 0x7ff0) return -1;
   return (int)B;
 }
+// Packed tile: words per lane and step -- each half's R/2 cells fill
+// ceil(R/16) words of four 8-cell bit planes.
+FILTR_HD int pack_words_per_step(int R) { return 2 * ((R / 2 + 7) / 8); }
 FILTR_HD uint64_t pack_strip_tb_words(int64_t jlo, int64_t jhi, int R) {
-  return jhi >= jlo ? (uint64_t)((jhi - jlo + 1) + 63) * (uint64_t)(R / 8) * 32u : 0;
+  return jhi >= jlo ? (uint64_t)((jhi - jlo + 1) + 63) * (uint64_t)pack_words_per_step(R) * 32u : 0;
 }
 
 struct BatchDev {
@@ -225,7 +228,7 @@ int long_blocks_per_sm(const ScoreParams &sp);
 cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
 int full_smem_bytes(int R, int alphabet);
 int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
-cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);  // R = 16, 32
+cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);  // R = 8, 16, 24, 32
 int pack_max_blocks_per_sm(int R, const ScoreParams &sp);
 cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
                          uint32_t *n_overflow, cudaStream_t s);

@@ -29,9 +29,9 @@
 // value.  The query profile in shared memory holds s + 64 (7 bits, 0 for rows
 // past M), so one byte permute builds a register's two scores.
 //
-// Traceback, per strip: step-major, then word, then lane; R/8 words per lane
-// and step, word h*P/8 + g holding cells 8g..8g+7 of half h as four bit
-// planes -- byte 0: E > D, byte 1: F > max(D, E), byte 2: E took the
+// Traceback, per strip: step-major, then word, then lane; 2G words per lane
+// and step (G = ceil(P/8)), word h*G + g holding cells 8g..8g+7 of half h as
+// four bit planes -- byte 0: E > D, byte 1: F > max(D, E), byte 2: E took the
 // extension, byte 3: F took the extension; bit c of each byte is cell 8g + c.
 // The planes are gathered by sign-replicating byte permutes (the two halves'
 // sign bits of two differences per permute, each widened to a 0x00 / 0xff
@@ -87,8 +87,19 @@ struct ScoreSel {  // low half <- byte B of the low word, high half <- byte B of
 template <int R>
 struct HalfProf;
 template <>
+struct HalfProf<8> {
+  using T = uint32_t;
+};
+template <>
 struct HalfProf<16> {
   using T = uint2;
+};
+struct HalfProf24 {
+  uint32_t a, b, c;
+};
+template <>
+struct HalfProf<24> {
+  using T = HalfProf24;
 };
 template <>
 struct HalfProf<32> {
@@ -119,7 +130,7 @@ __device__ __forceinline__ void best_put(Best &b, int v, int i, int j) {
 template <int R, bool LOCAL, bool AFFINE, bool TB>
 __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb_base, int2 *buf,
                                            Best &best, int &endH) {
-  constexpr int HS = 32 * R, P = R / 2, G = P / 8, WPS = R / 8;
+  constexpr int HS = 32 * R, P = R / 2, G = (P + 7) / 8, WPS = 2 * G;
   using HW = typename HalfProf<R>::T;
   const int lane = threadIdx.x & 31;
   const int M = PP.M, N = PP.N, o = PP.o, e = PP.e, B = PP.B;
@@ -263,7 +274,7 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
             if ((k & 7) == 0) accB = 0;
             accB = plane_or(accB, Pb, k & 7);
           }
-          if ((k & 7) == 7) {
+          if ((k & 7) == 7 || k == P - 1) {  // a group of (up to) 8 registers is complete
             tbw[k >> 3] = perm<0x5410>(accA, accB);      // low half, group k/8
             tbw[G + (k >> 3)] = perm<0x7632>(accA, accB);  // high half
           }
@@ -473,7 +484,9 @@ int occ_pr(const ScoreParams &sp) {
 cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s) {
   if (a.sp.use_band) return cudaErrorInvalidValue;  // unbanded pairs only
   switch (R) {
+    case 8: return dispatch_pr<8>(a, grid, s);
     case 16: return dispatch_pr<16>(a, grid, s);
+    case 24: return dispatch_pr<24>(a, grid, s);
     case 32: return dispatch_pr<32>(a, grid, s);
     default: return cudaErrorInvalidValue;
   }
@@ -481,7 +494,9 @@ cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s) {
 
 int pack_max_blocks_per_sm(int R, const ScoreParams &sp) {
   switch (R) {
+    case 8: return occ_pr<8>(sp);
     case 16: return occ_pr<16>(sp);
+    case 24: return occ_pr<24>(sp);
     case 32: return occ_pr<32>(sp);
     default: return 0;
   }

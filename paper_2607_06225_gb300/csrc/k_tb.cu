@@ -51,7 +51,7 @@ __device__ __forceinline__ uint32_t full_bits(const uint32_t *tb, FullGeom &g, i
 }
 
 // The int16x2 tiled kernel's layout (unbanded): every strip has N + 63 steps
-// of R/8 words per lane; the high half of a lane's rows runs one step behind.
+// of 2 * ceil(R/16) words per lane; the high half of a lane's rows runs one step behind.
 struct PackGeom {
   int R;
   int64_t strip_words;
@@ -64,9 +64,8 @@ __device__ __forceinline__ uint32_t pack_bits(const uint32_t *tb, const PackGeom
   const int l = rho / g.R, kk = rho - l * g.R;
   const int h = kk >= P ? 1 : 0, k = kk - h * P;
   const int64_t t = (int64_t)j - 1 + 2 * l + h;
-  const int wps = g.R / 8;
-  const uint32_t w =
-      __ldg(tb + s * g.strip_words + (t * wps + h * (P / 8) + (k >> 3)) * 32 + l);
+  const int G = (P + 7) / 8, wps = 2 * G;
+  const uint32_t w = __ldg(tb + s * g.strip_words + (t * wps + h * G + (k >> 3)) * 32 + l);
   const int c = k & 7;
   return (((w >> c) & 1u) << 3) | (((w >> (8 + c)) & 1u) << 2) | (((w >> (16 + c)) & 1u) << 1) |
          ((w >> (24 + c)) & 1u);

@@ -21,7 +21,8 @@ namespace filtr {
 // instruction mix; filtr_autotune replaces them with timed values).
 const ShapeCost kDefaultShapeCost[SHAPE_TILED] = {
     {32, 31, 16.0f, 30.0f, false}, {24, 31, 16.0f, 30.0f, false}, {16, 31, 16.0f, 30.0f, false},
-    {8, 31, 16.0f, 30.0f, false},  {32, 63, 6.5f, 40.0f, true},   {16, 63, 6.5f, 40.0f, true}};
+    {8, 31, 16.0f, 30.0f, false},  {32, 63, 12.0f, 40.0f, true},  {24, 63, 12.0f, 40.0f, true},
+    {16, 63, 12.0f, 40.0f, true},  {8, 63, 12.0f, 40.0f, true}};
 
 double shape_cost(const ShapeCost &c, uint32_t M, uint32_t N) {
   const uint64_t hs = 32u * c.R;
@@ -138,8 +139,8 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->cells_estimate = 0;
 
   // per pair: kernel shape key, cost bucket, traceback words (flat arrays)
-  // shape keys: 0..3 the int32 tiled kernel with R = 32, 24, 16, 8; 4, 5 the
-  // int16x2 tiled kernel with R = 32, 16; 6 the X-drop kernel
+  // shape keys: 0..3 the int32 tiled kernel with R = 32, 24, 16, 8; 4..7 the
+  // int16x2 tiled kernel with R = 32, 24, 16, 8; 8 the X-drop kernel
   const ShapeCost *costs = in.shape_cost ? in.shape_cost : kDefaultShapeCost;
   const bool pack_ok = !sp.use_band && !sp.use_xdrop && sp.precision != FILTR_PREC_I32;
   std::vector<uint8_t> bucket(n), shape(n);

@@ -34,8 +34,8 @@ struct Plan {
   uint64_t cells_estimate = 0;
 };
 
-// Tiled kernel shapes (int32 R = 32, 24, 16, 8; int16x2 R = 32, 16), then X-drop.
-enum : int { SHAPE_TILED = 6, SHAPE_XDROP = 6, SHAPE_KEYS = 7 };
+// Tiled kernel shapes (int32 and int16x2, R = 32, 24, 16, 8), then X-drop.
+enum : int { SHAPE_TILED = 8, SHAPE_XDROP = 8, SHAPE_KEYS = 9 };
 struct ShapeCost {
   int R, fill;        // rows per lane; fill steps per strip (staircase)
   float per_row;      // cost of one row (int32) or one packed register pair of rows / 2

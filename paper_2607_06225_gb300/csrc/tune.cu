@@ -1,7 +1,7 @@
 // tune.cu -- filtr_autotune: measured costs of the tiled kernel shapes.
 //
-// The planner gives each pair the tiled shape (int32 tile with R = 32, 24, 16
-// or 8 rows per lane, or the int16x2 tile with R = 32 or 16) whose predicted
+// The planner gives each pair the tiled shape (the int32 tile or the int16x2
+// tile, each with R = 32, 24, 16 or 8 rows per lane) whose predicted
 // time, strips x (N + fill steps) x cost-per-warp-step, is smallest.  The
 // built-in costs come from instruction counts; this entry point replaces them
 // with the device time per warp step measured on this GPU for one recurrence
