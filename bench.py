@@ -67,6 +67,11 @@ def parse():
                     help="cell width of the tiled kernels (results are identical)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the built-in shape costs instead of timed ones")
+    ap.add_argument("--tune-save", default=None,
+                    help="write the autotuned shape costs to this JSON file")
+    ap.add_argument("--tune-load", default=None,
+                    help="install shape costs from this JSON file instead of timing them "
+                         "(so a profiled run plans as the unprofiled one did)")
     return ap.parse_args()
 
 
@@ -441,7 +446,16 @@ def main():
 
     tune = None
     if not args.no_autotune and not sc.get("xdrop") and not sc.get("zdrop"):
-        tune = ctx.autotune(params)  # one-time setup, outside every timed region
+        # one-time setup, outside every timed region
+        if args.tune_load:
+            with open(args.tune_load) as f:
+                tune = json.load(f)
+            ctx.tune_apply(params, tune)
+        else:
+            tune = ctx.autotune(params)
+            if args.tune_save:
+                with open(args.tune_save, "w") as f:
+                    json.dump(tune, f)
     ctx.set_timing(True)
     for _ in range(max(args.warmup, 1)):
         step()

@@ -262,7 +262,8 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
  * alphabet, band).  Later filtr_align_batch calls of the same kind give each
  * pair the shape whose predicted time, strips x (N + fill steps) x that cost,
  * is smallest.  Results never change: the shapes are bit-exact alternatives.
- *   out: optional; rows_per_lane / packed describe the eight shapes, and
+ *   out: optional; rows_per_lane / packed describe the eight shapes, always in
+ *        this order: int32 R = 32, 24, 16, 8, then int16x2 R = 32, 24, 16, 8; and
  *        ns_per_warp_step is 0 for shapes not timed (not allowed for these
  *        parameters, or too large for the workspace).
  * Synchronous (waits for the context's previous call); uses the workspace.
@@ -275,6 +276,18 @@ typedef struct {
   double ns_per_warp_step[8];
 } filtr_tune_report;
 filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params, filtr_tune_report *out);
+
+/* Install a tune report saved from an earlier filtr_autotune of the same
+ * recurrence kind on the same kind of device (no counterpart in the paper):
+ * a service restarts with its measured shape costs instead of timing again,
+ * and a profiled run plans exactly as an unprofiled one did.  Shapes whose
+ * ns_per_warp_step is 0 keep the built-in cost scaled to the given ones.
+ * Host only: launches nothing, does not wait for the GPU.
+ * Errors: FILTR_ERR_INVALID (NULL ctx or report, bad params, X-drop
+ * parameters, a shape list other than the eight filtr_autotune reports in its
+ * order, a negative or non-finite cost, or no positive cost). */
+filtr_status filtr_tune_apply(filtr_ctx *ctx, const filtr_params *params,
+                              const filtr_tune_report *report);
 
 /* Measured integer / DPX throughput of this device, used as the cell-update
  * roofline denominator: out[0] = int32 add/max ops per second (all SMs,

@@ -53,6 +53,11 @@ class Stats(C.Structure):
                 ("pairs_i16x2", C.c_uint32), ("reserved", C.c_uint32)]
 
 
+# the eight tiled shapes in the order filtr_autotune reports them
+TUNE_SHAPES = [("i32", 32), ("i32", 24), ("i32", 16), ("i32", 8),
+               ("i16x2", 32), ("i16x2", 24), ("i16x2", 16), ("i16x2", 8)]
+
+
 class TuneReport(C.Structure):
     _fields_ = [("rows_per_lane", C.c_int32 * 8), ("packed", C.c_int32 * 8),
                 ("ns_per_warp_step", C.c_double * 8)]
@@ -107,6 +112,8 @@ def lib():
         L.filtr_ctx_last_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
         L.filtr_autotune.restype = i32
         L.filtr_autotune.argtypes = [C.c_void_p, C.POINTER(Params), C.POINTER(TuneReport)]
+        L.filtr_tune_apply.restype = i32
+        L.filtr_tune_apply.argtypes = [C.c_void_p, C.POINTER(Params), C.POINTER(TuneReport)]
         L.filtr_probe_int_peak.restype = i32
         L.filtr_probe_int_peak.argtypes = [C.c_void_p, C.POINTER(C.c_double * 5)]
         L.filtr_test_long_timeout.restype = i32
@@ -239,6 +246,17 @@ class Context:
                 kind = "i16x2" if rep.packed[k] else "i32"
                 out[f"{kind} R={rep.rows_per_lane[k]}"] = rep.ns_per_warp_step[k]
         return out
+
+    def tune_apply(self, params, table: dict):
+        """Install costs from an earlier autotune() table (filtr_tune_apply);
+        shapes missing from the table keep the scaled built-in cost."""
+        rep = TuneReport()
+        for k, (kind, R) in enumerate(TUNE_SHAPES):
+            rep.rows_per_lane[k] = R
+            rep.packed[k] = 1 if kind == "i16x2" else 0
+            rep.ns_per_warp_step[k] = float(table.get(f"{kind} R={R}", 0.0))
+        check(lib().filtr_tune_apply(self.handle, C.byref(params), C.byref(rep)),
+              "filtr_tune_apply")
 
     def probe(self):
         arr = (C.c_double * 5)()

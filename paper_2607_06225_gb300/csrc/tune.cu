@@ -146,6 +146,26 @@ double time_shape(Ctx *c, const ScoreParams &sp, const ShapeCost &shape, cudaStr
   return (double)best_ms * 1e6 / warp_steps;
 }
 
+// Keep measured costs (ns per warp step; 0 = not timed) for this recurrence
+// kind.  Untimed shapes keep the model's cost scaled to the timed ones.
+void install_costs(Ctx *c, const ScoreParams &sp, const double *ns_k) {
+  std::vector<ShapeCost> tab(kDefaultShapeCost, kDefaultShapeCost + SHAPE_TILED);
+  double scale_num = 0, scale_den = 0;
+  for (int k = 0; k < SHAPE_TILED; ++k)
+    if (ns_k[k] > 0) {
+      const ShapeCost &d = kDefaultShapeCost[k];
+      scale_num += ns_k[k];
+      scale_den += d.per_row * d.R + d.per_step;
+    }
+  for (int k = 0; k < SHAPE_TILED; ++k) {
+    const double model = tab[k].per_row * tab[k].R + tab[k].per_step;
+    tab[k].per_row = 0.0f;
+    tab[k].per_step = (float)(ns_k[k] > 0 ? ns_k[k]
+                                          : (scale_den > 0 ? model * scale_num / scale_den : model));
+  }
+  c->tuned[Ctx::tune_key(sp)] = tab;
+}
+
 }  // namespace
 }  // namespace filtr
 
@@ -174,12 +194,11 @@ extern "C" filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *param
   cudaStream_t st = nullptr;
   e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-  std::vector<ShapeCost> tab(kDefaultShapeCost, kDefaultShapeCost + SHAPE_TILED);
   if (out) memset(out, 0, sizeof *out);
   double ns_k[SHAPE_TILED] = {};
   bool any = false;
   for (int k = 0; k < SHAPE_TILED; ++k) {
-    ShapeCost &s = tab[k];
+    const ShapeCost &s = kDefaultShapeCost[k];
     if (out) {
       out->rows_per_lane[k] = s.R;
       out->packed[k] = s.packed ? 1 : 0;
@@ -194,8 +213,6 @@ extern "C" filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *param
       return trc;
     }
     if (ns <= 0) continue;  // keeps the built-in estimate
-    s.per_row = 0.0f;
-    s.per_step = (float)ns;
     ns_k[k] = ns;
     any = true;
     if (out) out->ns_per_warp_step[k] = ns;
@@ -205,20 +222,44 @@ extern "C" filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *param
     set_error("filtr_autotune: the workspace cannot hold one calibration batch");
     return FILTR_ERR_NOMEM;
   }
-  // untimed shapes keep the model's cost scaled to the timed ones
-  double scale_num = 0, scale_den = 0;
-  for (int k = 0; k < SHAPE_TILED; ++k)
-    if (ns_k[k] > 0) {
-      const ShapeCost &d = kDefaultShapeCost[k];
-      scale_num += ns_k[k];
-      scale_den += d.per_row * d.R + d.per_step;
+  install_costs(c, sp, ns_k);
+  return FILTR_OK;
+}
+
+extern "C" filtr_status filtr_tune_apply(filtr_ctx *ctx, const filtr_params *params,
+                                         const filtr_tune_report *report) {
+  ScoreParams sp;
+  filtr_status rc = to_score_params(params, &sp);
+  if (rc != FILTR_OK) return rc;
+  if (!ctx || !report) {
+    set_error("filtr_tune_apply: ctx or report is NULL");
+    return FILTR_ERR_INVALID;
+  }
+  if (sp.use_xdrop) {
+    set_error("filtr_tune_apply: X-drop parameters have no tiled shapes to tune");
+    return FILTR_ERR_INVALID;
+  }
+  double ns_k[SHAPE_TILED] = {};
+  bool any = false;
+  for (int k = 0; k < SHAPE_TILED; ++k) {
+    const ShapeCost &d = kDefaultShapeCost[k];
+    if (report->rows_per_lane[k] != d.R || report->packed[k] != (d.packed ? 1 : 0)) {
+      set_error("filtr_tune_apply: shape %d is not (R=%d, packed=%d) as filtr_autotune reports it",
+                k, d.R, d.packed ? 1 : 0);
+      return FILTR_ERR_INVALID;
     }
-  for (int k = 0; k < SHAPE_TILED; ++k)
-    if (ns_k[k] <= 0) {  // not timed
-      const double model = tab[k].per_row * tab[k].R + tab[k].per_step;
-      tab[k].per_row = 0.0f;
-      tab[k].per_step = (float)(scale_den > 0 ? model * scale_num / scale_den : model);
+    const double ns = report->ns_per_warp_step[k];
+    if (!(ns >= 0.0 && ns < 1e9)) {  // also rejects NaN
+      set_error("filtr_tune_apply: ns_per_warp_step[%d] must be finite and >= 0", k);
+      return FILTR_ERR_INVALID;
     }
-  c->tuned[Ctx::tune_key(sp)] = tab;
+    ns_k[k] = ns;
+    any = any || ns > 0;
+  }
+  if (!any) {
+    set_error("filtr_tune_apply: the report holds no timed shape");
+    return FILTR_ERR_INVALID;
+  }
+  install_costs(reinterpret_cast<Ctx *>(ctx), sp, ns_k);
   return FILTR_OK;
 }

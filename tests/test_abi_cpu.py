@@ -79,3 +79,19 @@ def test_ctx_create_without_gpu_fails_cleanly(L):
     rc = L.lib().filtr_ctx_create(0, 1 << 20, C.byref(h))
     assert rc in (L.ERR_CUDA, L.ERR_INVALID)
     assert not h.value
+
+
+def test_tune_apply_rejects_on_host(L):
+    """filtr_tune_apply validates its arguments before touching the context."""
+    S = np.zeros((4, 4), np.int8)
+    p = L.make_params(S, gap_open=4, gap_extend=2)
+    rep = L.TuneReport()
+    for k, (kind, R) in enumerate(L.TUNE_SHAPES):
+        rep.rows_per_lane[k] = R
+        rep.packed[k] = int(kind == "i16x2")
+        rep.ns_per_warp_step[k] = 0.5
+    lib = L.lib()
+    assert lib.filtr_tune_apply(None, C.byref(p), C.byref(rep)) == L.ERR_INVALID
+    assert lib.filtr_tune_apply(None, C.byref(p), None) == L.ERR_INVALID
+    assert lib.filtr_tune_apply(None, None, C.byref(rep)) == L.ERR_INVALID
+    assert "NULL" in L.last_error()

@@ -167,3 +167,41 @@ def test_autotune_keeps_results(F):
             c.autotune(xd)
     finally:
         c.close()
+
+
+def test_tune_apply_reproduces_plan(F):
+    """A table saved from filtr_autotune, installed with filtr_tune_apply in a
+    fresh context, plans the same shapes (same packed count); a table that
+    prices the packed tile out sends no pair to it; results never change."""
+    b = synth.protein_pairs(n=120, lmin=40, lmax=1100, seed=27)
+    params = F.make_params(b.subst, **b.scoring)
+    c1 = F.Context(0, 2 << 30)
+    try:
+        table = c1.autotune(params)
+        c1.set_timing(True)
+        r1, g1, rc = F.align_batch(c1, params, b)
+        assert rc == 0, F.last_error()
+        n1 = c1.last_stats()["pairs_i16x2"]
+    finally:
+        c1.close()
+    c2 = F.Context(0, 2 << 30)
+    try:
+        c2.tune_apply(params, table)
+        c2.set_timing(True)
+        r2, g2, rc = F.align_batch(c2, params, b)
+        assert rc == 0, F.last_error()
+        assert c2.last_stats()["pairs_i16x2"] == n1
+        assert np.array_equal(r1, r2)
+        used = int((r1["cigar_off"] + r1["cigar_len"]).max())
+        assert np.array_equal(g1[:used], g2[:used])
+        dear = {k: (v * 100 if k.startswith("i16x2") else v) for k, v in table.items()}
+        c2.tune_apply(params, dear)
+        r3, g3, rc = F.align_batch(c2, params, b)
+        assert rc == 0, F.last_error()
+        assert c2.last_stats()["pairs_i16x2"] == 0
+        assert np.array_equal(r1, r3)
+        assert np.array_equal(g1[:used], g3[:used])
+        with pytest.raises(F.FiltrError):
+            c2.tune_apply(params, {"i32 R=32": -1.0})
+    finally:
+        c2.close()
