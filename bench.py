@@ -469,7 +469,7 @@ def main():
 
     sampler = ClockSampler(local_rank)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    fwd_ms, walk_ms, launches = [], [], []
+    fwd_ms, walk_ms, launches, other_ms = [], [], [], {}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -485,6 +485,8 @@ def main():
         st = ctx.last_stats()  # waits for the step; device-side phase times
         fwd_ms.append(st["ms_forward"])
         walk_ms.append(st["ms_walk"])
+        for key in ("ms_validate", "ms_place", "ms_total", "ms_host_wait", "ms_host_plan"):
+            other_ms.setdefault(key[3:], []).append(st[key])
         launches.append(st["launches"])
         packed = st.get("pairs_i16x2", 0)
     torch.cuda.synchronize()
@@ -531,7 +533,8 @@ def main():
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replica x{world}"},
             "plain_per_pair": plain,
-            "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms},
+            "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms,
+                          **{k: statistics.median(v) for k, v in other_ms.items()}},
             "autotune_ns_per_warp_step": tune,
             "roofline": roof,
             "e2e": e2e,

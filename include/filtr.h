@@ -247,7 +247,9 @@ typedef struct {
   uint32_t waves;
   uint64_t cells_planned;
   uint32_t pairs_i16x2; /* pairs that ran in the int16x2 tiled kernel */
-  uint32_t reserved;
+  uint32_t device_plan; /* 1: the call was planned on the device, 0: on the host */
+  double ms_host_wait;  /* host wall time blocked on the validation and length read-back */
+  double ms_host_plan;  /* host wall time from the lengths' arrival to the plan's upload */
 } filtr_stats;
 filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);

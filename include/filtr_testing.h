@@ -35,6 +35,13 @@ filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on);
  * restores the default.  Results do not depend on it. */
 filtr_status filtr_test_set_first_width(filtr_ctx *ctx, int32_t warps);
 
+/* Which planner filtr_align_batch uses for tiled batches: 0 the default (the
+ * device planner from a few hundred pairs, see filtr_stats.device_plan), 1 the
+ * host planner always, 2 the device planner for every batch it can serve
+ * (not X-drop, not one launch per pair; batches whose traceback needs more than
+ * one wave still fall back to the host).  Results do not depend on it. */
+filtr_status filtr_test_set_device_plan(filtr_ctx *ctx, int32_t mode);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,7 +50,8 @@ class Stats(C.Structure):
     _fields_ = [("ms_validate", C.c_double), ("ms_forward", C.c_double), ("ms_walk", C.c_double),
                 ("ms_place", C.c_double), ("ms_total", C.c_double), ("launches", C.c_uint32),
                 ("waves", C.c_uint32), ("cells_planned", C.c_uint64),
-                ("pairs_i16x2", C.c_uint32), ("reserved", C.c_uint32)]
+                ("pairs_i16x2", C.c_uint32), ("device_plan", C.c_uint32),
+                ("ms_host_wait", C.c_double), ("ms_host_plan", C.c_double)]
 
 
 # the eight tiled shapes in the order filtr_autotune reports them
@@ -125,6 +126,8 @@ def lib():
         L.filtr_test_force_recompute.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_test_set_first_width.restype = i32
         L.filtr_test_set_first_width.argtypes = [C.c_void_p, C.c_int32]
+        L.filtr_test_set_device_plan.restype = i32
+        L.filtr_test_set_device_plan.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_serve_create.restype = i32
         L.filtr_serve_create.argtypes = [C.c_void_p, C.c_size_t, C.c_uint32, C.POINTER(C.c_void_p)]
         L.filtr_serve_submit.restype = i32

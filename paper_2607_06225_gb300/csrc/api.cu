@@ -1,6 +1,8 @@
 // api.cu -- the C ABI (include/filtr.h): contexts, parameter checks, the
 // batched call (plan, wave launches, traceback walk, CIGAR placement), its
 // host-buffer and per-pair-launch variants, packing and the throughput probe.
+#include <chrono>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -208,48 +210,119 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   ctx->spans.clear();
   uint32_t launches = 0;
 
-  // 1. lengths back to the host and residue validation (one synchronisation)
-  const size_t lens_bytes = (size_t)n * 4 * 2;
-  if (!ctx->ensure_host(lens_bytes + 64)) {
-    set_error("pinned host allocation of %zu bytes failed", lens_bytes);
+  // 1. workspace parts whose size depends on n only
+  Carver c{ctx->ws, ctx->ws_bytes};
+  DevPlanState *d_ps = c.take<DevPlanState>(1);
+  uint32_t *d_bad = reinterpret_cast<uint32_t *>(  // residue validation count (bad[0])
+      reinterpret_cast<char *>(d_ps) + offsetof(DevPlanState, bad));
+  uint32_t *d_order = c.take<uint32_t>(n);
+  TbLayout *d_tbl = c.take<TbLayout>(n);
+  uint64_t *d_stage_off = c.take<uint64_t>(n);
+  FwdOut *d_fwd = c.take<FwdOut>(n);
+  uint64_t *d_offs = c.take<uint64_t>(n);
+  const size_t n_counters = (size_t)n + 4096;
+  uint32_t *d_counters = c.take<uint32_t>(n_counters);
+  uint64_t *d_total = c.take<uint64_t>(4);
+  uint32_t *d_ovf = c.take<uint32_t>(n);
+  uint32_t *d_novf = c.take<uint32_t>(4);
+  uint32_t *d_rerun = c.take<uint32_t>(n);
+  // The device planner serves tiled batches (not X-drop, not one launch per
+  // pair) once planning on the host would cost more than the read-back: when
+  // the lengths must come back anyway, from a few hundred pairs; otherwise
+  // (host lengths, already validated) from a few thousand.
+  const bool must_sync = !(prevalidated && host_ql);
+  bool dev_plan = !plain && !sp.use_xdrop &&
+                  (ctx->dev_plan_mode == 2 ||
+                   (ctx->dev_plan_mode == 0 && n >= (must_sync ? 256u : 4096u)));
+  const uint32_t plan_blocks = (n + DEV_PLAN_BLOCK - 1) / DEV_PLAN_BLOCK;
+  uint16_t *d_pkey = dev_plan ? c.take<uint16_t>(n) : nullptr;
+  uint64_t *d_pwords = dev_plan ? c.take<uint64_t>(n) : nullptr;
+  uint64_t *d_pblk = dev_plan ? c.take<uint64_t>(plan_blocks) : nullptr;
+  if (c.used > ctx->ws_bytes) {
+    set_error("workspace of %zu bytes is too small for this batch's fixed buffers (%zu bytes)",
+              ctx->ws_bytes, c.used);
     return FILTR_ERR_NOMEM;
   }
-  uint32_t *h_ql = reinterpret_cast<uint32_t *>(ctx->h_stage);
+  const ShapeCost *costs = ctx->tuned_costs(sp);
+  if (!costs) costs = kDefaultShapeCost;
+
+  // 2. residue validation, the device plan, and the lengths or the plan's
+  // totals back to the host (one synchronisation)
+  const size_t head_bytes = offsetof(DevPlanState, hist);
+  const size_t lens_bytes = (size_t)n * 4 * 2;
+  if (!ctx->ensure_host(head_bytes + lens_bytes + 64)) {
+    set_error("pinned host allocation of %zu bytes failed", head_bytes + lens_bytes);
+    return FILTR_ERR_NOMEM;
+  }
+  DevPlanState *h_ps = reinterpret_cast<DevPlanState *>(ctx->h_stage);  // bad[] and sum only
+  uint32_t *h_ql = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(ctx->h_stage) +
+                                                (head_bytes + 255) / 256 * 256);
   uint32_t *h_rl = h_ql + n;
-  uint32_t *h_bad = h_rl + n;
-  Carver pre{ctx->ws, ctx->ws_bytes};
-  uint32_t *d_bad = pre.take<uint32_t>(64);
-  *h_bad = 0;
-  if (!(prevalidated && host_ql)) {
-    ce = cudaMemsetAsync(d_bad, 0, 64 * sizeof(uint32_t), st);
+  memset(h_ps, 0, head_bytes);
+  using clk = std::chrono::steady_clock;
+  const auto ms_since = [](clk::time_point t) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t).count();
+  };
+  ctx->last_host_wait_ms = ctx->last_host_plan_ms = 0;
+  ce = cudaMemsetAsync(d_ps, 0, sizeof(DevPlanState), st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "clearing the plan state");
+  if (!prevalidated) {
     ctx->span_begin(Ctx::PH_VALIDATE, st);
-    if (ce == cudaSuccess) ce = launch_validate_pairs(b, n, sp.alphabet, d_bad, st);
+    ce = launch_validate_pairs(b, n, sp.alphabet, d_bad, st);
     ctx->span_end(st);
     ++launches;
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_bad, d_bad, 4, cudaMemcpyDeviceToHost, st);
-    if (!host_ql) {
+  }
+  DevPlanArgs pa{};
+  if (dev_plan && ce == cudaSuccess) {
+    pa.q_len = b.q_len;
+    pa.r_len = b.r_len;
+    pa.n = n;
+    pa.sp = sp;
+    pa.tab = make_shape_table(costs, sp);
+    pa.state = d_ps;
+    pa.key = d_pkey;
+    pa.words = d_pwords;
+    pa.blk = d_pblk;
+    pa.order = d_order;
+    pa.tbl = d_tbl;
+    pa.stage_off = d_stage_off;
+    ce = launch_plan(pa, st);
+    launches += 3;
+  }
+  if (must_sync || dev_plan) {
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_ps, d_ps, head_bytes, cudaMemcpyDeviceToHost, st);
+    if (!host_ql && !dev_plan) {
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_ql, b.q_len, n * 4, cudaMemcpyDeviceToHost, st);
       if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_rl, b.r_len, n * 4, cudaMemcpyDeviceToHost, st);
     }
+    const auto t_wait = clk::now();
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) return cuda_fail(ce, "reading lengths");
+    ctx->last_host_wait_ms = ms_since(t_wait);
   }
-  if (host_ql) {
-    memcpy(h_ql, host_ql, n * 4);
-    memcpy(h_rl, host_rl, n * 4);
-  }
-  if (*h_bad) {
-    set_error("%u residue codes are >= the alphabet size %d", *h_bad, sp.alphabet);
+  if (ce != cudaSuccess) return cuda_fail(ce, "validation and planning");
+  const auto t_plan = clk::now();
+  if (h_ps->bad[0]) {
+    set_error("%u residue codes are >= the alphabet size %d", h_ps->bad[0], sp.alphabet);
     return FILTR_ERR_INVALID;
   }
+  const DevPlanSummary dsum = h_ps->sum;  // the staging area is reused below
 
-  // 2. fixed workspace parts, then the plan
-  const std::vector<uint32_t> ql(h_ql, h_ql + n), rl(h_rl, h_rl + n);
+  // 3. sizes, then the workspace parts that depend on them
   uint64_t max_m = 0, max_n = 0, stage_words = 0;
-  for (uint32_t p = 0; p < n; ++p) {
-    max_m = std::max<uint64_t>(max_m, h_ql[p]);
-    max_n = std::max<uint64_t>(max_n, h_rl[p]);
-    if (sp.traceback) stage_words += (uint64_t)h_ql[p] + h_rl[p] + 1;
+  if (dev_plan) {
+    max_m = dsum.max_m;
+    max_n = dsum.max_n;
+    stage_words = dsum.stage_words;
+  } else {
+    if (host_ql) {
+      memcpy(h_ql, host_ql, n * 4);
+      memcpy(h_rl, host_rl, n * 4);
+    }
+    for (uint32_t p = 0; p < n; ++p) {
+      max_m = std::max<uint64_t>(max_m, h_ql[p]);
+      max_n = std::max<uint64_t>(max_n, h_rl[p]);
+      if (sp.traceback) stage_words += (uint64_t)h_ql[p] + h_rl[p] + 1;
+    }
   }
   if (max_m >= (1u << 30) || max_n >= (1u << 30)) {
     set_error("sequence longer than 2^30");
@@ -262,23 +335,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   int blocks_per_sm = 1;
   for (int R : {8, 16, 24, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->full_blocks_per_sm(R, sp));
   if (!sp.use_band && !sp.use_xdrop && sp.precision != FILTR_PREC_I32)
-    for (int R : {16, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->pack_blocks_per_sm(R, sp));
+    for (int R : {8, 16, 24, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->pack_blocks_per_sm(R, sp));
   const int grid_max = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * blocks_per_sm,
                                                           ((int64_t)n + FULL_WARPS - 1) / FULL_WARPS);
   const uint32_t strip_stride = (uint32_t)(max_n + 2);
-  Carver c{ctx->ws, ctx->ws_bytes};
-  c.take<uint32_t>(64);  // d_bad
-  uint32_t *d_order = c.take<uint32_t>(n);
-  TbLayout *d_tbl = c.take<TbLayout>(n);
-  uint64_t *d_stage_off = c.take<uint64_t>(n);
-  FwdOut *d_fwd = c.take<FwdOut>(n);
-  uint64_t *d_offs = c.take<uint64_t>(n);
-  const size_t n_counters = (size_t)n + 4096;
-  uint32_t *d_counters = c.take<uint32_t>(n_counters);
-  uint64_t *d_total = c.take<uint64_t>(4);
-  uint32_t *d_ovf = c.take<uint32_t>(n);
-  uint32_t *d_novf = c.take<uint32_t>(4);
-  uint32_t *d_rerun = c.take<uint32_t>(n);
   int2 *d_strip = c.take<int2>((size_t)grid_max * FULL_WARPS * strip_stride);
   uint32_t *d_stage = sp.traceback ? c.take<uint32_t>(stage_words) : nullptr;
   uint32_t *d_tb = c.take<uint32_t>(0);
@@ -289,31 +349,75 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   }
   const uint64_t tb_budget = (ctx->ws_bytes - c.used) / 4;
 
-  Plan P;
-  PlanInput in{&sp, n, h_ql, h_rl, tb_budget, 8, ctx->xdrop_warps0};
-  in.shape_cost = ctx->tuned_costs(sp);
-  if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
-
-  // 3. upload the plan
-  const uint32_t n_main = (uint32_t)P.order.size();
-  std::vector<uint32_t> order_all = P.order;
-  order_all.insert(order_all.end(), P.trivial.begin(), P.trivial.end());
-  const size_t up_bytes = n * (4 + sizeof(TbLayout) + 8) + 64;
-  if (!ctx->ensure_host(up_bytes + 64)) {
-    set_error("pinned host allocation failed");
-    return FILTR_ERR_NOMEM;
+  // 4. the plan: the device's when its traceback fits one wave, else the host's
+  Plan &P = ctx->plan;
+  uint32_t n_main = 0, n_trivial = 0;
+  if (dev_plan && (!sp.traceback || dsum.tb_words <= tb_budget)) {
+    P.waves.clear();
+    P.trivial.clear();
+    Wave w;
+    w.tb_words = dsum.tb_words;
+    uint32_t at = 0;
+    for (int k = 0; k < SHAPE_TILED; ++k) {
+      if (!dsum.count[k]) continue;
+      Group g;
+      g.family = costs[k].packed ? FAM_PACK : FAM_FULL;
+      g.R = (uint8_t)costs[k].R;
+      g.warps = 1;
+      g.begin = at;
+      g.end = at + dsum.count[k];
+      at = g.end;
+      w.groups.push_back(g);
+    }
+    n_main = at;
+    n_trivial = dsum.count[KEY_TRIVIAL];
+    w.walk_begin = 0;
+    w.walk_end = n_main;
+    if (n_main) P.waves.push_back(w);
+    P.cigar_upper = dsum.cigar_upper;
+    P.cells_estimate = dsum.cells;
+    P.xdrop_w0 = 1;
+    ce = cudaMemsetAsync(d_counters, 0, n_counters * 4, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "clearing the work queues");
+  } else {
+    if (dev_plan && !host_ql) {  // the host plan needs the lengths after all
+      ce = cudaMemcpyAsync(h_ql, b.q_len, n * 4, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_rl, b.r_len, n * 4, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) return cuda_fail(ce, "reading lengths");
+    } else if (dev_plan) {
+      memcpy(h_ql, host_ql, n * 4);
+      memcpy(h_rl, host_rl, n * 4);
+    }
+    dev_plan = false;
+    ctx->h_ql.assign(h_ql, h_ql + n);  // the staging area is reused for the plan upload
+    ctx->h_rl.assign(h_rl, h_rl + n);
+    PlanInput in{&sp, n, ctx->h_ql.data(), ctx->h_rl.data(), tb_budget, 8, ctx->xdrop_warps0};
+    in.shape_cost = costs;
+    if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
+    n_main = (uint32_t)P.order.size();
+    n_trivial = (uint32_t)P.trivial.size();
+    const size_t up_bytes = n * (4 + sizeof(TbLayout) + 8) + 64;
+    if (!ctx->ensure_host(up_bytes + 64)) {
+      set_error("pinned host allocation failed");
+      return FILTR_ERR_NOMEM;
+    }
+    char *hs = reinterpret_cast<char *>(ctx->h_stage);
+    memcpy(hs, P.order.data(), (size_t)n_main * 4);  // then the trivial pairs
+    if (n_trivial) memcpy(hs + (size_t)n_main * 4, P.trivial.data(), (size_t)n_trivial * 4);
+    memcpy(hs + n * 4, P.tbl.data(), n * sizeof(TbLayout));
+    memcpy(hs + n * (4 + sizeof(TbLayout)), P.stage_off.data(), n * 8);
+    ce = cudaMemcpyAsync(d_order, hs, n * 4, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(d_tbl, hs + n * 4, n * sizeof(TbLayout), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(d_stage_off, hs + n * (4 + sizeof(TbLayout)), n * 8, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d_counters, 0, n_counters * 4, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "uploading the plan");
   }
-  char *hs = reinterpret_cast<char *>(ctx->h_stage);
-  memcpy(hs, order_all.data(), n * 4);
-  memcpy(hs + n * 4, P.tbl.data(), n * sizeof(TbLayout));
-  memcpy(hs + n * (4 + sizeof(TbLayout)), P.stage_off.data(), n * 8);
-  ce = cudaMemcpyAsync(d_order, hs, n * 4, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(d_tbl, hs + n * 4, n * sizeof(TbLayout), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(d_stage_off, hs + n * (4 + sizeof(TbLayout)), n * 8, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d_counters, 0, n_counters * 4, st);
-  if (ce != cudaSuccess) return cuda_fail(ce, "uploading the plan");
+  ctx->last_dev_plan = dev_plan;
+  const std::vector<uint32_t> &ql = ctx->h_ql, &rl = ctx->h_rl;
+  ctx->last_host_plan_ms = ms_since(t_plan);
 
   FullArgs fa;
   fa.b = b;
@@ -367,7 +471,9 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       fa.n_order = cnt;
       fa.counter = d_counters + (counter_i++ % n_counters);
       const int bps = pk ? ctx->pack_blocks_per_sm(R, sp) : ctx->full_blocks_per_sm(R, sp);
+      // the strip buffer holds grid_max blocks' warps
       int grid = (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + FULL_WARPS - 1) / FULL_WARPS);
+      grid = std::min(grid, grid_max);
       ce = pk ? launch_pack(fa, R, std::max(grid, 1), st) : launch_full(fa, R, std::max(grid, 1), st);
       ++launches;
       return ce == cudaSuccess;
@@ -487,12 +593,12 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       i0 = i1;
     }
   }
-  if (!P.trivial.empty()) {
-    ce = launch_trivial(b, sp, d_order + n_main, (uint32_t)P.trivial.size(), out, d_fwd, st);
+  if (n_trivial) {
+    ce = launch_trivial(b, sp, d_order + n_main, n_trivial, out, d_fwd, st);
     ++launches;
     if (ce == cudaSuccess && sp.traceback) {
       wa.order = d_order + n_main;
-      wa.n_order = (uint32_t)P.trivial.size();
+      wa.n_order = n_trivial;
       ce = launch_walk(wa, st);
       ++launches;
     }
@@ -780,6 +886,9 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out) {
   out->waves = (uint32_t)c->last_waves;
   out->cells_planned = c->last_cells_estimate;
   out->pairs_i16x2 = c->last_pairs_packed;
+  out->device_plan = c->last_dev_plan ? 1u : 0u;
+  out->ms_host_wait = c->last_host_wait_ms;
+  out->ms_host_plan = c->last_host_plan_ms;
   cudaSetDevice(c->device);
   double *acc[4] = {&out->ms_validate, &out->ms_forward, &out->ms_walk, &out->ms_place};
   cudaEvent_t first = nullptr, last = nullptr;

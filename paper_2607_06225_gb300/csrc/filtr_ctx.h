@@ -25,6 +25,11 @@ struct Ctx {
   std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
   uint64_t last_cells_estimate = 0;
   uint32_t last_pairs_packed = 0;
+  double last_host_wait_ms = 0, last_host_plan_ms = 0;
+  Plan plan;                       // the last call's plan; its buffers are reused
+  int dev_plan_mode = 0;           // 0: device planner by batch size, 1: never, 2: always
+  bool last_dev_plan = false;      // the last call was planned on the device
+  std::vector<uint32_t> h_ql, h_rl;  // the last call's lengths (host copies)
   int last_waves = 0;
   uint32_t last_launches = 0;
   int xdrop_warps0 = 0;       // first window width (warps) of X-drop pairs, 0: estimated

@@ -512,6 +512,15 @@ filtr_status filtr_test_set_first_width(filtr_ctx *ctx, int32_t warps) {
   return FILTR_OK;
 }
 
+filtr_status filtr_test_set_device_plan(filtr_ctx *ctx, int32_t mode) {
+  if (!ctx || mode < 0 || mode > 2) {
+    set_error("filtr_test_set_device_plan: bad arguments");
+    return FILTR_ERR_INVALID;
+  }
+  reinterpret_cast<Ctx *>(ctx)->dev_plan_mode = mode;
+  return FILTR_OK;
+}
+
 filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on) {
   if (!ctx) {
     set_error("filtr_test_force_recompute: ctx is NULL");

@@ -25,9 +25,7 @@ const ShapeCost kDefaultShapeCost[SHAPE_TILED] = {
     {16, 63, 12.0f, 40.0f, true},  {8, 63, 12.0f, 40.0f, true}};
 
 double shape_cost(const ShapeCost &c, uint32_t M, uint32_t N) {
-  const uint64_t hs = 32u * c.R;
-  const uint64_t strips = (M + hs - 1) / hs;
-  return (double)strips * (double)(N + c.fill) * ((double)c.per_row * c.R + c.per_step);
+  return (double)strips_of(M, c.R) * (double)(N + c.fill) * ((double)c.per_row * c.R + c.per_step);
 }
 
 // Rows per lane: the tile height 32R whose padded work, strips x (N + 31 steps)
@@ -45,44 +43,6 @@ int full_rows_per_lane(uint32_t M, uint32_t N) {
     }
   }
   return best;
-}
-
-uint64_t full_tb_words(uint32_t M, uint32_t N, int R, const ScoreParams &sp) {
-  const int64_t HS = 32 * R;
-  const bool band = sp.use_band != 0;
-  if (!band) return (uint64_t)((M + HS - 1) / HS) * (uint64_t)strip_tb_words(1, N, R);
-  int64_t lo = -(int64_t)M - 1, hi = (int64_t)N + 1;
-  if (band) band_limits(M, N, sp.band, sp.band_literal, &lo, &hi);
-  uint64_t w = 0;
-  const int64_t ns = (M + HS - 1) / HS;
-  for (int64_t s = 0; s < ns; ++s) {
-    int64_t jl, jh;
-    strip_cols(s * HS, HS, M, N, band, lo, hi, &jl, &jh);
-    if (jl > jh) break;
-    w += (uint64_t)strip_tb_words(jl, jh, R);
-  }
-  return w;
-}
-
-uint64_t band_cells(uint32_t M, uint32_t N, const ScoreParams &sp) {
-  if (!sp.use_band) return (uint64_t)M * N;
-  int64_t lo, hi;
-  band_limits(M, N, sp.band, sp.band_literal, &lo, &hi);
-  // Sum over diagonals d in [lo, hi] of the cells of diagonal d inside the
-  // matrix, f(d) = min(M, N - d) - max(0, -d) for 1-M <= d <= N-1.  f is linear
-  // between its kinks at d = 0 and d = N - M, so each piece is an arithmetic sum.
-  const int64_t Mi = M, Ni = N;
-  const int64_t A = std::max<int64_t>(lo, 1 - Mi), B = std::min<int64_t>(hi, Ni - 1);
-  if (A > B) return 0;
-  auto f = [&](int64_t d) { return std::min<int64_t>(Mi, Ni - d) - std::max<int64_t>(0, -d); };
-  const int64_t k1 = std::min<int64_t>(0, Ni - Mi), k2 = std::max<int64_t>(0, Ni - Mi);
-  const int64_t cut[4] = {A - 1, std::min(std::max(k1, A - 1), B), std::min(std::max(k2, A - 1), B), B};
-  uint64_t c = 0;
-  for (int s = 0; s < 3; ++s) {
-    const int64_t a = cut[s] + 1, b = cut[s + 1];
-    if (b >= a) c += (uint64_t)((f(a) + f(b)) * (b - a + 1) / 2);
-  }
-  return c;
 }
 
 // X-drop / Z-drop live region: a cell delta places off the best cell along an
@@ -116,14 +76,6 @@ int xdrop_first_width(const ScoreParams &sp, uint32_t n, const uint32_t *q_len,
   return 32;
 }
 
-// half-octave buckets: 2 * floor(log2(cost)) + the next bit
-static int cost_bucket(uint64_t cost) {
-  if (cost < 2) return 0;
-  const int lg = 63 - __builtin_clzll(cost);
-  const int b = 2 * lg + (int)((cost >> (lg - 1)) & 1);
-  return b < 63 ? b : 63;
-}
-
 bool make_plan(const PlanInput &in, Plan *P) {
   const ScoreParams &sp = *in.sp;
   const uint32_t n = in.n;
@@ -142,23 +94,29 @@ bool make_plan(const PlanInput &in, Plan *P) {
   // shape keys: 0..3 the int32 tiled kernel with R = 32, 24, 16, 8; 4..7 the
   // int16x2 tiled kernel with R = 32, 24, 16, 8; 8 the X-drop kernel
   const ShapeCost *costs = in.shape_cost ? in.shape_cost : kDefaultShapeCost;
-  const bool pack_ok = !sp.use_band && !sp.use_xdrop && sp.precision != FILTR_PREC_I32;
-  std::vector<uint8_t> bucket(n), shape(n);
-  std::vector<uint64_t> words(n);
-  std::vector<uint32_t> cnt(64, 0);
+  const ShapeTable tab = make_shape_table(costs, sp);
+  P->s_bucket.resize(n);
+  P->s_shape.resize(n);
+  P->s_words.resize(n);
+  uint8_t *bucket = P->s_bucket.data(), *shape = P->s_shape.data();
+  uint64_t *words = P->s_words.data();
+  uint32_t cnt[64] = {};
   const int xw = in.xdrop_warps > 0
                      ? in.xdrop_warps
                      : (sp.use_xdrop ? xdrop_first_width(sp, n, in.q_len, in.r_len, in.xdrop_slots) : 1);
   P->xdrop_w0 = xw;
   uint32_t live = 0;
+  // running totals in locals: the byte stores below may alias *P
+  uint64_t max_n = 0, max_m = 0, cigar_upper = 0, stage_words = 0, cells = 0;
+  uint64_t *stage_off = P->stage_off.data();
   for (uint32_t p = 0; p < n; ++p) {
     const uint32_t M = in.q_len[p], N = in.r_len[p];
-    if (N > P->max_n) P->max_n = N;
-    if (M > P->max_m) P->max_m = M;
-    P->cigar_upper += (uint64_t)M + N;
+    max_n = N > max_n ? N : max_n;
+    max_m = M > max_m ? M : max_m;
+    cigar_upper += (uint64_t)M + N;
     if (sp.traceback) {
-      P->stage_off[p] = P->stage_words;
-      P->stage_words += (uint64_t)M + N + 1;
+      stage_off[p] = stage_words;
+      stage_words += (uint64_t)M + N + 1;
     }
     // an empty side leaves no cell to evaluate, except under X-drop, where the
     // gap cells of row 0 / column 0 are themselves subject to the prune test
@@ -168,33 +126,15 @@ bool make_plan(const PlanInput &in, Plan *P) {
       continue;
     }
     const uint64_t cost = band_cells(M, N, sp);
-    P->cells_estimate += cost;
+    cells += cost;
     uint64_t w = 0;
     if (sp.use_xdrop) {
       shape[p] = SHAPE_XDROP;
       if (sp.traceback) w = xd_tb_words(M, N, xw, in.xdrop_slots);
     } else {
-      // cheapest eligible shape; FILTR_PREC_I16X2 takes the packed kernel
-      // whenever the pair's score range fits it
-      const bool packable =
-          pack_ok && pack_bias(sp.mode, sp.o, sp.e, sp.smin, sp.smax, M, N) >= 0;
-      int best = -1;
-      double bc = 0;
-      for (int k = 0; k < SHAPE_TILED; ++k) {
-        if (costs[k].packed && !packable) continue;
-        if (sp.use_band && costs[k].packed) continue;
-        if (packable && sp.precision == FILTR_PREC_I16X2 && !costs[k].packed) continue;
-        const double c = shape_cost(costs[k], M, N);
-        if (best < 0 || c < bc) {
-          best = k;
-          bc = c;
-        }
-      }
-      shape[p] = (uint8_t)best;
-      const ShapeCost &sc = costs[best];
-      if (sp.traceback)
-        w = sc.packed ? (uint64_t)((M + 32u * sc.R - 1) / (32u * sc.R)) * pack_strip_tb_words(1, N, sc.R)
-                      : full_tb_words(M, N, sc.R, sp);
+      const int k = choose_shape(tab, sp, M, N);
+      shape[p] = (uint8_t)k;
+      if (sp.traceback) w = shape_tb_words(tab, k, M, N, sp);
     }
     if (sp.traceback && w > in.tb_budget_words) {
       set_error("pair %u needs %llu traceback bytes, more than the workspace allows", p,
@@ -202,15 +142,21 @@ bool make_plan(const PlanInput &in, Plan *P) {
       return false;
     }
     words[p] = w;
-    bucket[p] = (uint8_t)(63 - cost_bucket(cost));
+    bucket[p] = (uint8_t)cost_bucket_desc(cost);
     cnt[bucket[p]]++;
     ++live;
   }
+  P->max_n = max_n;
+  P->max_m = max_m;
+  P->cigar_upper = cigar_upper;
+  P->stage_words = stage_words;
+  P->cells_estimate = cells;
 
   // counting sort of pair ids, most expensive bucket first
-  std::vector<uint32_t> start(64, 0);
+  uint32_t start[64] = {};
   for (int b = 1; b < 64; ++b) start[b] = start[b - 1] + cnt[b - 1];
-  std::vector<uint32_t> sorted(live);
+  P->s_sorted.resize(live);
+  std::vector<uint32_t> &sorted = P->s_sorted;
   for (uint32_t p = 0; p < n; ++p)
     if (shape[p] != 255) sorted[start[bucket[p]]++] = p;
 

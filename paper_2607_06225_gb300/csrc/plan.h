@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "filtr_internal.h"
+#include "plan_pair.h"
 
 namespace filtr {
 
@@ -32,16 +33,13 @@ struct Plan {
   uint64_t cigar_upper = 0;       // sum over pairs of M + N: no CIGAR can be longer
   int xdrop_w0 = 1;               // group width X-drop / Z-drop pairs first run at
   uint64_t cells_estimate = 0;
+  // per-pair scratch of make_plan, kept with the plan so that a context that
+  // plans batch after batch reuses its pages
+  std::vector<uint8_t> s_bucket, s_shape;
+  std::vector<uint64_t> s_words;
+  std::vector<uint32_t> s_sorted;
 };
 
-// Tiled kernel shapes (int32 and int16x2, R = 32, 24, 16, 8), then X-drop.
-enum : int { SHAPE_TILED = 8, SHAPE_XDROP = 8, SHAPE_KEYS = 9 };
-struct ShapeCost {
-  int R, fill;        // rows per lane; fill steps per strip (staircase)
-  float per_row;      // cost of one row (int32) or one packed register pair of rows / 2
-  float per_step;     // per-step overhead of a lane
-  bool packed;
-};
 extern const ShapeCost kDefaultShapeCost[SHAPE_TILED];
 double shape_cost(const ShapeCost &c, uint32_t M, uint32_t N);
 
@@ -62,12 +60,56 @@ int xdrop_first_width(const ScoreParams &sp, uint32_t n, const uint32_t *q_len,
 
 // Rows per lane of the tiled kernel for an M x N pair.
 int full_rows_per_lane(uint32_t M, uint32_t N);
-// Traceback words of one pair in the tiled kernel.
-uint64_t full_tb_words(uint32_t M, uint32_t N, int R, const ScoreParams &sp);
-// Cell count of one pair under a static band (or the full matrix).
-uint64_t band_cells(uint32_t M, uint32_t N, const ScoreParams &sp);
 
 // Returns false (and sets the error message) if a single pair cannot fit.
 bool make_plan(const PlanInput &in, Plan *out);
+
+// ---- the same plan built on the device (tiled batches in one wave) ----
+//
+// Three launches over the pairs: classify (shape and cost bucket of each pair,
+// a block histogram of the keys, block sums of the CIGAR staging words and
+// batch totals), scan (key histogram and block sums to starting offsets), and
+// place (pair ids scattered into shape-major, cost-descending order with
+// warp-aggregated atomics; disjoint traceback offsets; staging offsets in pair
+// order).  Pairs with an empty side take key KEY_TRIVIAL, after every shape.
+// Shapes and buckets are those make_plan gives; the order inside one (shape,
+// bucket) cell and the placement of traceback areas depend on atomics, which
+// changes no result.
+enum : int { KEY_TRIVIAL = SHAPE_TILED, PLAN_KEYS = (SHAPE_TILED + 1) * 64 };
+
+struct DevPlanSummary {
+  uint32_t count[SHAPE_TILED + 1];  // pairs per tiled shape, then empty pairs
+  uint32_t max_m, max_n;
+  uint32_t pad;
+  unsigned long long tb_words;      // traceback words of all pairs
+  unsigned long long cells;         // cells of the non-empty pairs
+  unsigned long long stage_words;   // sum of M + N + 1 (traceback on)
+  unsigned long long cigar_upper;   // sum of M + N
+};
+
+// Zeroed before each call.  The host reads back bad[] and sum with one copy.
+struct DevPlanState {
+  uint32_t bad[64];                 // residue validation count in bad[0]
+  DevPlanSummary sum;
+  uint32_t hist[PLAN_KEYS];
+  uint32_t cursor[PLAN_KEYS];
+  unsigned long long tb_cursor;
+};
+
+struct DevPlanArgs {
+  const uint32_t *q_len, *r_len;
+  uint32_t n;
+  ScoreParams sp;
+  ShapeTable tab;
+  DevPlanState *state;
+  uint16_t *key;        // per pair: shape * 64 + bucket
+  uint64_t *words;      // per pair: traceback words
+  uint64_t *blk;        // per block of DEV_PLAN_BLOCK pairs: staging words, then base
+  uint32_t *order;      // out: pair ids
+  TbLayout *tbl;        // out: per pair
+  uint64_t *stage_off;  // out: per pair (traceback on)
+};
+constexpr int DEV_PLAN_BLOCK = 256;
+cudaError_t launch_plan(const DevPlanArgs &a, cudaStream_t st);
 
 }  // namespace filtr
