@@ -129,7 +129,7 @@ class ClockSampler:
         return out
 
 
-TILED_SOURCES = ("k_strip.cuh", "k_full_impl.cuh", "k_pack.cu")
+TILED_SOURCES = ("k_strip.cuh", "k_full_impl.cuh", "k_pack_impl.cuh")
 
 
 def tiled_source_sha():

@@ -257,25 +257,29 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
 /* Autotuning of the tiled kernel shapes (the paper leaves autotuning to
  * future work, Sec. 11).  Times every tiled shape -- the int32 tile with 32,
  * 24, 16 or 8 rows per lane and, where the parameters allow it, the int16x2
- * tile with the same heights -- on calibration batches that fill every resident warp
- * slot of the device three times (pairs of one full strip of query rows by 512
- * reference residues, random codes), and keeps in ctx the device time per warp
- * step of each shape for this recurrence kind (mode, gap model, traceback,
- * alphabet, band).  Later filtr_align_batch calls of the same kind give each
- * pair the shape whose predicted time, strips x (N + fill steps) x that cost,
- * is smallest.  Results never change: the shapes are bit-exact alternatives.
- *   out: optional; rows_per_lane / packed describe the eight shapes, always in
- *        this order: int32 R = 32, 24, 16, 8, then int16x2 R = 32, 24, 16, 8; and
- *        ns_per_warp_step is 0 for shapes not timed (not allowed for these
- *        parameters, or too large for the workspace).
+ * tile with 32, 28, 24, 20, 16, 12 or 8 -- on calibration batches that fill
+ * every resident warp slot of the device three times (pairs of one full strip
+ * of query rows by 512 reference residues, random codes), and keeps in ctx the
+ * device time per warp step of each shape for this recurrence kind (mode, gap
+ * model, traceback, alphabet, band).  Later filtr_align_batch calls of the same
+ * kind give each pair the shape whose predicted time, strips x (N + fill
+ * steps) x that cost, is smallest.  Results never change: the shapes are
+ * bit-exact alternatives.
+ *   out: optional; n_shapes (11) entries of rows_per_lane / packed describe the
+ *        shapes, always in this order: int32 R = 32, 24, 16, 8, then int16x2
+ *        R = 32, 28, 24, 20, 16, 12, 8; ns_per_warp_step is 0 for shapes not
+ *        timed (not allowed for these parameters, or too large for the
+ *        workspace); entries past n_shapes are 0.
  * Synchronous (waits for the context's previous call); uses the workspace.
  * Errors: FILTR_ERR_INVALID (NULL ctx, bad params, X-drop parameters, which
  * use the antidiagonal kernel only), FILTR_ERR_NOMEM (the workspace holds no
  * calibration batch), FILTR_ERR_CUDA. */
+#define FILTR_TUNE_MAX_SHAPES 16
 typedef struct {
-  int32_t rows_per_lane[8];
-  int32_t packed[8];
-  double ns_per_warp_step[8];
+  int32_t n_shapes;
+  int32_t rows_per_lane[FILTR_TUNE_MAX_SHAPES];
+  int32_t packed[FILTR_TUNE_MAX_SHAPES];
+  double ns_per_warp_step[FILTR_TUNE_MAX_SHAPES];
 } filtr_tune_report;
 filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params, filtr_tune_report *out);
 
@@ -286,7 +290,7 @@ filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params, filtr_tu
  * ns_per_warp_step is 0 keep the built-in cost scaled to the given ones.
  * Host only: launches nothing, does not wait for the GPU.
  * Errors: FILTR_ERR_INVALID (NULL ctx or report, bad params, X-drop
- * parameters, a shape list other than the eight filtr_autotune reports in its
+ * parameters, a shape list other than the one filtr_autotune reports, in its
  * order, a negative or non-finite cost, or no positive cost). */
 filtr_status filtr_tune_apply(filtr_ctx *ctx, const filtr_params *params,
                               const filtr_tune_report *report);

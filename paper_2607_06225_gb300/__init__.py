@@ -11,7 +11,8 @@ import numpy as np
 from ._lib import (ALPHA_DNA, ALPHA_PROTEIN, ERR_CIGAR_CAP, ERR_INVALID, ERR_UNSUPPORTED, GLOBAL,
                    LOCAL, OK, PREC_AUTO, PREC_I16X2, PREC_I32, PRUNE_BAND, PRUNE_BAND_LITERAL,
                    PRUNE_XDROP, PRUNE_ZDROP, RESULT_DTYPE, ST_DROPPED, ST_EMPTY, ST_OK, ST_TOO_WIDE,
-                   ST_UNREACHABLE, XDROP_INF, Context, FiltrError, Params, check, last_error, lib,
+                   ST_UNREACHABLE, TUNE_SHAPES, XDROP_INF, Context, FiltrError, Params, check,
+                   last_error, lib,
                    make_params)
 
 __all__ = ["Context", "FiltrError", "Params", "make_params", "DeviceBatch", "align_batch",

@@ -56,12 +56,15 @@ class Stats(C.Structure):
 
 # the eight tiled shapes in the order filtr_autotune reports them
 TUNE_SHAPES = [("i32", 32), ("i32", 24), ("i32", 16), ("i32", 8),
-               ("i16x2", 32), ("i16x2", 24), ("i16x2", 16), ("i16x2", 8)]
+               ("i16x2", 32), ("i16x2", 28), ("i16x2", 24), ("i16x2", 20), ("i16x2", 16),
+               ("i16x2", 12), ("i16x2", 8)]
+TUNE_MAX_SHAPES = 16
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("rows_per_lane", C.c_int32 * 8), ("packed", C.c_int32 * 8),
-                ("ns_per_warp_step", C.c_double * 8)]
+    _fields_ = [("n_shapes", C.c_int32), ("rows_per_lane", C.c_int32 * TUNE_MAX_SHAPES),
+                ("packed", C.c_int32 * TUNE_MAX_SHAPES),
+                ("ns_per_warp_step", C.c_double * TUNE_MAX_SHAPES)]
 
 
 RESULT_DTYPE = np.dtype([("score", np.int32), ("q_begin", np.int32), ("q_end", np.int32),
@@ -244,7 +247,7 @@ class Context:
         rep = TuneReport()
         check(lib().filtr_autotune(self.handle, C.byref(params), C.byref(rep)), "filtr_autotune")
         out = {}
-        for k in range(8):
+        for k in range(rep.n_shapes):
             if rep.ns_per_warp_step[k] > 0:
                 kind = "i16x2" if rep.packed[k] else "i32"
                 out[f"{kind} R={rep.rows_per_lane[k]}"] = rep.ns_per_warp_step[k]
@@ -254,6 +257,7 @@ class Context:
         """Install costs from an earlier autotune() table (filtr_tune_apply);
         shapes missing from the table keep the scaled built-in cost."""
         rep = TuneReport()
+        rep.n_shapes = len(TUNE_SHAPES)
         for k, (kind, R) in enumerate(TUNE_SHAPES):
             rep.rows_per_lane[k] = R
             rep.packed[k] = 1 if kind == "i16x2" else 0

@@ -335,7 +335,9 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   int blocks_per_sm = 1;
   for (int R : {8, 16, 24, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->full_blocks_per_sm(R, sp));
   if (!sp.use_band && !sp.use_xdrop && sp.precision != FILTR_PREC_I32)
-    for (int R : {8, 16, 24, 32}) blocks_per_sm = std::max(blocks_per_sm, ctx->pack_blocks_per_sm(R, sp));
+    for (int k = 0; k < SHAPE_TILED; ++k)
+      if (kDefaultShapeCost[k].packed)
+        blocks_per_sm = std::max(blocks_per_sm, ctx->pack_blocks_per_sm(kDefaultShapeCost[k].R, sp));
   const int grid_max = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * blocks_per_sm,
                                                           ((int64_t)n + FULL_WARPS - 1) / FULL_WARPS);
   const uint32_t strip_stride = (uint32_t)(max_n + 2);

@@ -161,6 +161,9 @@ FILTR_HD int pack_bias(int mode, int o, int e, int smin, int smax, int64_t M, in
 // Packed tile: words per lane and step -- each half's R/2 cells fill
 // ceil(R/16) words of four 8-cell bit planes.
 FILTR_HD int pack_words_per_step(int R) { return 2 * ((R / 2 + 7) / 8); }
+// Packed tile query profile: per residue, 32 lanes x two halves x ceil(R/8)
+// words (each half's R/2 bytes padded to whole words).
+FILTR_HD constexpr int pack_prof_stride(int R) { return 256 * ((R / 2 + 3) / 4); }
 FILTR_HD uint64_t pack_strip_tb_words(int64_t jlo, int64_t jhi, int R) {
   return jhi >= jlo ? (uint64_t)((jhi - jlo + 1) + 63) * (uint64_t)pack_words_per_step(R) * 32u : 0;
 }
@@ -228,8 +231,14 @@ int long_blocks_per_sm(const ScoreParams &sp);
 cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
 int full_smem_bytes(int R, int alphabet);
 int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
-cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);  // R = 8, 16, 24, 32
+// int16x2 tile, R = 8, 12, 16, 20, 24, 28, 32 (k_pack.cu; 12, 20, 28 in k_pack_mid.cu)
+cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);
 int pack_max_blocks_per_sm(int R, const ScoreParams &sp);
+cudaError_t launch_pack_mid(const FullArgs &a, int R, int grid, cudaStream_t s);
+int pack_mid_blocks_per_sm(int R, const ScoreParams &sp);
+inline int pack_smem_bytes(int R, int alphabet) {
+  return 512 + FULL_WARPS * alphabet * pack_prof_stride(R);
+}
 cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
                          uint32_t *n_overflow, cudaStream_t s);
 int xd_pairs_per_cta(int W);

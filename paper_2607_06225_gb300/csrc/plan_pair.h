@@ -8,8 +8,9 @@
 
 namespace filtr {
 
-// Tiled kernel shapes (int32 and int16x2, R = 32, 24, 16, 8), then X-drop.
-enum : int { SHAPE_TILED = 8, SHAPE_XDROP = 8, SHAPE_KEYS = 9 };
+// Tiled kernel shapes (int32 R = 32, 24, 16, 8; int16x2 R = 32, 28, 24, 20,
+// 16, 12, 8), then X-drop.
+enum : int { SHAPE_TILED = 11, SHAPE_XDROP = 11, SHAPE_KEYS = 12 };
 struct ShapeCost {
   int R, fill;        // rows per lane; fill steps per strip (staircase)
   float per_row;      // cost of one row (int32) or one packed register pair of rows / 2
@@ -17,18 +18,23 @@ struct ShapeCost {
   bool packed;
 };
 
-// ceil(M / 32R) for R = 8, 16, 24, 32: tile heights are multiples of 256 rows,
-// and ceil(ceil(M / 256) / (R / 8)) = ceil(M / 32R), so one shift and a
-// division by a small constant give all four.
-FILTR_HD uint64_t strips_of(uint32_t M, int R) {
-  const uint32_t s256 = (M + 255u) >> 8;
-  switch (R) {
-    case 8: return s256;
-    case 16: return (s256 + 1u) >> 1;
-    case 24: return (s256 + 2u) / 3u;
-    case 32: return (s256 + 3u) >> 2;
-    default: return ((uint64_t)M + 32u * R - 1) / (32u * R);
+// ceil(M / 32R) for R a multiple of 4 from 8 to 32: tile heights are multiples
+// of 128 rows, and ceil(ceil(M / 128) / (R / 4)) = ceil(M / 32R), so one shift
+// and a division by a small constant give every height.
+FILTR_HD uint32_t strips_s128(uint32_t s128, int d) {  // ceil(s128 / d), d = R / 4
+  switch (d) {
+    case 2: return (s128 + 1u) >> 1;
+    case 3: return (s128 + 2u) / 3u;
+    case 4: return (s128 + 3u) >> 2;
+    case 5: return (s128 + 4u) / 5u;
+    case 6: return (s128 + 5u) / 6u;
+    case 7: return (s128 + 6u) / 7u;
+    default: return (s128 + 7u) >> 3;
   }
+}
+FILTR_HD uint64_t strips_of(uint32_t M, int R) {
+  if (R % 4 != 0 || R < 8 || R > 32) return ((uint64_t)M + 32u * R - 1) / (32u * R);
+  return strips_s128((uint32_t)(((uint64_t)M + 127u) >> 7), R / 4);
 }
 
 // Traceback words of one pair in the int32 tile of R rows per lane.
@@ -95,7 +101,7 @@ struct ShapeTable {
   double coef[SHAPE_TILED];  // per_row x R + per_step
   double fill[SHAPE_TILED];
   int R[SHAPE_TILED];
-  int hidx[SHAPE_TILED];     // R / 8 - 1
+  int hidx[SHAPE_TILED];     // R / 4 - 2
   int packed[SHAPE_TILED];
   int elig[SHAPE_TILED];     // shapes the recurrence kind allows, in table order
   int n_elig, n_elig_packed;
@@ -108,7 +114,7 @@ inline ShapeTable make_shape_table(const ShapeCost *costs, const ScoreParams &sp
     t.coef[k] = (double)costs[k].per_row * costs[k].R + costs[k].per_step;
     t.fill[k] = (double)costs[k].fill;
     t.R[k] = costs[k].R;
-    t.hidx[k] = costs[k].R / 8 - 1;
+    t.hidx[k] = costs[k].R / 4 - 2;
     t.packed[k] = costs[k].packed ? 1 : 0;
     if (costs[k].packed && !pack_ok) continue;
     t.elig[t.n_elig++] = k;
@@ -126,9 +132,10 @@ FILTR_HD int choose_shape(const ShapeTable &t, const ScoreParams &sp, uint32_t M
   const bool packable =
       t.n_elig_packed > 0 && pack_bias(sp.mode, sp.o, sp.e, sp.smin, sp.smax, M, N) >= 0;
   const bool only_packed = packable && sp.precision == FILTR_PREC_I16X2;
-  const uint32_t s256 = (M + 255u) >> 8;
-  const double strips[4] = {(double)s256, (double)((s256 + 1u) >> 1), (double)((s256 + 2u) / 3u),
-                            (double)((s256 + 3u) >> 2)};
+  const uint32_t s128 = (uint32_t)(((uint64_t)M + 127u) >> 7);
+  double strips[7];  // R = 8, 12, ..., 32
+#pragma unroll
+  for (int d = 2; d <= 8; ++d) strips[d - 2] = (double)strips_s128(s128, d);
   const double Nd = (double)N;
   int best = t.elig[0];
   double bc = 1e300;

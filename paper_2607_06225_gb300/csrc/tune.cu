@@ -1,7 +1,7 @@
 // tune.cu -- filtr_autotune: measured costs of the tiled kernel shapes.
 //
-// The planner gives each pair the tiled shape (the int32 tile or the int16x2
-// tile, each with R = 32, 24, 16 or 8 rows per lane) whose predicted
+// The planner gives each pair the tiled shape (the int32 tile with R = 32, 24,
+// 16 or 8 rows per lane, or the int16x2 tile with R = 32, 28, ..., 8) whose predicted
 // time, strips x (N + fill steps) x cost-per-warp-step, is smallest.  The
 // built-in costs come from instruction counts; this entry point replaces them
 // with the device time per warp step measured on this GPU for one recurrence
@@ -194,7 +194,11 @@ extern "C" filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *param
   cudaStream_t st = nullptr;
   e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-  if (out) memset(out, 0, sizeof *out);
+  static_assert(SHAPE_TILED <= FILTR_TUNE_MAX_SHAPES, "tune report too small");
+  if (out) {
+    memset(out, 0, sizeof *out);
+    out->n_shapes = SHAPE_TILED;
+  }
   double ns_k[SHAPE_TILED] = {};
   bool any = false;
   for (int k = 0; k < SHAPE_TILED; ++k) {
@@ -241,6 +245,11 @@ extern "C" filtr_status filtr_tune_apply(filtr_ctx *ctx, const filtr_params *par
   }
   double ns_k[SHAPE_TILED] = {};
   bool any = false;
+  if (report->n_shapes != SHAPE_TILED) {
+    set_error("filtr_tune_apply: the report lists %d shapes, this library has %d", report->n_shapes,
+              SHAPE_TILED);
+    return FILTR_ERR_INVALID;
+  }
   for (int k = 0; k < SHAPE_TILED; ++k) {
     const ShapeCost &d = kDefaultShapeCost[k];
     if (report->rows_per_lane[k] != d.R || report->packed[k] != (d.packed ? 1 : 0)) {

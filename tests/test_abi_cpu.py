@@ -86,6 +86,7 @@ def test_tune_apply_rejects_on_host(L):
     S = np.zeros((4, 4), np.int8)
     p = L.make_params(S, gap_open=4, gap_extend=2)
     rep = L.TuneReport()
+    rep.n_shapes = len(L.TUNE_SHAPES)
     for k, (kind, R) in enumerate(L.TUNE_SHAPES):
         rep.rows_per_lane[k] = R
         rep.packed[k] = int(kind == "i16x2")
