@@ -254,6 +254,48 @@ typedef struct {
 filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
 
+/* ---- Captured batch pipeline (CUDA graph) --------------------------------
+ * The batched path of filtr_align_batch for tiled batches (full matrix or
+ * static band, no X-drop), captured once as a CUDA graph and replayed per batch
+ * with no host synchronisation: the residue check, the device plan, one
+ * persistent launch per tiled shape, the traceback walks and the CIGAR
+ * placement run back to back on the device (the batching pattern of the
+ * paper's GPU-side design; the paper itself has no counterpart).  Results are
+ * identical to filtr_align_batch's.
+ *
+ * filtr_graph_create: bounds fixed at creation -- at most max_pairs pairs per
+ *   launch, every query and reference at most max_len residues -- and the
+ *   graph's own device memory, workspace_bytes in all (capacity-sized plan
+ *   arrays, strip buffers and CIGAR staging of max_pairs x (2 max_len + 1)
+ *   words, then the traceback area: the rest).  Plans with the context's tuned
+ *   shape costs as they are at creation.  Synchronous; allocates.
+ *   Errors: FILTR_ERR_INVALID (NULL ctx or out, bad params, zero bounds,
+ *   max_len >= 2^30), FILTR_ERR_UNSUPPORTED (X-drop / Z-drop parameters, or
+ *   scores that could exceed the int32 range for max_len), FILTR_ERR_NOMEM
+ *   (workspace_bytes below the fixed parts), FILTR_ERR_CUDA.
+ * filtr_graph_launch: one batch, arguments as filtr_align_batch's (device
+ *   pointers); enqueues the graph on stream and returns.  Launches of one graph
+ *   share its memory: issue them on one stream (or order them), from one host
+ *   thread at a time.  Errors found on the host: FILTR_ERR_INVALID (NULL
+ *   graph or pointers, n_pairs > max_pairs), FILTR_ERR_CUDA.  n_pairs = 0
+ *   launches nothing.
+ * filtr_graph_status: after the stream has finished the last launch, that
+ *   launch's outcome: FILTR_OK, FILTR_ERR_INVALID (a residue code >= the
+ *   alphabet size, or a sequence longer than max_len: nothing was aligned),
+ *   FILTR_ERR_NOMEM (the batch's traceback exceeds the traceback area: nothing
+ *   was aligned), FILTR_ERR_CIGAR_CAP (results complete, CIGARs that do not
+ *   fit cigar_cap not written).
+ * filtr_graph_destroy: waits for the device, frees the graph; NULL is a no-op. */
+typedef struct filtr_graph filtr_graph;
+filtr_status filtr_graph_create(filtr_ctx *ctx, const filtr_params *params, uint32_t max_pairs,
+                                uint32_t max_len, size_t workspace_bytes, filtr_graph **out);
+filtr_status filtr_graph_launch(filtr_graph *graph, uint32_t n_pairs, const uint8_t *q_seq,
+                                const uint64_t *q_off, const uint32_t *q_len, const uint8_t *r_seq,
+                                const uint64_t *r_off, const uint32_t *r_len, filtr_result *out,
+                                uint32_t *cigar, uint64_t cigar_cap, void *stream);
+filtr_status filtr_graph_status(filtr_graph *graph);
+filtr_status filtr_graph_destroy(filtr_graph *graph);
+
 /* Autotuning of the tiled kernel shapes (the paper leaves autotuning to
  * future work, Sec. 11).  Times every tiled shape -- the int32 tile with 32,
  * 24, 16 or 8 rows per lane and, where the parameters allow it, the int16x2

@@ -8,11 +8,12 @@ from __future__ import annotations
 
 import numpy as np
 
-from ._lib import (ALPHA_DNA, ALPHA_PROTEIN, ERR_CIGAR_CAP, ERR_INVALID, ERR_UNSUPPORTED, GLOBAL,
+from ._lib import (ALPHA_DNA, ALPHA_PROTEIN, ERR_CIGAR_CAP, ERR_INVALID, ERR_NOMEM, ERR_UNSUPPORTED,
+                   GLOBAL,
                    LOCAL, OK, PREC_AUTO, PREC_I16X2, PREC_I32, PRUNE_BAND, PRUNE_BAND_LITERAL,
                    PRUNE_XDROP, PRUNE_ZDROP, RESULT_DTYPE, ST_DROPPED, ST_EMPTY, ST_OK, ST_TOO_WIDE,
-                   ST_UNREACHABLE, TUNE_SHAPES, XDROP_INF, Context, FiltrError, Params, check,
-                   last_error, lib,
+                   ST_UNREACHABLE, TUNE_SHAPES, XDROP_INF, Context, FiltrError, Graph, Params,
+                   check, last_error, lib,
                    make_params)
 
 __all__ = ["Context", "FiltrError", "Params", "make_params", "DeviceBatch", "align_batch",
@@ -74,6 +75,26 @@ def align_batch(ctx: Context, params: Params, batch, stream=None, plain: bool = 
     res = results_to_numpy(out_t, db.n)
     cig = cig_t.cpu().numpy().view(np.uint32).copy() if params.traceback else np.zeros(0, np.uint32)
     return res, cig, rc
+
+
+def graph_align(graph: Graph, batch, stream=None, cigar_cap: int | None = None, device="cuda"):
+    """One launch of a captured pipeline over a synth.Batch or DeviceBatch; waits
+    for it and returns (results, cigar ops, the launch's filtr_graph_status)."""
+    import torch
+
+    db = batch if isinstance(batch, DeviceBatch) else DeviceBatch(batch, device)
+    cap = db.cigar_upper if cigar_cap is None else int(cigar_cap)
+    out_t, cig_t = alloc_outputs(db.n, cap, device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    tb = bool(graph.params.traceback)
+    rc = graph.launch_ptr(db.n, *db.ptrs(), out_t.data_ptr(), cig_t.data_ptr() if tb else None,
+                          cap if tb else 0, stream=s.cuda_stream)
+    check(rc, "filtr_graph_launch")
+    s.synchronize()
+    status = graph.status() if db.n else OK
+    res = results_to_numpy(out_t, db.n)
+    cig = cig_t.cpu().numpy().view(np.uint32).copy() if tb else np.zeros(0, np.uint32)
+    return res, cig, status
 
 
 def align_batch_host(ctx: Context, params: Params, batch, cigar_cap: int | None = None):

@@ -131,6 +131,16 @@ def lib():
         L.filtr_test_set_first_width.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_test_set_device_plan.restype = i32
         L.filtr_test_set_device_plan.argtypes = [C.c_void_p, C.c_int32]
+        L.filtr_graph_create.restype = i32
+        L.filtr_graph_create.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32,
+                                         C.c_size_t, C.POINTER(C.c_void_p)]
+        L.filtr_graph_launch.restype = i32
+        L.filtr_graph_launch.argtypes = [C.c_void_p, C.c_uint32, _P, _P, _P, _P, _P, _P, _P, _P,
+                                         C.c_uint64, _P]
+        L.filtr_graph_status.restype = i32
+        L.filtr_graph_status.argtypes = [C.c_void_p]
+        L.filtr_graph_destroy.restype = i32
+        L.filtr_graph_destroy.argtypes = [C.c_void_p]
         L.filtr_serve_create.restype = i32
         L.filtr_serve_create.argtypes = [C.c_void_p, C.c_size_t, C.c_uint32, C.POINTER(C.c_void_p)]
         L.filtr_serve_submit.restype = i32
@@ -270,3 +280,36 @@ class Context:
         check(lib().filtr_probe_int_peak(self.handle, C.byref(arr)), "filtr_probe_int_peak")
         return dict(int_ops=arr[0], viaddmax=arr[1], vimax3=arr[2], viaddmax_s16x2_lanes=arr[3],
                     sm_hz=arr[4])
+
+
+class Graph:
+    """The batched tiled pipeline captured as a CUDA graph (filtr_graph_*)."""
+
+    def __init__(self, ctx: "Context", params: Params, max_pairs: int, max_len: int,
+                 workspace_bytes: int):
+        h = C.c_void_p()
+        check(lib().filtr_graph_create(ctx.handle, C.byref(params), int(max_pairs), int(max_len),
+                                       int(workspace_bytes), C.byref(h)), "filtr_graph_create")
+        self.handle = h
+        self.params = params
+        self.max_pairs = int(max_pairs)
+
+    def launch_ptr(self, n: int, q_seq, q_off, q_len, r_seq, r_off, r_len, out, cigar,
+                   cigar_cap: int, stream: int = 0) -> int:
+        return lib().filtr_graph_launch(self.handle, int(n), q_seq, q_off, q_len, r_seq, r_off,
+                                        r_len, out, cigar, int(cigar_cap),
+                                        C.c_void_p(int(stream)) if stream else None)
+
+    def status(self) -> int:
+        return lib().filtr_graph_status(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().filtr_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

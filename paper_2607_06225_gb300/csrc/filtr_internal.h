@@ -174,6 +174,22 @@ struct BatchDev {
   const uint32_t *q_len, *r_len;
 };
 
+// Per-launch values of a captured batch pipeline (filtr_graph), in device
+// memory.  A graph's kernels are captured once with fixed by-value arguments;
+// where a kernel's gd argument is set it takes the batch, the pair count and
+// the outputs from here instead (written by the graph's first node at each
+// launch), and does nothing once abort is set (a check node found a residue
+// code or a length outside the graph's bounds, or traceback over its budget).
+struct GraphDesc {
+  BatchDev b;
+  filtr_result *out;
+  uint32_t *cigar;
+  uint64_t cap;
+  uint32_t n;
+  int32_t abort;   // 0, or the filtr_status that stopped this launch
+};
+struct DevPlanSummary;
+
 struct FullArgs {
   BatchDev b;
   ScoreParams sp;
@@ -189,6 +205,12 @@ struct FullArgs {
   uint32_t max_n;          // 0, or the longest reference the strip buffers hold
   uint32_t max_m;          // 0, or the longest query accepted
   const struct XdCkpt *ck; // X-drop kernel: checkpoint mode (nullptr = normal)
+  // captured pipeline (tiled kernels only): b and out come from gd, and the
+  // launch takes order[begin, begin + count[gshape]) with begin the pairs of
+  // the shapes before gshape in the device plan's summary
+  const GraphDesc *gd = nullptr;
+  const DevPlanSummary *gsum = nullptr;
+  int gshape = 0;
 };
 
 struct WalkArgs {
@@ -202,6 +224,7 @@ struct WalkArgs {
   const TbLayout *tbl;
   uint32_t *stage;          // per pair scratch for reversed CIGAR ops
   const uint64_t *stage_off;
+  const GraphDesc *gd = nullptr;  // captured pipeline: b, out and n_order from here
 };
 
 struct LaneBest;
@@ -250,16 +273,19 @@ cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s);
 cudaError_t launch_walk_xd(const WalkArgs &a, cudaStream_t s);  // X-drop pairs, a warp each
 cudaError_t launch_walk_pool(const WalkArgs &a, const uint32_t *pool, const int32_t *seg_ck_all,
                              const uint64_t *seg_off, const int32_t *seg_w, int C, cudaStream_t s);
+// In a captured pipeline (gd set) the n given here is the graph's capacity,
+// which sizes the grid; the kernels take the launch's n from gd.
 cudaError_t launch_scan_offsets(const filtr_result *out, uint32_t n, uint64_t *offs,
-                                uint64_t *total, cudaStream_t s);
+                                uint64_t *total, cudaStream_t s, const GraphDesc *gd = nullptr);
 cudaError_t launch_compact(const WalkArgs &a, uint32_t n, const uint64_t *offs, uint32_t *cigar,
                            uint64_t cap, filtr_result *out, cudaStream_t s);
 cudaError_t launch_trivial(const BatchDev &b, const ScoreParams &sp, const uint32_t *order,
-                           uint32_t n, filtr_result *out, FwdOut *fwd, cudaStream_t s);
+                           uint32_t n, filtr_result *out, FwdOut *fwd, cudaStream_t s,
+                           const GraphDesc *gd = nullptr, const DevPlanSummary *gsum = nullptr);
 cudaError_t launch_validate(const uint8_t *codes, uint64_t n, int alphabet, uint32_t *bad,
                             cudaStream_t s);
 cudaError_t launch_validate_pairs(const BatchDev &b, uint32_t n, int alphabet, uint32_t *bad,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const GraphDesc *gd = nullptr);
 cudaError_t launch_pack(const uint8_t *codes, uint64_t n, int alphabet, uint32_t *packed,
                         uint32_t *bad, cudaStream_t s);
 cudaError_t run_probe(double out[5]);

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "k_strip.cuh"
+#include "plan.h"
 
 namespace filtr {
 namespace {
@@ -28,6 +29,8 @@ template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND>
 __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
   constexpr int HS = 32 * R;
   extern __shared__ __align__(16) int8_t smem[];
+  const LaunchView V = launch_view(a);
+  if (V.stop) return;  // uniform over the grid
   const int A = a.sp.alphabet;
   int8_t *s_sub = smem;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -40,13 +43,13 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
     uint32_t t0 = 0;
     if (lane == 0) t0 = atomicAdd(a.counter, 1u);
     t0 = __shfl_sync(STRIP_FULLMASK, t0, 0);
-    if (t0 >= a.n_order) break;
-    const uint32_t p = a.order ? a.order[t0] : t0;
+    if (t0 >= V.n) break;
+    const uint32_t p = V.order ? V.order[t0] : t0;
     StripPair P;
-    P.M = (int)a.b.q_len[p];
-    P.N = (int)a.b.r_len[p];
-    P.q = a.b.q_seq + a.b.q_off[p];
-    P.r = a.b.r_seq + a.b.r_off[p];
+    P.M = (int)V.b.q_len[p];
+    P.N = (int)V.b.r_len[p];
+    P.q = V.b.q_seq + V.b.q_off[p];
+    P.r = V.b.r_seq + V.b.r_off[p];
     P.lo = -P.M - 1;
     P.hi = P.N + 1;
     if (BAND) {
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
       if (lane == 0) {
         filtr_result res{};
         res.status = FILTR_ST_TOO_WIDE;
-        a.out[p] = res;
+        V.out[p] = res;
       }
       continue;
     }
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
       res.reserved = 0;
       res.cigar_off = 0;
       res.cells = cells;
-      a.out[p] = res;
+      V.out[p] = res;
       if (a.fwd) {
         FwdOut f;
         f.score = score;

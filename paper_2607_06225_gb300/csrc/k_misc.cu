@@ -2,15 +2,27 @@
 // packing, and the integer / DPX throughput probe used as the roofline
 // denominator of the cell update.
 #include "filtr_internal.h"
+#include "plan.h"
 
 namespace filtr {
 namespace {
 
 // Pairs with M == 0 or N == 0 evaluate no cell.  Global: the only alignment is
 // one gap of max(M, N) (score -(o + L*e), 0 if both are empty); local: empty.
-__global__ void k_trivial(const BatchDev b, const ScoreParams sp, const uint32_t *order, uint32_t n,
-                          filtr_result *out, FwdOut *fwd) {
+__global__ void k_trivial(const BatchDev b0, const ScoreParams sp, const uint32_t *order, uint32_t n,
+                          filtr_result *out, FwdOut *fwd, const GraphDesc *gd,
+                          const DevPlanSummary *gsum) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  BatchDev b = b0;
+  if (gd) {  // captured pipeline: the empty pairs follow every shape's slice
+    if (gd->abort) return;
+    b = gd->b;
+    out = gd->out;
+    uint32_t begin = 0;
+    for (int k = 0; k < SHAPE_TILED; ++k) begin += gsum->count[k];
+    order += begin;
+    n = gsum->count[KEY_TRIVIAL];
+  }
   if (t >= n) return;
   const uint32_t p = order[t];
   const int M = (int)b.q_len[p], N = (int)b.r_len[p];
@@ -65,9 +77,12 @@ __global__ void k_validate(const uint8_t *codes, uint64_t n, int alphabet, uint3
 }
 
 // One warp per pair: count residue codes >= alphabet in q and r.
-__global__ void k_validate_pairs(const BatchDev b, uint32_t n, int alphabet, uint32_t *bad) {
+__global__ void k_validate_pairs(const BatchDev b0, uint32_t n, int alphabet, uint32_t *bad,
+                                 const GraphDesc *gd) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  const BatchDev b = gd ? gd->b : b0;  // captured pipeline: batch and count from gd
+  if (gd) n = gd->n;
   if (w >= n) return;
   uint32_t cnt = 0;
   const uint8_t *q = b.q_seq + b.q_off[w];
@@ -174,9 +189,10 @@ double probe_one(int sms, int *sink, long long *clk, unsigned long long *ns, dou
 }  // namespace
 
 cudaError_t launch_trivial(const BatchDev &b, const ScoreParams &sp, const uint32_t *order,
-                           uint32_t n, filtr_result *out, FwdOut *fwd, cudaStream_t s) {
+                           uint32_t n, filtr_result *out, FwdOut *fwd, cudaStream_t s,
+                           const GraphDesc *gd, const DevPlanSummary *gsum) {
   if (n == 0) return cudaSuccess;
-  k_trivial<<<(n + 127) / 128, 128, 0, s>>>(b, sp, order, n, out, fwd);
+  k_trivial<<<(n + 127) / 128, 128, 0, s>>>(b, sp, order, n, out, fwd, gd, gsum);
   return cudaGetLastError();
 }
 
@@ -191,10 +207,10 @@ cudaError_t launch_validate(const uint8_t *codes, uint64_t n, int alphabet, uint
 }
 
 cudaError_t launch_validate_pairs(const BatchDev &b, uint32_t n, int alphabet, uint32_t *bad,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const GraphDesc *gd) {
   if (n == 0) return cudaSuccess;
   const uint64_t threads = (uint64_t)n * 32;
-  k_validate_pairs<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(b, n, alphabet, bad);
+  k_validate_pairs<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(b, n, alphabet, bad, gd);
   return cudaGetLastError();
 }
 

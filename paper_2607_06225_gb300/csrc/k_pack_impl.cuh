@@ -45,6 +45,7 @@
 #include <type_traits>
 
 #include "filtr_internal.h"
+#include "plan.h"
 
 namespace filtr {
 namespace {
@@ -360,6 +361,8 @@ template <int R, bool LOCAL, bool AFFINE, bool TB>
 __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
   constexpr int HS = 32 * R;
   extern __shared__ __align__(16) int8_t smem[];
+  const LaunchView V = launch_view(a);
+  if (V.stop) return;  // uniform over the grid
   const int A = a.sp.alphabet;
   int8_t *s_sub = smem;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -372,13 +375,13 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
     uint32_t t0 = 0;
     if (lane == 0) t0 = atomicAdd(a.counter, 1u);
     t0 = __shfl_sync(PFULL, t0, 0);
-    if (t0 >= a.n_order) break;
-    const uint32_t p = a.order ? a.order[t0] : t0;
+    if (t0 >= V.n) break;
+    const uint32_t p = V.order ? V.order[t0] : t0;
     PackPair PP;
-    PP.M = (int)a.b.q_len[p];
-    PP.N = (int)a.b.r_len[p];
-    PP.q = a.b.q_seq + a.b.q_off[p];
-    PP.r = a.b.r_seq + a.b.r_off[p];
+    PP.M = (int)V.b.q_len[p];
+    PP.N = (int)V.b.r_len[p];
+    PP.q = V.b.q_seq + V.b.q_off[p];
+    PP.r = V.b.r_seq + V.b.r_off[p];
     PP.o = a.sp.o;
     PP.e = a.sp.e;
     PP.A = A;
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
       res.reserved = 0;
       res.cigar_off = 0;
       res.cells = (uint64_t)M * (uint64_t)N;
-      a.out[p] = res;
+      V.out[p] = res;
       if (a.fwd) {
         FwdOut f;
         f.score = score;

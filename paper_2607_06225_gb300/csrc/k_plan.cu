@@ -42,9 +42,22 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return before + x - v;
 }
 
+// The pair count and lengths of this launch (a captured pipeline's come from
+// its descriptor; its grids are sized for the graph's capacity).
+struct PlanView {
+  uint32_t n;
+  const uint32_t *q_len, *r_len;
+};
+__device__ __forceinline__ PlanView plan_view(const DevPlanArgs &a) {
+  if (a.gd) return PlanView{a.gd->n, a.gd->b.q_len, a.gd->b.r_len};
+  return PlanView{a.n, a.q_len, a.r_len};
+}
+
 // Shape, cost bucket and traceback words of each pair; block histogram of the
 // keys; batch totals; staging words per block.
 __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanArgs a) {
+  const PlanView V = plan_view(a);
+  if (blockIdx.x * DEV_PLAN_BLOCK >= V.n) return;  // uniform over the block
   __shared__ uint32_t hist[PLAN_KEYS];
   __shared__ unsigned long long part[4][DEV_PLAN_BLOCK / 32];
   __shared__ uint32_t pmax[2][DEV_PLAN_BLOCK / 32];
@@ -54,8 +67,8 @@ __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanA
   // traceback words, cells, staging words, M + N
   unsigned long long v[4] = {0ull, 0ull, 0ull, 0ull};
   uint32_t mm = 0, mn = 0;
-  if (p < a.n) {
-    const uint32_t M = a.q_len[p], N = a.r_len[p];
+  if (p < V.n) {
+    const uint32_t M = V.q_len[p], N = V.r_len[p];
     mm = M;
     mn = N;
     v[3] = (unsigned long long)M + N;
@@ -114,6 +127,7 @@ __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanA
 __global__ void __launch_bounds__(1024) k_plan_scan(const DevPlanArgs a, uint32_t nblk) {
   __shared__ unsigned long long ws[32];
   DevPlanState *S = a.state;
+  if (a.gd) nblk = (a.gd->n + DEV_PLAN_BLOCK - 1) / DEV_PLAN_BLOCK;
   const uint32_t t = threadIdx.x;
   unsigned long long tot;
   const unsigned long long h = t < PLAN_KEYS ? S->hist[t] : 0ull;
@@ -139,15 +153,17 @@ __global__ void __launch_bounds__(1024) k_plan_scan(const DevPlanArgs a, uint32_
 // layouts and staging offsets.
 __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_place(const DevPlanArgs a) {
   __shared__ unsigned long long ws[DEV_PLAN_BLOCK / 32];
+  const PlanView V = plan_view(a);
+  if (blockIdx.x * DEV_PLAN_BLOCK >= V.n) return;  // uniform over the block
   const uint32_t p = blockIdx.x * DEV_PLAN_BLOCK + threadIdx.x;
-  const bool valid = p < a.n;
+  const bool valid = p < V.n;
   const int lane = threadIdx.x & 31;
   uint32_t key = 0xffffu;
   unsigned long long w = 0, sw = 0;
   if (valid) {
     key = a.key[p];
     w = a.words[p];
-    if (a.sp.traceback) sw = (unsigned long long)a.q_len[p] + a.r_len[p] + 1;
+    if (a.sp.traceback) sw = (unsigned long long)V.q_len[p] + V.r_len[p] + 1;
   }
   unsigned long long tot;
   const unsigned long long sx = block_excl_scan<DEV_PLAN_BLOCK>(sw, ws, &tot);

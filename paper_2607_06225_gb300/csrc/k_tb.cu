@@ -93,17 +93,21 @@ struct Emitter {
 
 __global__ void k_walk(const WalkArgs a) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_order) return;
+  const GraphDesc *gd = a.gd;  // captured pipeline: batch, outputs and count from here
+  if (gd && gd->abort) return;
+  if (t >= (gd ? gd->n : a.n_order)) return;
+  const BatchDev b = gd ? gd->b : a.b;
+  filtr_result *const out = gd ? gd->out : a.out;
   const uint32_t p = a.order[t];
   const FwdOut f = a.fwd[p];
   const TbLayout L = a.tbl[p];
   if (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED) {
-    a.out[p].cigar_len = 0;
+    out[p].cigar_len = 0;
     return;
   }
-  const int M = (int)a.b.q_len[p], N = (int)a.b.r_len[p];
-  const uint8_t *q = a.b.q_seq + a.b.q_off[p];
-  const uint8_t *r = a.b.r_seq + a.b.r_off[p];
+  const int M = (int)b.q_len[p], N = (int)b.r_len[p];
+  const uint8_t *q = b.q_seq + b.q_off[p];
+  const uint8_t *r = b.r_seq + b.r_off[p];
   const bool local = a.sp.mode == FILTR_LOCAL;
   const int A = a.sp.alphabet, e = a.sp.e, oe = a.sp.o + a.sp.e;
   const uint32_t *tb = a.tb + L.off;
@@ -202,7 +206,7 @@ __global__ void k_walk(const WalkArgs a) {
     }
   }
   em.flush();
-  filtr_result *res = a.out + p;
+  filtr_result *res = out + p;
   res->q_begin = i;
   res->r_begin = j;
   res->cigar_len = em.n;
@@ -478,9 +482,15 @@ __global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
 }
 
 // Exclusive scan of cigar_len (pair order) into offs; *total = sum.  One CTA.
-__global__ void k_scan(const filtr_result *out, uint32_t n, uint64_t *offs, uint64_t *total) {
+__global__ void k_scan(const filtr_result *out, uint32_t n, uint64_t *offs, uint64_t *total,
+                       const GraphDesc *gd) {
   __shared__ uint64_t part[1024];
   __shared__ uint64_t carry;
+  if (gd) {  // captured pipeline (uniform over the block)
+    if (gd->abort) return;
+    out = gd->out;
+    n = gd->n;
+  }
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   constexpr int PER = 8;
@@ -519,6 +529,13 @@ __global__ void k_compact(const WalkArgs a, uint32_t n, const uint64_t *offs, ui
                           uint64_t cap, filtr_result *out) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  if (a.gd) {  // captured pipeline
+    if (a.gd->abort) return;
+    n = a.gd->n;
+    cigar = a.gd->cigar;
+    cap = a.gd->cap;
+    out = a.gd->out;
+  }
   if (w >= n) return;
   const uint32_t len = out[w].cigar_len;
   const uint64_t off = offs[w];
@@ -555,8 +572,8 @@ cudaError_t launch_walk_segment(const WalkArgs &a, const uint32_t *seg_tb, const
 }
 
 cudaError_t launch_scan_offsets(const filtr_result *out, uint32_t n, uint64_t *offs,
-                                uint64_t *total, cudaStream_t s) {
-  k_scan<<<1, 1024, 0, s>>>(out, n, offs, total);
+                                uint64_t *total, cudaStream_t s, const GraphDesc *gd) {
+  k_scan<<<1, 1024, 0, s>>>(out, n, offs, total, gd);
   return cudaGetLastError();
 }
 

@@ -108,8 +108,37 @@ struct DevPlanArgs {
   uint32_t *order;      // out: pair ids
   TbLayout *tbl;        // out: per pair
   uint64_t *stage_off;  // out: per pair (traceback on)
+  const GraphDesc *gd = nullptr;  // captured pipeline: n (at most the n above) and lengths from here
 };
 constexpr int DEV_PLAN_BLOCK = 256;
 cudaError_t launch_plan(const DevPlanArgs &a, cudaStream_t st);
+
+#ifdef __CUDACC__
+// What one tiled launch works on: its by-value arguments, or in a captured
+// pipeline the batch and outputs of the graph descriptor and the slice of the
+// order that the device plan gave this launch's shape.
+struct LaunchView {
+  BatchDev b;
+  filtr_result *out;
+  const uint32_t *order;
+  uint32_t n;
+  bool stop;  // the pipeline was aborted before this launch
+};
+__device__ __forceinline__ LaunchView launch_view(const FullArgs &a) {
+  LaunchView v{a.b, a.out, a.order, a.n_order, false};
+  if (a.gd) {
+    v.b = a.gd->b;
+    v.out = a.gd->out;
+    v.stop = a.gd->abort != 0;
+    if (a.gsum) {
+      uint32_t begin = 0;
+      for (int k = 0; k < a.gshape; ++k) begin += a.gsum->count[k];
+      v.order = a.order + begin;
+      v.n = a.gsum->count[a.gshape];
+    }
+  }
+  return v;
+}
+#endif
 
 }  // namespace filtr

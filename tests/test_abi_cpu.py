@@ -96,3 +96,16 @@ def test_tune_apply_rejects_on_host(L):
     assert lib.filtr_tune_apply(None, C.byref(p), None) == L.ERR_INVALID
     assert lib.filtr_tune_apply(None, None, C.byref(rep)) == L.ERR_INVALID
     assert "NULL" in L.last_error()
+
+
+def test_graph_rejects_on_host(L):
+    lib = L.lib()
+    S = np.zeros((4, 4), np.int8)
+    p = L.make_params(S, gap_open=4, gap_extend=2)
+    h = C.c_void_p()
+    assert lib.filtr_graph_create(None, C.byref(p), 10, 100, 1 << 26, C.byref(h)) == L.ERR_INVALID
+    assert lib.filtr_graph_create(None, C.byref(p), 10, 100, 1 << 26, None) == L.ERR_INVALID
+    assert lib.filtr_graph_launch(None, 1, None, None, None, None, None, None, None, None, 0,
+                                  None) == L.ERR_INVALID
+    assert lib.filtr_graph_status(None) == L.ERR_INVALID
+    assert lib.filtr_graph_destroy(None) == L.OK
