@@ -67,6 +67,9 @@ def parse():
                     help="cell width of the tiled kernels (results are identical)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plan with the built-in shape costs instead of timed ones")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip the captured-pipeline (filtr_graph) leg")
+    ap.add_argument("--graph-workspace-gb", type=float, default=40.0)
     ap.add_argument("--tune-save", default=None,
                     help="write the autotuned shape costs to this JSON file")
     ap.add_argument("--tune-load", default=None,
@@ -385,6 +388,45 @@ def plain_per_pair(F, ctx, params, batch, nsample, stream, dev, tb_on):
             "ms_plain": tp_ms, "ms_batched": tb_ms}
 
 
+def graph_bench(F, ctx, params, batch, db, res_ref, cells, steps, warmup, stream, flush, dev,
+                tb_on, ws_gb):
+    """The same workload through the captured pipeline (filtr_graph_launch: one
+    CUDA graph per step, no host synchronisation inside the step)."""
+    import torch
+
+    max_len = int(max(batch.q_len.max(), batch.r_len.max()))
+    g = F.Graph(ctx, params, db.n, max_len, int(ws_gb * (1 << 30)))
+    out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
+
+    def gstep():
+        rc = g.launch_ptr(db.n, *db.ptrs(), out_t.data_ptr(), cig_t.data_ptr() if tb_on else None,
+                          db.cigar_upper if tb_on else 0, stream=stream.cuda_stream)
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+
+    try:
+        for _ in range(max(warmup, 1)):
+            gstep()
+        torch.cuda.synchronize()
+        status = g.status()
+        res = F.results_to_numpy(out_t, db.n)
+        assert status == 0 and np.array_equal(res, res_ref), "graph results differ"
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_((k + 7) & 0xFF)
+            ev[k][0].record(stream)
+            gstep()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        return {"value": cells / (ms * 1e-3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
+                "call": "filtr_graph_launch (captured pipeline, no host synchronisation)",
+                "status": status}
+    finally:
+        g.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -542,6 +584,10 @@ def main():
             "clocks": clocks,
             "wall_s_timed": wall,
         }
+        if wl in ("protein-sw-100k", "short-dna-1k") and not args.no_graph:
+            line["graph"] = graph_bench(F, ctx, params, batch, db, res, cells, args.steps,
+                                        args.warmup, stream, flush, dev, tb_on,
+                                        args.graph_workspace_gb)
         if not args.no_serve and wl == "protein-sw-100k":
             line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
         if not args.no_cpu_baseline and not is_long:

@@ -284,7 +284,9 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
  *   alphabet size, or a sequence longer than max_len: nothing was aligned),
  *   FILTR_ERR_NOMEM (the batch's traceback exceeds the traceback area: nothing
  *   was aligned), FILTR_ERR_CIGAR_CAP (results complete, CIGARs that do not
- *   fit cigar_cap not written).
+ *   fit cigar_cap not written), FILTR_ERR_UNSUPPORTED (the plan chose a tile
+ *   shape that the graph, which launches only the shapes some pair within its
+ *   bounds can take, does not hold: nothing was aligned; not expected).
  * filtr_graph_destroy: waits for the device, frees the graph; NULL is a no-op. */
 typedef struct filtr_graph filtr_graph;
 filtr_status filtr_graph_create(filtr_ctx *ctx, const filtr_params *params, uint32_t max_pairs,

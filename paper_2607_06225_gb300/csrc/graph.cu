@@ -13,8 +13,10 @@
 // traceback within budget, CIGAR capacity) run as graph nodes: a failed check
 // sets the descriptor's abort code, later nodes do nothing, and the code lands
 // in a host-mapped word that filtr_graph_status returns once the stream is done.
+#include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <vector>
 
 #include "filtr_ctx.h"
 
@@ -27,14 +29,32 @@ __global__ void k_graph_desc(GraphDesc d, GraphDesc *dst) {
 }
 
 // One thread: the checks filtr_align_batch makes on the host.
+// One thread: the checks filtr_align_batch makes on the host, and that every
+// pair's shape is one the graph launches (shapes_in: bit k for shape k).
 __global__ void k_graph_check(const DevPlanState *ps, GraphDesc *gd, uint32_t max_len,
-                              unsigned long long tb_cap, unsigned long long stage_cap) {
+                              unsigned long long tb_cap, unsigned long long stage_cap,
+                              uint32_t shapes_in) {
   int32_t code = 0;
   if (ps->bad[0] != 0 || ps->sum.max_m > max_len || ps->sum.max_n > max_len)
     code = FILTR_ERR_INVALID;
   else if (ps->sum.tb_words > tb_cap || ps->sum.stage_words > stage_cap)
     code = FILTR_ERR_NOMEM;
+  for (int k = 0; k < SHAPE_TILED && code == 0; ++k)
+    if (!(shapes_in >> k & 1u) && ps->sum.count[k] != 0) code = FILTR_ERR_UNSUPPORTED;
   gd->abort = code;
+}
+
+// One condition per tiled shape: its conditional node runs the shape's kernel
+// only when the device plan gave it pairs (and nothing was aborted).
+struct CondArgs {
+  cudaGraphConditionalHandle h[SHAPE_TILED];
+  int shape[SHAPE_TILED];
+  int n;
+};
+__global__ void k_graph_setcond(const CondArgs c, const DevPlanSummary *sum, const GraphDesc *gd) {
+  const bool go = gd->abort == 0;
+  for (int i = 0; i < c.n; ++i)  // one thread: no concurrent setters
+    cudaGraphSetConditional(c.h[i], (go && sum->count[c.shape[i]] > 0) ? 1u : 0u);
 }
 
 __global__ void k_graph_finish(const GraphDesc *gd, const uint64_t *cigar_total, int traceback,
@@ -87,10 +107,80 @@ void graph_free(Graph *g) {
   delete g;
 }
 
-// Capture the pipeline on st into g->graph.  Returns the first error.
-cudaError_t capture(Graph *g, const ShapeCost *costs, uint64_t tb_words, uint64_t stage_cap,
-                    int grid_max, const GCarve &layout_in, cudaStream_t st) {
-  Ctx *c = g->ctx;
+// The tiled shapes a graph launches, and each one's persistent grid.
+struct ShapeSet {
+  int k[SHAPE_TILED];
+  int grid[SHAPE_TILED];
+  int n = 0;
+};
+// Shapes choose_shape can give some pair with both lengths at most max_len.
+// Within one count of 128-row strips a shape's cost is a line in N, so the
+// cheapest shape changes only where two lines cross: evaluating the choice at
+// N = 1, N = max_len and beside every crossing finds every winner, for pairs
+// that fit 15 bits and for pairs that do not.  Above 2^20 every allowed shape
+// is kept (the scan would take too long).
+void reachable_shapes(const ShapeTable &t, const ScoreParams &sp, uint32_t max_len,
+                      bool *reach) {
+  for (int k = 0; k < SHAPE_TILED; ++k) reach[k] = false;
+  if (max_len > (1u << 20)) {
+    for (int i = 0; i < t.n_elig; ++i) reach[t.elig[i]] = true;
+    return;
+  }
+  const uint32_t smax = (max_len + 127) / 128;
+  std::vector<uint32_t> ns;
+  for (uint32_t s = 1; s <= smax; ++s) {
+    const uint32_t M = std::min<uint32_t>(128 * s, max_len);
+    // lines a_k (N + f_k) for this strip count
+    double a[SHAPE_TILED];
+    for (int i = 0; i < t.n_elig; ++i) {
+      const int k = t.elig[i];
+      a[k] = (double)strips_of(M, t.R[k]) * t.coef[k];
+    }
+    ns.assign({1u, max_len});
+    for (int i = 0; i < t.n_elig; ++i)
+      for (int j = i + 1; j < t.n_elig; ++j) {
+        const int k1 = t.elig[i], k2 = t.elig[j];
+        if (a[k1] == a[k2]) continue;
+        const double x = (a[k2] * t.fill[k2] - a[k1] * t.fill[k1]) / (a[k1] - a[k2]);
+        if (!(x > 0 && x < (double)max_len + 1)) continue;
+        for (double d : {-1.0, 0.0, 1.0, 2.0}) {
+          const double v = std::floor(x) + d;
+          if (v >= 1 && v <= max_len) ns.push_back((uint32_t)v);
+        }
+      }
+    for (uint32_t N : ns)
+      for (int pk = 0; pk < 2; ++pk) {
+        if (pk && t.n_elig_packed == 0) continue;
+        const bool packable = pk == 1;
+        reach[choose_shape_p(t, packable, packable && sp.precision == FILTR_PREC_I16X2, M, N)] = true;
+      }
+  }
+}
+
+ShapeSet graph_shapes(Ctx *c, const ScoreParams &sp, const ShapeCost *costs, uint32_t max_len) {
+  ShapeSet ss;
+  const bool pack_ok = !sp.use_band && sp.precision != FILTR_PREC_I32;
+  bool reach[SHAPE_TILED];
+  reachable_shapes(make_shape_table(costs, sp), sp, max_len, reach);
+  for (int k = 0; k < SHAPE_TILED; ++k) {
+    if (costs[k].packed && !pack_ok) continue;
+    if (!reach[k]) continue;
+    const int R = costs[k].R;
+    const int bps = costs[k].packed ? c->pack_blocks_per_sm(R, sp) : c->full_blocks_per_sm(R, sp);
+    ss.k[ss.n] = k;
+    ss.grid[ss.n] = c->sms * bps;
+    ++ss.n;
+  }
+  return ss;
+}
+
+// Capture the pipeline on st into g->graph.  The shapes' kernels sit in
+// conditional nodes on parallel branches (each with its own strip buffers and
+// queue counter), so a shape the plan leaves empty costs nothing and the
+// shapes' tails overlap.  Returns the first error.
+cudaError_t capture(Graph *g, const ShapeCost *costs, const ShapeSet &ss, uint64_t tb_words,
+                    uint64_t stage_cap, const GCarve &layout_in, cudaStream_t st,
+                    cudaStream_t st2) {
   const ScoreParams &sp = g->sp;
   const uint32_t NP = g->max_pairs;
   GCarve cv = layout_in;
@@ -106,7 +196,9 @@ cudaError_t capture(Graph *g, const ShapeCost *costs, uint64_t tb_words, uint64_
   uint64_t *d_pwords = cv.take<uint64_t>(NP);
   uint64_t *d_pblk = cv.take<uint64_t>((NP + DEV_PLAN_BLOCK - 1) / DEV_PLAN_BLOCK);
   const uint32_t strip_stride = g->max_len + 2;
-  int2 *d_strip = cv.take<int2>((size_t)grid_max * FULL_WARPS * strip_stride);
+  int2 *d_strip[SHAPE_TILED];
+  for (int i = 0; i < ss.n; ++i)
+    d_strip[i] = cv.take<int2>((size_t)ss.grid[i] * FULL_WARPS * strip_stride);
   uint32_t *d_stage = sp.traceback ? cv.take<uint32_t>(stage_cap) : nullptr;
   uint32_t *d_tb = cv.take<uint32_t>(tb_words);
   uint32_t *d_bad = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(d_ps) +
@@ -135,11 +227,32 @@ cudaError_t capture(Graph *g, const ShapeCost *costs, uint64_t tb_words, uint64_
   pa.gd = g->d_gd;
   if (e == cudaSuccess) e = launch_plan(pa, st);
   if (e == cudaSuccess) {
+    uint32_t shapes_in = 0;
+    for (int i = 0; i < ss.n; ++i) shapes_in |= 1u << ss.k[i];
     k_graph_check<<<1, 1, 0, st>>>(d_ps, g->d_gd, g->max_len, (unsigned long long)tb_words,
-                                   (unsigned long long)(sp.traceback ? stage_cap : ~0ull));
+                                   (unsigned long long)(sp.traceback ? stage_cap : ~0ull),
+                                   shapes_in);
     e = cudaGetLastError();
   }
-  // one persistent launch per tiled shape; each takes its slice of the order
+  // conditions, then one conditional branch per shape
+  cudaGraph_t cg = nullptr;
+  cudaStreamCaptureStatus cs{};
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  CondArgs ca{};
+  ca.n = ss.n;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg);
+  for (int i = 0; i < ss.n && e == cudaSuccess; ++i) {
+    ca.shape[i] = ss.k[i];
+    e = cudaGraphConditionalHandleCreate(&ca.h[i], cg, 0, cudaGraphCondAssignDefault);
+  }
+  if (e == cudaSuccess) {
+    k_graph_setcond<<<1, 1, 0, st>>>(ca, &d_ps->sum, g->d_gd);
+    e = cudaGetLastError();
+  }
+  std::vector<cudaGraphNode_t> fork, join;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess) fork.assign(deps, deps + ndeps);
   FullArgs fa{};
   fa.b = none;
   fa.sp = sp;
@@ -149,20 +262,35 @@ cudaError_t capture(Graph *g, const ShapeCost *costs, uint64_t tb_words, uint64_
   fa.fwd = d_fwd;
   fa.tb = d_tb;
   fa.tbl = d_tbl;
-  fa.strip_buf = d_strip;
   fa.strip_stride = strip_stride;
   fa.gd = g->d_gd;
   fa.gsum = &d_ps->sum;
-  const bool pack_ok = !sp.use_band && sp.precision != FILTR_PREC_I32;
-  for (int k = 0; k < SHAPE_TILED && e == cudaSuccess; ++k) {
-    if (costs[k].packed && !pack_ok) continue;
+  for (int i = 0; i < ss.n && e == cudaSuccess; ++i) {
+    const int k = ss.k[i];
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = ca.h[i];
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, cg, fork.data(), nullptr, fork.size(), &np);
+    if (e != cudaSuccess) break;
+    join.push_back(node);
+    e = cudaStreamBeginCaptureToGraph(st2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
     fa.counter = d_counters + k;
     fa.gshape = k;
-    const int R = costs[k].R;
-    const int bps = costs[k].packed ? c->pack_blocks_per_sm(R, sp) : c->full_blocks_per_sm(R, sp);
-    const int grid = std::min(c->sms * bps, grid_max);
-    e = costs[k].packed ? launch_pack(fa, R, grid, st) : launch_full(fa, R, grid, st);
+    fa.strip_buf = d_strip[i];
+    e = costs[k].packed ? launch_pack(fa, costs[k].R, ss.grid[i], st2)
+                        : launch_full(fa, costs[k].R, ss.grid[i], st2);
+    cudaGraph_t body = nullptr;
+    const cudaError_t eb = cudaStreamEndCapture(st2, &body);
+    if (e == cudaSuccess) e = eb;
   }
+  if (e == cudaSuccess && !join.empty())
+    e = cudaStreamUpdateCaptureDependencies(st, join.data(), nullptr, join.size(),
+                                            cudaStreamSetCaptureDependencies);
   if (e == cudaSuccess)
     e = launch_trivial(none, sp, d_order, NP, nullptr, d_fwd, st, g->d_gd, &d_ps->sum);
   if (sp.traceback && e == cudaSuccess) {
@@ -234,16 +362,9 @@ filtr_status filtr_graph_create(filtr_ctx *ctx, const filtr_params *params, uint
   const ShapeCost *costs = c->tuned_costs(sp);
   if (!costs) costs = kDefaultShapeCost;
 
-  // layout: fixed parts (capacity-sized), strip buffers, staging, traceback
-  int bps_max = 1;
-  const bool pack_ok = !sp.use_band && sp.precision != FILTR_PREC_I32;
-  for (int k = 0; k < SHAPE_TILED; ++k) {
-    if (costs[k].packed && !pack_ok) continue;
-    const int R = costs[k].R;
-    bps_max = std::max(bps_max, costs[k].packed ? c->pack_blocks_per_sm(R, sp)
-                                                : c->full_blocks_per_sm(R, sp));
-  }
-  const int grid_max = c->sms * bps_max;
+  // layout: fixed parts (capacity-sized), strip buffers per shape, staging,
+  // traceback
+  const ShapeSet ss = graph_shapes(c, sp, costs, max_len);
   const uint64_t stage_cap = sp.traceback ? (uint64_t)max_pairs * (2ull * max_len + 1) : 0;
   GCarve probe{nullptr};  // the same sequence of parts as capture() carves
   {
@@ -259,7 +380,7 @@ filtr_status filtr_graph_create(filtr_ctx *ctx, const filtr_params *params, uint
     probe.take<uint16_t>(max_pairs);
     probe.take<uint64_t>(max_pairs);
     probe.take<uint64_t>((max_pairs + DEV_PLAN_BLOCK - 1) / DEV_PLAN_BLOCK);
-    probe.take<int2>((size_t)grid_max * FULL_WARPS * (max_len + 2));
+    for (int i = 0; i < ss.n; ++i) probe.take<int2>((size_t)ss.grid[i] * FULL_WARPS * (max_len + 2));
     if (sp.traceback) probe.take<uint32_t>(stage_cap);
     probe.take<uint32_t>(0);
   }
@@ -290,14 +411,17 @@ filtr_status filtr_graph_create(filtr_ctx *ctx, const filtr_params *params, uint
   *g->h_status = FILTR_OK;
   GCarve lay{g->mem};
   g->d_gd = lay.take<GraphDesc>(1);
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr, st2 = nullptr;
   e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    if (st) cudaStreamDestroy(st);
     graph_free(g);
     return cuda_fail(e, "cudaStreamCreate");
   }
-  e = capture(g, costs, tb_words, stage_cap, grid_max, lay, st);
+  e = capture(g, costs, ss, tb_words, stage_cap, lay, st, st2);
   cudaStreamDestroy(st);
+  cudaStreamDestroy(st2);
   if (e != cudaSuccess) {
     graph_free(g);
     return cuda_fail(e, "filtr_graph_create: capture");
@@ -368,6 +492,8 @@ filtr_status filtr_graph_status(filtr_graph *graph) {
     set_error("filtr_graph: the batch's traceback exceeds the graph's workspace");
   else if (code == FILTR_ERR_CIGAR_CAP)
     set_error("filtr_graph: the CIGARs exceed cigar_cap");
+  else if (code == FILTR_ERR_UNSUPPORTED)
+    set_error("filtr_graph: the plan chose a tile shape the graph does not launch");
   return (filtr_status)code;
 }
 

@@ -122,7 +122,7 @@ struct LaunchView {
   filtr_result *out;
   const uint32_t *order;
   uint32_t n;
-  bool stop;  // the pipeline was aborted before this launch
+  bool stop;  // nothing to do: the pipeline was aborted, or no pair is left for this block
 };
 __device__ __forceinline__ LaunchView launch_view(const FullArgs &a) {
   LaunchView v{a.b, a.out, a.order, a.n_order, false};
@@ -135,6 +135,9 @@ __device__ __forceinline__ LaunchView launch_view(const FullArgs &a) {
       for (int k = 0; k < a.gshape; ++k) begin += a.gsum->count[k];
       v.order = a.order + begin;
       v.n = a.gsum->count[a.gshape];
+      // the persistent grid is sized for the whole device: blocks past the
+      // pairs this shape got would find the queue empty
+      if ((uint64_t)blockIdx.x * FULL_WARPS >= v.n) v.stop = true;
     }
   }
   return v;

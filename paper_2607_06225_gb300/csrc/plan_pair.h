@@ -128,10 +128,8 @@ inline ShapeTable make_shape_table(const ShapeCost *costs, const ScoreParams &sp
 // bound fits 15 bits, and then always under FILTR_PREC_I16X2.  The minimum is
 // taken without branches (the winner changes from pair to pair); ties go to the
 // earlier shape of the table.
-FILTR_HD int choose_shape(const ShapeTable &t, const ScoreParams &sp, uint32_t M, uint32_t N) {
-  const bool packable =
-      t.n_elig_packed > 0 && pack_bias(sp.mode, sp.o, sp.e, sp.smin, sp.smax, M, N) >= 0;
-  const bool only_packed = packable && sp.precision == FILTR_PREC_I16X2;
+FILTR_HD int choose_shape_p(const ShapeTable &t, bool packable, bool only_packed, uint32_t M,
+                            uint32_t N) {
   const uint32_t s128 = (uint32_t)(((uint64_t)M + 127u) >> 7);
   double strips[7];  // R = 8, 12, ..., 32
 #pragma unroll
@@ -149,6 +147,11 @@ FILTR_HD int choose_shape(const ShapeTable &t, const ScoreParams &sp, uint32_t M
     bc = lt ? c : bc;
   }
   return best;
+}
+FILTR_HD int choose_shape(const ShapeTable &t, const ScoreParams &sp, uint32_t M, uint32_t N) {
+  const bool packable =
+      t.n_elig_packed > 0 && pack_bias(sp.mode, sp.o, sp.e, sp.smin, sp.smax, M, N) >= 0;
+  return choose_shape_p(t, packable, packable && sp.precision == FILTR_PREC_I16X2, M, N);
 }
 
 // Traceback words of an M x N pair in shape k.

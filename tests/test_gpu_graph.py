@@ -3,6 +3,8 @@ filtr_align_batch and to the oracle, one graph replayed over batches of
 different sizes, and the checks that run inside the graph (bad residues,
 lengths over the bound, traceback over the budget, CIGAR capacity) reported by
 filtr_graph_status without disturbing the next launch."""
+import re
+
 import numpy as np
 import pytest
 
@@ -128,8 +130,13 @@ def test_traceback_budget(F, ctx):
     small = synth.protein_pairs(n=20, lmin=100, lmax=300, seed=69)
     big = synth.protein_pairs(n=400, lmin=300, lmax=400, seed=70)
     params = F.make_params(small.subst, **small.scoring)
-    # fixed parts for 400 x 400: under 20 MB; 400 pairs of ~350^2 cells need ~42 MB
-    g = F.Graph(ctx, params, max_pairs=400, max_len=450, workspace_bytes=40 << 20)
+    # the fixed parts depend on the device's occupancy: read them from the
+    # refusal, then leave ~24 MB of traceback area (400 pairs of ~350^2 cells
+    # need ~42 MB, 20 pairs of ~200^2 about 1 MB)
+    with pytest.raises(F.FiltrError) as ei:
+        F.Graph(ctx, params, max_pairs=400, max_len=450, workspace_bytes=1 << 20)
+    fixed = int(re.search(r"need (\d+)", str(ei.value)).group(1))
+    g = F.Graph(ctx, params, max_pairs=400, max_len=450, workspace_bytes=fixed + (24 << 20))
     try:
         same(F, ctx, g, params, small)
         _, _, st = F.graph_align(g, big)
