@@ -167,6 +167,30 @@ void Ctx::span_end(cudaStream_t st) {
   if (spans.back().b) cudaEventRecord(spans.back().b, st);
 }
 
+bool Ctx::ensure_side(int n) {
+  if (!fork_ev && cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+    fork_ev = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  while ((int)side.size() < n) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamDestroy(s);
+      cudaGetLastError();
+      return false;
+    }
+    side.push_back(s);
+    join_ev.push_back(e);
+  }
+  return true;
+}
+
 bool Ctx::ensure_host(size_t bytes) {
   if (h_stage_bytes >= bytes) return true;
   if (h_stage) cudaFreeHost(h_stage);
@@ -341,7 +365,32 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   const int grid_max = plain ? 1 : (int)std::min<int64_t>((int64_t)ctx->sms * blocks_per_sm,
                                                           ((int64_t)n + FULL_WARPS - 1) / FULL_WARPS);
   const uint32_t strip_stride = (uint32_t)(max_n + 2);
-  int2 *d_strip = c.take<int2>((size_t)grid_max * FULL_WARPS * strip_stride);
+  // Strip buffers: one region for launches in sequence; when the device plan
+  // gives pairs to several tiled shapes, their launches run concurrently on
+  // side streams (one launch's tail overlaps the others' work), each shape
+  // with its own region.
+  size_t strip_elems = (size_t)grid_max * FULL_WARPS * strip_stride;
+  size_t shape_strip[SHAPE_TILED] = {};
+  int shape_grid[SHAPE_TILED] = {};
+  int n_conc = 0;
+  if (dev_plan) {
+    size_t tot = 0;
+    for (int k = 0; k < SHAPE_TILED; ++k) {
+      if (!dsum.count[k]) continue;
+      const int bps = costs[k].packed ? ctx->pack_blocks_per_sm(costs[k].R, sp)
+                                      : ctx->full_blocks_per_sm(costs[k].R, sp);
+      shape_grid[k] = (int)std::min<int64_t>((int64_t)ctx->sms * bps,
+                                             ((int64_t)dsum.count[k] + FULL_WARPS - 1) / FULL_WARPS);
+      shape_strip[k] = tot;
+      tot += (size_t)shape_grid[k] * FULL_WARPS * strip_stride;
+      ++n_conc;
+    }
+    if (n_conc >= 2 && ctx->ensure_side(n_conc))
+      strip_elems = std::max(strip_elems, tot);
+    else
+      n_conc = 0;
+  }
+  int2 *d_strip = c.take<int2>(strip_elems);
   uint32_t *d_stage = sp.traceback ? c.take<uint32_t>(stage_words) : nullptr;
   uint32_t *d_tb = c.take<uint32_t>(0);
   if (c.used > ctx->ws_bytes) {
@@ -366,6 +415,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       g.family = costs[k].packed ? FAM_PACK : FAM_FULL;
       g.R = (uint8_t)costs[k].R;
       g.warps = 1;
+      g.shape = (int8_t)k;
       g.begin = at;
       g.end = at + dsum.count[k];
       at = g.end;
@@ -392,6 +442,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       memcpy(h_rl, host_rl, n * 4);
     }
     dev_plan = false;
+    n_conc = 0;
     ctx->h_ql.assign(h_ql, h_ql + n);  // the staging area is reused for the plan upload
     ctx->h_rl.assign(h_rl, h_rl + n);
     PlanInput in{&sp, n, ctx->h_ql.data(), ctx->h_rl.data(), tb_budget, 8, ctx->xdrop_warps0};
@@ -447,7 +498,8 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   // through the overflow list and are rerun with a wider group (1 -> 4 -> 16
   // warps) once the wave's walk is done with the traceback area.
   size_t counter_i = 0;
-  auto run_group = [&](const uint32_t *d_ord, uint32_t cnt, uint8_t family, int R, int W) -> bool {
+  auto run_group = [&](const uint32_t *d_ord, uint32_t cnt, uint8_t family, int R, int W,
+                       cudaStream_t gs, int grid_cap) -> bool {
     if (cnt == 0) return true;
     if (family == FAM_FULL || family == FAM_PACK) {
       const bool pk = family == FAM_PACK;
@@ -473,10 +525,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       fa.n_order = cnt;
       fa.counter = d_counters + (counter_i++ % n_counters);
       const int bps = pk ? ctx->pack_blocks_per_sm(R, sp) : ctx->full_blocks_per_sm(R, sp);
-      // the strip buffer holds grid_max blocks' warps
+      // the strip buffer region holds grid_cap blocks' warps
       int grid = (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + FULL_WARPS - 1) / FULL_WARPS);
-      grid = std::min(grid, grid_max);
-      ce = pk ? launch_pack(fa, R, std::max(grid, 1), st) : launch_full(fa, R, std::max(grid, 1), st);
+      grid = std::min(grid, grid_cap);
+      ce = pk ? launch_pack(fa, R, std::max(grid, 1), gs) : launch_full(fa, R, std::max(grid, 1), gs);
       ++launches;
       return ce == cudaSuccess;
     }
@@ -542,9 +594,29 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       ce = cudaMemsetAsync(d_novf, 0, 4, st);
       if (ce != cudaSuccess) return cuda_fail(ce, "overflow reset");
     }
-    for (const Group &g : w.groups)
-      if (!run_group(d_order + g.begin, g.end - g.begin, g.family, g.R, g.warps))
-        return cuda_fail(ce, "forward kernel launch");
+    if (n_conc) {  // fork: each shape on its own side stream and strip region; join on st
+      ce = cudaEventRecord(ctx->fork_ev, st);
+      int si = 0;
+      for (const Group &g : w.groups) {
+        if (ce != cudaSuccess) break;
+        cudaStream_t s2 = ctx->side[si];
+        ce = cudaStreamWaitEvent(s2, ctx->fork_ev, 0);
+        fa.strip_buf = d_strip + shape_strip[g.shape];
+        if (ce == cudaSuccess &&
+            !run_group(d_order + g.begin, g.end - g.begin, g.family, g.R, g.warps, s2,
+                       shape_grid[g.shape]))
+          return cuda_fail(ce, "forward kernel launch");
+        if (ce == cudaSuccess) ce = cudaEventRecord(ctx->join_ev[si], s2);
+        ++si;
+      }
+      for (int i = 0; i < si && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(st, ctx->join_ev[i], 0);
+      fa.strip_buf = d_strip;
+      if (ce != cudaSuccess) return cuda_fail(ce, "forking the forward launches");
+    } else {
+      for (const Group &g : w.groups)
+        if (!run_group(d_order + g.begin, g.end - g.begin, g.family, g.R, g.warps, st, grid_max))
+          return cuda_fail(ce, "forward kernel launch");
+    }
     ctx->span_end(st);
     std::vector<uint32_t> ovf;
     if (has_xd && !read_overflow(&ovf)) return cuda_fail(ce, "reading the overflow list");
@@ -586,7 +658,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       if (ce == cudaSuccess) ce = cudaMemsetAsync(d_novf, 0, 4, st);
       if (ce != cudaSuccess) return cuda_fail(ce, "rerun upload");
       ctx->span_begin(Ctx::PH_FORWARD, st);
-      if (!run_group(d_rerun, cnt, FAM_XDROP, 8, W)) return cuda_fail(ce, "rerun launch");
+      if (!run_group(d_rerun, cnt, FAM_XDROP, 8, W, st, grid_max)) return cuda_fail(ce, "rerun launch");
       ctx->span_end(st);
       std::vector<uint32_t> ovf;
       if (!read_overflow(&ovf)) return cuda_fail(ce, "reading the overflow list");
@@ -733,6 +805,12 @@ void ctx_delete(Ctx *c) {
     cudaEventDestroy(c->done_ev);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaStream_t s : c->side) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t e : c->join_ev) cudaEventDestroy(e);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->ws) cudaFree(c->ws);
   if (c->d_small) cudaFree(c->d_small);
   if (c->d_io) cudaFree(c->d_io);

@@ -22,6 +22,11 @@ struct Ctx {
   char *d_small = nullptr;    // 4 KiB of device memory for per-call scalars
   size_t d_io_bytes = 0;
   cudaStream_t own_stream = nullptr;
+  // side streams and fork / join events for tiled shapes launched concurrently
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  bool ensure_side(int n);
   std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
   uint64_t last_cells_estimate = 0;
   uint32_t last_pairs_packed = 0;

@@ -13,6 +13,7 @@ namespace filtr {
 
 struct Group {          // pairs of one wave that share one kernel instance
   uint8_t family, R, warps;
+  int8_t shape = -1;    // tiled shape index (device plan), -1 otherwise
   uint32_t begin, end;  // slice of Plan::order
 };
 
