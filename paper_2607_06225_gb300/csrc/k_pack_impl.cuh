@@ -146,6 +146,9 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
   const int oe = AFFINE ? o + e : e;
   const uint32_t MOE = (uint32_t)(-(int64_t)oe * 65537);
   const uint32_t ME = (uint32_t)(-(int64_t)e * 65537);
+  // -e in each half for the per-half (DPX) add: ME above is the 32-bit
+  // constant, whose high half is -e - 1 to absorb the low half's borrow
+  const uint32_t ME16 = ((uint32_t)(-e) & 0xffffu) * 0x10001u;
   const uint32_t K64M = (uint32_t)(-(int64_t)64 * 65537);
   const uint32_t K7F = 0x7fff7fffu;
   const uint32_t K7FME = K7F + ME;
@@ -268,12 +271,14 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
         }
         const uint32_t D = fadd2(Hdg, fadd2(sc, K64M, one), one);
         const uint32_t Hol = Hm[k];
-        uint32_t E, F, Eext = 0, Fext = 0;
+        uint32_t E, F;
         if (AFFINE) {
-          Eext = fadd2(Ec[k], ME, one);
-          E = max2(Hol, Eext);
-          Fext = fadd2(Fup, ME, one);
-          F = max2(Hmup, Fext);
+          // per half max(E_left - e, H_left - (o+e)): one DPX add-max in place of
+          // an add and a max, which leaves room on the FMA pipe for X3 below.
+          // Signed halves: every biased value is below 0x8000, so the sum
+          // stays inside the 16-bit range
+          E = __viaddmax_s16x2(Ec[k], ME16, Hol);
+          F = __viaddmax_s16x2(Fup, ME16, Hmup);
         } else {
           E = Hol;
           F = Hmup;
@@ -281,7 +286,7 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
         const uint32_t DE = max2(D, E);
         const uint32_t H = LOCAL ? __vimax3_u16x2(DE, F, BZ) : max2(DE, F);
         if (TB) {
-          const uint32_t X3 = E - D + K7F;   // E > D
+          const uint32_t X3 = fadd2(fadd2(E, K7F, one), D, mone);  // E > D (on the FMA pipe)
           const uint32_t X2 = F - DE + K7F;  // F > max(D, E)
           // bytes: low-half sign of X3, of X2, high-half sign of X3, of X2
           const uint32_t Pa = perm<0xfbd9>(X3, X2);
