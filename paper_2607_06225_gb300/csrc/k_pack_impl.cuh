@@ -37,8 +37,9 @@
 // extension, byte 3: F took the extension; bit c of each byte is cell 8g + c.
 // The planes are gathered by sign-replicating byte permutes (the two halves'
 // sign bits of two differences per permute, each widened to a 0x00 / 0xff
-// byte) and one three-input logic op per permute that keeps bit c of each
-// byte.
+// byte, i.e. 255 x flag) accumulated as sum(permute x 2^c) by multiply-adds on
+// the FMA pipe; one multiply by the inverse of 255 mod 2^32 per group of eight
+// registers turns the sum into the plane word.
 #pragma once
 
 #include <climits>
@@ -74,10 +75,6 @@ __device__ __forceinline__ uint32_t fmad32(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t r;
   asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
   return r;
-}
-// acc | (p & (0x01010101 << c)), c a compile-time constant after unrolling
-__device__ __forceinline__ uint32_t plane_or(uint32_t acc, uint32_t p, int c) {
-  return acc | (p & (0x01010101u << c));
 }
 // (x & m) | (y & ~m)
 __device__ __forceinline__ uint32_t select_bits(uint32_t m, uint32_t x, uint32_t y) {
@@ -286,22 +283,25 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
         const uint32_t DE = max2(D, E);
         const uint32_t H = LOCAL ? __vimax3_u16x2(DE, F, BZ) : max2(DE, F);
         if (TB) {
-          const uint32_t X3 = fadd2(fadd2(E, K7F, one), D, mone);  // E > D (on the FMA pipe)
+          const uint32_t X3 = E - D + K7F;   // E > D
           const uint32_t X2 = F - DE + K7F;  // F > max(D, E)
-          // bytes: low-half sign of X3, of X2, high-half sign of X3, of X2
+          // bytes: low-half sign of X3, of X2, high-half sign of X3, of X2, each
+          // 0x00 or 0xff = 255 x flag; summing Pa x 2^c over the group's
+          // registers (one multiply-add each, on the FMA pipe) gives 255 x W
+          // mod 2^32, W the plane word with flag c in bit c of each byte
           const uint32_t Pa = perm<0xfbd9>(X3, X2);
-          if ((k & 7) == 0) accA = 0;
-          accA = plane_or(accA, Pa, k & 7);
+          accA = (k & 7) == 0 ? Pa : fmad32(Pa, 1u << (k & 7), accA);
           if (AFFINE) {
             const uint32_t X1 = fadd2(fadd2(Ec[k], K7FME, one), Hol, mone);  // E took the extension
             const uint32_t X0 = fadd2(fadd2(Fup, K7FME, one), Hmup, mone);   // F took the extension
             const uint32_t Pb = perm<0xfbd9>(X1, X0);
-            if ((k & 7) == 0) accB = 0;
-            accB = plane_or(accB, Pb, k & 7);
+            accB = (k & 7) == 0 ? Pb : fmad32(Pb, 1u << (k & 7), accB);
           }
           if ((k & 7) == 7 || k == P - 1) {  // a group of (up to) 8 registers is complete
-            tbw[k >> 3] = perm<0x5410>(accA, accB);      // low half, group k/8
-            tbw[G + (k >> 3)] = perm<0x7632>(accA, accB);  // high half
+            // 255 is odd: W = (255 W) x 255^-1 mod 2^32, 255^-1 = 0xfefefeff
+            const uint32_t WA = accA * 0xfefefeffu, WB = accB * 0xfefefeffu;
+            tbw[k >> 3] = perm<0x5410>(WA, WB);      // low half, group k/8
+            tbw[G + (k >> 3)] = perm<0x7632>(WA, WB);  // high half
           }
         }
         const uint32_t Hmn = fadd2(H, MOE, one);
