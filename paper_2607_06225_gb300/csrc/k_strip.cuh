@@ -16,9 +16,12 @@
 //   E = max(E_left - e, H_left - (o+e))
 //   F = max(F_up - e, H_up - (o+e))
 //   H = max(max(H_diag + s, E), F) [, 0]
-// The DPX forms (__viaddmax_s32, __vimax3_s32) compute the same values but
-// issue at half the plain integer rate on sm_103 (filtr_probe_int_peak
-// measures both), so the plain forms are used.  Substitution scores come from
+// Plain adds issue on the FMA pipe (written as multiply-adds) and maxima on
+// the ALU pipe; a DPX add-max (__viaddmax_s32) or three-way max (__vimax3_s32)
+// takes one ALU slot for two operations (filtr_probe_int_peak measures both
+// rates).  E and F use the add-max and the traceback's extension bits come from
+// H - (o+e) - E and H - (o+e) - F, which balances the two pipes at about 8.5
+// instructions each per affine traceback cell.  Substitution scores come from
 // a per-strip query profile in shared memory (profile[a][row] = s(q_row, a)):
 // one 8- or 16-byte load per lane per step.
 //
@@ -242,15 +245,16 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
         const int D = fadd(Hdg, sc[k], one);
         int E, F, H;
         if (AFFINE) {
-          const int Hol = fadd(Hl, moe, one), Eext = fadd(Ec[k], me, one);
-          const int Hou = fadd(Hup, moe, one), Fext = fadd(Fup, me, one);
-          E = max(Hol, Eext);
-          F = max(Hou, Fext);
+          const int Hol = fadd(Hl, moe, one), Hou = fadd(Hup, moe, one);
+          E = __viaddmax_s32(Ec[k], me, Hol);  // DPX add-max: one ALU slot
+          F = __viaddmax_s32(Fup, me, Hou);
           const int DE = max(D, E);
           H = LOCAL ? __vimax3_s32(DE, F, 0) : max(DE, F);  // DPX: one ALU slot
+          // E took the extension iff E_left - e > H_left - (o+e) iff E != Hol
+          // (a tie keeps the open), so Hol - E < 0 carries the bit
           if (TB)
-            tb_push4(tbw[k >> 3], fsub(D, E, mone), fsub(DE, F, mone), fsub(Hol, Eext, mone),
-                     fsub(Hou, Fext, mone));
+            tb_push4(tbw[k >> 3], fsub(D, E, mone), fsub(DE, F, mone), fsub(Hol, E, mone),
+                     fsub(Hou, F, mone));
         } else {
           E = fadd(Hl, me, one);
           F = fadd(Hup, me, one);
