@@ -145,6 +145,17 @@ int Ctx::pack_blocks_per_sm(int R, const ScoreParams &sp) {
   return nb;
 }
 
+int Ctx::graph_blocks_per_sm(int R, bool packed, const ScoreParams &sp) {
+  const auto key = std::make_tuple(R | (packed ? 0x300 : 0x200), sp.mode, sp.affine, sp.traceback,
+                                   sp.use_band, sp.alphabet);
+  auto it = occ_cache.find(key);
+  if (it != occ_cache.end()) return it->second;
+  int nb = packed ? pack_graph_blocks_per_sm(R, sp) : full_graph_blocks_per_sm(R, sp);
+  if (nb < 1) nb = 1;
+  occ_cache[key] = nb;
+  return nb;
+}
+
 cudaEvent_t Ctx::next_event() {
   if (ev_used == ev_pool.size()) {
     cudaEvent_t e = nullptr;

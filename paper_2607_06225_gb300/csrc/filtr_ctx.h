@@ -67,6 +67,7 @@ struct Ctx {
 
   int full_blocks_per_sm(int R, const ScoreParams &sp);
   int pack_blocks_per_sm(int R, const ScoreParams &sp);
+  int graph_blocks_per_sm(int R, bool packed, const ScoreParams &sp);  // filtr_graph instances
   bool ensure_host(size_t bytes);
   cudaEvent_t next_event();
   // open / close a timed span on stream st (no-ops when timing is off)

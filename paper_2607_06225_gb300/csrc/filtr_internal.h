@@ -259,6 +259,10 @@ cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);
 int pack_max_blocks_per_sm(int R, const ScoreParams &sp);
 cudaError_t launch_pack_mid(const FullArgs &a, int R, int grid, cudaStream_t s);
 int pack_mid_blocks_per_sm(int R, const ScoreParams &sp);
+// occupancy of the captured-pipeline instances (launch_full / launch_pack pick
+// them when FullArgs::gd is set)
+int full_graph_blocks_per_sm(int R, const ScoreParams &sp);
+int pack_graph_blocks_per_sm(int R, const ScoreParams &sp);
 inline int pack_smem_bytes(int R, int alphabet) {
   return 512 + FULL_WARPS * alphabet * pack_prof_stride(R);
 }

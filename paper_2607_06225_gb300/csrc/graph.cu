@@ -166,7 +166,7 @@ ShapeSet graph_shapes(Ctx *c, const ScoreParams &sp, const ShapeCost *costs, uin
     if (costs[k].packed && !pack_ok) continue;
     if (!reach[k]) continue;
     const int R = costs[k].R;
-    const int bps = costs[k].packed ? c->pack_blocks_per_sm(R, sp) : c->full_blocks_per_sm(R, sp);
+    const int bps = c->graph_blocks_per_sm(R, costs[k].packed, sp);
     ss.k[ss.n] = k;
     ss.grid[ss.n] = c->sms * bps;
     ++ss.n;

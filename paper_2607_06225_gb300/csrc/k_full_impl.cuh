@@ -25,12 +25,11 @@ struct WarpIO {
   __device__ void done_col(int, int, int) {}
 };
 
-template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND>
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
   constexpr int HS = 32 * R;
   extern __shared__ __align__(16) int8_t smem[];
-  const LaunchView V = launch_view(a);
-  if (V.stop) return;  // uniform over the grid
+  if (launch_idle<GR>(a)) return;  // uniform over the block
   const int A = a.sp.alphabet;
   int8_t *s_sub = smem;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -43,13 +42,15 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
     uint32_t t0 = 0;
     if (lane == 0) t0 = atomicAdd(a.counter, 1u);
     t0 = __shfl_sync(STRIP_FULLMASK, t0, 0);
-    if (t0 >= V.n) break;
-    const uint32_t p = V.order ? V.order[t0] : t0;
+    if (t0 >= launch_n<GR>(a)) break;
+    const uint32_t *order = launch_order<GR>(a);
+    const uint32_t p = order ? order[t0] : t0;
+    const BatchDev bv = launch_batch<GR>(a);
     StripPair P;
-    P.M = (int)V.b.q_len[p];
-    P.N = (int)V.b.r_len[p];
-    P.q = V.b.q_seq + V.b.q_off[p];
-    P.r = V.b.r_seq + V.b.r_off[p];
+    P.M = (int)bv.q_len[p];
+    P.N = (int)bv.r_len[p];
+    P.q = bv.q_seq + bv.q_off[p];
+    P.r = bv.r_seq + bv.r_off[p];
     P.lo = -P.M - 1;
     P.hi = P.N + 1;
     if (BAND) {
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
       if (lane == 0) {
         filtr_result res{};
         res.status = FILTR_ST_TOO_WIDE;
-        V.out[p] = res;
+        launch_out<GR>(a)[p] = res;
       }
       continue;
     }
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
       res.reserved = 0;
       res.cigar_off = 0;
       res.cells = cells;
-      V.out[p] = res;
+      launch_out<GR>(a)[p] = res;
       if (a.fwd) {
         FwdOut f;
         f.score = score;
@@ -157,9 +158,9 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_full(const FullArgs a) {
   }
 }
 
-template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND>
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 cudaError_t launch_t(const FullArgs &a, int grid, cudaStream_t s) {
-  auto k = k_full<R, LOCAL, AFFINE, TB, BAND>;
+  auto k = k_full<R, LOCAL, AFFINE, TB, BAND, GR>;
   const int smem = full_smem_bytes(R, a.sp.alphabet);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -167,12 +168,12 @@ cudaError_t launch_t(const FullArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND>
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 int occ_t(int smem) {
   int nb = 0;
-  cudaFuncSetAttribute(k_full<R, LOCAL, AFFINE, TB, BAND>,
+  cudaFuncSetAttribute(k_full<R, LOCAL, AFFINE, TB, BAND, GR>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_full<R, LOCAL, AFFINE, TB, BAND>,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_full<R, LOCAL, AFFINE, TB, BAND, GR>,
                                                 FULL_WARPS * 32, smem);
   return nb;
 }
@@ -195,23 +196,23 @@ int occ_t(int smem) {
   X(true, true, true, false)    \
   X(true, true, true, true)
 
-template <int R>
+template <int R, bool GR>
 cudaError_t dispatch_r(const FullArgs &a, int grid, cudaStream_t s) {
   const bool L = a.sp.mode == FILTR_LOCAL, AF = a.sp.affine != 0, T = a.sp.traceback != 0,
              B = a.sp.use_band != 0;
 #define FILTR_CASE(l, af, t, b) \
-  if (L == l && AF == af && T == t && B == b) return launch_t<R, l, af, t, b>(a, grid, s);
+  if (L == l && AF == af && T == t && B == b) return launch_t<R, l, af, t, b, GR>(a, grid, s);
   FILTR_FULL_CASES(FILTR_CASE)
 #undef FILTR_CASE
   return cudaErrorInvalidValue;
 }
 
-template <int R>
+template <int R, bool GR>
 int occ_r(const ScoreParams &sp, int smem) {
   const bool L = sp.mode == FILTR_LOCAL, AF = sp.affine != 0, T = sp.traceback != 0,
              B = sp.use_band != 0;
 #define FILTR_CASE(l, af, t, b) \
-  if (L == l && AF == af && T == t && B == b) return occ_t<R, l, af, t, b>(smem);
+  if (L == l && AF == af && T == t && B == b) return occ_t<R, l, af, t, b, GR>(smem);
   FILTR_FULL_CASES(FILTR_CASE)
 #undef FILTR_CASE
   return 0;

@@ -5,13 +5,16 @@
 
 namespace filtr {
 
+cudaError_t launch_pack_graph(const FullArgs &a, int R, int grid, cudaStream_t s);
+
 cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s) {
   if (a.sp.use_band) return cudaErrorInvalidValue;  // unbanded pairs only
+  if (a.gd) return launch_pack_graph(a, R, grid, s);  // captured pipeline instances
   switch (R) {
-    case 8: return dispatch_pr<8>(a, grid, s);
-    case 16: return dispatch_pr<16>(a, grid, s);
-    case 24: return dispatch_pr<24>(a, grid, s);
-    case 32: return dispatch_pr<32>(a, grid, s);
+    case 8: return dispatch_pr<8, false>(a, grid, s);
+    case 16: return dispatch_pr<16, false>(a, grid, s);
+    case 24: return dispatch_pr<24, false>(a, grid, s);
+    case 32: return dispatch_pr<32, false>(a, grid, s);
     case 12:
     case 20:
     case 28: return launch_pack_mid(a, R, grid, s);
@@ -21,10 +24,10 @@ cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s) {
 
 int pack_max_blocks_per_sm(int R, const ScoreParams &sp) {
   switch (R) {
-    case 8: return occ_pr<8>(sp);
-    case 16: return occ_pr<16>(sp);
-    case 24: return occ_pr<24>(sp);
-    case 32: return occ_pr<32>(sp);
+    case 8: return occ_pr<8, false>(sp);
+    case 16: return occ_pr<16, false>(sp);
+    case 24: return occ_pr<24, false>(sp);
+    case 32: return occ_pr<32, false>(sp);
     case 12:
     case 20:
     case 28: return pack_mid_blocks_per_sm(R, sp);

@@ -1,0 +1,25 @@
+// k_pack_graph_mid.cu -- the int16x2 tiled kernel's captured-pipeline
+// instances for R = 12, 20 and 28 (see k_pack_graph.cu).
+#include "k_pack_impl.cuh"
+
+namespace filtr {
+
+cudaError_t launch_pack_graph_mid(const FullArgs &a, int R, int grid, cudaStream_t s) {
+  switch (R) {
+    case 12: return dispatch_pr<12, true>(a, grid, s);
+    case 20: return dispatch_pr<20, true>(a, grid, s);
+    case 28: return dispatch_pr<28, true>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int pack_graph_blocks_per_sm_mid(int R, const ScoreParams &sp) {
+  switch (R) {
+    case 12: return occ_pr<12, true>(sp);
+    case 20: return occ_pr<20, true>(sp);
+    case 28: return occ_pr<28, true>(sp);
+    default: return 0;
+  }
+}
+
+}  // namespace filtr

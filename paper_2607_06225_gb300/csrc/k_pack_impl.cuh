@@ -362,12 +362,11 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
   __syncwarp();
 }
 
-template <int R, bool LOCAL, bool AFFINE, bool TB>
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool GR>
 __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
   constexpr int HS = 32 * R;
   extern __shared__ __align__(16) int8_t smem[];
-  const LaunchView V = launch_view(a);
-  if (V.stop) return;  // uniform over the grid
+  if (launch_idle<GR>(a)) return;  // uniform over the block
   const int A = a.sp.alphabet;
   int8_t *s_sub = smem;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -380,13 +379,15 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
     uint32_t t0 = 0;
     if (lane == 0) t0 = atomicAdd(a.counter, 1u);
     t0 = __shfl_sync(PFULL, t0, 0);
-    if (t0 >= V.n) break;
-    const uint32_t p = V.order ? V.order[t0] : t0;
+    if (t0 >= launch_n<GR>(a)) break;
+    const uint32_t *order = launch_order<GR>(a);
+    const uint32_t p = order ? order[t0] : t0;
+    const BatchDev bv = launch_batch<GR>(a);
     PackPair PP;
-    PP.M = (int)V.b.q_len[p];
-    PP.N = (int)V.b.r_len[p];
-    PP.q = V.b.q_seq + V.b.q_off[p];
-    PP.r = V.b.r_seq + V.b.r_off[p];
+    PP.M = (int)bv.q_len[p];
+    PP.N = (int)bv.r_len[p];
+    PP.q = bv.q_seq + bv.q_off[p];
+    PP.r = bv.r_seq + bv.r_off[p];
     PP.o = a.sp.o;
     PP.e = a.sp.e;
     PP.A = A;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
       res.reserved = 0;
       res.cigar_off = 0;
       res.cells = (uint64_t)M * (uint64_t)N;
-      V.out[p] = res;
+      launch_out<GR>(a)[p] = res;
       if (a.fwd) {
         FwdOut f;
         f.score = score;
@@ -455,9 +456,9 @@ __global__ void __launch_bounds__(FULL_WARPS * 32) k_pack(const FullArgs a) {
   }
 }
 
-template <int R, bool LOCAL, bool AFFINE, bool TB>
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool GR>
 cudaError_t launch_pt(const FullArgs &a, int grid, cudaStream_t s) {
-  auto k = k_pack<R, LOCAL, AFFINE, TB>;
+  auto k = k_pack<R, LOCAL, AFFINE, TB, GR>;
   const int smem = pack_smem_bytes(R, a.sp.alphabet);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -465,12 +466,12 @@ cudaError_t launch_pt(const FullArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int R, bool LOCAL, bool AFFINE, bool TB>
+template <int R, bool LOCAL, bool AFFINE, bool TB, bool GR>
 int occ_pt(int smem) {
   int nb = 0;
-  cudaFuncSetAttribute(k_pack<R, LOCAL, AFFINE, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pack<R, LOCAL, AFFINE, TB>,
+  cudaFuncSetAttribute(k_pack<R, LOCAL, AFFINE, TB, GR>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pack<R, LOCAL, AFFINE, TB, GR>,
                                                 FULL_WARPS * 32, smem);
   return nb;
 }
@@ -485,22 +486,22 @@ int occ_pt(int smem) {
   X(true, true, false)      \
   X(true, true, true)
 
-template <int R>
+template <int R, bool GR>
 cudaError_t dispatch_pr(const FullArgs &a, int grid, cudaStream_t s) {
   const bool L = a.sp.mode == FILTR_LOCAL, AF = a.sp.affine != 0, T = a.sp.traceback != 0;
 #define FILTR_CASE(l, af, t) \
-  if (L == l && AF == af && T == t) return launch_pt<R, l, af, t>(a, grid, s);
+  if (L == l && AF == af && T == t) return launch_pt<R, l, af, t, GR>(a, grid, s);
   FILTR_PACK_CASES(FILTR_CASE)
 #undef FILTR_CASE
   return cudaErrorInvalidValue;
 }
 
-template <int R>
+template <int R, bool GR>
 int occ_pr(const ScoreParams &sp) {
   const bool L = sp.mode == FILTR_LOCAL, AF = sp.affine != 0, T = sp.traceback != 0;
   const int smem = pack_smem_bytes(R, sp.alphabet);
 #define FILTR_CASE(l, af, t) \
-  if (L == l && AF == af && T == t) return occ_pt<R, l, af, t>(smem);
+  if (L == l && AF == af && T == t) return occ_pt<R, l, af, t, GR>(smem);
   FILTR_PACK_CASES(FILTR_CASE)
 #undef FILTR_CASE
   return 0;

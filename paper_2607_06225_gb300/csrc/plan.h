@@ -115,33 +115,67 @@ constexpr int DEV_PLAN_BLOCK = 256;
 cudaError_t launch_plan(const DevPlanArgs &a, cudaStream_t st);
 
 #ifdef __CUDACC__
-// What one tiled launch works on: its by-value arguments, or in a captured
-// pipeline the batch and outputs of the graph descriptor and the slice of the
-// order that the device plan gave this launch's shape.
-struct LaunchView {
-  BatchDev b;
-  filtr_result *out;
-  const uint32_t *order;
-  uint32_t n;
-  bool stop;  // nothing to do: the pipeline was aborted, or no pair is left for this block
-};
-__device__ __forceinline__ LaunchView launch_view(const FullArgs &a) {
-  LaunchView v{a.b, a.out, a.order, a.n_order, false};
-  if (a.gd) {
-    v.b = a.gd->b;
-    v.out = a.gd->out;
-    v.stop = a.gd->abort != 0;
-    if (a.gsum) {
-      uint32_t begin = 0;
-      for (int k = 0; k < a.gshape; ++k) begin += a.gsum->count[k];
-      v.order = a.order + begin;
-      v.n = a.gsum->count[a.gshape];
-      // the persistent grid is sized for the whole device: blocks past the
-      // pairs this shape got would find the queue empty
-      if ((uint64_t)blockIdx.x * FULL_WARPS >= v.n) v.stop = true;
-    }
+// What one tiled launch works on.  The batched call's instances (GR = false)
+// read their by-value arguments, which live in the parameter bank and cost no
+// register.  A captured pipeline's instances (GR = true) take the batch and
+// outputs from the graph descriptor and their slice of the order from the
+// device plan, read per pair (volatile: never hoisted into registers that
+// live across the persistent loop).
+template <bool GR>
+__device__ __forceinline__ uint32_t launch_n(const FullArgs &a) {
+  if constexpr (GR) {
+    const volatile DevPlanSummary *s = a.gsum;
+    return s->count[a.gshape];
+  } else {
+    return a.n_order;
   }
-  return v;
+}
+template <bool GR>
+__device__ __forceinline__ const uint32_t *launch_order(const FullArgs &a) {
+  if constexpr (GR) {
+    const volatile DevPlanSummary *s = a.gsum;
+    uint32_t begin = 0;
+    for (int k = 0; k < a.gshape; ++k) begin += s->count[k];
+    return a.order + begin;
+  } else {
+    return a.order;
+  }
+}
+template <bool GR>
+__device__ __forceinline__ BatchDev launch_batch(const FullArgs &a) {
+  if constexpr (GR) {
+    const volatile GraphDesc *g = a.gd;
+    BatchDev b;
+    b.q_seq = g->b.q_seq;
+    b.r_seq = g->b.r_seq;
+    b.q_off = g->b.q_off;
+    b.r_off = g->b.r_off;
+    b.q_len = g->b.q_len;
+    b.r_len = g->b.r_len;
+    return b;
+  } else {
+    return a.b;
+  }
+}
+template <bool GR>
+__device__ __forceinline__ filtr_result *launch_out(const FullArgs &a) {
+  if constexpr (GR) {
+    const volatile GraphDesc *g = a.gd;
+    return g->out;
+  } else {
+    return a.out;
+  }
+}
+// Nothing to do (captured pipeline): the pipeline was aborted, or the
+// persistent grid (sized for the whole device) has more blocks than this
+// shape has pairs.
+template <bool GR>
+__device__ __forceinline__ bool launch_idle(const FullArgs &a) {
+  if constexpr (GR) {
+    return a.gd->abort != 0 || (uint64_t)blockIdx.x * FULL_WARPS >= launch_n<GR>(a);
+  } else {
+    return false;
+  }
 }
 #endif
 
