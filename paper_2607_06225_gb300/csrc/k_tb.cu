@@ -71,6 +71,17 @@ __device__ __forceinline__ uint32_t pack_bits(const uint32_t *tb, const PackGeom
          ((w >> (24 + c)) & 1u);
 }
 
+// Choice bits of cell (i, j) of an unbanded int32 tile: every strip has N + 31
+// steps of R / 8 words per lane.
+__device__ __forceinline__ uint32_t full_bits_unbanded(const uint32_t *tb, int R, int N, int i,
+                                                       int j) {
+  const int HS = 32 * R, s = (i - 1) / HS, rho = (i - 1) - s * HS;
+  const int l = rho / R, k = rho - l * R, wps = R / 8;
+  const int64_t t = (int64_t)j - 1 + l;
+  const int64_t base = (int64_t)s * strip_tb_words(1, N, R);
+  return tb_nibble(__ldg(tb + base + (t * wps + (k >> 3)) * 32 + l), k);
+}
+
 struct Emitter {
   uint32_t *st;
   uint32_t n;
@@ -91,14 +102,9 @@ struct Emitter {
   }
 };
 
-__global__ void k_walk(const WalkArgs a) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  const GraphDesc *gd = a.gd;  // captured pipeline: batch, outputs and count from here
-  if (gd && gd->abort) return;
-  if (t >= (gd ? gd->n : a.n_order)) return;
-  const BatchDev b = gd ? gd->b : a.b;
-  filtr_result *const out = gd ? gd->out : a.out;
-  const uint32_t p = a.order[t];
+// One thread walks pair p (any layout).
+__device__ __forceinline__ void walk_thread(const WalkArgs &a, const BatchDev &b,
+                                            filtr_result *out, uint32_t p) {
   const FwdOut f = a.fwd[p];
   const TbLayout L = a.tbl[p];
   if (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED) {
@@ -212,6 +218,14 @@ __global__ void k_walk(const WalkArgs a) {
   res->cigar_len = em.n;
 }
 
+__global__ void k_walk(const WalkArgs a) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const GraphDesc *gd = a.gd;  // captured pipeline: batch, outputs and count from here
+  if (gd && gd->abort) return;
+  if (t >= (gd ? gd->n : a.n_order)) return;
+  walk_thread(a, gd ? gd->b : a.b, gd ? gd->out : a.out, a.order[t]);
+}
+
 // ---- warp walks over the antidiagonal (X-drop) layout ------------------------
 // The walk itself is serial, and one thread per pair spends it waiting on two
 // dependent loads per step (the window origin c_k, then the traceback word).
@@ -257,6 +271,7 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
     if (k <= k_stop || k < k_low) return false;
     if (w.state == 0) {
       const uint32_t nib = bits(w.i, w.j);
+      if (nib > 15u) return false;  // not cached: the warp refills around (i, j)
       if (nib & TB_PF) {
         w.state = 2;
       } else if (nib & TB_PE) {
@@ -274,6 +289,7 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
         continue;
       }
       const uint32_t nib = bits(w.i, w.j);
+      if (nib > 15u) return false;
       w.em.put(OP_D, 1);
       if (nib & TB_EEXT) {
         w.v += w.e;
@@ -288,6 +304,7 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
         continue;
       }
       const uint32_t nib = bits(w.i, w.j);
+      if (nib > 15u) return false;
       w.em.put(OP_I, 1);
       if (nib & TB_FEXT) {
         w.v += w.e;
@@ -397,6 +414,87 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
   if (lane == 0) {
     w.em.flush();
     filtr_result *res = a.out + p;
+    res->q_begin = w.i;
+    res->r_begin = w.j;
+    res->cigar_len = w.em.n;
+  }
+}
+
+// ---- warp walk over the tiled layouts ---------------------------------------
+// One thread per pair waits on one dependent load per step.  A warp instead
+// caches, from the current cell (i0, j0), the choice bits of three lines of 32
+// cells: the diagonal (i0 - d, j0 - d), the row (i0, j0 - d) and the column
+// (i0 - d, j0) -- lane d loads its three words at once.  Matches and
+// mismatches follow the diagonal, a gap the row or the column, so lane 0 walks
+// from the cache until the path leaves all three lines (a gap's start or end),
+// and the warp refills there: about two refills per gap instead of a load per
+// step.  Banded int32 pairs (strip offsets that depend on the band) are walked
+// by lane 0 alone.
+
+struct TileCache {
+  uint8_t d[32], row[32], col[32];
+};
+
+struct TileCacheBits {
+  const TileCache *C;
+  int i0, j0;
+  __device__ uint32_t operator()(int ii, int jj) const {
+    const int di = i0 - ii, dj = j0 - jj;
+    if (di == dj && di < 32) return C->d[di];
+    if (di == 0 && dj < 32) return C->row[dj];
+    if (dj == 0 && di < 32) return C->col[di];
+    return 0xffu;  // not cached
+  }
+};
+
+__global__ void __launch_bounds__(128) k_walk_tw(const WalkArgs a) {
+  __shared__ TileCache cache[4];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t t = blockIdx.x * 4 + wib;
+  const GraphDesc *gd = a.gd;  // captured pipeline: batch, outputs and count from here
+  if (gd && gd->abort) return;
+  if (t >= (gd ? gd->n : a.n_order)) return;
+  const BatchDev b = gd ? gd->b : a.b;
+  filtr_result *const out = gd ? gd->out : a.out;
+  const uint32_t p = a.order[t];
+  const TbLayout L = a.tbl[p];
+  const bool pk = L.family == FAM_PACK;
+  if (!L.valid || !(pk || (L.family == FAM_FULL && !a.sp.use_band))) {
+    if (lane == 0) walk_thread(a, b, out, p);  // empty pairs, banded int32 tiles
+    return;
+  }
+  const FwdOut f = a.fwd[p];
+  if (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED) {
+    if (lane == 0) out[p].cigar_len = 0;
+    return;
+  }
+  const int N = (int)b.r_len[p];
+  const uint32_t *tb = a.tb + L.off;
+  const PackGeom pg{L.R, (int64_t)pack_strip_tb_words(1, N, L.R)};
+  WalkCore w{b.q_seq + b.q_off[p], b.r_seq + b.r_off[p], a.sp.subst, a.sp.alphabet,
+             a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
+             Emitter{a.stage + a.stage_off[p], 0, -1, 0}};
+  TileCache &C = cache[wib];
+  bool done = false;
+  auto cell = [&](int ii, int jj) -> uint8_t {
+    if (ii < 1 || jj < 1) return 0;
+    return (uint8_t)(pk ? pack_bits(tb, pg, ii, jj) : full_bits_unbanded(tb, L.R, N, ii, jj));
+  };
+  for (;;) {
+    const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
+    if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
+    const uint8_t cd = cell(i0 - lane, j0 - lane), cr = cell(i0, j0 - lane),
+                  cc = cell(i0 - lane, j0);
+    C.d[lane] = cd;
+    C.row[lane] = cr;
+    C.col[lane] = cc;
+    __syncwarp();
+    if (lane == 0) done = walk_run(w, TileCacheBits{&C, i0, j0}, -1, INT64_MIN);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    w.em.flush();
+    filtr_result *res = out + p;
     res->q_begin = w.i;
     res->r_begin = w.j;
     res->cigar_len = w.em.n;
@@ -549,9 +647,18 @@ __global__ void k_compact(const WalkArgs a, uint32_t n, const uint64_t *offs, ui
 
 cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s) {
   if (a.n_order == 0) return cudaSuccess;
-  k_walk<<<(a.n_order + 127) / 128, 128, 0, s>>>(a);
+  // A warp per pair keeps more loads in flight for each pair but issues the
+  // serial walk as a whole warp's instructions: for one or a few pairs (plain
+  // per-pair calls, a long pair) it is the faster form; with thousands of pairs
+  // a thread per pair (32 pairs per instruction stream) is (2.3 ms against
+  // 5.2 ms for the 100,000-pair protein batch).
+  if (a.n_order <= 256)
+    k_walk_tw<<<(a.n_order + 3) / 4, 128, 0, s>>>(a);
+  else
+    k_walk<<<(a.n_order + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
+
 
 cudaError_t launch_walk_xd(const WalkArgs &a, cudaStream_t s) {
   if (a.n_order == 0) return cudaSuccess;
