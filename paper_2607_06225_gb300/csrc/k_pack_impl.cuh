@@ -210,10 +210,14 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
   int rc_lo = PP.r[0], rc_hi = rc_lo;
   int rc_next = PP.r[min(max(1 - 2 * lane, 1), N) - 1];
 
-#pragma unroll 1
-  for (int t = 0; t < nsteps; ++t) {
+  // one step; the steps where some lane has a half outside [1, N] (the first
+  // 63 and those from N on) run the masked form, the steady ones the plain
+  auto step = [&](const int t, auto edge_tag) {
+    constexpr bool EDGE_STEP = decltype(edge_tag)::value;
     const int cL = 1 + t - 2 * lane, cH = cL - 1;
-    const bool actL = cL >= 1 && cL <= N, actH = cH >= 1 && cH <= N;
+    // steady steps (63 <= t <= N - 1) have every lane's halves inside [1, N]
+    const bool actL = !EDGE_STEP || (cL >= 1 && cL <= N);
+    const bool actH = !EDGE_STEP || (cH >= 1 && cH <= N);
     uint32_t sH = __shfl_up_sync(PFULL, outH, 1);
     uint32_t sF = __shfl_up_sync(PFULL, outF, 1);
     if (lane == 0) {
@@ -235,7 +239,7 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
     // profile words: low half at column cL, high half at cH (last step's cL)
     rc_hi = rc_lo;
     rc_lo = rc_next;
-    rc_next = PP.r[min(max(cL + 1, 1), N) - 1];
+    rc_next = PP.r[(EDGE_STEP ? min(max(cL + 1, 1), N) : min(cL + 1, N)) - 1];
     const HW wl = *reinterpret_cast<const HW *>(PP.prof + rc_lo * PS + lane * 8 * PW);
     const HW wh = *reinterpret_cast<const HW *>(PP.prof + rc_hi * PS + lane * 8 * PW + 4 * PW);
     const uint32_t *wlw = reinterpret_cast<const uint32_t *>(&wl);
@@ -247,7 +251,6 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
     hprev = Hc[P - 1];
     prevS = sH;
     uint32_t Hmup = fadd2(Hup, MOE, one);
-    const bool edge = !(t >= 63 && t <= N - 1);  // warp-uniform
     const uint32_t KM = (actL ? 0x0000ffffu : 0u) | (actH ? 0xffff0000u : 0u);
     uint32_t mkey = 0;  // largest best-cell key of this step (local mode)
     uint32_t accA = 0, accB = 0;
@@ -327,10 +330,7 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
         }
       }
     };
-    if (edge)
-      regs(std::true_type{});
-    else
-      regs(std::false_type{});
+    regs(edge_tag);
     outH = Hc[P - 1];
     outF = Fup;
     Flast = Fup;
@@ -351,7 +351,13 @@ __device__ __forceinline__ void pack_strip(const PackPair &PP, int s, int64_t tb
       best.i = top + row;
       best.j = row < P ? cL : cH;
     }
-  }
+  };
+#pragma unroll 1
+  for (int t = 0; t < min(63, nsteps); ++t) step(t, std::true_type{});
+#pragma unroll 1
+  for (int t = 63; t < N; ++t) step(t, std::false_type{});
+#pragma unroll 1
+  for (int t = max(63, N); t < nsteps; ++t) step(t, std::true_type{});
   if (!LOCAL && s == nstrips - 1 && top <= M && M < top + R) {
 #pragma unroll
     for (int k = 0; k < P; ++k) {
