@@ -301,7 +301,7 @@ filtr_status filtr_graph_destroy(filtr_graph *graph);
 /* Autotuning of the tiled kernel shapes (the paper leaves autotuning to
  * future work, Sec. 11).  Times every tiled shape -- the int32 tile with 32,
  * 24, 16 or 8 rows per lane and, where the parameters allow it, the int16x2
- * tile with 32, 28, 24, 20, 16, 12 or 8 -- on calibration batches that fill
+ * tile with any even height from 32 down to 8 -- on calibration batches that fill
  * every resident warp slot of the device three times (pairs of one full strip
  * of query rows by 512 reference residues, random codes), and keeps in ctx the
  * device time per warp step of each shape for this recurrence kind (mode, gap
@@ -309,16 +309,16 @@ filtr_status filtr_graph_destroy(filtr_graph *graph);
  * kind give each pair the shape whose predicted time, strips x (N + fill
  * steps) x that cost, is smallest.  Results never change: the shapes are
  * bit-exact alternatives.
- *   out: optional; n_shapes (11) entries of rows_per_lane / packed describe the
+ *   out: optional; n_shapes (17) entries of rows_per_lane / packed describe the
  *        shapes, always in this order: int32 R = 32, 24, 16, 8, then int16x2
- *        R = 32, 28, 24, 20, 16, 12, 8; ns_per_warp_step is 0 for shapes not
+ *        R = 32, 30, 28, ..., 10, 8; ns_per_warp_step is 0 for shapes not
  *        timed (not allowed for these parameters, or too large for the
  *        workspace); entries past n_shapes are 0.
  * Synchronous (waits for the context's previous call); uses the workspace.
  * Errors: FILTR_ERR_INVALID (NULL ctx, bad params, X-drop parameters, which
  * use the antidiagonal kernel only), FILTR_ERR_NOMEM (the workspace holds no
  * calibration batch), FILTR_ERR_CUDA. */
-#define FILTR_TUNE_MAX_SHAPES 16
+#define FILTR_TUNE_MAX_SHAPES 24
 typedef struct {
   int32_t n_shapes;
   int32_t rows_per_lane[FILTR_TUNE_MAX_SHAPES];

@@ -55,10 +55,9 @@ class Stats(C.Structure):
 
 
 # the eight tiled shapes in the order filtr_autotune reports them
-TUNE_SHAPES = [("i32", 32), ("i32", 24), ("i32", 16), ("i32", 8),
-               ("i16x2", 32), ("i16x2", 28), ("i16x2", 24), ("i16x2", 20), ("i16x2", 16),
-               ("i16x2", 12), ("i16x2", 8)]
-TUNE_MAX_SHAPES = 16
+TUNE_SHAPES = [("i32", 32), ("i32", 24), ("i32", 16), ("i32", 8)] + [
+    ("i16x2", R) for R in range(32, 7, -2)]
+TUNE_MAX_SHAPES = 24
 
 
 class TuneReport(C.Structure):

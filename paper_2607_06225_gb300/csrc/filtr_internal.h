@@ -254,11 +254,14 @@ int long_blocks_per_sm(const ScoreParams &sp);
 cudaError_t launch_full(const FullArgs &a, int R, int grid, cudaStream_t s);
 int full_smem_bytes(int R, int alphabet);
 int full_max_blocks_per_sm(int R, const ScoreParams &sp, int alphabet);
-// int16x2 tile, R = 8, 12, 16, 20, 24, 28, 32 (k_pack.cu; 12, 20, 28 in k_pack_mid.cu)
+// int16x2 tile, every even R from 8 to 32 (k_pack.cu dispatches; instances in
+// k_pack.cu, k_pack_mid.cu, k_pack_odd.cu and k_pack_odd_hi.cu)
 cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s);
 int pack_max_blocks_per_sm(int R, const ScoreParams &sp);
 cudaError_t launch_pack_mid(const FullArgs &a, int R, int grid, cudaStream_t s);
 int pack_mid_blocks_per_sm(int R, const ScoreParams &sp);
+cudaError_t launch_pack_odd(const FullArgs &a, int R, int grid, cudaStream_t s);  // R = 10, ..., 30
+int pack_odd_blocks_per_sm(int R, const ScoreParams &sp);
 // occupancy of the captured-pipeline instances (launch_full / launch_pack pick
 // them when FullArgs::gd is set)
 int full_graph_blocks_per_sm(int R, const ScoreParams &sp);

@@ -114,11 +114,11 @@ struct ShapeSet {
   int n = 0;
 };
 // Shapes choose_shape can give some pair with both lengths at most max_len.
-// Within one count of 128-row strips a shape's cost is a line in N, so the
-// cheapest shape changes only where two lines cross: evaluating the choice at
-// N = 1, N = max_len and beside every crossing finds every winner, for pairs
-// that fit 15 bits and for pairs that do not.  Above 2^20 every allowed shape
-// is kept (the scan would take too long).
+// Within one block of 64 query rows every shape's strip count is fixed and its
+// cost is a line in N, so the cheapest shape changes only where two lines
+// cross: evaluating the choice at N = 1, N = max_len and beside every crossing
+// finds every winner, for pairs that fit 15 bits and for pairs that do not.
+// Above 2^20 every allowed shape is kept (the scan would take too long).
 void reachable_shapes(const ShapeTable &t, const ScoreParams &sp, uint32_t max_len,
                       bool *reach) {
   for (int k = 0; k < SHAPE_TILED; ++k) reach[k] = false;
@@ -126,10 +126,10 @@ void reachable_shapes(const ShapeTable &t, const ScoreParams &sp, uint32_t max_l
     for (int i = 0; i < t.n_elig; ++i) reach[t.elig[i]] = true;
     return;
   }
-  const uint32_t smax = (max_len + 127) / 128;
+  const uint32_t smax = (max_len + 63) / 64;  // strip counts change every 64 rows
   std::vector<uint32_t> ns;
   for (uint32_t s = 1; s <= smax; ++s) {
-    const uint32_t M = std::min<uint32_t>(128 * s, max_len);
+    const uint32_t M = std::min<uint32_t>(64 * s, max_len);
     // lines a_k (N + f_k) for this strip count
     double a[SHAPE_TILED];
     for (int i = 0; i < t.n_elig; ++i) {

@@ -1,6 +1,7 @@
 // k_pack.cu -- instances of the int16x2 tiled kernel (k_pack_impl.cuh) for
 // R = 8, 16, 24 and 32 rows per lane, and the dispatch over every packed height
-// (R = 12, 20 and 28 are instantiated in k_pack_mid.cu, compiled in parallel).
+// (R = 12, 20, 28 in k_pack_mid.cu, the heights with an odd number of rows per
+// half in k_pack_odd.cu; the translation units compile in parallel).
 #include "k_pack_impl.cuh"
 
 namespace filtr {
@@ -18,7 +19,7 @@ cudaError_t launch_pack(const FullArgs &a, int R, int grid, cudaStream_t s) {
     case 12:
     case 20:
     case 28: return launch_pack_mid(a, R, grid, s);
-    default: return cudaErrorInvalidValue;
+    default: return launch_pack_odd(a, R, grid, s);
   }
 }
 
@@ -31,7 +32,7 @@ int pack_max_blocks_per_sm(int R, const ScoreParams &sp) {
     case 12:
     case 20:
     case 28: return pack_mid_blocks_per_sm(R, sp);
-    default: return 0;
+    default: return pack_odd_blocks_per_sm(R, sp);
   }
 }
 

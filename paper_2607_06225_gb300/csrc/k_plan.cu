@@ -130,9 +130,14 @@ __global__ void __launch_bounds__(1024) k_plan_scan(const DevPlanArgs a, uint32_
   if (a.gd) nblk = (a.gd->n + DEV_PLAN_BLOCK - 1) / DEV_PLAN_BLOCK;
   const uint32_t t = threadIdx.x;
   unsigned long long tot;
-  const unsigned long long h = t < PLAN_KEYS ? S->hist[t] : 0ull;
-  const unsigned long long ex = block_excl_scan<1024>(h, ws, &tot);
-  if (t < PLAN_KEYS) S->cursor[t] = (uint32_t)ex;
+  unsigned long long kcarry = 0;
+  for (uint32_t base = 0; base < (uint32_t)PLAN_KEYS; base += 1024) {
+    const uint32_t i = base + t;
+    const unsigned long long h = i < (uint32_t)PLAN_KEYS ? S->hist[i] : 0ull;
+    const unsigned long long ex = block_excl_scan<1024>(h, ws, &tot);
+    if (i < (uint32_t)PLAN_KEYS) S->cursor[i] = (uint32_t)(kcarry + ex);
+    kcarry += tot;
+  }
   if (t <= KEY_TRIVIAL) {
     uint32_t c = 0;
     for (int b = 0; b < 64; ++b) c += S->hist[t * 64 + b];

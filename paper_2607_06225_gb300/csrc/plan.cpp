@@ -21,9 +21,11 @@ namespace filtr {
 // instruction mix; filtr_autotune replaces them with timed values).
 const ShapeCost kDefaultShapeCost[SHAPE_TILED] = {
     {32, 31, 16.0f, 30.0f, false}, {24, 31, 16.0f, 30.0f, false}, {16, 31, 16.0f, 30.0f, false},
-    {8, 31, 16.0f, 30.0f, false},  {32, 63, 12.0f, 40.0f, true},  {28, 63, 12.0f, 40.0f, true},
-    {24, 63, 12.0f, 40.0f, true},  {20, 63, 12.0f, 40.0f, true},  {16, 63, 12.0f, 40.0f, true},
-    {12, 63, 12.0f, 40.0f, true},  {8, 63, 12.0f, 40.0f, true}};
+    {8, 31, 16.0f, 30.0f, false},  {32, 63, 12.0f, 40.0f, true},  {30, 63, 12.0f, 40.0f, true},
+    {28, 63, 12.0f, 40.0f, true},  {26, 63, 12.0f, 40.0f, true},  {24, 63, 12.0f, 40.0f, true},
+    {22, 63, 12.0f, 40.0f, true},  {20, 63, 12.0f, 40.0f, true},  {18, 63, 12.0f, 40.0f, true},
+    {16, 63, 12.0f, 40.0f, true},  {14, 63, 12.0f, 40.0f, true},  {12, 63, 12.0f, 40.0f, true},
+    {10, 63, 12.0f, 40.0f, true},  {8, 63, 12.0f, 40.0f, true}};
 
 double shape_cost(const ShapeCost &c, uint32_t M, uint32_t N) {
   return (double)strips_of(M, c.R) * (double)(N + c.fill) * ((double)c.per_row * c.R + c.per_step);

@@ -8,9 +8,9 @@
 
 namespace filtr {
 
-// Tiled kernel shapes (int32 R = 32, 24, 16, 8; int16x2 R = 32, 28, 24, 20,
-// 16, 12, 8), then X-drop.
-enum : int { SHAPE_TILED = 11, SHAPE_XDROP = 11, SHAPE_KEYS = 12 };
+// Tiled kernel shapes (int32 R = 32, 24, 16, 8; int16x2 R = 32, 30, ..., 10,
+// 8), then X-drop.
+enum : int { SHAPE_TILED = 17, SHAPE_XDROP = 17, SHAPE_KEYS = 18 };
 struct ShapeCost {
   int R, fill;        // rows per lane; fill steps per strip (staircase)
   float per_row;      // cost of one row (int32) or one packed register pair of rows / 2
@@ -18,23 +18,29 @@ struct ShapeCost {
   bool packed;
 };
 
-// ceil(M / 32R) for R a multiple of 4 from 8 to 32: tile heights are multiples
-// of 128 rows, and ceil(ceil(M / 128) / (R / 4)) = ceil(M / 32R), so one shift
-// and a division by a small constant give every height.
-FILTR_HD uint32_t strips_s128(uint32_t s128, int d) {  // ceil(s128 / d), d = R / 4
+// ceil(M / 32R) for even R from 8 to 32: tile heights are multiples of 64
+// rows, and ceil(ceil(M / 64) / (R / 2)) = ceil(M / 32R), so one shift and a
+// division by a small constant give every height.
+FILTR_HD uint32_t strips_s64(uint32_t s64, int d) {  // ceil(s64 / d), d = R / 2
   switch (d) {
-    case 2: return (s128 + 1u) >> 1;
-    case 3: return (s128 + 2u) / 3u;
-    case 4: return (s128 + 3u) >> 2;
-    case 5: return (s128 + 4u) / 5u;
-    case 6: return (s128 + 5u) / 6u;
-    case 7: return (s128 + 6u) / 7u;
-    default: return (s128 + 7u) >> 3;
+    case 4: return (s64 + 3u) >> 2;
+    case 5: return (s64 + 4u) / 5u;
+    case 6: return (s64 + 5u) / 6u;
+    case 7: return (s64 + 6u) / 7u;
+    case 8: return (s64 + 7u) >> 3;
+    case 9: return (s64 + 8u) / 9u;
+    case 10: return (s64 + 9u) / 10u;
+    case 11: return (s64 + 10u) / 11u;
+    case 12: return (s64 + 11u) / 12u;
+    case 13: return (s64 + 12u) / 13u;
+    case 14: return (s64 + 13u) / 14u;
+    case 15: return (s64 + 14u) / 15u;
+    default: return (s64 + 15u) >> 4;
   }
 }
 FILTR_HD uint64_t strips_of(uint32_t M, int R) {
-  if (R % 4 != 0 || R < 8 || R > 32) return ((uint64_t)M + 32u * R - 1) / (32u * R);
-  return strips_s128((uint32_t)(((uint64_t)M + 127u) >> 7), R / 4);
+  if (R % 2 != 0 || R < 8 || R > 32) return ((uint64_t)M + 32u * R - 1) / (32u * R);
+  return strips_s64((uint32_t)(((uint64_t)M + 63u) >> 6), R / 2);
 }
 
 // Traceback words of one pair in the int32 tile of R rows per lane.
@@ -101,7 +107,6 @@ struct ShapeTable {
   double coef[SHAPE_TILED];  // per_row x R + per_step
   double fill[SHAPE_TILED];
   int R[SHAPE_TILED];
-  int hidx[SHAPE_TILED];     // R / 4 - 2
   int packed[SHAPE_TILED];
   int elig[SHAPE_TILED];     // shapes the recurrence kind allows, in table order
   int n_elig, n_elig_packed;
@@ -114,7 +119,6 @@ inline ShapeTable make_shape_table(const ShapeCost *costs, const ScoreParams &sp
     t.coef[k] = (double)costs[k].per_row * costs[k].R + costs[k].per_step;
     t.fill[k] = (double)costs[k].fill;
     t.R[k] = costs[k].R;
-    t.hidx[k] = costs[k].R / 4 - 2;
     t.packed[k] = costs[k].packed ? 1 : 0;
     if (costs[k].packed && !pack_ok) continue;
     t.elig[t.n_elig++] = k;
@@ -130,17 +134,14 @@ inline ShapeTable make_shape_table(const ShapeCost *costs, const ScoreParams &sp
 // earlier shape of the table.
 FILTR_HD int choose_shape_p(const ShapeTable &t, bool packable, bool only_packed, uint32_t M,
                             uint32_t N) {
-  const uint32_t s128 = (uint32_t)(((uint64_t)M + 127u) >> 7);
-  double strips[7];  // R = 8, 12, ..., 32
-#pragma unroll
-  for (int d = 2; d <= 8; ++d) strips[d - 2] = (double)strips_s128(s128, d);
+  const uint32_t s64 = (uint32_t)(((uint64_t)M + 63u) >> 6);
   const double Nd = (double)N;
   int best = t.elig[0];
   double bc = 1e300;
   for (int i = 0; i < t.n_elig; ++i) {
     const int k = t.elig[i];
     const bool skip = t.packed[k] ? !packable : only_packed;
-    double c = strips[t.hidx[k]] * (Nd + t.fill[k]) * t.coef[k];
+    double c = (double)strips_s64(s64, t.R[k] / 2) * (Nd + t.fill[k]) * t.coef[k];
     c = skip ? 1e300 : c;
     const bool lt = c < bc;
     best = lt ? k : best;

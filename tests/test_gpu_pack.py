@@ -207,7 +207,7 @@ def test_tune_apply_reproduces_plan(F):
         c2.close()
 
 
-@pytest.mark.parametrize("R", [8, 12, 16, 20, 24, 28, 32])
+@pytest.mark.parametrize("R", list(range(8, 33, 2)))
 @pytest.mark.parametrize("mode", ["global", "local"])
 def test_each_packed_height(F, R, mode):
     """Every packed tile height, forced by a tune table that prices the other
