@@ -200,7 +200,7 @@ filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
  *   max_query_len / max_ref_len: the longest query / reference of the batch;
  *                   the strip buffers are sized by max_ref_len, so the batch
  *                   runs on fewer warps as it grows, and it is rejected with
- *                   FILTR_ERR_UNSUPPORTED beyond 1,048,566 reference residues (or when
+ *                   FILTR_ERR_UNSUPPORTED beyond 2,097,134 reference residues (or when
  *                   scores could reach 2^28); a pair longer than the limits it
  *                   was given gets status FILTR_ST_TOO_WIDE.
  * Results equal filtr_align_batch's (score, end coordinates, status, cells;

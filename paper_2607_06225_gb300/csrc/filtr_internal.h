@@ -20,7 +20,7 @@ namespace filtr {
 constexpr int32_t NEG = -(1 << 29);
 constexpr int32_t NEG_HALF = NEG / 2;
 constexpr int MAX_ALPHA = 20;
-constexpr int FULL_WARPS = 4;  // warps per CTA of the tiled wavefront kernel
+constexpr int FULL_WARPS = 2;  // warps per CTA of the tiled wavefront kernel
 
 // Band limits on d = j - i (Sec. 7.1 prune axis), widened to hold both corners
 // unless the literal +-B band is asked for.

@@ -86,7 +86,7 @@ filtr_status filtr_align_batch_noalloc(const filtr_params *params, uint32_t n_pa
     set_error("filtr_align_batch_noalloc: NULL pointer");
     return FILTR_ERR_INVALID;
   }
-  // the strip buffers must hold at least one 4-warp CTA
+  // the strip buffers must hold at least one CTA's warps
   const uint64_t per_warp = ((uint64_t)max_ref_len + 2) * sizeof(int2);
   const uint64_t max_warps = (NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / per_warp;
   if (max_ref_len == 0 || max_query_len == 0 || max_warps < (uint64_t)FULL_WARPS ||

@@ -67,6 +67,6 @@ def test_rejects_what_it_cannot_hold(F):
     rc = F.lib().filtr_align_batch_noalloc(C.byref(p), 4, *db.ptrs(), 200, 200, out.data_ptr(), None)
     assert rc == F.ERR_UNSUPPORTED
     p = F.make_params(b.subst, **dict(b.scoring, traceback=False))
-    rc = F.lib().filtr_align_batch_noalloc(C.byref(p), 4, *db.ptrs(), 200, 2_000_000,
+    rc = F.lib().filtr_align_batch_noalloc(C.byref(p), 4, *db.ptrs(), 200, 3_000_000,
                                            out.data_ptr(), None)
     assert rc == F.ERR_UNSUPPORTED
