@@ -1,10 +1,11 @@
-"""Python face of the plain C oracle (oracle.c).
+"""Python face of the plain C oracle (oracle.c, search.c).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
 benchmark's CPU-baseline leg; the product path never imports it.
 
-`align(...)` runs one pair; `align_batch(...)` runs many on a thread pool.  Both
-return plain dicts / numpy arrays.  The library is compiled with gcc on first
+`align(...)` runs one pair; `align_batch(...)` runs many on a thread pool;
+`search(...)` / `search_batch(...)` give the edit distance by the search
+traversal.  All return plain dicts / numpy arrays.  The library is compiled with gcc on first
 use (or by `build()`), next to this file.
 """
 from __future__ import annotations
@@ -18,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_SEARCH = os.path.join(_HERE, "search.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
@@ -46,15 +48,28 @@ class Result(C.Structure):
     ]
 
 
+class SearchParams(C.Structure):
+    _fields_ = [("traceback", C.c_int32), ("use_band", C.c_int32), ("band", C.c_int64),
+                ("adapt_min_len", C.c_int64), ("adapt_max_dist", C.c_int64)]
+
+
+class SearchResult(C.Structure):
+    _fields_ = [("distance", C.c_int64), ("cells", C.c_int64), ("n_ops", C.c_int64)]
+
+
+SEARCH_RESULT_DTYPE = np.dtype([("distance", np.int64), ("cells", np.int64), ("n_ops", np.int64)])
+assert SEARCH_RESULT_DTYPE.itemsize == C.sizeof(SearchResult)
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (no CUDA)."""
     with _lock:
         stale = (not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_SEARCH), os.path.getmtime(_HDR)))
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC,
-                                   "-lpthread"])
+                                   _SRC_SEARCH, "-lpthread"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -73,6 +88,12 @@ def lib():
         L.orc_domain.restype = C.c_int64
         L.orc_domain.argtypes = [C.POINTER(Params), C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                  C.c_void_p, C.c_void_p, C.c_int64]
+        L.orc_search.restype = C.c_int
+        L.orc_search.argtypes = [C.POINTER(SearchParams), C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_int64, C.POINTER(SearchResult), C.c_void_p, C.c_int64]
+        L.orc_search_batch.restype = C.c_int
+        L.orc_search_batch.argtypes = [C.POINTER(SearchParams), C.c_int64] + [C.c_void_p] * 6 + [
+            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         _lib = L
     return _lib
 
@@ -183,3 +204,61 @@ def domain(q, r, subst, **kw):
 
 def cigar_str(ops) -> str:
     return "".join(f"{int(o) >> 4}{OP_CHARS[int(o) & 15]}" for o in ops)
+
+
+def make_search_params(traceback=True, band=None, adapt=None):
+    """adapt = (min_len, max_dist) turns WFA-Adapt on."""
+    p = SearchParams()
+    p.traceback = 1 if traceback else 0
+    p.use_band = 0 if band is None else 1
+    p.band = 0 if band is None else int(band)
+    p.adapt_min_len, p.adapt_max_dist = (0, 0) if adapt is None else (int(adapt[0]),
+                                                                      int(adapt[1]))
+    return p
+
+
+def search(q, r, traceback=True, band=None, adapt=None) -> dict:
+    """Edit distance of one pair by the search traversal (Sec. 6.3): distance,
+    wavefront cells evaluated, and the CIGAR when traceback is on."""
+    p = make_search_params(traceback, band, adapt)
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.uint8))
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.uint8))
+    res = SearchResult()
+    cap = int(q.shape[0] + r.shape[0] + 1)
+    ops = np.zeros(cap, dtype=np.uint32)
+    rc = lib().orc_search(C.byref(p), q.ctypes.data, q.shape[0], r.ctypes.data, r.shape[0],
+                          C.byref(res), ops.ctypes.data, cap)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    d = dict(distance=res.distance, cells=res.cells, n_ops=res.n_ops)
+    if traceback:
+        d["cigar"] = ops[: res.n_ops].copy()
+    return d
+
+
+def search_batch(batch, nthreads: int | None = None, traceback=True, band=None, adapt=None):
+    """search() over every pair of a synth.Batch on a thread pool.  Returns
+    (results, ops, ops_off) like align_batch."""
+    p = make_search_params(traceback, band, adapt)
+    n = int(batch.q_len.shape[0])
+    res = np.zeros(n, dtype=SEARCH_RESULT_DTYPE)
+    cap = (batch.q_len.astype(np.uint64) + batch.r_len.astype(np.uint64) + 1)
+    off = np.zeros(n, dtype=np.uint64)
+    if n:
+        off[1:] = np.cumsum(cap[:-1])
+    ops = np.zeros(int(cap.sum()) if (traceback and n) else 1, dtype=np.uint32)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    q = np.ascontiguousarray(batch.q_seq)
+    r = np.ascontiguousarray(batch.r_seq)
+    qo = np.ascontiguousarray(batch.q_off, dtype=np.uint64)
+    ro = np.ascontiguousarray(batch.r_off, dtype=np.uint64)
+    ql = np.ascontiguousarray(batch.q_len, dtype=np.uint32)
+    rl = np.ascontiguousarray(batch.r_len, dtype=np.uint32)
+    rc = lib().orc_search_batch(C.byref(p), n, q.ctypes.data, qo.ctypes.data, ql.ctypes.data,
+                                r.ctypes.data, ro.ctypes.data, rl.ctypes.data, res.ctypes.data,
+                                ops.ctypes.data if traceback else None, off.ctypes.data,
+                                cap.ctypes.data, int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return res, ops, off

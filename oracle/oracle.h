@@ -24,8 +24,18 @@
  *     diag_best(k-1) being the diagonal of antidiagonal k-1's best cell (the
  *     largest H; among equal H the smallest i, i.e. the largest diagonal);
  *   - traceback with fixed tie-breaks, emitted as a SAM/BAM CIGAR.
+ *   - edit distance by the search traversal (Sec. 6.3): the furthest row
+ *     F[s][d] reached on diagonal d = j - i with s edits, from the three shifted
+ *     terms of wavefront s-1 and a greedy run of matches; optionally inside a
+ *     static band (Sec. 7.1 maps the band to d) and with WFA-Adapt trimming
+ *     (Sec. 7.2, 9.3), read as: once a wavefront spans at least min_len
+ *     diagonals, its domain bounds move inwards past every diagonal whose
+ *     remaining distance max(M - i, N - j) exceeds the smallest one on the
+ *     wavefront by more than max_dist.
  * Parity of the tie-break order and of the X-drop domain reading is pinned only
- * by hand-worked examples (the paper does not fix them).
+ * by hand-worked examples (the paper does not fix them); the search's distance is
+ * pinned by the plain edit distance, its CIGAR choice and the WFA-Adapt reading
+ * are not pinned beyond validity (parity unpinned).
  */
 #ifndef FILTR_ORACLE_H
 #define FILTR_ORACLE_H
@@ -84,6 +94,32 @@ int orc_align_batch(const orc_params *p, int64_t n, const uint8_t *q_seq,
  * also a flag per cell, 1 if it was left unpruned.  Returns the cell count. */
 int64_t orc_domain(const orc_params *p, const uint8_t *q, int64_t M, const uint8_t *r,
                    int64_t N, int64_t *cells_ij, uint8_t *alive, int64_t cap);
+
+typedef struct {
+  int32_t traceback;   /* 1: emit the CIGAR */
+  int32_t use_band;    /* 1: diagonals restricted to [min(0,N-M) - band, max(0,N-M) + band] */
+  int64_t band;
+  int64_t adapt_min_len;  /* 0: exact search; else WFA-Adapt from this wavefront width */
+  int64_t adapt_max_dist;
+} orc_search_params;
+
+typedef struct {
+  int64_t distance;   /* edits of the alignment found (the edit distance when exact) */
+  int64_t cells;      /* wavefront entries evaluated: sum over s of the domain's width */
+  int64_t n_ops;      /* CIGAR ops written (or needed, if cap was too small) */
+} orc_search_result;
+
+/* Edit distance of one pair by the search traversal.  ops as in orc_align.
+ * Returns 0, or -1 on invalid arguments / out of memory. */
+int orc_search(const orc_search_params *p, const uint8_t *q, int64_t M, const uint8_t *r,
+               int64_t N, orc_search_result *res, uint32_t *ops, int64_t cap);
+
+/* orc_search over n pairs on nthreads threads (layout as orc_align_batch). */
+int orc_search_batch(const orc_search_params *p, int64_t n, const uint8_t *q_seq,
+                     const uint64_t *q_off, const uint32_t *q_len, const uint8_t *r_seq,
+                     const uint64_t *r_off, const uint32_t *r_len, orc_search_result *res,
+                     uint32_t *ops, const uint64_t *ops_off, const uint64_t *ops_cap,
+                     int nthreads);
 
 #ifdef __cplusplus
 }

@@ -302,6 +302,24 @@ def serve_mix(n_req: int, rate_hz: float, seed: int = 4, median: float = 2000.0,
     return out, psub
 
 
+def edit_pairs(n: int, length: int, div: float, seed: int = 6) -> Batch:
+    """Edit-distance pairs of the search-versus-antidiagonal comparison (Sec. 9.4's
+    synthetic pairs at 1 / 5 / 30% divergence): reference uniform ACGT of
+    `length`; query = reference with `div` divergence split equally into
+    single-base substitutions, insertions and deletions.  The scoring given is
+    unit-cost global alignment (match 0, mismatch -1, linear gap 1), whose
+    score is minus the edit distance."""
+    rng = np.random.default_rng(seed)
+    qs, rs = [], []
+    for _ in range(n):
+        r = rng.integers(0, DNA, size=length).astype(np.uint8)
+        qs.append(mutate(rng, r, div / 3, div / 3, div / 3, None))
+        rs.append(r)
+    unit = np.where(np.eye(DNA, dtype=bool), 0, -1).astype(np.int8)
+    return pack(qs, rs, DNA, unit,
+                dict(mode="global", affine=False, gap_open=0, gap_extend=1, traceback=False), seed)
+
+
 def random_pairs(n: int, mmax: int, nmax: int, alphabet: int, seed: int, mmin: int = 0,
                  nmin: int = 0, related: float = 0.5) -> tuple[list, list]:
     """Small random pairs for parity tests: lengths uniform in [min, max]; with

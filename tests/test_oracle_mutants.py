@@ -41,16 +41,46 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_reject_mutant(name, tmp_path):
-    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
-    a, b = MUTANTS[name]
+SEARCH_MUTANTS = {
+    "search_mismatch_no_step": ("v + 1 + d <= c->N) {\n    best = v + 1;",
+                                "v + 1 + d <= c->N) {\n    best = v;"),
+    "search_insertion_wrong_side": ("wave_get(prev, d + 1, &v)", "wave_get(prev, d - 1, &v)"),
+    "search_deletion_steps_row": ("(which < 0 || v > best)) {\n    best = v;",
+                                  "(which < 0 || v > best)) {\n    best = v + 1;"),
+    "search_domain_frozen_low": ("(w->alo - 1 > dlo) ? w->alo - 1", "(w->alo > dlo) ? w->alo"),
+    "search_target_mirrored": ("const int64_t target = N - M;", "const int64_t target = M - N;"),
+    "search_extend_short": ("while (i < c->M && i + d < c->N", "while (i + 1 < c->M && i + d < c->N"),
+    "search_cells_narrow": ("cells += hi - lo + 1;", "cells += hi - lo;"),
+    "search_band_edge": ("- p->band;\n    const int64_t bhi", "- p->band + 1;\n    const int64_t bhi"),
+    "adapt_non_strict": ("rmin > p->adapt_max_dist))\n        ++alo;",
+                         "rmin >= p->adapt_max_dist))\n        ++alo;"),
+    "adapt_min_remaining": ("return a > b ? a : b;", "return a < b ? a : b;"),
+    "adapt_keeps_unreached": ("while (alo <= ahi && (!w->reached[alo - w->lo] ||",
+                              "while (alo <= ahi && (0 ||"),
+    "walk_insertion_moves_down": ("i = row - 1;\n        d = d + 1;", "i = row - 1;\n        d = d - 1;"),
+}
+
+
+def _run_mutant(src_name, pins, a, b, name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", src_name)).read()
     assert src.count(a) >= 1, "mutation site moved; update the mutant"
     ign = shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*")
     for d in ("oracle", "tests", "synth"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=ign)
-    (tmp_path / "oracle" / "oracle.c").write_text(src.replace(a, b, 1))
+    (tmp_path / "oracle" / src_name).write_text(src.replace(a, b, 1))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py"], capture_output=True, text=True, cwd=tmp_path,
+                        f"tests/{pins}"], capture_output=True, text=True, cwd=tmp_path,
                        timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    a, b = MUTANTS[name]
+    _run_mutant("oracle.c", "test_oracle_pins.py", a, b, name, tmp_path)
+
+
+@pytest.mark.parametrize("name", sorted(SEARCH_MUTANTS))
+def test_search_pins_reject_mutant(name, tmp_path):
+    a, b = SEARCH_MUTANTS[name]
+    _run_mutant("search.c", "test_oracle_search_pins.py", a, b, name, tmp_path)
