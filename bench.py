@@ -70,6 +70,10 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="skip the captured-pipeline (filtr_graph) leg")
     ap.add_argument("--graph-workspace-gb", type=float, default=40.0)
+    ap.add_argument("--no-search", action="store_true",
+                    help="skip the search-versus-antidiagonal edit-distance table")
+    ap.add_argument("--search-only", action="store_true",
+                    help="run only the search-versus-antidiagonal table and print it")
     ap.add_argument("--tune-save", default=None,
                     help="write the autotuned shape costs to this JSON file")
     ap.add_argument("--tune-load", default=None,
@@ -427,6 +431,94 @@ def graph_bench(F, ctx, params, batch, db, res_ref, cells, steps, warmup, stream
         g.close()
 
 
+# Sec. 9.4's comparison of the search traversal with the antidiagonal one for
+# edit distance: (length, pairs per batch) and divergences; the paper's CPU
+# speedups (search over antidiagonal, its Table) for context.
+SEARCH_TABLE = ((500, 32768), (2000, 16384), (4000, 8192))
+SEARCH_DIVS = (0.01, 0.05, 0.30)
+PAPER_SEARCH_SPEEDUP = {(500, 0.01): 97, (2000, 0.01): 98, (4000, 0.01): 300,
+                        (500, 0.05): 27, (2000, 0.05): 14, (4000, 0.05): 23,
+                        (500, 0.30): 0.45, (2000, 0.30): 0.45, (4000, 0.30): 0.72}
+
+
+def search_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True):
+    """Edit distance of one batch per (length, divergence) through the search
+    traversal (filtr_search_batch, score only) and through the antidiagonal
+    kernels (filtr_align_batch with unit costs, whose score is minus the edit
+    distance): CUDA events on the stream, L2 flushed between steps, distances
+    checked equal.  With cpu, the oracle's search on a few pairs (one thread)."""
+    import torch
+
+    import synth
+
+    def timed(fn):
+        for _ in range(max(warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_((k + 3) & 0xFF)
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sorted(a.elapsed_time(b) for a, b in ev)[steps // 2]
+
+    sp = F.make_search_params(traceback=False)
+    tuned = False
+    rows = []
+    for length, n in SEARCH_TABLE:
+        for div in SEARCH_DIVS:
+            b = synth.edit_pairs(n, length, div, seed=6)
+            db = F.DeviceBatch(b, dev)
+            out_s, _ = F.alloc_outputs(db.n, 0, dev)
+            out_a, _ = F.alloc_outputs(db.n, 0, dev)
+            ap = F.make_params(b.subst, **b.scoring)
+            if not tuned:  # setup, untimed: the antidiagonal kernels' shape costs
+                ctx.autotune(ap)
+                tuned = True
+
+            def sr():
+                rc = ctx.search_batch_ptr(sp, db.n, *db.ptrs(), out_s.data_ptr(), None, 0,
+                                          stream=stream.cuda_stream)
+                if rc != 0:
+                    raise F.FiltrError(rc, F.last_error())
+
+            def ad():
+                rc = ctx.align_batch_ptr(ap, db.n, *db.ptrs(), out_a.data_ptr(), None, 0,
+                                         stream=stream.cuda_stream)
+                if rc != 0:
+                    raise F.FiltrError(rc, F.last_error())
+
+            t_sr, t_ad = timed(sr), timed(ad)
+            rs, ra = F.results_to_numpy(out_s, db.n), F.results_to_numpy(out_a, db.n)
+            assert np.array_equal(rs["score"], ra["score"]), "search and antidiagonal disagree"
+            full = float((b.q_len.astype(np.float64) * b.r_len).sum())
+            row = {"length": length, "divergence": div, "pairs": n,
+                   "search_ms": t_sr, "antidiagonal_ms": t_ad, "speedup": t_ad / t_sr,
+                   "paper_cpu_speedup": PAPER_SEARCH_SPEEDUP[(length, div)],
+                   "search_pairs_per_s": n / (t_sr * 1e-3),
+                   "search_gcups_equiv": full / (t_sr * 1e-3) / 1e9,
+                   "antidiagonal_gcups": full / (t_ad * 1e-3) / 1e9,
+                   "mean_distance": float(-rs["score"].mean()),
+                   "wavefront_cells_per_pair": float(rs["cells"].mean())}
+            if cpu:
+                import oracle
+
+                sub = synth.pack([b.pair(p)[0] for p in range(4)], [b.pair(p)[1] for p in range(4)],
+                                 4, b.subst)
+                t0 = time.perf_counter()
+                ores, _, _ = oracle.search_batch(sub, nthreads=1, traceback=False)
+                row["oracle_ms_per_pair_1core"] = (time.perf_counter() - t0) * 1e3 / 4
+                assert np.array_equal(-ores["distance"], rs["score"][:4])
+            rows.append(row)
+            del db, out_s, out_a
+    return {"call": "filtr_search_batch (score only) vs filtr_align_batch (unit-cost global, "
+                    "score only), same pairs",
+            "l2": "flushed between timed steps", "steps": steps, "rows": rows}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -473,6 +565,13 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     is_long = wl == "long-pair-1m"
     tb_on = bool(sc.get("traceback"))
+    if args.search_only:
+        if rank == 0:
+            tab = search_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
+                               cpu=not args.no_cpu_baseline)
+            print(json.dumps({"search_table": tab}), flush=True)
+        ctx.close()
+        return
 
     def step():
         if is_long:
@@ -588,6 +687,9 @@ def main():
             line["graph"] = graph_bench(F, ctx, params, batch, db, res, cells, args.steps,
                                         args.warmup, stream, flush, dev, tb_on,
                                         args.graph_workspace_gb)
+        if not args.no_search and wl == "protein-sw-100k":
+            line["search"] = search_table(F, ctx, 3, 1, stream, flush, dev,
+                                          cpu=not args.no_cpu_baseline)
         if not args.no_serve and wl == "protein-sw-100k":
             line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
         if not args.no_cpu_baseline and not is_long:

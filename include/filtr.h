@@ -254,6 +254,62 @@ typedef struct {
 filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);
 
+/* ---- search traversal: edit distance score-major (Sec. 6.3) ----------------
+ * The edit-distance recurrence F(i,j) = min(F(i-1,j-1) + [q_i != r_j],
+ * F(i-1,j) + 1, F(i,j-1) + 1) iterated by cost instead of position: wavefront
+ * s holds, for each diagonal d = j - i of its domain, the furthest row that s
+ * edits reach, from the mismatch, insertion and deletion terms of wavefront s-1
+ * (diagonals d, d+1, d-1) followed by a free run of matches; each domain is one
+ * diagonal wider on each side than the last, clipped to the matrix, and the
+ * search ends at the first s whose wavefront reaches (M, N).  Exact: s is the
+ * edit distance.  Options (Sec. 7):
+ *   band           : >= 0 restricts the diagonals to
+ *                    [min(0, N-M) - band, max(0, N-M) + band] (the band of
+ *                    filtr_align_batch, mapped to d as Sec. 7.1 describes);
+ *                    < 0: no band.  The result is the best path inside the band.
+ *   adapt_min_len  : 0 = exact.  > 0 turns on WFA-Adapt (Sec. 7.2, 9.3): once a
+ *   adapt_max_dist   wavefront spans at least adapt_min_len diagonals, its
+ *                    bounds move inwards past unreached diagonals and past those
+ *                    whose remaining distance max(M - i, N - j) exceeds the
+ *                    wavefront's smallest by more than adapt_max_dist; only the
+ *                    diagonals left feed the next score.  A heuristic: the
+ *                    distance found can exceed the edit distance, its CIGAR
+ *                    always costs exactly that distance.
+ *   traceback      : 1 = CIGAR ('=' 'X' 'I' 'D').  Walking back from (M, N),
+ *                    each score level takes the first of mismatch, insertion,
+ *                    deletion that gives its value.
+ */
+typedef struct {
+  int32_t traceback;
+  int32_t band;
+  int32_t adapt_min_len;
+  int32_t adapt_max_dist;
+} filtr_search_params;
+
+/* Edit distance of n_pairs independent pairs by the search traversal.
+ *   q_seq / r_seq / offsets / lengths : DEVICE, as filtr_align_batch; codes are
+ *       compared for equality only (any byte value)
+ *   out   : DEVICE, n_pairs filtr_result: score = minus the distance found (the
+ *           unit-cost global alignment score: match 0, mismatch -1, gap 1 per
+ *           residue), q_begin = r_begin = 0, q_end = M, r_end = N, status
+ *           FILTR_ST_OK, cells = wavefront entries evaluated (the sum over scores
+ *           of the domain's width)
+ *   cigar : DEVICE, cigar_cap ops (may be NULL without traceback); CIGARs in
+ *           pair order, FILTR_ERR_CIGAR_CAP as filtr_align_batch.
+ * The call reads the lengths back once (a short synchronisation on `stream`);
+ * with traceback it also reads back each pair's wavefront storage (a second
+ * synchronisation) and recomputes the pairs with every wavefront kept, in
+ * waves that fit the workspace.  FILTR_ERR_INVALID for NULL pointers or
+ * negative adapt thresholds; FILTR_ERR_UNSUPPORTED when a pair has
+ * M + N > FILTR_SEARCH_MAX_LEN (its sequences are staged in shared memory);
+ * FILTR_ERR_NOMEM when one pair's wavefronts do not fit the workspace. */
+#define FILTR_SEARCH_MAX_LEN 180000u
+filtr_status filtr_search_batch(filtr_ctx *ctx, const filtr_search_params *params,
+                                uint32_t n_pairs, const uint8_t *q_seq, const uint64_t *q_off,
+                                const uint32_t *q_len, const uint8_t *r_seq,
+                                const uint64_t *r_off, const uint32_t *r_len, filtr_result *out,
+                                uint32_t *cigar, uint64_t cigar_cap, void *stream);
+
 /* ---- Captured batch pipeline (CUDA graph) --------------------------------
  * The batched path of filtr_align_batch for tiled batches (full matrix or
  * static band, no X-drop), captured once as a CUDA graph and replayed per batch

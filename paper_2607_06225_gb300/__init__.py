@@ -13,11 +13,11 @@ from ._lib import (ALPHA_DNA, ALPHA_PROTEIN, ERR_CIGAR_CAP, ERR_INVALID, ERR_NOM
                    LOCAL, OK, PREC_AUTO, PREC_I16X2, PREC_I32, PRUNE_BAND, PRUNE_BAND_LITERAL,
                    PRUNE_XDROP, PRUNE_ZDROP, RESULT_DTYPE, ST_DROPPED, ST_EMPTY, ST_OK, ST_TOO_WIDE,
                    ST_UNREACHABLE, TUNE_SHAPES, XDROP_INF, Context, FiltrError, Graph, Params,
-                   check, last_error, lib,
-                   make_params)
+                   SearchParams, check, last_error, lib, make_params, make_search_params)
 
 __all__ = ["Context", "FiltrError", "Params", "make_params", "DeviceBatch", "align_batch",
-           "align_batch_host", "align_long", "RESULT_DTYPE", "lib", "last_error"]
+           "align_batch_host", "align_long", "RESULT_DTYPE", "lib", "last_error", "SearchParams",
+           "make_search_params", "search_batch"]
 
 
 class DeviceBatch:
@@ -71,6 +71,28 @@ def align_batch(ctx: Context, params: Params, batch, stream=None, plain: bool = 
                              stream=s.cuda_stream, plain=plain)
     if rc not in (OK, ERR_CIGAR_CAP) and raise_on_error:
         check(rc, "filtr_align_batch")
+    s.synchronize()
+    res = results_to_numpy(out_t, db.n)
+    cig = cig_t.cpu().numpy().view(np.uint32).copy() if params.traceback else np.zeros(0, np.uint32)
+    return res, cig, rc
+
+
+def search_batch(ctx: Context, params: SearchParams, batch, stream=None,
+                 cigar_cap: int | None = None, device="cuda", raise_on_error=True):
+    """Edit distance of every pair of a synth.Batch or DeviceBatch by the search
+    traversal (filtr_search_batch).  Returns (results, cigar ops, status code);
+    results' score is minus the distance found."""
+    import torch
+
+    db = batch if isinstance(batch, DeviceBatch) else DeviceBatch(batch, device)
+    cap = db.cigar_upper + db.n if cigar_cap is None else int(cigar_cap)
+    out_t, cig_t = alloc_outputs(db.n, cap, device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = ctx.search_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(),
+                              cig_t.data_ptr() if params.traceback else None,
+                              cap if params.traceback else 0, stream=s.cuda_stream)
+    if rc not in (OK, ERR_CIGAR_CAP) and raise_on_error:
+        check(rc, "filtr_search_batch")
     s.synchronize()
     res = results_to_numpy(out_t, db.n)
     cig = cig_t.cpu().numpy().view(np.uint32).copy() if params.traceback else np.zeros(0, np.uint32)

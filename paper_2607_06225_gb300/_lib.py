@@ -46,6 +46,22 @@ class Result(C.Structure):
                 ("cells", C.c_uint64)]
 
 
+class SearchParams(C.Structure):
+    _fields_ = [("traceback", C.c_int32), ("band", C.c_int32), ("adapt_min_len", C.c_int32),
+                ("adapt_max_dist", C.c_int32)]
+
+
+def make_search_params(traceback=True, band=None, adapt=None) -> SearchParams:
+    """filtr_search_params: band=None for none; adapt=(min_len, max_dist) turns
+    WFA-Adapt on."""
+    p = SearchParams()
+    p.traceback = 1 if traceback else 0
+    p.band = -1 if band is None else int(band)
+    p.adapt_min_len, p.adapt_max_dist = (0, 0) if adapt is None else (int(adapt[0]),
+                                                                      int(adapt[1]))
+    return p
+
+
 class Stats(C.Structure):
     _fields_ = [("ms_validate", C.c_double), ("ms_forward", C.c_double), ("ms_walk", C.c_double),
                 ("ms_place", C.c_double), ("ms_total", C.c_double), ("launches", C.c_uint32),
@@ -97,6 +113,9 @@ def lib():
         L.filtr_pack.argtypes = [_P, C.c_uint64, C.c_int32, _P, _P, _P]
         batch_args = [C.c_void_p, C.POINTER(Params), C.c_uint32, _P, _P, _P, _P, _P, _P, _P, _P,
                       C.c_uint64]
+        L.filtr_search_batch.restype = i32
+        L.filtr_search_batch.argtypes = [C.c_void_p, C.POINTER(SearchParams), C.c_uint32, _P, _P,
+                                         _P, _P, _P, _P, _P, _P, C.c_uint64, C.c_void_p]
         for name in ("filtr_align_batch", "filtr_align_batch_plain"):
             f = getattr(L, name)
             f.restype = i32
@@ -230,6 +249,12 @@ class Context:
         f = lib().filtr_align_batch_plain if plain else lib().filtr_align_batch
         return f(self.handle, C.byref(params), int(n), q_seq, q_off, q_len, r_seq, r_off, r_len,
                  out, cigar, int(cigar_cap), C.c_void_p(int(stream)) if stream else None)
+
+    def search_batch_ptr(self, params: SearchParams, n: int, q_seq, q_off, q_len, r_seq, r_off,
+                         r_len, out, cigar, cigar_cap: int, stream: int = 0) -> int:
+        return lib().filtr_search_batch(self.handle, C.byref(params), int(n), q_seq, q_off, q_len,
+                                        r_seq, r_off, r_len, out, cigar, int(cigar_cap),
+                                        C.c_void_p(int(stream)) if stream else None)
 
     def align_batch_host_ptr(self, params: Params, n: int, q_seq, q_off, q_len, r_seq, r_off,
                              r_len, out, cigar, cigar_cap: int) -> int:

@@ -109,3 +109,15 @@ def test_graph_rejects_on_host(L):
                                   None) == L.ERR_INVALID
     assert lib.filtr_graph_status(None) == L.ERR_INVALID
     assert lib.filtr_graph_destroy(None) == L.OK
+
+
+def test_search_rejects_on_host(L):
+    """filtr_search_batch argument checks that need no device."""
+    lib = L.lib()
+    p = L.make_search_params(traceback=True)
+    assert lib.filtr_search_batch(None, C.byref(p), 1, None, None, None, None, None, None, None,
+                                  None, 0, None) == L.ERR_INVALID
+    assert "NULL" in L.last_error()
+    assert p.band == -1 and (p.adapt_min_len, p.adapt_max_dist) == (0, 0)
+    q = L.make_search_params(traceback=False, band=7, adapt=(100, 20))
+    assert (q.traceback, q.band, q.adapt_min_len, q.adapt_max_dist) == (0, 7, 100, 20)
