@@ -571,5 +571,5 @@ extern "C" filtr_status filtr_search_batch(filtr_ctx *ctx, const filtr_search_pa
   Ctx *c = reinterpret_cast<Ctx *>(ctx);
   BatchDev b{q_seq, r_seq, q_off, r_off, q_len, r_len};
   return search_impl(c, params, n_pairs, b, out, cigar, cigar_cap,
-                     stream ? static_cast<cudaStream_t>(stream) : c->own_stream);
+                     static_cast<cudaStream_t>(stream));  // NULL: the default stream
 }
