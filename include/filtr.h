@@ -288,7 +288,9 @@ typedef struct {
 
 /* Edit distance of n_pairs independent pairs by the search traversal.
  *   q_seq / r_seq / offsets / lengths : DEVICE, as filtr_align_batch; codes are
- *       compared for equality only (any byte value)
+ *       compared for equality only (any byte value).  Each sequence is loaded
+ *       in whole 16-byte-aligned blocks, so up to 15 bytes on either side of it
+ *       are read (never outside the 16-byte blocks holding its ends).
  *   out   : DEVICE, n_pairs filtr_result: score = minus the distance found (the
  *           unit-cost global alignment score: match 0, mismatch -1, gap 1 per
  *           residue), q_begin = r_begin = 0, q_end = M, r_end = N, status

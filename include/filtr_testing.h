@@ -42,6 +42,12 @@ filtr_status filtr_test_set_first_width(filtr_ctx *ctx, int32_t warps);
  * one wave still fall back to the host).  Results do not depend on it. */
 filtr_status filtr_test_set_device_plan(filtr_ctx *ctx, int32_t mode);
 
+/* Entries of each per-warp shared-memory wavefront ring of filtr_search_batch's
+ * score pass (a power of two from 32 to 4096; 0 restores the default).
+ * Wavefronts wider than the ring continue in global memory, so results do not
+ * depend on it; it trades shared memory (occupancy) against load latency. */
+filtr_status filtr_test_set_search_ring(filtr_ctx *ctx, int32_t entries);
+
 #ifdef __cplusplus
 }
 #endif

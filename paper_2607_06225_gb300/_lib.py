@@ -149,6 +149,8 @@ def lib():
         L.filtr_test_set_first_width.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_test_set_device_plan.restype = i32
         L.filtr_test_set_device_plan.argtypes = [C.c_void_p, C.c_int32]
+        L.filtr_test_set_search_ring.restype = i32
+        L.filtr_test_set_search_ring.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_graph_create.restype = i32
         L.filtr_graph_create.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32,
                                          C.c_size_t, C.POINTER(C.c_void_p)]

@@ -33,6 +33,7 @@ struct Ctx {
   double last_host_wait_ms = 0, last_host_plan_ms = 0;
   Plan plan;                       // the last call's plan; its buffers are reused
   int dev_plan_mode = 0;           // 0: device planner by batch size, 1: never, 2: always
+  int search_ring = 0;             // search score pass: shared-memory ring entries, 0 default
   bool last_dev_plan = false;      // the last call was planned on the device
   std::vector<uint32_t> h_ql, h_rl;  // the last call's lengths (host copies)
   int last_waves = 0;

@@ -28,6 +28,7 @@
 #include <cstring>
 #include <vector>
 
+#include "../../include/filtr_testing.h"
 #include "filtr_ctx.h"
 
 namespace filtr {
@@ -36,6 +37,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int UNREACHED = -1;
 constexpr uint32_t OP_I = 1, OP_D = 2, OP_EQ = 7, OP_X = 8;
+constexpr int SEARCH_CHUNKS = 4;  // chunks of 32 diagonals a warp has in flight per iteration
 
 struct SearchArgs {
   BatchDev b;
@@ -51,6 +53,7 @@ struct SearchArgs {
   uint32_t *stage;            // traceback pass: reversed CIGAR ops, per pair id
   const uint64_t *stage_off;
   uint32_t q_words, r_words;  // shared-memory staging per warp (32-bit words)
+  uint32_t ring_c;            // score pass: entries of each shared-memory ring (power of two)
   int band;                   // < 0: none
   int adapt_min, adapt_max;   // adapt_min == 0: exact
 };
@@ -61,41 +64,74 @@ __device__ __forceinline__ uint32_t load4(const uint32_t *w, int i) {
   return __funnelshift_r(a, b, (i & 3) * 8);
 }
 
+// A sequence staged in shared memory: residue i at byte ph + i of w.
+struct Staged {
+  const uint32_t *w;
+  int ph;
+};
+
 // The free transitions: row reached from row i on diagonal d by matches.
-__device__ __forceinline__ int extend(const uint32_t *sq, const uint32_t *sr, int i, int d,
-                                      int M, int N) {
+__device__ __forceinline__ int extend(const Staged &q, const Staged &r, int i, int d, int M,
+                                      int N) {
   for (;;) {
     const int rem = min(M - i, N - i - d);
     if (rem <= 0) return i;
-    uint32_t x = load4(sq, i) ^ load4(sr, i + d);
+    uint32_t x = load4(q.w, q.ph + i) ^ load4(r.w, r.ph + i + d);
     if (rem < 4) x |= 0xffffffffu << (8 * rem);  // residues past an end never match
     if (x) return i + ((__ffs(x) - 1) >> 3);
     i += 4;
   }
 }
 
-// Largest term of F[s][d] from the previous wavefront pv (values at pv[d - pbase],
-// alive diagonals [palo, pahi]); UNREACHED when none exists.  *which: 0 mismatch,
-// 1 insertion, 2 deletion (the first in that order on ties).
-__device__ __forceinline__ int terms(const int *pv, int pbase, int palo, int pahi, int d, int M,
-                                     int N, int *which) {
+// Copy the 16-byte blocks that hold g[0, len) into dst (16-byte aligned) with
+// 16-byte loads; returns the byte of dst that holds g[0].  The blocks lie
+// within g's own 16-byte-aligned span, so no load crosses a page.
+__device__ __forceinline__ int stage_seq(const uint8_t *g, int len, uint32_t *dst, int lane) {
+  const uintptr_t ga = reinterpret_cast<uintptr_t>(g);
+  const int ph = (int)(ga & 15u);
+  const uint4 *src = reinterpret_cast<const uint4 *>(ga - (uintptr_t)ph);
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+  const int nblk = len > 0 ? (ph + len + 15) >> 4 : 0;
+  for (int k = lane; k < nblk; k += 32) d4[k] = __ldg(src + k);
+  return ph;
+}
+
+// Where a wavefront's values live: level s in b0 (s even) or b1 (s odd), the
+// value of diagonal d at index (d + off) & mask -- a power-of-two ring in shared
+// memory (off 0, mask C - 1: two's complement wraps negative d) or a buffer of
+// M + N + 1 entries in global memory (off M, mask all ones).
+struct Wf {
+  int *b0, *b1;
+  int off;
+  uint32_t mask;
+};
+__device__ __forceinline__ int at(int d, int off, uint32_t mask) {
+  return (int)((uint32_t)(d + off) & mask);
+}
+__device__ __forceinline__ int *level_buf(const Wf &w, int s) { return (s & 1) ? w.b1 : w.b0; }
+
+// Largest term of F[s][d] from the previous wavefront pv (alive diagonals
+// [palo, pahi]); UNREACHED when none exists.  *which: 0 mismatch, 1 insertion,
+// 2 deletion (the first in that order on ties).
+__device__ __forceinline__ int terms(const int *pv, int off, uint32_t mask, int palo, int pahi,
+                                     int d, int M, int N, int *which) {
   int best = UNREACHED, w = -1;
   if (d >= palo && d <= pahi) {
-    const int v = pv[d - pbase];
+    const int v = pv[at(d, off, mask)];
     if (v >= 0 && v + 1 <= M && v + 1 + d <= N) {
       best = v + 1;
       w = 0;
     }
   }
   if (d + 1 >= palo && d + 1 <= pahi) {
-    const int v = pv[d + 1 - pbase];
+    const int v = pv[at(d + 1, off, mask)];
     if (v >= 0 && v + 1 <= M && v + 1 > best) {
       best = v + 1;
       w = 1;
     }
   }
   if (d - 1 >= palo && d - 1 <= pahi) {
-    const int v = pv[d - 1 - pbase];
+    const int v = pv[at(d - 1, off, mask)];
     if (v >= 0 && v + d <= N && v > best) {
       best = v;
       w = 2;
@@ -103,6 +139,36 @@ __device__ __forceinline__ int terms(const int *pv, int pbase, int palo, int pah
   }
   *which = w;
   return best;
+}
+
+// WFA-Adapt: the diagonals of [lo, hi] that survive -- reached, and remaining
+// distance max(M - i, N - j) within amax of the wavefront's smallest; the
+// bounds move inwards to the outermost survivors.
+__device__ __forceinline__ void adapt_bounds(const int *cv, int off, uint32_t mask, int lo, int hi,
+                                             int M, int N, int amax, int lane, int *alo,
+                                             int *ahi) {
+  int rmin = INT_MAX;
+  for (int d0 = lo; d0 <= hi; d0 += 32) {
+    const int d = d0 + lane;
+    if (d <= hi) {
+      const int f = cv[at(d, off, mask)];
+      if (f >= 0) rmin = min(rmin, max(M - f, N - f - d));
+    }
+  }
+  rmin = __reduce_min_sync(FULL, rmin);
+  int qlo = INT_MAX, qhi = INT_MIN;
+  for (int d0 = lo; d0 <= hi; d0 += 32) {
+    const int d = d0 + lane;
+    if (d <= hi) {
+      const int f = cv[at(d, off, mask)];
+      if (f >= 0 && max(M - f, N - f - d) - rmin <= amax) {
+        qlo = min(qlo, d);
+        qhi = max(qhi, d);
+      }
+    }
+  }
+  *alo = __reduce_min_sync(FULL, qlo);
+  *ahi = __reduce_max_sync(FULL, qhi);
 }
 
 // Run-length ops, written last op first.
@@ -125,14 +191,114 @@ struct RevEmitter {
   }
 };
 
-template <bool TB>
-__global__ void __launch_bounds__(128) k_search(const SearchArgs a) {
-  extern __shared__ uint32_t smem[];
+// One pair's shape, shared by both passes.
+struct PairView {
+  int M, N, dlo, dhi, target;
+  Staged q, r;
+};
+
+// Stage the pair's sequences in shared memory and set up its domain limits.
+__device__ __forceinline__ PairView stage_pair(const SearchArgs &a, uint32_t p, uint32_t *sq,
+                                               uint32_t *sr, int lane) {
+  PairView v;
+  v.M = (int)a.b.q_len[p];
+  v.N = (int)a.b.r_len[p];
+  v.q = Staged{sq, stage_seq(a.b.q_seq + a.b.q_off[p], v.M, sq, lane)};
+  v.r = Staged{sr, stage_seq(a.b.r_seq + a.b.r_off[p], v.N, sr, lane)};
+  __syncwarp();
+  v.dlo = -v.M;
+  v.dhi = v.N;
+  if (a.band >= 0) {
+    v.dlo = max(v.dlo, min(0, v.N - v.M) - a.band);
+    v.dhi = min(v.dhi, max(0, v.N - v.M) + a.band);
+  }
+  v.target = v.N - v.M;
+  return v;
+}
+
+// Progress of one pair's search.
+struct Lev {
+  int lo, hi, s;
+  uint64_t cells;
+  int state;  // 0 running, 1 reached (M, N), 2 gave up (not expected)
+};
+
+// Score levels from L.s on, until (M, N) is reached or -- in a shared-memory
+// ring of C entries -- the next wavefront would not fit (state stays 0).
+template <bool SMEM, int CH>
+__device__ __forceinline__ void levels(Lev &L, const Wf &w, int C, const PairView &v, int amin,
+                                       int amax, int lane) {
+  const int M = v.M, N = v.N;
+  for (;;) {
+    const int *cv = level_buf(w, L.s);
+    bool done = false;
+    if (lane == 0 && v.target >= L.lo && v.target <= L.hi)
+      done = cv[at(v.target, w.off, w.mask)] >= M;
+    done = __shfl_sync(FULL, done, 0);
+    if (done) {
+      L.state = 1;
+      return;
+    }
+    int alo = L.lo, ahi = L.hi;
+    if (amin > 0 && L.hi - L.lo + 1 >= amin)
+      adapt_bounds(cv, w.off, w.mask, L.lo, L.hi, M, N, amax, lane, &alo, &ahi);
+    if (L.s >= M + N + 1 || alo > ahi) {  // the leading diagonal always survives
+      L.state = 2;
+      return;
+    }
+    const int nlo = max(alo - 1, v.dlo), nhi = min(ahi + 1, v.dhi);
+    if (SMEM && nhi - nlo + 1 > C) return;
+    int *nv = level_buf(w, L.s + 1);
+    // CH chunks of 32 diagonals per iteration: one load per diagonal of the
+    // previous wavefront (alive diagonals only), the neighbours d - 1 and d + 1
+    // by shuffles, the chunk edges from the neighbouring chunk or one load
+    for (int d0 = nlo; d0 <= nhi; d0 += 32 * CH) {
+      int vc[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int d = d0 + 32 * u + lane;
+        vc[u] = (d >= alo && d <= ahi) ? cv[at(d, w.off, w.mask)] : UNREACHED;
+      }
+      const int dl = d0 - 1, dr = d0 + 32 * CH;
+      const int el = (lane == 0 && dl >= alo && dl <= ahi) ? cv[at(dl, w.off, w.mask)] : UNREACHED;
+      const int er = (lane == 31 && dr >= alo && dr <= ahi) ? cv[at(dr, w.off, w.mask)] : UNREACHED;
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int d = d0 + 32 * u + lane;
+        const int up = __shfl_up_sync(FULL, vc[u], 1);
+        const int dn = __shfl_down_sync(FULL, vc[u], 1);
+        const int prev_last = __shfl_sync(FULL, u > 0 ? vc[u > 0 ? u - 1 : 0] : el, 31);
+        const int next_first = __shfl_sync(FULL, u + 1 < CH ? vc[u + 1 < CH ? u + 1 : 0] : er, 0);
+        const int vl = lane == 0 ? (u > 0 ? prev_last : el) : up;     // F[s][d - 1]
+        const int vr = lane == 31 ? (u + 1 < CH ? next_first : er) : dn;  // F[s][d + 1]
+        int row = UNREACHED;
+        if (vc[u] >= 0 && vc[u] + 1 <= M && vc[u] + 1 + d <= N) row = vc[u] + 1;  // mismatch
+        if (vr >= 0 && vr + 1 <= M && vr + 1 > row) row = vr + 1;                // insertion
+        if (vl >= 0 && vl + d <= N && vl > row) row = vl;                        // deletion
+        if (d <= nhi) nv[at(d, w.off, w.mask)] = row >= 0 ? extend(v.q, v.r, row, d, M, N) : UNREACHED;
+      }
+    }
+    __syncwarp();
+    L.cells += (uint64_t)(nhi - nlo + 1);
+    L.lo = nlo;
+    L.hi = nhi;
+    ++L.s;
+  }
+}
+
+// Score pass: distance and wavefront cells of every pair, and the words its
+// traceback pass would store.  Per warp in shared memory: the two sequences,
+// then two rings of ring_c entries; a pair whose wavefront outgrows them moves
+// to the warp's buffers in global memory.
+__global__ void __launch_bounds__(128) k_search_score(const SearchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint32_t *sq = smem + (size_t)wib * (a.q_words + a.r_words);
+  uint32_t *sq = smem + (size_t)wib * (a.q_words + a.r_words + 2 * a.ring_c);
   uint32_t *sr = sq + a.q_words;
+  int *ra = reinterpret_cast<int *>(sr + a.r_words), *rb = ra + a.ring_c;
   const uint64_t slot = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  int *ring = TB ? nullptr : a.ring + slot * 2 * a.ring_half;
+  int *g = a.ring + slot * 2 * a.ring_half;
+  const Wf ws{ra, rb, 0, a.ring_c - 1u};
 
   for (;;) {
     uint32_t t = 0;
@@ -140,135 +306,119 @@ __global__ void __launch_bounds__(128) k_search(const SearchArgs a) {
     t = __shfl_sync(FULL, t, 0);
     if (t >= a.n) return;
     const uint32_t p = a.order ? a.order[t] : t;
-    if (TB && a.out[p].status != FILTR_ST_OK) {  // the score pass gave up on it (not expected)
+    const PairView v = stage_pair(a, p, sq, sr, lane);
+    // score 0: the origin and its run of matches
+    if (lane == 0) ra[at(0, ws.off, ws.mask)] = extend(v.q, v.r, 0, 0, v.M, v.N);
+    __syncwarp();
+    Lev L{0, 0, 0, 1ull, 0};
+    levels<true, SEARCH_CHUNKS>(L, ws, (int)a.ring_c, v, a.adapt_min, a.adapt_max, lane);
+    if (L.state == 0) {  // level L.s to global memory, then on from there
+      const Wf wg{g, g + a.ring_half, v.M, 0xffffffffu};
+      const int *src = level_buf(ws, L.s);
+      int *dst = level_buf(wg, L.s);
+      for (int d = L.lo + lane; d <= L.hi; d += 32)
+        dst[at(d, wg.off, wg.mask)] = src[at(d, ws.off, ws.mask)];
+      __syncwarp();
+      levels<false, SEARCH_CHUNKS>(L, wg, 0, v, a.adapt_min, a.adapt_max, lane);
+    }
+    if (lane == 0) {
+      const bool ok = L.state == 1;
+      filtr_result r;
+      r.score = ok ? -L.s : 0;
+      r.q_begin = 0;
+      r.q_end = v.M;
+      r.r_begin = 0;
+      r.r_end = v.N;
+      r.status = ok ? FILTR_ST_OK : FILTR_ST_TOO_WIDE;
+      r.cigar_len = 0;
+      r.reserved = 0;
+      r.cigar_off = 0;
+      r.cells = L.cells;
+      a.out[p] = r;
+      if (a.need) a.need[p] = ok ? 4ull * (uint64_t)(L.s + 1) + L.cells : 0ull;
+    }
+    __syncwarp();
+  }
+}
+
+// Traceback pass: the same levels again, every wavefront kept in the pair's
+// store (per score: lo, hi and the alive bounds, then the values), then lane 0
+// walks back from (M, N).
+__global__ void __launch_bounds__(128) k_search_tb(const SearchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t *sq = smem + (size_t)wib * (a.q_words + a.r_words);
+  uint32_t *sr = sq + a.q_words;
+
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(FULL, t, 0);
+    if (t >= a.n) return;
+    const uint32_t p = a.order ? a.order[t] : t;
+    if (a.out[p].status != FILTR_ST_OK) {  // the score pass gave up on it (not expected)
       if (lane == 0) a.out[p].cigar_len = 0;
       continue;
     }
-    const int M = (int)a.b.q_len[p], N = (int)a.b.r_len[p];
-    const uint8_t *gq = a.b.q_seq + a.b.q_off[p], *gr = a.b.r_seq + a.b.r_off[p];
-    uint8_t *sq8 = reinterpret_cast<uint8_t *>(sq), *sr8 = reinterpret_cast<uint8_t *>(sr);
-    for (int x = lane; x < M; x += 32) sq8[x] = gq[x];
-    for (int x = lane; x < N; x += 32) sr8[x] = gr[x];
-    __syncwarp();
-
-    int dlo = -M, dhi = N;
-    if (a.band >= 0) {
-      dlo = max(dlo, min(0, N - M) - a.band);
-      dhi = min(dhi, max(0, N - M) + a.band);
-    }
-    const int target = N - M;
-    int S = 0;
-    if (TB) S = -a.out[p].score;
-    int *meta = TB ? a.arena + a.arena_off[p] : nullptr;  // per score: lo, hi, alo, ahi
-    int *waves = TB ? meta + 4 * (S + 1) : nullptr;
-
-    // score 0: the origin and its run of matches
+    const PairView v = stage_pair(a, p, sq, sr, lane);
+    const int M = v.M, N = v.N;
+    const int S = -a.out[p].score;
+    int *meta = a.arena + a.arena_off[p];  // per score: lo, hi, alo, ahi
+    int *waves = meta + 4 * (S + 1);
     int lo = 0, hi = 0;
-    int *cv = TB ? waves : ring;
-    int cbase = TB ? 0 : -M;
-    uint64_t woff = 0, cells = 1;
-    {
-      const int f = lane == 0 ? extend(sq, sr, 0, 0, M, N) : 0;
-      if (lane == 0) cv[0 - cbase] = f;
-    }
+    int *cv = waves;
+    uint64_t woff = 0;
+    if (lane == 0) cv[0] = extend(v.q, v.r, 0, 0, M, N);
     __syncwarp();
     int s = 0;
     bool ok = true;
     for (;;) {
-      // reached (M, N)?
       bool done = false;
-      if (target >= lo && target <= hi && lane == 0) done = cv[target - cbase] >= M;
+      if (v.target >= lo && v.target <= hi && lane == 0) done = cv[v.target - lo] >= M;
       done = __shfl_sync(FULL, done, 0);
       int alo = lo, ahi = hi;
-      if (!done && a.adapt_min > 0 && hi - lo + 1 >= a.adapt_min) {
-        int rmin = INT_MAX;
-        for (int d0 = lo; d0 <= hi; d0 += 32) {
-          const int d = d0 + lane;
-          if (d <= hi) {
-            const int f = cv[d - cbase];
-            if (f >= 0) rmin = min(rmin, max(M - f, N - f - d));
-          }
-        }
-        rmin = __reduce_min_sync(FULL, rmin);
-        int qlo = INT_MAX, qhi = INT_MIN;
-        for (int d0 = lo; d0 <= hi; d0 += 32) {
-          const int d = d0 + lane;
-          if (d <= hi) {
-            const int f = cv[d - cbase];
-            if (f >= 0 && max(M - f, N - f - d) - rmin <= a.adapt_max) {
-              qlo = min(qlo, d);
-              qhi = max(qhi, d);
-            }
-          }
-        }
-        alo = __reduce_min_sync(FULL, qlo);
-        ahi = __reduce_max_sync(FULL, qhi);
-      }
-      if (TB && lane == 0) {
+      if (!done && a.adapt_min > 0 && hi - lo + 1 >= a.adapt_min)
+        adapt_bounds(cv, -lo, 0xffffffffu, lo, hi, M, N, a.adapt_max, lane, &alo, &ahi);
+      if (lane == 0) {
         meta[4 * s + 0] = lo;
         meta[4 * s + 1] = hi;
         meta[4 * s + 2] = alo;
         meta[4 * s + 3] = ahi;
       }
       if (done) break;
-      if (s >= M + N + 1 || alo > ahi || (TB && s >= S)) {
-        // not expected: the leading diagonal always survives and the search reaches (M, N)
+      if (s >= S || alo > ahi) {  // not expected: the score pass reached (M, N) at S
         ok = false;
         break;
       }
-      // next wavefront
       const int *pv = cv;
-      const int pbase = cbase;
-      const int nlo = max(alo - 1, dlo), nhi = min(ahi + 1, dhi);
-      if (TB) {
-        woff += (uint64_t)(hi - lo + 1);
-        cv = waves + woff;
-        cbase = nlo;
-      } else {
-        cv = ring + ((s + 1) & 1) * a.ring_half;
-      }
+      const int pbase = lo;
+      const int nlo = max(alo - 1, v.dlo), nhi = min(ahi + 1, v.dhi);
+      woff += (uint64_t)(hi - lo + 1);
+      cv = waves + woff;
       for (int d0 = nlo; d0 <= nhi; d0 += 32) {
         const int d = d0 + lane;
         if (d <= nhi) {
           int which;
-          const int row = terms(pv, pbase, alo, ahi, d, M, N, &which);
-          cv[d - cbase] = row >= 0 ? extend(sq, sr, row, d, M, N) : UNREACHED;
+          const int row = terms(pv, -pbase, 0xffffffffu, alo, ahi, d, M, N, &which);
+          cv[d - nlo] = row >= 0 ? extend(v.q, v.r, row, d, M, N) : UNREACHED;
         }
       }
       __syncwarp();
-      cells += (uint64_t)(nhi - nlo + 1);
       lo = nlo;
       hi = nhi;
       ++s;
     }
-
-    if (!TB) {
-      if (lane == 0) {
-        filtr_result r;
-        r.score = ok ? -s : 0;
-        r.q_begin = 0;
-        r.q_end = M;
-        r.r_begin = 0;
-        r.r_end = N;
-        r.status = ok ? FILTR_ST_OK : FILTR_ST_TOO_WIDE;
-        r.cigar_len = 0;
-        r.reserved = 0;
-        r.cigar_off = 0;
-        r.cells = cells;
-        a.out[p] = r;
-        if (a.need) a.need[p] = ok ? 4ull * (uint64_t)(s + 1) + cells : 0ull;
-      }
-    } else if (lane == 0) {
+    if (lane == 0) {
       // walk back from (M, N): per score, the matches after the edit, then the edit
       RevEmitter em{a.stage + a.stage_off[p]};
       if (ok) {
-        int d = target, i = M;
+        int d = v.target, i = M;
         for (int u = s; u > 0; --u) {
           const int plo = meta[4 * (u - 1)], phi = meta[4 * (u - 1) + 1];
           const int palo = meta[4 * (u - 1) + 2], pahi = meta[4 * (u - 1) + 3];
           woff -= (uint64_t)(phi - plo + 1);
           int which;
-          const int row = terms(waves + woff, plo, palo, pahi, d, M, N, &which);
+          const int row = terms(waves + woff, -plo, 0xffffffffu, palo, pahi, d, M, N, &which);
           em.put(OP_EQ, (uint32_t)(i - row));
           if (which == 0) {
             em.put(OP_X, 1);
@@ -304,46 +454,41 @@ struct Carve {
   }
 };
 
-// Warps per block for a per-warp shared-memory staging of `bytes`.
-int search_warps_per_block(size_t bytes) {
-  if (bytes * 4 <= 64 * 1024) return 4;
-  if (bytes * 2 <= 96 * 1024) return 2;
-  return 1;
+// Block shape of a kernel with `wbytes` of shared memory per warp: the warps per
+// block (4, 2 or 1) that keep the most warps resident per SM.
+struct LaunchCfg {
+  int wpb = 1, per_sm = 0;
+  size_t smem = 0;
+};
+template <class K>
+cudaError_t pick_cfg(K kern, size_t wbytes, LaunchCfg *cfg) {
+  LaunchCfg best;
+  for (int wpb : {4, 2, 1}) {
+    const size_t smem = wbytes * wpb;
+    if (smem > 227 * 1024) continue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm * wpb > best.per_sm * best.wpb) best = LaunchCfg{wpb, per_sm, smem};
+  }
+  if (best.per_sm < 1) return cudaErrorInvalidConfiguration;
+  *cfg = best;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best.smem);
 }
 
-// One persistent launch: at most max_warps warps (the score pass's ring slots).
-template <bool TB>
-cudaError_t launch_search(const SearchArgs &a, int sms, uint64_t max_warps, cudaStream_t st) {
-  const size_t wbytes = (size_t)(a.q_words + a.r_words) * 4;
-  const int wpb = search_warps_per_block(wbytes);
-  const size_t smem = wbytes * wpb;
-  cudaError_t e = cudaFuncSetAttribute(k_search<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<TB>, 32 * wpb, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  const uint64_t want = ((uint64_t)a.n + wpb - 1) / wpb;
-  const int grid = (int)std::min<uint64_t>(std::min<uint64_t>(want, (uint64_t)sms * per_sm),
-                                           max_warps / wpb);
+// One persistent launch of at most max_warps warps.
+template <class K>
+cudaError_t launch_cfg(K kern, const LaunchCfg &cfg, const SearchArgs &a, int sms,
+                       uint64_t max_warps, cudaStream_t st) {
+  const uint64_t want = ((uint64_t)a.n + cfg.wpb - 1) / cfg.wpb;
+  const uint64_t grid =
+      std::min<uint64_t>(std::min<uint64_t>(want, (uint64_t)sms * cfg.per_sm), max_warps / cfg.wpb);
   if (grid == 0) return cudaSuccess;
-  k_search<TB><<<grid, 32 * wpb, smem, st>>>(a);
+  kern<<<(unsigned)grid, 32 * cfg.wpb, cfg.smem, st>>>(a);
   return cudaGetLastError();
-}
-
-// Resident warps of the score pass, rounded to whole blocks (sizes its ring).
-int search_slots(size_t wbytes, int sms) {
-  const int wpb = search_warps_per_block(wbytes);
-  const size_t smem = wbytes * wpb;
-  if (cudaFuncSetAttribute(k_search<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return -1;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search<false>, 32 * wpb, smem) !=
-      cudaSuccess)
-    return -1;
-  return std::max(per_sm, 1) * sms * wpb;
 }
 
 }  // namespace
@@ -409,12 +554,20 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   a.band = prm->band;
   a.adapt_min = prm->adapt_min_len;
   a.adapt_max = prm->adapt_max_dist;
-  a.q_words = (max_m + 8) / 4 + 1;
-  a.r_words = (max_n + 8) / 4 + 1;
+  // staging: the 16-byte blocks holding a sequence (up to 15 bytes before its
+  // first residue) and the word after its last, in whole 16-byte blocks
+  a.q_words = (max_m + 48) / 16 * 4;
+  a.r_words = (max_n + 48) / 16 * 4;
   a.ring_half = max_m + max_n + 1;
-  const size_t wbytes = (size_t)(a.q_words + a.r_words) * 4;
-  const int slots = search_slots(wbytes, ctx->sms);
-  if (slots < 0) return cuda_fail(cudaGetLastError(), "search kernel occupancy");
+  // shared-memory rings: small, so they cost little occupancy; a pair whose
+  // wavefront grows wider continues in global memory
+  const uint32_t ring_cap = ctx->search_ring > 0 ? (uint32_t)ctx->search_ring : 32u;
+  a.ring_c = 32;
+  while (a.ring_c < a.ring_half && a.ring_c < ring_cap) a.ring_c <<= 1;
+  LaunchCfg cfg_score, cfg_tb;
+  ce = pick_cfg(k_search_score, (size_t)(a.q_words + a.r_words + 2 * a.ring_c) * 4, &cfg_score);
+  if (ce == cudaSuccess && tb) ce = pick_cfg(k_search_tb, (size_t)(a.q_words + a.r_words) * 4, &cfg_tb);
+  if (ce != cudaSuccess) return cuda_fail(ce, "search kernel occupancy");
 
   Carve c{ctx->ws, ctx->ws_bytes};
   uint32_t *d_counter = c.take<uint32_t>(64);
@@ -426,10 +579,12 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   uint64_t *d_total = tb ? c.take<uint64_t>(4) : nullptr;
   uint32_t *d_stage = tb ? c.take<uint32_t>(stage_words) : nullptr;
   const size_t ring_mark = c.used;
-  // ring slots: no more warps than pairs, and no more than the workspace holds
+  // global buffers for wavefronts that outgrow the rings: one per resident warp,
+  // no more warps than pairs, no more than the workspace holds
   const uint64_t slot_bytes = 2ull * a.ring_half * sizeof(int);
-  const int wpb = search_warps_per_block(wbytes);
-  uint64_t n_slots = std::min<uint64_t>((uint64_t)slots, ((uint64_t)n + wpb - 1) / wpb * wpb);
+  const int wpb = cfg_score.wpb;
+  uint64_t n_slots = std::min<uint64_t>((uint64_t)ctx->sms * cfg_score.per_sm * wpb,
+                                        ((uint64_t)n + wpb - 1) / wpb * wpb);
   const size_t ring_base = (c.used + 255) / 256 * 256;
   const uint64_t fit = ctx->ws_bytes > ring_base ? (ctx->ws_bytes - ring_base) / slot_bytes : 0;
   n_slots = std::min<uint64_t>(n_slots, fit / wpb * wpb);
@@ -448,7 +603,7 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   a.need = d_need;
   a.ring = d_ring;
   ctx->span_begin(Ctx::PH_FORWARD, st);
-  ce = launch_search<false>(a, ctx->sms, n_slots, st);
+  ce = launch_cfg(k_search_score, cfg_score, a, ctx->sms, n_slots, st);
   ctx->span_end(st);
   ++launches;
   if (ce != cudaSuccess) return cuda_fail(ce, "search score pass");
@@ -515,7 +670,7 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
       a.order = d_order + wave_ranges[w].first;
       a.n = wave_ranges[w].second - wave_ranges[w].first;
       a.counter = d_counter + 1 + w;
-      ce = launch_search<true>(a, ctx->sms, UINT64_MAX, st);
+      ce = launch_cfg(k_search_tb, cfg_tb, a, ctx->sms, UINT64_MAX, st);
       ++launches;
       if (ce != cudaSuccess) break;
     }
@@ -557,6 +712,15 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
 }  // namespace filtr
 
 using namespace filtr;
+
+extern "C" filtr_status filtr_test_set_search_ring(filtr_ctx *ctx, int32_t entries) {
+  if (!ctx || (entries != 0 && (entries < 32 || entries > 4096 || (entries & (entries - 1))))) {
+    set_error("filtr_test_set_search_ring: bad arguments");
+    return FILTR_ERR_INVALID;
+  }
+  reinterpret_cast<Ctx *>(ctx)->search_ring = entries;
+  return FILTR_OK;
+}
 
 extern "C" filtr_status filtr_search_batch(filtr_ctx *ctx, const filtr_search_params *params,
                                            uint32_t n_pairs, const uint8_t *q_seq,

@@ -121,3 +121,8 @@ def test_search_rejects_on_host(L):
     assert p.band == -1 and (p.adapt_min_len, p.adapt_max_dist) == (0, 0)
     q = L.make_search_params(traceback=False, band=7, adapt=(100, 20))
     assert (q.traceback, q.band, q.adapt_min_len, q.adapt_max_dist) == (0, 7, 100, 20)
+
+
+def test_search_ring_hook_rejects_on_host(L):
+    lib = L.lib()
+    assert lib.filtr_test_set_search_ring(None, 256) == L.ERR_INVALID
