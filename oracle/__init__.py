@@ -36,7 +36,7 @@ class Params(C.Structure):
         ("gap_extend", C.c_int64), ("alphabet", C.c_int32), ("subst", C.POINTER(C.c_int8)),
         ("use_band", C.c_int32), ("band_literal", C.c_int32), ("band", C.c_int64),
         ("use_xdrop", C.c_int32), ("xdrop", C.c_int64), ("traceback", C.c_int32),
-        ("order", C.c_int32), ("zdrop", C.c_int32),
+        ("order", C.c_int32), ("zdrop", C.c_int32), ("running", C.c_int32),
     ]
 
 
@@ -99,7 +99,8 @@ def lib():
 
 
 def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
-                band_literal=False, xdrop=None, zdrop=None, traceback=True, order=0, **_ignored):
+                band_literal=False, xdrop=None, zdrop=None, traceback=True, order=0,
+                xdrop_running=False, **_ignored):
     s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
     a = int(s.shape[0])
     p = Params()
@@ -120,6 +121,7 @@ def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, ban
     p.zdrop = 0 if zdrop is None else 1
     p.traceback = 1 if traceback else 0
     p.order = int(order)
+    p.running = 1 if xdrop_running else 0
     p._keep = s  # keep the table alive
     return p
 

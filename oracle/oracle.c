@@ -303,8 +303,10 @@ static int run_xdrop(ctx_t *c, int64_t *cells, int64_t *last_k) {
       }
     }
     if (!any) break;
-    best = nbest;
-    dbest = ndbest;
+    if (!c->p->running || nbest > best) { /* running: keep the first maximum */
+      best = nbest;
+      dbest = ndbest;
+    }
     lo = nlo;
     hi = nhi;
   }

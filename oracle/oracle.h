@@ -23,6 +23,10 @@
  *     k is pruned when best(k-1) - H > Z + |diag(i,j) - diag_best(k-1)|,
  *     diag_best(k-1) being the diagonal of antidiagonal k-1's best cell (the
  *     largest H; among equal H the smallest i, i.e. the largest diagonal);
+ *   - the running variant of both (the BLAST-style reading of Sec. 9.3's "best
+ *     score seen so far"): best is the largest best(t) over t <= k-1, and for
+ *     Z-drop the reference diagonal is that of the antidiagonal that first
+ *     reached it;
  *   - traceback with fixed tie-breaks, emitted as a SAM/BAM CIGAR.
  *   - edit distance by the search traversal (Sec. 6.3): the furthest row
  *     F[s][d] reached on diagonal d = j - i with s edits, from the three shifted
@@ -60,6 +64,8 @@ typedef struct {
   int32_t traceback;   /* 1: emit CIGAR and begin coordinates */
   int32_t order;       /* evaluation order for unpruned / banded runs: 0 row-major, 1 antidiagonal */
   int32_t zdrop;       /* with use_xdrop: 1 = Z-drop with Z = xdrop (distance term added) */
+  int32_t running;     /* with use_xdrop: 1 = the threshold follows the best score of every
+                          antidiagonal so far (running maximum) instead of antidiagonal k-1's */
 } orc_params;
 
 typedef struct {

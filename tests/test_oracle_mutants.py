@@ -23,7 +23,9 @@ MUTANTS = {
                           "if (out->vE && (!out->vH || out->E >= out->H))"),
     "H_tie_F_over_E": ("if (out->vF && (!out->vH || out->F > out->H))",
                        "if (out->vF && (!out->vH || out->F >= out->H))"),
-    "xdrop_running_max": ("    best = nbest;\n", "    if (nbest > best) best = nbest;\n"),
+    "xdrop_running_max": ("if (!c->p->running || nbest > best)", "if (nbest > best)"),
+    "running_ties_move_reference": ("if (!c->p->running || nbest > best)",
+                                    "if (!c->p->running || nbest >= best)"),
     "xdrop_non_strict": ("tmp.H >= best - X", "tmp.H > best - X"),
     "xdrop_domain_no_growth": ("if (lo - 1 > dl) dl = lo - 1;", "if (lo > dl) dl = lo;"),
     "band_edge_shift": ("c.hi = ((N - M) > 0 ? (N - M) : 0) + p->band;\n    }\n  }\n  memset(res",
@@ -35,7 +37,7 @@ MUTANTS = {
                           "const int64_t dist = 0;"),
     "zdrop_signed_distance": ("(d > dbest ? d - dbest : dbest - d)", "(d - dbest)"),
     "zdrop_tie_smallest_i_flipped": ("(tmp.H == nbest && d > ndbest)", "(tmp.H == nbest && d < ndbest)"),
-    "zdrop_best_diagonal_frozen": ("    dbest = ndbest;\n", "\n"),
+    "zdrop_best_diagonal_frozen": ("      dbest = ndbest;\n", "\n"),
     "cells_count_boundary": ("      if (i >= 1 && j >= 1) ++*cells;\n      if (alive)",
                              "      ++*cells;\n      if (alive)"),
 }

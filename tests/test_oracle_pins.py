@@ -228,7 +228,8 @@ def test_hand_worked(case, oracle_lib):
     S = np.full((4, 4), case["mismatch"], np.int8)
     np.fill_diagonal(S, case["match"])
     kw = dict(mode=case["mode"], affine=case["affine"], gap_open=case["gap_open"],
-              gap_extend=case["gap_extend"], xdrop=case.get("xdrop"), zdrop=case.get("zdrop"))
+              gap_extend=case["gap_extend"], xdrop=case.get("xdrop"), zdrop=case.get("zdrop"),
+              xdrop_running=case.get("running", False))
     res = oracle.align(q, r, S, **kw)
     assert res["score"] == case["score"]
     assert res["status"] == case["status"]
@@ -274,3 +275,39 @@ def test_invalid_arguments(oracle_lib):
         oracle.align(np.array([5], np.uint8), np.array([0], np.uint8), DNA_S)
     with pytest.raises(ValueError):
         oracle.align(np.array([0], np.uint8), np.array([0], np.uint8), DNA_S, gap_open=-1)
+
+
+@pytest.mark.parametrize("zd", [False, True])
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_running_threshold(mode, zd, oracle_lib):
+    """The running-maximum variant: with X = infinity it is the unpruned run.  For
+    X-drop its threshold is never below the literal one, so it keeps a subset of
+    the cells the literal run keeps (evaluated and alive); Z-drop's distance term
+    is measured from another reference diagonal, so there only the CIGAR is
+    checked."""
+    rng = np.random.default_rng(31)
+    S = np.where(np.eye(4, dtype=bool), 2, -3).astype(np.int8)
+    for _ in range(40):
+        M, N = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+        q = rng.integers(0, 4, size=M).astype(np.uint8)
+        r = q[:N].copy() if rng.random() < 0.5 and N <= M else rng.integers(0, 4, size=N).astype(np.uint8)
+        N = len(r)
+        base = dict(mode=mode, affine=True, gap_open=2, gap_extend=1)
+        key = "zdrop" if zd else "xdrop"
+        inf = oracle.align(q, r, S, **base, **{key: oracle.INF}, xdrop_running=True)
+        un = oracle.align(q, r, S, **base)
+        assert (inf["score"], inf["q_end"], inf["r_end"]) == (un["score"], un["q_end"], un["r_end"])
+        for X in (0, 3, 8):
+            lit = oracle.align(q, r, S, **base, **{key: X})
+            run = oracle.align(q, r, S, **base, **{key: X}, xdrop_running=True)
+            if run["status"] == 0:
+                _check_cigar(run, q, r, S, 2, 1)
+            if zd:
+                continue
+            assert run["cells"] <= lit["cells"]
+            ij_l, al_l = oracle.domain(q, r, S, **base, **{key: X})
+            ij_r, al_r = oracle.domain(q, r, S, **base, **{key: X}, xdrop_running=True)
+            lit_cells = {tuple(x) for x in ij_l.tolist()}
+            lit_alive = {tuple(x) for x, a in zip(ij_l.tolist(), al_l) if a}
+            assert {tuple(x) for x in ij_r.tolist()} <= lit_cells
+            assert {tuple(x) for x, a in zip(ij_r.tolist(), al_r) if a} <= lit_alive
