@@ -65,7 +65,13 @@ typedef enum {
 enum { FILTR_GLOBAL = 0, FILTR_LOCAL = 1 };
 enum { FILTR_ALPHA_DNA = 4, FILTR_ALPHA_PROTEIN = 20 };
 enum { FILTR_PRUNE_BAND = 1u, FILTR_PRUNE_XDROP = 2u, FILTR_PRUNE_BAND_LITERAL = 4u,
-       FILTR_PRUNE_ZDROP = 8u };  /* XDROP and ZDROP exclude each other */
+       FILTR_PRUNE_ZDROP = 8u,          /* XDROP and ZDROP exclude each other */
+       FILTR_PRUNE_XDROP_RUNNING = 16u  /* with XDROP or ZDROP: the threshold follows the
+                                           best score of every antidiagonal so far (a running
+                                           maximum, Sec. 9.3's "best score seen so far")
+                                           instead of antidiagonal k-1's; for Z-drop the
+                                           reference diagonal is that of the antidiagonal that
+                                           first reached the running best */ };
 enum { FILTR_PREC_AUTO = 0, FILTR_PREC_I32 = 1, FILTR_PREC_I16X2 = 2 };
 enum { FILTR_XDROP_INF = 0x7fffffff };
 

@@ -18,7 +18,7 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_CIGAR_CAP, ERR_UNSU
     -1, -2, -3, -4, -5, -6, -7)
 GLOBAL, LOCAL = 0, 1
 ALPHA_DNA, ALPHA_PROTEIN = 4, 20
-PRUNE_BAND, PRUNE_XDROP, PRUNE_BAND_LITERAL, PRUNE_ZDROP = 1, 2, 4, 8
+PRUNE_BAND, PRUNE_XDROP, PRUNE_BAND_LITERAL, PRUNE_ZDROP, PRUNE_XDROP_RUNNING = 1, 2, 4, 8, 16
 PREC_AUTO, PREC_I32, PREC_I16X2 = 0, 1, 2
 XDROP_INF = 0x7FFFFFFF
 ST_OK, ST_DROPPED, ST_UNREACHABLE, ST_EMPTY, ST_TOO_WIDE = 0, 1, 2, 3, 4
@@ -189,7 +189,7 @@ def check(rc: int, what: str = ""):
 
 def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
                 band_literal=False, xdrop=None, zdrop=None, traceback=False, precision=PREC_AUTO,
-                **_ignored) -> Params:
+                xdrop_running=False, **_ignored) -> Params:
     """Build a filtr_params block; the substitution table is kept alive on it."""
     s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
     p = Params()
@@ -208,6 +208,8 @@ def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, ban
         prune |= PRUNE_XDROP
     if zdrop is not None:
         prune |= PRUNE_ZDROP
+    if xdrop_running:
+        prune |= PRUNE_XDROP_RUNNING
     thr = xdrop if zdrop is None else zdrop
     p.prune = prune
     p.band = 0 if band is None else int(band)

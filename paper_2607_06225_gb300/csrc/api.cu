@@ -60,7 +60,7 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
     return FILTR_ERR_INVALID;
   }
   if (p->prune & ~(uint32_t)(FILTR_PRUNE_BAND | FILTR_PRUNE_XDROP | FILTR_PRUNE_BAND_LITERAL |
-                             FILTR_PRUNE_ZDROP)) {
+                             FILTR_PRUNE_ZDROP | FILTR_PRUNE_XDROP_RUNNING)) {
     set_error("unknown prune bits 0x%x", p->prune);
     return FILTR_ERR_INVALID;
   }
@@ -69,6 +69,10 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
   const bool xd = (p->prune & FILTR_PRUNE_XDROP) != 0 || zd;
   if (zd && (p->prune & FILTR_PRUNE_XDROP)) {
     set_error("FILTR_PRUNE_XDROP and FILTR_PRUNE_ZDROP exclude each other");
+    return FILTR_ERR_INVALID;
+  }
+  if ((p->prune & FILTR_PRUNE_XDROP_RUNNING) && !xd) {
+    set_error("FILTR_PRUNE_XDROP_RUNNING needs FILTR_PRUNE_XDROP or FILTR_PRUNE_ZDROP");
     return FILTR_ERR_INVALID;
   }
   if (band && p->band < 0) {
@@ -98,6 +102,7 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
   sp->band = band ? p->band : 0;
   sp->use_xdrop = xd ? 1 : 0;
   sp->zdrop = zd ? 1 : 0;
+  sp->xrun = (p->prune & FILTR_PRUNE_XDROP_RUNNING) ? 1 : 0;
   sp->xdrop = xd ? p->xdrop : 0;
   sp->traceback = p->traceback;
   sp->precision = p->precision;

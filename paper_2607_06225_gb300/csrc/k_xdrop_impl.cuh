@@ -4,7 +4,8 @@
 // parallel.
 //
 // X-drop decides antidiagonal k from best(k-1), the largest unpruned H of
-// antidiagonal k-1, and the diagonal range [lo(k-1), hi(k-1)] of its unpruned
+// antidiagonal k-1 (with FILTR_PRUNE_XDROP_RUNNING the largest of every
+// antidiagonal up to k-1), and the diagonal range [lo(k-1), hi(k-1)] of its unpruned
 // cells, so antidiagonals are processed strictly one after another: compute all
 // cells of k, reduce (max H, min / max diagonal of the unpruned cells), then
 // move on.  A group of W warps (one pair) holds a window of WIN = W*32*S slots;
@@ -466,8 +467,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         ended = true;
         break;
       }
-      best = gmax;
-      if (ZD) dbest = 2 * (cn + gbs) - k;
+      if (!a.sp.xrun || gmax > best) {  // running best: the first maximum keeps its diagonal
+        best = gmax;
+        if (ZD) dbest = 2 * (cn + gbs) - k;
+      }
       lo = 2 * (cn + glo) - k;
       hi = 2 * (cn + ghi) - k;
       if (k == M + N) corner = true;

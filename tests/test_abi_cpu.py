@@ -68,6 +68,12 @@ def test_params_check(L):
     assert L.lib().filtr_params_check(C.byref(p)) == L.OK
     p.prune |= L.PRUNE_XDROP
     assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
+    # the running threshold needs X-drop or Z-drop
+    for kw in (dict(xdrop=3), dict(zdrop=3)):
+        p = L.make_params(S, xdrop_running=True, **kw)
+        assert L.lib().filtr_params_check(C.byref(p)) == L.OK, kw
+    p = L.make_params(S, xdrop_running=True)
+    assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
 
 
 def test_ctx_create_without_gpu_fails_cleanly(L):

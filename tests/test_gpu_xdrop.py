@@ -1,6 +1,7 @@
 """GPU parity of the X-drop antidiagonal kernel against the oracle (bit-exact):
 thresholds from 0 (stops on antidiagonal 1) to infinity (whole matrix), with and
-without a band, global and local, linear and affine, traceback on and off,
+without a band, global and local, linear and affine, traceback on and off, the
+running-maximum threshold (X-drop and Z-drop, batched and segmented long pairs),
 windows that overflow and are rerun with wider groups, and long-read pairs."""
 import numpy as np
 import pytest
@@ -132,3 +133,47 @@ def test_plain_equals_batched_xdrop(F, ctx):
     assert np.array_equal(c1[:used], c2[:used])
     ores, oops, ooff = oracle_batch(b, dict(b.scoring))
     compare(b, dict(b.scoring), r1, c1, ores, oops, ooff, label="plain")
+
+
+@pytest.mark.parametrize("kind", ["xdrop", "zdrop"])
+@pytest.mark.parametrize("X", [0, 6, 40])
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_running_threshold(F, ctx, kind, X, mode):
+    """FILTR_PRUNE_XDROP_RUNNING (the threshold follows the best of every
+    antidiagonal so far): bit-exact against the oracle's running variant, X-drop
+    and Z-drop, with traceback, including pairs whose window is rerun wider."""
+    b = mixed_pairs(200 + X, n=100)
+    run_both(F, ctx, b, {"mode": mode, "affine": True, "gap_open": 4, "gap_extend": 2,
+                         kind: X, "xdrop_running": True, "traceback": True})
+
+
+def test_running_long_reads(F, ctx):
+    b = synth.long_reads(n=60, lmin=2000, lmax=5000, seed=32)
+    for kind in ("xdrop", "zdrop"):
+        sc = dict(b.scoring, xdrop=None, xdrop_running=True)
+        sc[kind] = 400
+        run_both(F, ctx, b, sc)
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_running_long_pair_segmented(F, ctx, recompute):
+    """filtr_align_long with the running threshold through the segmented sweep
+    (the running best and its diagonal carried across checkpoints)."""
+    b = synth.long_pair(length=5000, seg=150, seed=33, xdrop=120)
+    q, r = b.pair(0)
+    for kind, X in (("xdrop", 100), ("zdrop", 60)):
+        sc = dict(b.scoring, xdrop=None, xdrop_running=True)
+        sc[kind] = X
+        params = F.make_params(b.subst, **sc)
+        assert F.lib().filtr_test_set_checkpoint(ctx.handle, 64) == 0
+        assert F.lib().filtr_test_force_recompute(ctx.handle, int(recompute)) == 0
+        try:
+            res, cig, rc = F.align_long(ctx, params, q, r)
+        finally:
+            F.lib().filtr_test_set_checkpoint(ctx.handle, 0)
+            F.lib().filtr_test_force_recompute(ctx.handle, 0)
+        assert rc == 0, F.last_error()
+        o = oracle.align(q, r, b.subst, **sc)
+        for f in ("score", "q_end", "r_end", "status", "cells"):
+            assert int(res[f]) == int(o[f]), (kind, f, int(res[f]), int(o[f]))
+        assert np.array_equal(cig, o["cigar"])
