@@ -74,6 +74,8 @@ def parse():
                     help="skip the search-versus-antidiagonal edit-distance table")
     ap.add_argument("--search-only", action="store_true",
                     help="run only the search-versus-antidiagonal table and print it")
+    ap.add_argument("--search-cells", default=None,
+                    help="table cells to run, 'length:divergence:pairs,...' (default: all nine)")
     ap.add_argument("--tune-save", default=None,
                     help="write the autotuned shape costs to this JSON file")
     ap.add_argument("--tune-load", default=None,
@@ -441,7 +443,18 @@ PAPER_SEARCH_SPEEDUP = {(500, 0.01): 97, (2000, 0.01): 98, (4000, 0.01): 300,
                         (500, 0.30): 0.45, (2000, 0.30): 0.45, (4000, 0.30): 0.72}
 
 
-def search_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True):
+def search_cells(spec):
+    """The table's (length, divergence, pairs) cells, or those `spec` names."""
+    if not spec:
+        return [(length, div, n) for length, n in SEARCH_TABLE for div in SEARCH_DIVS]
+    out = []
+    for item in spec.split(","):
+        length, div, n = item.split(":")
+        out.append((int(length), float(div), int(n)))
+    return out
+
+
+def search_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True, cells=None):
     """Edit distance of one batch per (length, divergence) through the search
     traversal (filtr_search_batch, score only) and through the antidiagonal
     kernels (filtr_align_batch with unit costs, whose score is minus the edit
@@ -468,52 +481,51 @@ def search_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True):
     sp = F.make_search_params(traceback=False)
     tuned = False
     rows = []
-    for length, n in SEARCH_TABLE:
-        for div in SEARCH_DIVS:
-            b = synth.edit_pairs(n, length, div, seed=6)
-            db = F.DeviceBatch(b, dev)
-            out_s, _ = F.alloc_outputs(db.n, 0, dev)
-            out_a, _ = F.alloc_outputs(db.n, 0, dev)
-            ap = F.make_params(b.subst, **b.scoring)
-            if not tuned:  # setup, untimed: the antidiagonal kernels' shape costs
-                ctx.autotune(ap)
-                tuned = True
+    for length, div, n in search_cells(cells):
+        b = synth.edit_pairs(n, length, div, seed=6)
+        db = F.DeviceBatch(b, dev)
+        out_s, _ = F.alloc_outputs(db.n, 0, dev)
+        out_a, _ = F.alloc_outputs(db.n, 0, dev)
+        ap = F.make_params(b.subst, **b.scoring)
+        if not tuned:  # setup, untimed: the antidiagonal kernels' shape costs
+            ctx.autotune(ap)
+            tuned = True
 
-            def sr():
-                rc = ctx.search_batch_ptr(sp, db.n, *db.ptrs(), out_s.data_ptr(), None, 0,
-                                          stream=stream.cuda_stream)
-                if rc != 0:
-                    raise F.FiltrError(rc, F.last_error())
+        def sr():
+            rc = ctx.search_batch_ptr(sp, db.n, *db.ptrs(), out_s.data_ptr(), None, 0,
+                                      stream=stream.cuda_stream)
+            if rc != 0:
+                raise F.FiltrError(rc, F.last_error())
 
-            def ad():
-                rc = ctx.align_batch_ptr(ap, db.n, *db.ptrs(), out_a.data_ptr(), None, 0,
-                                         stream=stream.cuda_stream)
-                if rc != 0:
-                    raise F.FiltrError(rc, F.last_error())
+        def ad():
+            rc = ctx.align_batch_ptr(ap, db.n, *db.ptrs(), out_a.data_ptr(), None, 0,
+                                     stream=stream.cuda_stream)
+            if rc != 0:
+                raise F.FiltrError(rc, F.last_error())
 
-            t_sr, t_ad = timed(sr), timed(ad)
-            rs, ra = F.results_to_numpy(out_s, db.n), F.results_to_numpy(out_a, db.n)
-            assert np.array_equal(rs["score"], ra["score"]), "search and antidiagonal disagree"
-            full = float((b.q_len.astype(np.float64) * b.r_len).sum())
-            row = {"length": length, "divergence": div, "pairs": n,
-                   "search_ms": t_sr, "antidiagonal_ms": t_ad, "speedup": t_ad / t_sr,
-                   "paper_cpu_speedup": PAPER_SEARCH_SPEEDUP[(length, div)],
-                   "search_pairs_per_s": n / (t_sr * 1e-3),
-                   "search_gcups_equiv": full / (t_sr * 1e-3) / 1e9,
-                   "antidiagonal_gcups": full / (t_ad * 1e-3) / 1e9,
-                   "mean_distance": float(-rs["score"].mean()),
-                   "wavefront_cells_per_pair": float(rs["cells"].mean())}
-            if cpu:
-                import oracle
+        t_sr, t_ad = timed(sr), timed(ad)
+        rs, ra = F.results_to_numpy(out_s, db.n), F.results_to_numpy(out_a, db.n)
+        assert np.array_equal(rs["score"], ra["score"]), "search and antidiagonal disagree"
+        full = float((b.q_len.astype(np.float64) * b.r_len).sum())
+        row = {"length": length, "divergence": div, "pairs": n,
+               "search_ms": t_sr, "antidiagonal_ms": t_ad, "speedup": t_ad / t_sr,
+               "paper_cpu_speedup": PAPER_SEARCH_SPEEDUP.get((length, div)),
+               "search_pairs_per_s": n / (t_sr * 1e-3),
+               "search_gcups_equiv": full / (t_sr * 1e-3) / 1e9,
+               "antidiagonal_gcups": full / (t_ad * 1e-3) / 1e9,
+               "mean_distance": float(-rs["score"].mean()),
+               "wavefront_cells_per_pair": float(rs["cells"].mean())}
+        if cpu:
+            import oracle
 
-                sub = synth.pack([b.pair(p)[0] for p in range(4)], [b.pair(p)[1] for p in range(4)],
-                                 4, b.subst)
-                t0 = time.perf_counter()
-                ores, _, _ = oracle.search_batch(sub, nthreads=1, traceback=False)
-                row["oracle_ms_per_pair_1core"] = (time.perf_counter() - t0) * 1e3 / 4
-                assert np.array_equal(-ores["distance"], rs["score"][:4])
-            rows.append(row)
-            del db, out_s, out_a
+            sub = synth.pack([b.pair(p)[0] for p in range(4)], [b.pair(p)[1] for p in range(4)],
+                             4, b.subst)
+            t0 = time.perf_counter()
+            ores, _, _ = oracle.search_batch(sub, nthreads=1, traceback=False)
+            row["oracle_ms_per_pair_1core"] = (time.perf_counter() - t0) * 1e3 / 4
+            assert np.array_equal(-ores["distance"], rs["score"][:4])
+        rows.append(row)
+        del db, out_s, out_a
     return {"call": "filtr_search_batch (score only) vs filtr_align_batch (unit-cost global, "
                     "score only), same pairs",
             "l2": "flushed between timed steps", "steps": steps, "rows": rows}
@@ -568,7 +580,7 @@ def main():
     if args.search_only:
         if rank == 0:
             tab = search_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
-                               cpu=not args.no_cpu_baseline)
+                               cpu=not args.no_cpu_baseline, cells=args.search_cells)
             print(json.dumps({"search_table": tab}), flush=True)
         ctx.close()
         return
