@@ -478,7 +478,7 @@ def search_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True, cells=None
         torch.cuda.synchronize()
         return sorted(a.elapsed_time(b) for a, b in ev)[steps // 2]
 
-    sp = F.make_search_params(traceback=False)
+    sp = F.make_search_params(traceback=False, alphabet=4)
     tuned = False
     rows = []
     for length, div, n in search_cells(cells):

@@ -290,6 +290,9 @@ typedef struct {
   int32_t band;
   int32_t adapt_min_len;
   int32_t adapt_max_dist;
+  int32_t alphabet;      /* 0: any byte codes; 4: DNA codes 0..3, held two bits each on
+                            chip (sixteen residues per comparison); every code is checked
+                            and a code >= 4 fails the call with FILTR_ERR_INVALID */
 } filtr_search_params;
 
 /* Edit distance of n_pairs independent pairs by the search traversal.
@@ -307,8 +310,9 @@ typedef struct {
  * The call reads the lengths back once (a short synchronisation on `stream`);
  * with traceback it also reads back each pair's wavefront storage (a second
  * synchronisation) and recomputes the pairs with every wavefront kept, in
- * waves that fit the workspace.  FILTR_ERR_INVALID for NULL pointers or
- * negative adapt thresholds; FILTR_ERR_UNSUPPORTED when a pair has
+ * waves that fit the workspace.  FILTR_ERR_INVALID for NULL pointers,
+ * negative adapt thresholds, an alphabet other than 0 or 4, or (alphabet 4) a
+ * code >= 4; FILTR_ERR_UNSUPPORTED when a pair has
  * M + N > FILTR_SEARCH_MAX_LEN (its sequences are staged in shared memory);
  * FILTR_ERR_NOMEM when one pair's wavefronts do not fit the workspace. */
 #define FILTR_SEARCH_MAX_LEN 180000u

@@ -48,13 +48,14 @@ class Result(C.Structure):
 
 class SearchParams(C.Structure):
     _fields_ = [("traceback", C.c_int32), ("band", C.c_int32), ("adapt_min_len", C.c_int32),
-                ("adapt_max_dist", C.c_int32)]
+                ("adapt_max_dist", C.c_int32), ("alphabet", C.c_int32)]
 
 
-def make_search_params(traceback=True, band=None, adapt=None) -> SearchParams:
+def make_search_params(traceback=True, band=None, adapt=None, alphabet=0) -> SearchParams:
     """filtr_search_params: band=None for none; adapt=(min_len, max_dist) turns
-    WFA-Adapt on."""
+    WFA-Adapt on; alphabet=4 for DNA codes 0..3 (held two bits each)."""
     p = SearchParams()
+    p.alphabet = int(alphabet)
     p.traceback = 1 if traceback else 0
     p.band = -1 if band is None else int(band)
     p.adapt_min_len, p.adapt_max_dist = (0, 0) if adapt is None else (int(adapt[0]),

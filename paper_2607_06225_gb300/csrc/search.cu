@@ -70,29 +70,55 @@ struct Staged {
   int ph;
 };
 
-// The free transitions: row reached from row i on diagonal d by matches.
+// Sixteen 2-bit residues starting at residue i of a packed sequence.
+__device__ __forceinline__ uint32_t load16(const uint32_t *w, int i) {
+  const uint32_t a = w[i >> 4], b = w[(i >> 4) + 1];
+  return __funnelshift_r(a, b, (i & 15) * 2);
+}
+
+// The free transitions: row reached from row i on diagonal d by matches, four
+// byte residues (P2: sixteen 2-bit residues) per comparison.
+template <bool P2>
 __device__ __forceinline__ int extend(const Staged &q, const Staged &r, int i, int d, int M,
                                       int N) {
-  for (;;) {
-    const int rem = min(M - i, N - i - d);
-    if (rem <= 0) return i;
-    uint32_t x = load4(q.w, q.ph + i) ^ load4(r.w, r.ph + i + d);
-    if (rem < 4) x |= 0xffffffffu << (8 * rem);  // residues past an end never match
-    if (x) return i + ((__ffs(x) - 1) >> 3);
-    i += 4;
+  constexpr int K = P2 ? 16 : 4, B = P2 ? 2 : 8;
+  int rem = min(M - i, N - i - d);  // residues left on the diagonal
+  int qi = q.ph + i, ri = r.ph + i + d;
+  while (rem > 0) {
+    uint32_t x = P2 ? (load16(q.w, qi) ^ load16(r.w, ri)) : (load4(q.w, qi) ^ load4(r.w, ri));
+    if (rem < K) x |= 0xffffffffu << (B * rem);  // residues past an end never match
+    if (x) return qi - q.ph + ((__ffs(x) - 1) / B);
+    qi += K;
+    ri += K;
+    rem -= K;
   }
+  return qi - q.ph + rem;  // rem <= 0: back to the end of the diagonal
 }
 
 // Copy the 16-byte blocks that hold g[0, len) into dst (16-byte aligned) with
 // 16-byte loads; returns the byte of dst that holds g[0].  The blocks lie
 // within g's own 16-byte-aligned span, so no load crosses a page.
+// P2 (codes 0..3): each 16-byte block becomes one word of 2-bit codes, so
+// residue i again sits at position ph + i, counted in 2-bit units.
+__device__ __forceinline__ uint32_t pack_bytes2(uint32_t x) {  // four codes < 4 -> 8 bits
+  return (x & 3u) | ((x >> 6) & 0xcu) | ((x >> 12) & 0x30u) | ((x >> 18) & 0xc0u);
+}
+template <bool P2>
 __device__ __forceinline__ int stage_seq(const uint8_t *g, int len, uint32_t *dst, int lane) {
   const uintptr_t ga = reinterpret_cast<uintptr_t>(g);
   const int ph = (int)(ga & 15u);
   const uint4 *src = reinterpret_cast<const uint4 *>(ga - (uintptr_t)ph);
-  uint4 *d4 = reinterpret_cast<uint4 *>(dst);
   const int nblk = len > 0 ? (ph + len + 15) >> 4 : 0;
-  for (int k = lane; k < nblk; k += 32) d4[k] = __ldg(src + k);
+  if (P2) {
+    for (int k = lane; k < nblk; k += 32) {
+      const uint4 v = __ldg(src + k);
+      dst[k] = pack_bytes2(v.x) | (pack_bytes2(v.y) << 8) | (pack_bytes2(v.z) << 16) |
+               (pack_bytes2(v.w) << 24);
+    }
+  } else {
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int k = lane; k < nblk; k += 32) d4[k] = __ldg(src + k);
+  }
   return ph;
 }
 
@@ -198,13 +224,14 @@ struct PairView {
 };
 
 // Stage the pair's sequences in shared memory and set up its domain limits.
+template <bool P2>
 __device__ __forceinline__ PairView stage_pair(const SearchArgs &a, uint32_t p, uint32_t *sq,
                                                uint32_t *sr, int lane) {
   PairView v;
   v.M = (int)a.b.q_len[p];
   v.N = (int)a.b.r_len[p];
-  v.q = Staged{sq, stage_seq(a.b.q_seq + a.b.q_off[p], v.M, sq, lane)};
-  v.r = Staged{sr, stage_seq(a.b.r_seq + a.b.r_off[p], v.N, sr, lane)};
+  v.q = Staged{sq, stage_seq<P2>(a.b.q_seq + a.b.q_off[p], v.M, sq, lane)};
+  v.r = Staged{sr, stage_seq<P2>(a.b.r_seq + a.b.r_off[p], v.N, sr, lane)};
   __syncwarp();
   v.dlo = -v.M;
   v.dhi = v.N;
@@ -225,7 +252,7 @@ struct Lev {
 
 // Score levels from L.s on, until (M, N) is reached or -- in a shared-memory
 // ring of C entries -- the next wavefront would not fit (state stays 0).
-template <bool SMEM, int CH>
+template <bool SMEM, int CH, bool P2>
 __device__ __forceinline__ void levels(Lev &L, const Wf &w, int C, const PairView &v, int amin,
                                        int amax, int lane) {
   const int M = v.M, N = v.N;
@@ -250,32 +277,32 @@ __device__ __forceinline__ void levels(Lev &L, const Wf &w, int C, const PairVie
     if (SMEM && nhi - nlo + 1 > C) return;
     int *nv = level_buf(w, L.s + 1);
     // CH chunks of 32 diagonals per iteration: one load per diagonal of the
-    // previous wavefront (alive diagonals only), the neighbours d - 1 and d + 1
-    // by shuffles, the chunk edges from the neighbouring chunk or one load
+    // previous wavefront (alive diagonals only); the neighbours d - 1 and d + 1
+    // by two rotating shuffles, in which lane 31 (lane 0) hands lane 0 (lane 31)
+    // the last (first) diagonal of the chunk before (after) instead of its own
+    const uint32_t mk = SMEM ? w.mask : 0xffffffffu;
     for (int d0 = nlo; d0 <= nhi; d0 += 32 * CH) {
       int vc[CH];
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
         const int d = d0 + 32 * u + lane;
-        vc[u] = (d >= alo && d <= ahi) ? cv[at(d, w.off, w.mask)] : UNREACHED;
+        vc[u] = (d >= alo && d <= ahi) ? cv[at(d, w.off, mk)] : UNREACHED;
       }
-      const int dl = d0 - 1, dr = d0 + 32 * CH;
-      const int el = (lane == 0 && dl >= alo && dl <= ahi) ? cv[at(dl, w.off, w.mask)] : UNREACHED;
-      const int er = (lane == 31 && dr >= alo && dr <= ahi) ? cv[at(dr, w.off, w.mask)] : UNREACHED;
+      const int dl = d0 - 1, dr = d0 + 32 * CH;  // outer edges: lane 31 / lane 0 load them
+      const int el = (lane == 31 && dl >= alo && dl <= ahi) ? cv[at(dl, w.off, mk)] : UNREACHED;
+      const int er = (lane == 0 && dr >= alo && dr <= ahi) ? cv[at(dr, w.off, mk)] : UNREACHED;
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
         const int d = d0 + 32 * u + lane;
-        const int up = __shfl_up_sync(FULL, vc[u], 1);
-        const int dn = __shfl_down_sync(FULL, vc[u], 1);
-        const int prev_last = __shfl_sync(FULL, u > 0 ? vc[u > 0 ? u - 1 : 0] : el, 31);
-        const int next_first = __shfl_sync(FULL, u + 1 < CH ? vc[u + 1 < CH ? u + 1 : 0] : er, 0);
-        const int vl = lane == 0 ? (u > 0 ? prev_last : el) : up;     // F[s][d - 1]
-        const int vr = lane == 31 ? (u + 1 < CH ? next_first : er) : dn;  // F[s][d + 1]
+        const int to_right = lane == 31 ? (u > 0 ? vc[u > 0 ? u - 1 : 0] : el) : vc[u];
+        const int to_left = lane == 0 ? (u + 1 < CH ? vc[u + 1 < CH ? u + 1 : 0] : er) : vc[u];
+        const int vl = __shfl_sync(FULL, to_right, (lane + 31) & 31);  // F[s][d - 1]
+        const int vr = __shfl_sync(FULL, to_left, (lane + 1) & 31);    // F[s][d + 1]
         int row = UNREACHED;
         if (vc[u] >= 0 && vc[u] + 1 <= M && vc[u] + 1 + d <= N) row = vc[u] + 1;  // mismatch
         if (vr >= 0 && vr + 1 <= M && vr + 1 > row) row = vr + 1;                // insertion
         if (vl >= 0 && vl + d <= N && vl > row) row = vl;                        // deletion
-        if (d <= nhi) nv[at(d, w.off, w.mask)] = row >= 0 ? extend(v.q, v.r, row, d, M, N) : UNREACHED;
+        if (d <= nhi) nv[at(d, w.off, mk)] = row >= 0 ? extend<P2>(v.q, v.r, row, d, M, N) : UNREACHED;
       }
     }
     __syncwarp();
@@ -290,6 +317,7 @@ __device__ __forceinline__ void levels(Lev &L, const Wf &w, int C, const PairVie
 // traceback pass would store.  Per warp in shared memory: the two sequences,
 // then two rings of ring_c entries; a pair whose wavefront outgrows them moves
 // to the warp's buffers in global memory.
+template <bool P2>
 __global__ void __launch_bounds__(128) k_search_score(const SearchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -306,12 +334,12 @@ __global__ void __launch_bounds__(128) k_search_score(const SearchArgs a) {
     t = __shfl_sync(FULL, t, 0);
     if (t >= a.n) return;
     const uint32_t p = a.order ? a.order[t] : t;
-    const PairView v = stage_pair(a, p, sq, sr, lane);
+    const PairView v = stage_pair<P2>(a, p, sq, sr, lane);
     // score 0: the origin and its run of matches
-    if (lane == 0) ra[at(0, ws.off, ws.mask)] = extend(v.q, v.r, 0, 0, v.M, v.N);
+    if (lane == 0) ra[at(0, ws.off, ws.mask)] = extend<P2>(v.q, v.r, 0, 0, v.M, v.N);
     __syncwarp();
     Lev L{0, 0, 0, 1ull, 0};
-    levels<true, SEARCH_CHUNKS>(L, ws, (int)a.ring_c, v, a.adapt_min, a.adapt_max, lane);
+    levels<true, SEARCH_CHUNKS, P2>(L, ws, (int)a.ring_c, v, a.adapt_min, a.adapt_max, lane);
     if (L.state == 0) {  // level L.s to global memory, then on from there
       const Wf wg{g, g + a.ring_half, v.M, 0xffffffffu};
       const int *src = level_buf(ws, L.s);
@@ -319,7 +347,7 @@ __global__ void __launch_bounds__(128) k_search_score(const SearchArgs a) {
       for (int d = L.lo + lane; d <= L.hi; d += 32)
         dst[at(d, wg.off, wg.mask)] = src[at(d, ws.off, ws.mask)];
       __syncwarp();
-      levels<false, SEARCH_CHUNKS>(L, wg, 0, v, a.adapt_min, a.adapt_max, lane);
+      levels<false, SEARCH_CHUNKS, P2>(L, wg, 0, v, a.adapt_min, a.adapt_max, lane);
     }
     if (lane == 0) {
       const bool ok = L.state == 1;
@@ -344,6 +372,7 @@ __global__ void __launch_bounds__(128) k_search_score(const SearchArgs a) {
 // Traceback pass: the same levels again, every wavefront kept in the pair's
 // store (per score: lo, hi and the alive bounds, then the values), then lane 0
 // walks back from (M, N).
+template <bool P2>
 __global__ void __launch_bounds__(128) k_search_tb(const SearchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -360,7 +389,7 @@ __global__ void __launch_bounds__(128) k_search_tb(const SearchArgs a) {
       if (lane == 0) a.out[p].cigar_len = 0;
       continue;
     }
-    const PairView v = stage_pair(a, p, sq, sr, lane);
+    const PairView v = stage_pair<P2>(a, p, sq, sr, lane);
     const int M = v.M, N = v.N;
     const int S = -a.out[p].score;
     int *meta = a.arena + a.arena_off[p];  // per score: lo, hi, alo, ahi
@@ -368,7 +397,7 @@ __global__ void __launch_bounds__(128) k_search_tb(const SearchArgs a) {
     int lo = 0, hi = 0;
     int *cv = waves;
     uint64_t woff = 0;
-    if (lane == 0) cv[0] = extend(v.q, v.r, 0, 0, M, N);
+    if (lane == 0) cv[0] = extend<P2>(v.q, v.r, 0, 0, M, N);
     __syncwarp();
     int s = 0;
     bool ok = true;
@@ -400,7 +429,7 @@ __global__ void __launch_bounds__(128) k_search_tb(const SearchArgs a) {
         if (d <= nhi) {
           int which;
           const int row = terms(pv, -pbase, 0xffffffffu, alo, ahi, d, M, N, &which);
-          cv[d - nlo] = row >= 0 ? extend(v.q, v.r, row, d, M, N) : UNREACHED;
+          cv[d - nlo] = row >= 0 ? extend<P2>(v.q, v.r, row, d, M, N) : UNREACHED;
         }
       }
       __syncwarp();
@@ -504,6 +533,11 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
     set_error("WFA-Adapt thresholds must be >= 0");
     return FILTR_ERR_INVALID;
   }
+  if (prm->alphabet != 0 && prm->alphabet != 4) {
+    set_error("search alphabet must be 0 (any byte codes) or 4 (DNA codes 0..3)");
+    return FILTR_ERR_INVALID;
+  }
+  const bool p2 = prm->alphabet == 4;
   if (n == 0) return FILTR_OK;
   if (!b.q_seq || !b.r_seq || !b.q_off || !b.r_off || !b.q_len || !b.r_len || !out) {
     set_error("a batch pointer is NULL");
@@ -529,11 +563,25 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
     set_error("pinned host allocation failed");
     return FILTR_ERR_NOMEM;
   }
+  ce = cudaSuccess;
   uint32_t *h_ql = reinterpret_cast<uint32_t *>(ctx->h_stage), *h_rl = h_ql + n;
-  ce = cudaMemcpyAsync(h_ql, b.q_len, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+  uint32_t *h_bad = h_rl + n;
+  uint32_t *d_bad = reinterpret_cast<uint32_t *>(ctx->d_small);
+  *h_bad = 0;
+  if (p2) {  // DNA codes are packed two bits each: every code must be below 4
+    ce = cudaMemsetAsync(d_bad, 0, 4, st);
+    if (ce == cudaSuccess) ce = launch_validate_pairs(b, n, 4, d_bad, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_bad, d_bad, 4, cudaMemcpyDeviceToHost, st);
+    ++launches;
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_ql, b.q_len, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_rl, b.r_len, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return cuda_fail(ce, "reading the lengths");
+  if (*h_bad) {
+    set_error("%u residue codes are 4 or more (search alphabet 4)", *h_bad);
+    return FILTR_ERR_INVALID;
+  }
   uint32_t max_m = 0, max_n = 0;
   uint64_t stage_words = 0;
   for (uint32_t p = 0; p < n; ++p) {
@@ -556,8 +604,9 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   a.adapt_max = prm->adapt_max_dist;
   // staging: the 16-byte blocks holding a sequence (up to 15 bytes before its
   // first residue) and the word after its last, in whole 16-byte blocks
-  a.q_words = (max_m + 48) / 16 * 4;
-  a.r_words = (max_n + 48) / 16 * 4;
+  // (P2: one word per block, and the word after the last residue's)
+  a.q_words = p2 ? (max_m + 48) / 64 * 4 + 4 : (max_m + 48) / 16 * 4;
+  a.r_words = p2 ? (max_n + 48) / 64 * 4 + 4 : (max_n + 48) / 16 * 4;
   a.ring_half = max_m + max_n + 1;
   // shared-memory rings: small, so they cost little occupancy; a pair whose
   // wavefront grows wider continues in global memory
@@ -565,8 +614,10 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   a.ring_c = 32;
   while (a.ring_c < a.ring_half && a.ring_c < ring_cap) a.ring_c <<= 1;
   LaunchCfg cfg_score, cfg_tb;
-  ce = pick_cfg(k_search_score, (size_t)(a.q_words + a.r_words + 2 * a.ring_c) * 4, &cfg_score);
-  if (ce == cudaSuccess && tb) ce = pick_cfg(k_search_tb, (size_t)(a.q_words + a.r_words) * 4, &cfg_tb);
+  auto k_score = p2 ? k_search_score<true> : k_search_score<false>;
+  auto k_tb = p2 ? k_search_tb<true> : k_search_tb<false>;
+  ce = pick_cfg(k_score, (size_t)(a.q_words + a.r_words + 2 * a.ring_c) * 4, &cfg_score);
+  if (ce == cudaSuccess && tb) ce = pick_cfg(k_tb, (size_t)(a.q_words + a.r_words) * 4, &cfg_tb);
   if (ce != cudaSuccess) return cuda_fail(ce, "search kernel occupancy");
 
   Carve c{ctx->ws, ctx->ws_bytes};
@@ -603,7 +654,7 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   a.need = d_need;
   a.ring = d_ring;
   ctx->span_begin(Ctx::PH_FORWARD, st);
-  ce = launch_cfg(k_search_score, cfg_score, a, ctx->sms, n_slots, st);
+  ce = launch_cfg(k_score, cfg_score, a, ctx->sms, n_slots, st);
   ctx->span_end(st);
   ++launches;
   if (ce != cudaSuccess) return cuda_fail(ce, "search score pass");
@@ -670,7 +721,7 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
       a.order = d_order + wave_ranges[w].first;
       a.n = wave_ranges[w].second - wave_ranges[w].first;
       a.counter = d_counter + 1 + w;
-      ce = launch_cfg(k_search_tb, cfg_tb, a, ctx->sms, UINT64_MAX, st);
+      ce = launch_cfg(k_tb, cfg_tb, a, ctx->sms, UINT64_MAX, st);
       ++launches;
       if (ce != cudaSuccess) break;
     }

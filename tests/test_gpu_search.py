@@ -57,15 +57,15 @@ def compare_search(b, res, cig, ores, oops, ooff, tb, idx=None, label=""):
     assert not bad, f"{label}: {len(bad)} mismatches, first: {bad[:8]}"
 
 
-def run(F, ctx, b, tb=True, band=None, adapt=None):
-    prm = F.make_search_params(traceback=tb, band=band, adapt=adapt)
+def run(F, ctx, b, tb=True, band=None, adapt=None, alphabet=0):
+    prm = F.make_search_params(traceback=tb, band=band, adapt=adapt, alphabet=alphabet)
     res, cig, rc = F.search_batch(ctx, prm, b)
     assert rc == 0, F.last_error()
     return res, cig
 
 
-def check(F, ctx, b, tb=True, band=None, adapt=None, label=""):
-    res, cig = run(F, ctx, b, tb, band, adapt)
+def check(F, ctx, b, tb=True, band=None, adapt=None, label="", alphabet=0):
+    res, cig = run(F, ctx, b, tb, band, adapt, alphabet)
     ores, oops, ooff = oracle.search_batch(b, traceback=tb, band=band, adapt=adapt)
     compare_search(b, res, cig, ores, oops, ooff, tb, label=label)
     return res
@@ -82,13 +82,26 @@ def with_edges(qs, rs, rng, alpha):
     return qs, rs
 
 
-@pytest.mark.parametrize("alpha", [4, 20])
+@pytest.mark.parametrize("alpha,packed", [(4, False), (4, True), (20, False)])
 @pytest.mark.parametrize("tb", [True, False])
-def test_small_exact(F, ctx, alpha, tb):
+def test_small_exact(F, ctx, alpha, packed, tb):
     qs, rs = synth.random_pairs(300, 300, 300, alpha, seed=61 + alpha, related=0.7)
     qs, rs = with_edges(qs, rs, np.random.default_rng(61), alpha)
     b = synth.pack(qs, rs, alpha, np.zeros((alpha, alpha), np.int8))
-    check(F, ctx, b, tb=tb, label=f"alpha {alpha} tb {tb}")
+    check(F, ctx, b, tb=tb, label=f"alpha {alpha} tb {tb}", alphabet=4 if packed else 0)
+
+
+def test_packed_rejects_codes(F, ctx):
+    """Alphabet 4 checks every code: a 4 anywhere fails the call before the search."""
+    qs, rs = synth.random_pairs(20, 50, 50, 4, seed=69)
+    rs[7] = rs[7].copy()
+    rs[7][3] = 4
+    b = synth.pack(qs, rs, 5, np.zeros((5, 5), np.int8))
+    prm = F.make_search_params(traceback=False, alphabet=4)
+    _, _, rc = F.search_batch(ctx, prm, b, raise_on_error=False)
+    assert rc == F.ERR_INVALID
+    _, _, rc = F.search_batch(ctx, F.make_search_params(traceback=False), b)
+    assert rc == 0
 
 
 @pytest.mark.parametrize("band", [0, 5, 40])
@@ -114,10 +127,11 @@ def test_table_workloads(F, ctx, length, div):
     pairs against the oracle; the score-only run agrees; the antidiagonal
     kernels' unit-cost global score is minus the same distance."""
     b = synth.edit_pairs(48, length, div, seed=64)
-    res = check(F, ctx, b, tb=True, label=f"{length} {div}")
-    res0, _ = run(F, ctx, b, tb=False)
-    assert np.array_equal(res0["score"], res["score"])
-    assert np.array_equal(res0["cells"], res["cells"])
+    res = check(F, ctx, b, tb=True, label=f"{length} {div}", alphabet=4)
+    for alphabet in (0, 4):
+        res0, _ = run(F, ctx, b, tb=False, alphabet=alphabet)
+        assert np.array_equal(res0["score"], res["score"])
+        assert np.array_equal(res0["cells"], res["cells"])
     params = F.make_params(b.subst, **b.scoring)
     ares, _, rc = F.align_batch(ctx, params, b)
     assert rc == 0, F.last_error()
@@ -128,7 +142,7 @@ def test_table_workloads(F, ctx, length, div):
 def test_bench_batches_sampled(F, ctx, length, div, n):
     """The batch sizes the benchmark times, sampled pairs against the oracle."""
     b = synth.edit_pairs(n, length, div, seed=6)
-    res, _ = run(F, ctx, b, tb=False)
+    res, _ = run(F, ctx, b, tb=False, alphabet=4)
     idx = np.random.default_rng(65).choice(b.n, size=40, replace=False)
     sub = synth.pack([b.pair(int(p))[0] for p in idx], [b.pair(int(p))[1] for p in idx], 4,
                      b.subst)
