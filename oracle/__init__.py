@@ -37,6 +37,7 @@ class Params(C.Structure):
         ("use_band", C.c_int32), ("band_literal", C.c_int32), ("band", C.c_int64),
         ("use_xdrop", C.c_int32), ("xdrop", C.c_int64), ("traceback", C.c_int32),
         ("order", C.c_int32), ("zdrop", C.c_int32), ("running", C.c_int32),
+        ("mid", C.c_int32),
     ]
 
 
@@ -100,7 +101,7 @@ def lib():
 
 def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
                 band_literal=False, xdrop=None, zdrop=None, traceback=True, order=0,
-                xdrop_running=False, **_ignored):
+                xdrop_running=False, mid=False, **_ignored):
     s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
     a = int(s.shape[0])
     p = Params()
@@ -122,6 +123,7 @@ def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, ban
     p.traceback = 1 if traceback else 0
     p.order = int(order)
     p.running = 1 if xdrop_running else 0
+    p.mid = 1 if mid else 0
     p._keep = s  # keep the table alive
     return p
 

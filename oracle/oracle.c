@@ -28,9 +28,9 @@
 #include <string.h>
 
 typedef struct {
-  int64_t H, E, F;
-  uint8_t vH, vE, vF, alive;
-  uint32_t pad;
+  int64_t H, E, F, M; /* M: the diagonal candidate H(i-1,j-1) + s (Table 1's M state) */
+  uint8_t vH, vE, vF, alive, vM;
+  uint8_t pad[3];
 } cell_t;
 
 typedef struct {
@@ -87,14 +87,17 @@ static void eval_cell(ctx_t *c, int64_t i, int64_t j, cell_t *out, choice_t *ch)
   if (i == 0 && j == 0) {
     out->H = 0;
     out->vH = 1;
+    out->M = 0; /* the origin is where every path starts in the M state */
+    out->vM = 1;
     ch->src = 3;
     return;
   }
+  const int mid = p->affine && p->mid; /* gaps open from M instead of H */
   /* E: horizontal gap ending at (i, j), from (i, j-1) */
   if (j >= 1) {
     cell_t *l = get(c, i, j - 1);
-    if (l && l->vH) {
-      out->E = l->H - o - e;
+    if (l && (mid ? l->vM : l->vH)) {
+      out->E = (mid ? l->M : l->H) - o - e;
       out->vE = 1;
     }
     if (p->affine && l && l->vE) {
@@ -109,8 +112,8 @@ static void eval_cell(ctx_t *c, int64_t i, int64_t j, cell_t *out, choice_t *ch)
   /* F: vertical gap ending at (i, j), from (i-1, j) */
   if (i >= 1) {
     cell_t *u = get(c, i - 1, j);
-    if (u && u->vH) {
-      out->F = u->H - o - e;
+    if (u && (mid ? u->vM : u->vH)) {
+      out->F = (mid ? u->M : u->H) - o - e;
       out->vF = 1;
     }
     if (p->affine && u && u->vF) {
@@ -128,6 +131,8 @@ static void eval_cell(ctx_t *c, int64_t i, int64_t j, cell_t *out, choice_t *ch)
     if (g && g->vH) {
       out->H = g->H + subst(c, i, j);
       out->vH = 1;
+      out->M = out->H;
+      out->vM = 1;
       ch->src = 0;
     }
   }
@@ -316,7 +321,8 @@ static int run_xdrop(ctx_t *c, int64_t *cells, int64_t *last_k) {
 /* Walk back from (i, j) in state H; write single-move ops (reversed) into mv.
  * Returns the number of moves; *bi, *bj receive the start cell. */
 static int64_t walk(ctx_t *c, int64_t i, int64_t j, uint8_t *mv, int64_t *bi, int64_t *bj) {
-  int state = 0; /* 0 H, 1 E, 2 F */
+  int state = 0; /* 0 H, 1 E, 2 F, 3 M (M/I/D: a gap opened here, so this cell is a diagonal step) */
+  const int after_open = (c->p->affine && c->p->mid) ? 3 : 0;
   int64_t n = 0;
   cell_t tmp;
   choice_t ch;
@@ -341,12 +347,18 @@ static int64_t walk(ctx_t *c, int64_t i, int64_t j, uint8_t *mv, int64_t *bi, in
       eval_cell(c, i, j, &tmp, &ch);
       mv[n++] = ORC_OP_D;
       --j;
-      if (!ch.e_ext) state = 0;
-    } else {
+      if (!ch.e_ext) state = after_open;
+    } else if (state == 2) {
       eval_cell(c, i, j, &tmp, &ch);
       mv[n++] = ORC_OP_I;
       --i;
-      if (!ch.f_ext) state = 0;
+      if (!ch.f_ext) state = after_open;
+    } else {
+      if (i == 0 && j == 0) break; /* the origin */
+      mv[n++] = (c->q[i - 1] == c->r[j - 1]) ? ORC_OP_EQ : ORC_OP_X;
+      --i;
+      --j;
+      state = 0;
     }
   }
   *bi = i;

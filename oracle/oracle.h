@@ -11,7 +11,9 @@
  *       linear : H = max(H[i-1][j-1] + s, H[i][j-1] - e, H[i-1][j] - e)
  *       affine : Gotoh H/E/F  (Table 1 "Sequence Alignment", Sec. 3; the H/E/F
  *                form lets E and F open from H, so an insertion may touch a
- *                deletion -- see the reading list in the design notes)
+ *                deletion -- see the reading list in the design notes), or
+ *                Table 1's own M/I/D form: M = max(M, I, D)(i-1, j-1) + s,
+ *                I and D open from M only (H = max(M, I, D) is the cell's score)
  *     global (Needleman-Wunsch) or local (Smith-Waterman, H floored at 0);
  *   - a static band as a prune axis  lo <= diag(i,j) <= hi  (Sec. 7.1);
  *   - X-drop as a dynamic prune (Sec. 5.2 conditional definition and the
@@ -66,6 +68,8 @@ typedef struct {
   int32_t zdrop;       /* with use_xdrop: 1 = Z-drop with Z = xdrop (distance term added) */
   int32_t running;     /* with use_xdrop: 1 = the threshold follows the best score of every
                           antidiagonal so far (running maximum) instead of antidiagonal k-1's */
+  int32_t mid;         /* with affine: 1 = Table 1's M/I/D form: gaps open from M (the
+                          diagonal state) only, so a deletion never touches an insertion */
 } orc_params;
 
 typedef struct {

@@ -53,6 +53,29 @@ def brute_global(q, r, S, o, e):
     return max(path_score(p, q, r, S, o, e) for p in all_paths(len(q), len(r)))
 
 
+def mid_ok(path) -> bool:
+    """Table 1's M/I/D grammar: I and D open from M only, so a horizontal gap
+    step never directly follows or precedes a vertical one."""
+    return all({a, b} != {"H", "V"} for a, b in zip(path, path[1:]))
+
+
+def brute_global_mid(q, r, S, o, e):
+    return max(path_score(p, q, r, S, o, e) for p in all_paths(len(q), len(r)) if mid_ok(p))
+
+
+def brute_local_mid(q, r, S, o, e):
+    best = 0
+    M, N = len(q), len(r)
+    for i0 in range(M + 1):
+        for i1 in range(i0, M + 1):
+            for j0 in range(N + 1):
+                for j1 in range(j0, N + 1):
+                    if i1 - i0 == 0 and j1 - j0 == 0:
+                        continue
+                    best = max(best, brute_global_mid(q[i0:i1], r[j0:j1], S, o, e))
+    return best
+
+
 def brute_local(q, r, S, o, e):
     best = 0  # the empty alignment
     M, N = len(q), len(r)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MUTANTS = {
     "transposed_subst": ("c->p->subst[(int)c->q[i - 1] * a + (int)c->r[j - 1]]",
                          "c->p->subst[(int)c->r[j - 1] * a + (int)c->q[i - 1]]"),
-    "E_open_drops_o": ("out->E = l->H - o - e;", "out->E = l->H - e;"),
+    "E_open_drops_o": ("out->E = (mid ? l->M : l->H) - o - e;", "out->E = (mid ? l->M : l->H) - e;"),
     "F_ext_wrong_sign": ("int64_t ext = u->F - e;", "int64_t ext = u->F + e;"),
     "E_tie_prefers_ext": ("if (!out->vE || ext > out->E) {", "if (!out->vE || ext >= out->E) {"),
     "H_tie_E_over_diag": ("if (out->vE && (!out->vH || out->E > out->H))",
@@ -38,6 +38,10 @@ MUTANTS = {
     "zdrop_signed_distance": ("(d > dbest ? d - dbest : dbest - d)", "(d - dbest)"),
     "zdrop_tie_smallest_i_flipped": ("(tmp.H == nbest && d > ndbest)", "(tmp.H == nbest && d < ndbest)"),
     "zdrop_best_diagonal_frozen": ("      dbest = ndbest;\n", "\n"),
+    "mid_E_opens_from_H": ("out->E = (mid ? l->M : l->H) - o - e;", "out->E = l->H - o - e;"),
+    "mid_F_opens_from_H": ("out->F = (mid ? u->M : u->H) - o - e;", "out->F = u->H - o - e;"),
+    "mid_walk_skips_forced_diagonal": ("if (!ch.e_ext) state = after_open;",
+                                       "if (!ch.e_ext) state = 0;"),
     "cells_count_boundary": ("      if (i >= 1 && j >= 1) ++*cells;\n      if (alive)",
                              "      ++*cells;\n      if (alive)"),
 }

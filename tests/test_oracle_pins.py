@@ -21,7 +21,8 @@ import numpy as np
 import pytest
 
 import oracle
-from pins import brute_global, brute_local, cigar_from_str, levenshtein, rescore_cigar
+from pins import (brute_global, brute_global_mid, brute_local, brute_local_mid, cigar_from_str,
+                  levenshtein, mid_ok, rescore_cigar)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DNA_S = np.array([[2, -4, -4, -4], [-4, 2, -4, -4], [-4, -4, 2, -4], [-4, -4, -4, 2]], np.int8)
@@ -229,7 +230,7 @@ def test_hand_worked(case, oracle_lib):
     np.fill_diagonal(S, case["match"])
     kw = dict(mode=case["mode"], affine=case["affine"], gap_open=case["gap_open"],
               gap_extend=case["gap_extend"], xdrop=case.get("xdrop"), zdrop=case.get("zdrop"),
-              xdrop_running=case.get("running", False))
+              xdrop_running=case.get("running", False), mid=case.get("mid", False))
     res = oracle.align(q, r, S, **kw)
     assert res["score"] == case["score"]
     assert res["status"] == case["status"]
@@ -311,3 +312,67 @@ def test_running_threshold(mode, zd, oracle_lib):
             lit_alive = {tuple(x) for x, a in zip(ij_l.tolist(), al_l) if a}
             assert {tuple(x) for x in ij_r.tolist()} <= lit_cells
             assert {tuple(x) for x, a in zip(ij_r.tolist(), al_r) if a} <= lit_alive
+
+
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_mid_brute_force(mode, oracle_lib):
+    """Table 1's M/I/D form against every alignment path of its grammar (no
+    insertion next to a deletion), asymmetric scores, M, N <= 5; the CIGAR obeys
+    the grammar and re-scores to the score."""
+    rng = np.random.default_rng(41)
+    for t in range(60):
+        S = _asym(rng, 3)
+        o, e = int(rng.integers(0, 4)), int(rng.integers(1, 3))
+        M, N = int(rng.integers(0 if mode == "global" else 1, 6)), int(rng.integers(1, 6))
+        q = rng.integers(0, 3, size=M).astype(np.uint8)
+        r = rng.integers(0, 3, size=N).astype(np.uint8)
+        res = oracle.align(q, r, S, mode=mode, affine=True, gap_open=o, gap_extend=e, mid=True)
+        want = (brute_global_mid if mode == "global" else brute_local_mid)(
+            q.tolist(), r.tolist(), S, o, e)
+        assert res["score"] == want, (t, q, r, o, e)
+        if res["status"] == 0:
+            _check_cigar(res, q, r, S, o, e)
+            steps = "".join({1: "V", 2: "H", 7: "M", 8: "M"}[op & 15] * (op >> 4)
+                            for op in res["cigar"].tolist())
+            assert mid_ok(steps)
+
+
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_mid_brute_force_cheap_gaps(mode, oracle_lib):
+    """Scores where a deletion beside an insertion would beat a mismatch (match 1,
+    mismatch -5, open 0 or 1, extend 1): the M/I/D form must still keep them
+    apart, and the H/E/F form must find the pairs that use them."""
+    rng = np.random.default_rng(43)
+    S = np.array([[1, -5, -5], [-5, 1, -5], [-5, -5, 1]], np.int8)
+    differ = 0
+    for t in range(200):
+        o = int(rng.integers(0, 2))
+        M, N = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+        q = rng.integers(0, 3, size=M).astype(np.uint8)
+        r = rng.integers(0, 3, size=N).astype(np.uint8)
+        res = oracle.align(q, r, S, mode=mode, affine=True, gap_open=o, gap_extend=1, mid=True)
+        want = (brute_global_mid if mode == "global" else brute_local_mid)(
+            q.tolist(), r.tolist(), S, o, 1)
+        assert res["score"] == want, (t, q, r, o)
+        if res["status"] == 0:
+            _check_cigar(res, q, r, S, o, 1)
+            steps = "".join({1: "V", 2: "H", 7: "M", 8: "M"}[op & 15] * (op >> 4)
+                            for op in res["cigar"].tolist())
+            assert mid_ok(steps), (t, oracle.cigar_str(res["cigar"]))
+        hef = oracle.align(q, r, S, mode=mode, affine=True, gap_open=o, gap_extend=1)
+        differ += hef["score"] != res["score"]
+    if mode == "global":  # local alignments end before such regions anyway
+        assert differ > 0
+
+
+def test_mid_equals_hef_on_dna_scoring(oracle_lib):
+    """With the DNA scoring of the workloads (+2/-4, open 4, extend 2) a deletion
+    next to an insertion never beats a mismatch, so both forms score alike."""
+    import synth
+    S = synth.dna_subst(2, -4)
+    qs, rs = synth.random_pairs(60, 80, 80, 4, seed=42, related=0.7)
+    for q, r in zip(qs, rs):
+        for mode in ("global", "local"):
+            a = oracle.align(q, r, S, mode=mode, affine=True, gap_open=4, gap_extend=2)
+            b = oracle.align(q, r, S, mode=mode, affine=True, gap_open=4, gap_extend=2, mid=True)
+            assert a["score"] == b["score"]
