@@ -85,10 +85,20 @@ enum {
   FILTR_ST_TIMEOUT = 5      /* a bounded wait of the intra-pair kernel ran out (no result) */
 };
 
+/* Table 1's own affine form: M(i,j) = max(M, I, D)(i-1, j-1) + s, I and D open
+ * from M only (o + e) and extend themselves (e), so an insertion never touches a
+ * deletion (the Gotoh H/E/F form, affine = 1, opens gaps from H = max(M, I, D)).
+ * It runs on the antidiagonal sweep: with FILTR_PRUNE_XDROP (running or not),
+ * the widened band, or no pruning (no threshold; a pair whose live antidiagonal
+ * outgrows 8192 cells reports FILTR_ST_TOO_WIDE).  Not with Z-drop, the literal
+ * band, filtr_align_long or filtr_graph_* (FILTR_ERR_UNSUPPORTED). */
+#define FILTR_AFFINE_MID 2
+
 typedef struct {
   int32_t mode;          /* FILTR_GLOBAL or FILTR_LOCAL */
   int32_t alphabet;      /* FILTR_ALPHA_DNA or FILTR_ALPHA_PROTEIN */
-  int32_t affine;        /* 1: Gotoh H/E/F; 0: linear gap (gap_open ignored) */
+  int32_t affine;        /* 1: Gotoh H/E/F; 0: linear gap (gap_open ignored);
+                            FILTR_AFFINE_MID: Table 1's M/I/D form (see below) */
   int32_t gap_open;      /* >= 0 */
   int32_t gap_extend;    /* >= 0 */
   const int8_t *subst;   /* HOST pointer: alphabet*alphabet scores, subst[q_code*alphabet + r_code];

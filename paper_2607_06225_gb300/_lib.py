@@ -190,13 +190,13 @@ def check(rc: int, what: str = ""):
 
 def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, band=None,
                 band_literal=False, xdrop=None, zdrop=None, traceback=False, precision=PREC_AUTO,
-                xdrop_running=False, **_ignored) -> Params:
+                xdrop_running=False, mid=False, **_ignored) -> Params:
     """Build a filtr_params block; the substitution table is kept alive on it."""
     s = np.ascontiguousarray(np.asarray(subst, dtype=np.int8))
     p = Params()
     p.mode = LOCAL if mode in ("local", LOCAL) else GLOBAL
     p.alphabet = int(s.shape[0])
-    p.affine = 1 if affine else 0
+    p.affine = (2 if mid else 1) if affine else 0  # 2: FILTR_AFFINE_MID
     p.gap_open = int(gap_open)
     p.gap_extend = int(gap_extend)
     p.subst = s.ctypes.data_as(C.POINTER(C.c_int8))

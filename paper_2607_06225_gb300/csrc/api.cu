@@ -46,8 +46,8 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
     set_error("alphabet must be 4 (DNA) or 20 (protein)");
     return FILTR_ERR_INVALID;
   }
-  if (p->affine != 0 && p->affine != 1) {
-    set_error("affine must be 0 or 1");
+  if (p->affine != 0 && p->affine != 1 && p->affine != FILTR_AFFINE_MID) {
+    set_error("affine must be 0, 1 or FILTR_AFFINE_MID");
     return FILTR_ERR_INVALID;
   }
   if (p->gap_extend < 0 || (p->affine && p->gap_open < 0) || p->gap_extend > (1 << 20) ||
@@ -71,6 +71,11 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
     set_error("FILTR_PRUNE_XDROP and FILTR_PRUNE_ZDROP exclude each other");
     return FILTR_ERR_INVALID;
   }
+  const bool mid = p->affine == FILTR_AFFINE_MID;
+  if (mid && (zd || (p->prune & FILTR_PRUNE_BAND_LITERAL))) {
+    set_error("the M/I/D form runs with X-drop or the widened band, not Z-drop or the literal band");
+    return FILTR_ERR_UNSUPPORTED;
+  }
   if ((p->prune & FILTR_PRUNE_XDROP_RUNNING) && !xd) {
     set_error("FILTR_PRUNE_XDROP_RUNNING needs FILTR_PRUNE_XDROP or FILTR_PRUNE_ZDROP");
     return FILTR_ERR_INVALID;
@@ -93,17 +98,20 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
   }
   memset(sp, 0, sizeof *sp);
   sp->mode = p->mode;
-  sp->affine = p->affine;
+  sp->affine = p->affine ? 1 : 0;
   sp->o = p->affine ? p->gap_open : 0;
   sp->e = p->gap_extend;
   sp->alphabet = p->alphabet;
   sp->use_band = band ? 1 : 0;
   sp->band_literal = (p->prune & FILTR_PRUNE_BAND_LITERAL) ? 1 : 0;
   sp->band = band ? p->band : 0;
-  sp->use_xdrop = xd ? 1 : 0;
+  // the M/I/D form runs on the antidiagonal sweep, without a threshold unless
+  // X-drop is asked for
+  sp->use_xdrop = (xd || mid) ? 1 : 0;
   sp->zdrop = zd ? 1 : 0;
   sp->xrun = (p->prune & FILTR_PRUNE_XDROP_RUNNING) ? 1 : 0;
-  sp->xdrop = xd ? p->xdrop : 0;
+  sp->xdrop = xd ? p->xdrop : (mid ? FILTR_XDROP_INF : 0);
+  sp->mid = mid ? 1 : 0;
   sp->traceback = p->traceback;
   sp->precision = p->precision;
   sp->smin = 127;

@@ -114,6 +114,7 @@ struct ScoreParams {
   int32_t use_xdrop, xdrop;    // X-drop or Z-drop sweep, threshold
   int32_t zdrop;               // 1: Z-drop (distance from the best diagonal lowers the threshold)
   int32_t xrun;                // 1: threshold from the running best of all antidiagonals so far
+  int32_t mid;                 // 1: Table 1's M/I/D form (gaps open from M), on the antidiagonal sweep
   int32_t traceback;
   int32_t precision;           // FILTR_PREC_*
   int32_t smin, smax;          // smallest / largest substitution score

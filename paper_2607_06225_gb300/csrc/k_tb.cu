@@ -190,10 +190,10 @@ __device__ __forceinline__ void walk_thread(const WalkArgs &a, const BatchDev &b
         v += e;
       } else {
         v += oe;
-        state = 0;
+        state = a.sp.mid ? 3 : 0;
       }
       --j;
-    } else {
+    } else if (state == 2) {
       if (i == 0) {
         state = 0;
         continue;
@@ -206,9 +206,17 @@ __device__ __forceinline__ void walk_thread(const WalkArgs &a, const BatchDev &b
         v += e;
       } else {
         v += oe;
-        state = 0;
+        state = a.sp.mid ? 3 : 0;
       }
       --i;
+    } else {  // state 3 (M/I/D): the gap opened from M here, a diagonal step
+      if (i == 0 && j == 0) break;
+      const int qc = q[i - 1], rc = r[j - 1];
+      em.put(qc == rc ? OP_EQ : OP_X, 1);
+      v -= a.sp.subst[qc * A + rc];
+      --i;
+      --j;
+      state = 0;
     }
   }
   em.flush();
@@ -245,6 +253,7 @@ struct WalkCore {
   bool local;
   int i, j, v, state;
   Emitter em;
+  bool mid = false;  // Table 1's M/I/D: a gap that opened leaves through a diagonal step (state 3)
 };
 
 // Walks until the alignment's start is reached (returns true), or until the
@@ -295,10 +304,10 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
         w.v += w.e;
       } else {
         w.v += w.oe;
-        w.state = 0;
+        w.state = w.mid ? 3 : 0;
       }
       --w.j;
-    } else {
+    } else if (w.state == 2) {
       if (w.i == 0) {
         w.state = 0;
         continue;
@@ -310,9 +319,17 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
         w.v += w.e;
       } else {
         w.v += w.oe;
-        w.state = 0;
+        w.state = w.mid ? 3 : 0;
       }
       --w.i;
+    } else {  // state 3: the gap opened from M here, so this cell is a diagonal step
+      if (w.i == 0 && w.j == 0) return true;
+      const int qc = w.q[w.i - 1], rc = w.r[w.j - 1];
+      w.em.put(qc == rc ? OP_EQ : OP_X, 1);
+      w.v -= w.subst[qc * w.A + rc];
+      --w.i;
+      --w.j;
+      w.state = 0;
     }
   }
 }
@@ -400,7 +417,7 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
   const int wpk = xd_words_per_k(L.warps, L.R);
   WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
-             Emitter{a.stage + a.stage_off[p], 0, -1, 0}};
+             Emitter{a.stage + a.stage_off[p], 0, -1, 0}, a.sp.mid != 0};
   XdCache &C = cache[wib];
   bool done = false;
   for (;;) {
@@ -473,7 +490,7 @@ __global__ void __launch_bounds__(128) k_walk_tw(const WalkArgs a) {
   const PackGeom pg{L.R, (int64_t)pack_strip_tb_words(1, N, L.R)};
   WalkCore w{b.q_seq + b.q_off[p], b.r_seq + b.r_off[p], a.sp.subst, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
-             Emitter{a.stage + a.stage_off[p], 0, -1, 0}};
+             Emitter{a.stage + a.stage_off[p], 0, -1, 0}, a.sp.mid != 0};
   TileCache &C = cache[wib];
   bool done = false;
   auto cell = [&](int ii, int jj) -> uint8_t {
@@ -515,7 +532,7 @@ __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int3
   const uint32_t p = a.order[0];
   WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, st.i, st.j, st.v, st.state,
-             Emitter{a.stage + a.stage_off[p], st.n, st.cur, st.run}};
+             Emitter{a.stage + a.stage_off[p], st.n, st.cur, st.run}, a.sp.mid != 0};
   bool done = false;
   for (;;) {
     const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
@@ -560,7 +577,7 @@ __global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
   }
   WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
-             Emitter{a.stage + a.stage_off[p], 0, -1, 0}};
+             Emitter{a.stage + a.stage_off[p], 0, -1, 0}, a.sp.mid != 0};
   bool done = false;
   for (;;) {
     const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);

@@ -7,17 +7,22 @@ namespace filtr {
 cudaError_t launch_zdrop_w(const FullArgs &a, int W, int grid, uint32_t *overflow,
                            uint32_t *n_overflow, cudaStream_t s);
 int zdrop_blocks_per_sm(int W, const ScoreParams &sp);
+cudaError_t launch_mid_w(const FullArgs &a, int W, int grid, uint32_t *overflow,
+                         uint32_t *n_overflow, cudaStream_t s);
+int mid_blocks_per_sm(int W, const ScoreParams &sp);
 
 int xd_pairs_per_cta(int W) { return W == 1 ? 4 : 1; }
 
 int xd_max_blocks_per_sm(int W, const ScoreParams &sp) {
-  return sp.zdrop ? zdrop_blocks_per_sm(W, sp) : occ_any_w<false>(W, sp);
+  if (sp.mid) return mid_blocks_per_sm(W, sp);
+  return sp.zdrop ? zdrop_blocks_per_sm(W, sp) : occ_any_w<0>(W, sp);
 }
 
 cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow, uint32_t *n_overflow,
                          cudaStream_t s) {
+  if (a.sp.mid) return launch_mid_w(a, W, grid, overflow, n_overflow, s);
   if (a.sp.zdrop) return launch_zdrop_w(a, W, grid, overflow, n_overflow, s);
-  return launch_any_w<false>(a, W, grid, overflow, n_overflow, s);
+  return launch_any_w<0>(a, W, grid, overflow, n_overflow, s);
 }
 
 }  // namespace filtr

@@ -1,7 +1,9 @@
 // k_xdrop_impl.cuh -- exact antidiagonal sweep for X-drop pruning (Sec. 5.2 / 7.2) and
 // Z-drop pruning (Sec. 9.3), optionally intersected with a static band (Sec. 7.1).
-// Instantiated by k_xdrop.cu (X-drop) and k_zdrop.cu (Z-drop), which compile in
-// parallel.
+// Instantiated by k_xdrop.cu (X-drop), k_zdrop.cu (Z-drop) and k_xdrop_mid.cu
+// (X-drop over Table 1's M/I/D recurrence, where gaps open from the diagonal
+// state M: one more state array, G, carries M of antidiagonal k-1), which
+// compile in parallel.
 //
 // X-drop decides antidiagonal k from best(k-1), the largest unpruned H of
 // antidiagonal k-1 (with FILTR_PRUNE_XDROP_RUNNING the largest of every
@@ -40,6 +42,7 @@ constexpr int XS = 8;  // slots per thread
 
 struct Edge {
   int H1, E1, F1, H2;
+  int G1;  // M/I/D: the diagonal state M on antidiagonal k-1 (gaps open from it)
 };
 
 template <int W>
@@ -66,12 +69,14 @@ __device__ __forceinline__ void codes_down(uint32_t (&w)[2], uint32_t in) {
   w[1] = (w[1] >> 8) | ((in & 0xffu) << 24);
 }
 
-template <int W, bool LOCAL, bool AFFINE, bool TB, bool ZD, int DELTA, int DOFF>
+template <int W, bool LOCAL, bool AFFINE, bool TB, int VAR, int DELTA, int DOFF>
 __device__ __forceinline__ void xd_cells(
-    int (&H1)[XS], int (&E1)[XS], int (&F1)[XS], int (&H2)[XS], int (&Hn)[XS], int (&En)[XS],
-    int (&Fn)[XS], const Edge &pv, const Edge &nx, const uint32_t (&qw)[2], const uint32_t (&rw)[2],
-    const int8_t *s_sub, int A, int o, int e, int vA, int vB, int thr, int zx, uint32_t &nibs,
-    int &tmax, int &tlo, int &thi, int &tbest_slot) {
+    int (&H1)[XS], int (&E1)[XS], int (&F1)[XS], int (&H2)[XS], int (&G1)[XS], int (&Hn)[XS],
+    int (&En)[XS], int (&Fn)[XS], int (&Gn)[XS], const Edge &pv, const Edge &nx,
+    const uint32_t (&qw)[2], const uint32_t (&rw)[2], const int8_t *s_sub, int A, int o, int e,
+    int vA, int vB, int thr, int zx, uint32_t &nibs, int &tmax, int &tlo, int &thi,
+    int &tbest_slot) {
+  constexpr bool ZD = VAR == 1, MIDF = VAR == 2;
   const int oe = o + e;
 #pragma unroll
   for (int s = 0; s < XS; ++s) {
@@ -79,13 +84,16 @@ __device__ __forceinline__ void xd_cells(
     const int Hl = (ls < 0) ? pv.H1 : H1[ls < 0 ? 0 : ls];
     const int El = (ls < 0) ? pv.E1 : E1[ls < 0 ? 0 : ls];
     const int Hu = (us >= XS) ? nx.H1 : H1[us >= XS ? XS - 1 : us];
+    // where a gap opens: H (Gotoh H/E/F) or the diagonal state M (Table 1's M/I/D)
+    const int Ol = MIDF ? ((ls < 0) ? pv.G1 : G1[ls < 0 ? 0 : ls]) : Hl;
+    const int Ou = MIDF ? ((us >= XS) ? nx.G1 : G1[us >= XS ? XS - 1 : us]) : Hu;
     const int Fu = (us >= XS) ? nx.F1 : F1[us >= XS ? XS - 1 : us];
     const int Hd = (ds < 0) ? pv.H2 : ((ds >= XS) ? nx.H2 : H2[ds < 0 ? 0 : (ds >= XS ? XS - 1 : ds)]);
     const int sc = s_sub[code_at(qw, s) * A + code_at(rw, s)];
     const int D = Hd + sc;
     int E, F, DE, H;
     if (AFFINE) {
-      const int Hol = Hl - oe, Eext = El - e, Hou = Hu - oe, Fext = Fu - e;
+      const int Hol = Ol - oe, Eext = El - e, Hou = Ou - oe, Fext = Fu - e;
       E = max(Hol, Eext);
       F = max(Hou, Fext);
       DE = max(D, E);
@@ -103,6 +111,7 @@ __device__ __forceinline__ void xd_cells(
     // antidiagonal's best diagonal, |d - d_best| = |zx + 2s|
     const int thr_s = ZD ? max(thr - abs(zx + 2 * s), NEG_HALF) : thr;
     const bool alive = (s >= vA) && (s <= vB) && (H >= thr_s);
+    if (MIDF) Gn[s] = alive ? D : NEG;
     if (!alive) {
       H = NEG;
       E = NEG;
@@ -123,7 +132,7 @@ __device__ __forceinline__ void xd_cells(
   }
 }
 
-template <int W, bool LOCAL, bool AFFINE, bool TB, bool ZD>
+template <int W, bool LOCAL, bool AFFINE, bool TB, int VAR>
 __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs a, uint32_t *overflow,
                                                               uint32_t *n_overflow) {
   constexpr int WIN = W * 32 * XS;
@@ -216,15 +225,18 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     }
 
     // ---- antidiagonal 0: the cell (0, 0) ---------------------------------------
-    int H1[XS], E1[XS], F1[XS], H2[XS];
+    constexpr bool ZD = VAR == 1, MIDF = VAR == 2;
+    int H1[XS], E1[XS], F1[XS], H2[XS], G1[XS];
 #pragma unroll
     for (int s = 0; s < XS; ++s) {
       H1[s] = NEG;
       E1[s] = NEG;
       F1[s] = NEG;
       H2[s] = NEG;
+      G1[s] = NEG;
     }
     if (tid == 0) H1[0] = 0;
+    if (MIDF && tid == 0) G1[0] = 0;  // every path starts at the origin in the M state
     int c = 0, dprev = 0;  // window origin and its last move
     int best = 0, lo = 0, hi = 0, dbest = 0;  // dbest: diagonal of the best cell (Z-drop)
     // running best cell of this thread: value, i, j (largest H, then smallest i, then j)
@@ -277,8 +289,8 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
     bool ended = false;  // the sweep stopped (empty antidiagonal or k = M + N)
     if (W > 1) {
       const int b0 = (k_first - 1) & 1;
-      if (lane == 0) sh.first[b0][warp] = Edge{H1[0], E1[0], F1[0], H2[0]};
-      if (lane == 31) sh.last[b0][warp] = Edge{H1[XS - 1], E1[XS - 1], F1[XS - 1], H2[XS - 1]};
+      if (lane == 0) sh.first[b0][warp] = Edge{H1[0], E1[0], F1[0], H2[0], G1[0]};
+      if (lane == 31) sh.last[b0][warp] = Edge{H1[XS - 1], E1[XS - 1], F1[XS - 1], H2[XS - 1], G1[XS - 1]};
       __syncthreads();
     }
 
@@ -343,18 +355,20 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       nx.F1 = __shfl_down_sync(FULLMASK, F1[0], 1);
       nx.E1 = NEG;
       nx.H2 = __shfl_down_sync(FULLMASK, H2[0], 1);
+      pv.G1 = MIDF ? __shfl_up_sync(FULLMASK, G1[XS - 1], 1) : NEG;
+      nx.G1 = MIDF ? __shfl_down_sync(FULLMASK, G1[0], 1) : NEG;
       const int buf = (k - 1) & 1;
       if (lane == 0) {
         if (W > 1 && warp > 0)
           pv = sh.last[buf][warp - 1];
         else
-          pv = Edge{NEG, NEG, NEG, NEG};
+          pv = Edge{NEG, NEG, NEG, NEG, NEG};
       }
       if (lane == 31) {
         if (W > 1 && warp < W - 1)
           nx = sh.first[buf][warp + 1];
         else
-          nx = Edge{NEG, NEG, NEG, NEG};
+          nx = Edge{NEG, NEG, NEG, NEG, NEG};
       }
 
       // ---- cells of antidiagonal k -------------------------------------------
@@ -363,7 +377,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
       int thr = NEG_HALF;
       if (!no_thresh) thr = (int)max((long long)best - (long long)X, (long long)NEG_HALF);
       const int zx = ZD ? 2 * (cn + base_slot) - k - dbest : 0;
-      int Hn[XS], En[XS], Fn[XS];
+      int Hn[XS], En[XS], Fn[XS], Gn[XS];
       uint32_t nibs = 0;
       int tmax = INT_MIN, tlo = INT_MAX, thi = INT_MIN, tbs = -1;
       const int doff = delta + dprev - 1;
@@ -375,20 +389,21 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
           Hn[s] = NEG;
           En[s] = NEG;
           Fn[s] = NEG;
+          Gn[s] = NEG;
         }
       } else if (delta == 1) {
         if (doff == 0)
-          xd_cells<W, LOCAL, AFFINE, TB, ZD, 1, 0>(H1, E1, F1, H2, Hn, En, Fn, pv, nx, qw, rw, s_sub, A,
+          xd_cells<W, LOCAL, AFFINE, TB, VAR, 1, 0>(H1, E1, F1, H2, G1, Hn, En, Fn, Gn, pv, nx, qw, rw, s_sub, A,
                                               o, e, vA, vB, thr, zx, nibs, tmax, tlo, thi, tbs);
         else
-          xd_cells<W, LOCAL, AFFINE, TB, ZD, 1, 1>(H1, E1, F1, H2, Hn, En, Fn, pv, nx, qw, rw, s_sub, A,
+          xd_cells<W, LOCAL, AFFINE, TB, VAR, 1, 1>(H1, E1, F1, H2, G1, Hn, En, Fn, Gn, pv, nx, qw, rw, s_sub, A,
                                               o, e, vA, vB, thr, zx, nibs, tmax, tlo, thi, tbs);
       } else {
         if (doff == 0)
-          xd_cells<W, LOCAL, AFFINE, TB, ZD, 0, 0>(H1, E1, F1, H2, Hn, En, Fn, pv, nx, qw, rw, s_sub, A,
+          xd_cells<W, LOCAL, AFFINE, TB, VAR, 0, 0>(H1, E1, F1, H2, G1, Hn, En, Fn, Gn, pv, nx, qw, rw, s_sub, A,
                                               o, e, vA, vB, thr, zx, nibs, tmax, tlo, thi, tbs);
         else
-          xd_cells<W, LOCAL, AFFINE, TB, ZD, 0, -1>(H1, E1, F1, H2, Hn, En, Fn, pv, nx, qw, rw, s_sub,
+          xd_cells<W, LOCAL, AFFINE, TB, VAR, 0, -1>(H1, E1, F1, H2, G1, Hn, En, Fn, Gn, pv, nx, qw, rw, s_sub,
                                                A, o, e, vA, vB, thr, zx, nibs, tmax, tlo, thi, tbs);
       }
 #pragma unroll
@@ -397,6 +412,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         H1[s] = Hn[s];
         E1[s] = En[s];
         F1[s] = Fn[s];
+        if (MIDF) G1[s] = Gn[s];
       }
       if (TB) {
         const int64_t row = (ckmode >= 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
@@ -443,9 +459,9 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
           sh.red[nb][warp][1] = wlo;
           sh.red[nb][warp][2] = whi;
           if (ZD) sh.red[nb][warp][3] = wbs;
-          sh.first[nb][warp] = Edge{H1[0], E1[0], F1[0], H2[0]};
+          sh.first[nb][warp] = Edge{H1[0], E1[0], F1[0], H2[0], G1[0]};
         }
-        if (lane == 31) sh.last[nb][warp] = Edge{H1[XS - 1], E1[XS - 1], F1[XS - 1], H2[XS - 1]};
+        if (lane == 31) sh.last[nb][warp] = Edge{H1[XS - 1], E1[XS - 1], F1[XS - 1], H2[XS - 1], G1[XS - 1]};
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -623,71 +639,84 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
   }
 }
 
-template <int W, bool LOCAL, bool AFFINE, bool TB, bool ZD>
+template <int W, bool LOCAL, bool AFFINE, bool TB, int VAR>
 cudaError_t launch_w(const FullArgs &a, int grid, uint32_t *ovf, uint32_t *novf, cudaStream_t s) {
-  k_xdrop<W, LOCAL, AFFINE, TB, ZD><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf);
+  k_xdrop<W, LOCAL, AFFINE, TB, VAR><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf);
   return cudaGetLastError();
 }
 
-template <int W, bool ZD>
+template <int W, int VAR>
 cudaError_t dispatch_w(const FullArgs &a, int grid, uint32_t *ovf, uint32_t *novf, cudaStream_t s) {
   const bool L = a.sp.mode == FILTR_LOCAL, AF = a.sp.affine != 0, T = a.sp.traceback != 0;
+  if constexpr (VAR == 2) {  // M/I/D: affine gaps only
+    if (!AF) return cudaErrorInvalidValue;
+    if (L)
+      return T ? launch_w<W, true, true, true, VAR>(a, grid, ovf, novf, s)
+               : launch_w<W, true, true, false, VAR>(a, grid, ovf, novf, s);
+    return T ? launch_w<W, false, true, true, VAR>(a, grid, ovf, novf, s)
+             : launch_w<W, false, true, false, VAR>(a, grid, ovf, novf, s);
+  }
   if (L) {
     if (AF)
-      return T ? launch_w<W, true, true, true, ZD>(a, grid, ovf, novf, s)
-               : launch_w<W, true, true, false, ZD>(a, grid, ovf, novf, s);
-    return T ? launch_w<W, true, false, true, ZD>(a, grid, ovf, novf, s)
-             : launch_w<W, true, false, false, ZD>(a, grid, ovf, novf, s);
+      return T ? launch_w<W, true, true, true, VAR>(a, grid, ovf, novf, s)
+               : launch_w<W, true, true, false, VAR>(a, grid, ovf, novf, s);
+    return T ? launch_w<W, true, false, true, VAR>(a, grid, ovf, novf, s)
+             : launch_w<W, true, false, false, VAR>(a, grid, ovf, novf, s);
   }
   if (AF)
-    return T ? launch_w<W, false, true, true, ZD>(a, grid, ovf, novf, s)
-             : launch_w<W, false, true, false, ZD>(a, grid, ovf, novf, s);
-  return T ? launch_w<W, false, false, true, ZD>(a, grid, ovf, novf, s)
-           : launch_w<W, false, false, false, ZD>(a, grid, ovf, novf, s);
+    return T ? launch_w<W, false, true, true, VAR>(a, grid, ovf, novf, s)
+             : launch_w<W, false, true, false, VAR>(a, grid, ovf, novf, s);
+  return T ? launch_w<W, false, false, true, VAR>(a, grid, ovf, novf, s)
+           : launch_w<W, false, false, false, VAR>(a, grid, ovf, novf, s);
 }
 
-template <int W, bool LOCAL, bool AFFINE, bool TB, bool ZD>
+template <int W, bool LOCAL, bool AFFINE, bool TB, int VAR>
 int occ_xd() {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_xdrop<W, LOCAL, AFFINE, TB, ZD>,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_xdrop<W, LOCAL, AFFINE, TB, VAR>,
                                                 W == 1 ? 128 : W * 32, 0);
   return nb;
 }
 
-template <int W, bool ZD>
+template <int W, int VAR>
 int occ_w(const ScoreParams &sp) {
   const bool L = sp.mode == FILTR_LOCAL, AF = sp.affine != 0, T = sp.traceback != 0;
-  if (L) {
-    if (AF) return T ? occ_xd<W, true, true, true, ZD>() : occ_xd<W, true, true, false, ZD>();
-    return T ? occ_xd<W, true, false, true, ZD>() : occ_xd<W, true, false, false, ZD>();
+  if constexpr (VAR == 2) {
+    if (!AF) return 0;
+    if (L) return T ? occ_xd<W, true, true, true, VAR>() : occ_xd<W, true, true, false, VAR>();
+    return T ? occ_xd<W, false, true, true, VAR>() : occ_xd<W, false, true, false, VAR>();
   }
-  if (AF) return T ? occ_xd<W, false, true, true, ZD>() : occ_xd<W, false, true, false, ZD>();
-  return T ? occ_xd<W, false, false, true, ZD>() : occ_xd<W, false, false, false, ZD>();
+  if (L) {
+    if (AF) return T ? occ_xd<W, true, true, true, VAR>() : occ_xd<W, true, true, false, VAR>();
+    return T ? occ_xd<W, true, false, true, VAR>() : occ_xd<W, true, false, false, VAR>();
+  }
+  if (AF) return T ? occ_xd<W, false, true, true, VAR>() : occ_xd<W, false, true, false, VAR>();
+  return T ? occ_xd<W, false, false, true, VAR>() : occ_xd<W, false, false, false, VAR>();
 }
 
-template <bool ZD>
+template <int VAR>
 cudaError_t launch_any_w(const FullArgs &a, int W, int grid, uint32_t *ovf, uint32_t *novf,
                          cudaStream_t s) {
   switch (W) {
-    case 1: return dispatch_w<1, ZD>(a, grid, ovf, novf, s);
-    case 2: return dispatch_w<2, ZD>(a, grid, ovf, novf, s);
-    case 4: return dispatch_w<4, ZD>(a, grid, ovf, novf, s);
-    case 8: return dispatch_w<8, ZD>(a, grid, ovf, novf, s);
-    case 16: return dispatch_w<16, ZD>(a, grid, ovf, novf, s);
-    case 32: return dispatch_w<32, ZD>(a, grid, ovf, novf, s);
+    case 1: return dispatch_w<1, VAR>(a, grid, ovf, novf, s);
+    case 2: return dispatch_w<2, VAR>(a, grid, ovf, novf, s);
+    case 4: return dispatch_w<4, VAR>(a, grid, ovf, novf, s);
+    case 8: return dispatch_w<8, VAR>(a, grid, ovf, novf, s);
+    case 16: return dispatch_w<16, VAR>(a, grid, ovf, novf, s);
+    case 32: return dispatch_w<32, VAR>(a, grid, ovf, novf, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <bool ZD>
+template <int VAR>
 int occ_any_w(int W, const ScoreParams &sp) {
   switch (W) {
-    case 1: return occ_w<1, ZD>(sp);
-    case 2: return occ_w<2, ZD>(sp);
-    case 4: return occ_w<4, ZD>(sp);
-    case 8: return occ_w<8, ZD>(sp);
-    case 16: return occ_w<16, ZD>(sp);
-    case 32: return occ_w<32, ZD>(sp);
+    case 1: return occ_w<1, VAR>(sp);
+    case 2: return occ_w<2, VAR>(sp);
+    case 4: return occ_w<4, VAR>(sp);
+    case 8: return occ_w<8, VAR>(sp);
+    case 16: return occ_w<16, VAR>(sp);
+    case 32: return occ_w<32, VAR>(sp);
     default: return 0;
   }
 }

@@ -7,9 +7,9 @@ namespace filtr {
 
 cudaError_t launch_zdrop_w(const FullArgs &a, int W, int grid, uint32_t *overflow,
                            uint32_t *n_overflow, cudaStream_t s) {
-  return launch_any_w<true>(a, W, grid, overflow, n_overflow, s);
+  return launch_any_w<1>(a, W, grid, overflow, n_overflow, s);
 }
 
-int zdrop_blocks_per_sm(int W, const ScoreParams &sp) { return occ_any_w<true>(W, sp); }
+int zdrop_blocks_per_sm(int W, const ScoreParams &sp) { return occ_any_w<1>(W, sp); }
 
 }  // namespace filtr

@@ -436,6 +436,10 @@ filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const 
   ScoreParams sp;
   filtr_status rc = to_score_params(params, &sp);
   if (rc != FILTR_OK) return rc;
+  if (sp.mid) {
+    set_error("filtr_align_long: the M/I/D form runs only in filtr_align_batch");
+    return FILTR_ERR_UNSUPPORTED;
+  }
   if (!ctx || !out || (M && !q) || (N && !r) || (sp.traceback && cigar_cap && !cigar)) {
     set_error("filtr_align_long: NULL argument");
     return FILTR_ERR_INVALID;

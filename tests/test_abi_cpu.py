@@ -74,6 +74,17 @@ def test_params_check(L):
         assert L.lib().filtr_params_check(C.byref(p)) == L.OK, kw
     p = L.make_params(S, xdrop_running=True)
     assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
+    # Table 1's M/I/D form: plain, X-drop or widened band; not Z-drop or the literal band
+    for kw in (dict(), dict(xdrop=5), dict(band=8), dict(xdrop=5, xdrop_running=True)):
+        p = L.make_params(S, gap_open=4, gap_extend=2, mid=True, **kw)
+        assert p.affine == 2
+        assert L.lib().filtr_params_check(C.byref(p)) == L.OK, kw
+    for kw in (dict(zdrop=5), dict(band=8, band_literal=True)):
+        p = L.make_params(S, gap_open=4, gap_extend=2, mid=True, **kw)
+        assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_UNSUPPORTED, kw
+    p = L.make_params(S)
+    p.affine = 3
+    assert L.lib().filtr_params_check(C.byref(p)) == L.ERR_INVALID
 
 
 def test_ctx_create_without_gpu_fails_cleanly(L):

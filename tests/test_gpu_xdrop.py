@@ -177,3 +177,35 @@ def test_running_long_pair_segmented(F, ctx, recompute):
         for f in ("score", "q_end", "r_end", "status", "cells"):
             assert int(res[f]) == int(o[f]), (kind, f, int(res[f]), int(o[f]))
         assert np.array_equal(cig, o["cigar"])
+
+
+@pytest.mark.parametrize("X", [None, 6, 40])
+@pytest.mark.parametrize("mode", ["global", "local"])
+@pytest.mark.parametrize("band", [None, 16])
+def test_mid_form(F, ctx, X, mode, band):
+    """Table 1's M/I/D recurrence (FILTR_AFFINE_MID) on the antidiagonal sweep,
+    with and without an X-drop threshold and a band: bit-exact against the
+    oracle's M/I/D form, CIGARs included (unpruned pairs outgrow the first window
+    and are rerun wider)."""
+    b = mixed_pairs(300 + (X or 0), n=90)
+    run_both(F, ctx, b, dict(mode=mode, affine=True, gap_open=4, gap_extend=2, xdrop=X,
+                             band=band, mid=True, traceback=True))
+
+
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_mid_protein(F, ctx, mode):
+    """Protein scores with cheap gaps (open 0, extend 1, mismatches down to -4),
+    where an insertion next to a deletion beats a mismatch, so the M/I/D and
+    H/E/F forms part ways: the GPU follows the M/I/D oracle, with and without the
+    running X-drop threshold."""
+    P = synth.protein_pairs(n=60, lmin=30, lmax=400, seed=22)
+    for extra in (dict(), dict(xdrop=30, xdrop_running=True)):
+        sc = dict(mode=mode, affine=True, gap_open=0, gap_extend=1, mid=True, traceback=True,
+                  **extra)
+        res = run_both(F, ctx, P, sc)
+        if not extra:
+            plain = res
+    hef = oracle_batch(P, dict(mode=mode, affine=True, gap_open=0, gap_extend=1, traceback=False))[0]
+    res = plain
+    if mode == "global":
+        assert (hef["score"] != res["score"].astype(np.int64)).any()
