@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SRC_SEARCH = os.path.join(_HERE, "search.c")
+_SRC_FOLD = os.path.join(_HERE, "fold.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
@@ -62,15 +63,32 @@ SEARCH_RESULT_DTYPE = np.dtype([("distance", np.int64), ("cells", np.int64), ("n
 assert SEARCH_RESULT_DTYPE.itemsize == C.sizeof(SearchResult)
 
 
+class FoldParams(C.Structure):
+    _fields_ = [("min_loop", C.c_int64), ("use_xdrop", C.c_int32), ("xdrop", C.c_int64),
+                ("warmup", C.c_int64), ("traceback", C.c_int32)]
+
+
+class FoldResult(C.Structure):
+    _fields_ = [("score", C.c_int64), ("i_end", C.c_int64), ("j_end", C.c_int64),
+                ("status", C.c_int32), ("cells", C.c_int64), ("last_k", C.c_int64)]
+
+
+FOLD_RESULT_DTYPE = np.dtype([("score", np.int64), ("i_end", np.int64), ("j_end", np.int64),
+                              ("status", np.int32), ("pad", np.int32), ("cells", np.int64),
+                              ("last_k", np.int64)])
+assert FOLD_RESULT_DTYPE.itemsize == C.sizeof(FoldResult)
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (no CUDA)."""
     with _lock:
         stale = (not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(_SRC_SEARCH), os.path.getmtime(_HDR)))
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_SEARCH), os.path.getmtime(_SRC_FOLD),
+            os.path.getmtime(_HDR)))
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC,
-                                   _SRC_SEARCH, "-lpthread"])
+                                   _SRC_SEARCH, _SRC_FOLD, "-lpthread"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -95,6 +113,12 @@ def lib():
         L.orc_search_batch.restype = C.c_int
         L.orc_search_batch.argtypes = [C.POINTER(SearchParams), C.c_int64] + [C.c_void_p] * 6 + [
             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.orc_fold.restype = C.c_int
+        L.orc_fold.argtypes = [C.POINTER(FoldParams), C.c_void_p, C.c_int64, C.POINTER(FoldResult),
+                               C.c_void_p]
+        L.orc_fold_batch.restype = C.c_int
+        L.orc_fold_batch.argtypes = [C.POINTER(FoldParams), C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         _lib = L
     return _lib
 
@@ -266,3 +290,45 @@ def search_batch(batch, nthreads: int | None = None, traceback=True, band=None, 
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return res, ops, off
+
+
+def make_fold_params(min_loop=3, xdrop=None, warmup=15, traceback=True):
+    p = FoldParams()
+    p.min_loop = int(min_loop)
+    p.use_xdrop = 0 if xdrop is None else 1
+    p.xdrop = 0 if xdrop is None else int(xdrop)
+    p.warmup = int(warmup)
+    p.traceback = 1 if traceback else 0
+    return p
+
+
+def fold(x, min_loop=3, xdrop=None, warmup=15, traceback=True) -> dict:
+    """Nussinov fold of one RNA (codes A=0 C=1 G=2 U=3), optionally under the
+    X-drop transfer of Sec. 9.5: score, status, end cell, cells and the partner
+    of every base (-1 unpaired)."""
+    p = make_fold_params(min_loop, xdrop, warmup, traceback)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+    res = FoldResult()
+    partner = np.full(max(x.shape[0], 1), -1, dtype=np.int32)
+    rc = lib().orc_fold(C.byref(p), x.ctypes.data, x.shape[0], C.byref(res), partner.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return dict(score=res.score, i_end=res.i_end, j_end=res.j_end, status=res.status,
+                cells=res.cells, last_k=res.last_k, partner=partner[: x.shape[0]].copy())
+
+
+def fold_batch(seq, off, lens, nthreads: int | None = None, **kw):
+    """fold() over concatenated sequences; returns (results, partners)."""
+    p = make_fold_params(**kw)
+    n = int(len(lens))
+    res = np.zeros(n, dtype=FOLD_RESULT_DTYPE)
+    seq = np.ascontiguousarray(seq, dtype=np.uint8)
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    lens = np.ascontiguousarray(lens, dtype=np.uint32)
+    partner = np.full(max(int(seq.shape[0]), 1), -1, dtype=np.int32)
+    rc = lib().orc_fold_batch(C.byref(p), n, seq.ctypes.data, off.ctypes.data, lens.ctypes.data,
+                              res.ctypes.data, partner.ctypes.data,
+                              int(nthreads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return res, partner

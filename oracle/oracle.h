@@ -131,6 +131,31 @@ int orc_search_batch(const orc_search_params *p, int64_t n, const uint8_t *q_seq
                      uint32_t *ops, const uint64_t *ops_off, const uint64_t *ops_cap,
                      int nthreads);
 
+/* Nussinov folding (Table 1, RNA folding) with X-drop transferred to it
+ * (Sec. 9.5); fold.c states the readings. */
+typedef struct {
+  int64_t min_loop;   /* a pair (i, j) needs j - i - 1 >= min_loop */
+  int32_t use_xdrop;  /* 1: X-drop on the span wavefronts */
+  int64_t xdrop;      /* X >= 0 */
+  int64_t warmup;     /* spans <= warmup are never pruned */
+  int32_t traceback;  /* 1: fill partner[] */
+} orc_fold_params;
+
+typedef struct {
+  int64_t score;       /* F of the end cell: base pairs of the fold */
+  int64_t i_end, j_end;
+  int32_t status;      /* ORC_OK, or ORC_DROPPED (the end cell is the best unpruned one) */
+  int64_t cells;       /* cells evaluated, span 0 included */
+  int64_t last_k;      /* last span evaluated */
+} orc_fold_result;
+
+/* Fold one RNA (codes A=0 C=1 G=2 U=3).  partner (n entries, may be NULL)
+ * receives each base's partner or -1.  Returns 0 or -1 (bad arguments). */
+int orc_fold(const orc_fold_params *p, const uint8_t *x, int64_t n, orc_fold_result *res,
+             int32_t *partner);
+int orc_fold_batch(const orc_fold_params *p, int64_t n, const uint8_t *seq, const uint64_t *off,
+                   const uint32_t *len, orc_fold_result *res, int32_t *partner, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

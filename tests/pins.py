@@ -134,3 +134,50 @@ def cigar_from_str(s: str):
             out.append((int(num) << 4) | code[ch])
             num = ""
     return np.array(out, dtype=np.uint32)
+
+
+# ---- RNA folding ------------------------------------------------------------
+RNA_PAIRS = {(0, 3), (3, 0), (1, 2), (2, 1), (2, 3), (3, 2)}  # AU UA CG GC GU UG
+
+
+def all_structures(n: int, can_pair):
+    """Every secondary structure on positions 0..n-1 (sets of non-crossing pairs
+    (i, j) with can_pair(i, j)), as tuples of pairs; exponential, for tiny n."""
+    def rec(lo, hi):
+        if lo >= hi:
+            return [()]
+        out = [s for s in rec(lo + 1, hi)]  # lo unpaired
+        for j in range(lo + 1, hi + 1):
+            if can_pair(lo, j):
+                for inner in rec(lo + 1, j - 1):
+                    for outer in rec(j + 1, hi):
+                        out.append(((lo, j),) + inner + outer)
+        return out
+    return rec(0, n - 1)
+
+
+def brute_fold(x, min_loop: int) -> int:
+    """Largest number of base pairs over all secondary structures."""
+    def can(i, j):
+        return (int(x[i]), int(x[j])) in RNA_PAIRS and j - i - 1 >= min_loop
+    return max(len(s) for s in all_structures(len(x), can))
+
+
+def check_structure(x, partner, min_loop: int) -> int:
+    """Validate a partner array (symmetric, allowed pairs, loops, non-crossing);
+    returns its number of pairs."""
+    n = len(x)
+    pairs = []
+    for i in range(n):
+        j = int(partner[i])
+        if j < 0:
+            continue
+        assert 0 <= j < n and int(partner[j]) == i, (i, j)
+        if i < j:
+            assert (int(x[i]), int(x[j])) in RNA_PAIRS, (i, j)
+            assert j - i - 1 >= min_loop, (i, j)
+            pairs.append((i, j))
+    for a, b in pairs:
+        for c, d in pairs:
+            assert not (a < c < b < d), ((a, b), (c, d))
+    return len(pairs)

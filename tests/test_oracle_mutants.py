@@ -67,6 +67,18 @@ SEARCH_MUTANTS = {
 }
 
 
+FOLD_MUTANTS = {
+    "fold_no_wobble": ("(a == 2 && b == 3) || (a == 3 && b == 2)", "0"),
+    "fold_min_loop_off_by_one": ("j - i - 1 >= c->p->min_loop && val(c, i + 1, j - 1, &a) &&\n      (!have",
+                                 "j - i >= c->p->min_loop && val(c, i + 1, j - 1, &a) &&\n      (!have"),
+    "fold_split_skips_odd": ("for (int64_t m = i; m < j; ++m) /* two", "for (int64_t m = i; m < j; m += 2) /* two"),
+    "fold_domain_no_growth": ("int64_t dl = lo - 1 > 0 ? lo - 1 : 0", "int64_t dl = lo"),
+    "fold_prune_strict": ("f >= best - p->xdrop", "f > best - p->xdrop"),
+    "fold_warmup_exclusive": ("k <= p->warmup", "k < p->warmup"),
+    "fold_cells_skip_span0": ("int64_t cells = n, lo = 0", "int64_t cells = 0, lo = 0"),
+}
+
+
 def _run_mutant(src_name, pins, a, b, name, tmp_path):
     src = open(os.path.join(ROOT, "oracle", src_name)).read()
     assert src.count(a) >= 1, "mutation site moved; update the mutant"
@@ -90,3 +102,10 @@ def test_pins_reject_mutant(name, tmp_path):
 def test_search_pins_reject_mutant(name, tmp_path):
     a, b = SEARCH_MUTANTS[name]
     _run_mutant("search.c", "test_oracle_search_pins.py", a, b, name, tmp_path)
+
+
+
+@pytest.mark.parametrize("name", sorted(FOLD_MUTANTS))
+def test_fold_pins_reject_mutant(name, tmp_path):
+    a, b = FOLD_MUTANTS[name]
+    _run_mutant("fold.c", "test_oracle_fold_pins.py", a, b, name, tmp_path)
