@@ -74,6 +74,10 @@ def parse():
                     help="skip the search-versus-antidiagonal edit-distance table")
     ap.add_argument("--search-only", action="store_true",
                     help="run only the search-versus-antidiagonal table and print it")
+    ap.add_argument("--no-fold", action="store_true",
+                    help="skip the RNA folding X-drop transfer table")
+    ap.add_argument("--fold-only", action="store_true",
+                    help="run only the RNA folding table and print it")
     ap.add_argument("--search-cells", default=None,
                     help="table cells to run, 'length:divergence:pairs,...' (default: all nine)")
     ap.add_argument("--tune-save", default=None,
@@ -531,6 +535,94 @@ def search_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True, cells=None
             "l2": "flushed between timed steps", "steps": steps, "rows": rows}
 
 
+# Sec. 9.5's transfer of X-drop to Nussinov folding: RNA lengths (its four
+# classes span 76-500 bases), sequences per batch, thresholds.
+FOLD_LENGTHS = ((76, 2048), (120, 2048), (300, 1024), (500, 1024))
+FOLD_XS = (2, 8, 32)
+
+
+def fold_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True):
+    """Fold one batch of structured synthetic RNAs per length unpruned and
+    under X-drop (15-span warm-up): CUDA events on the stream, L2 flushed
+    between steps; cells evaluated and agreement with the unpruned fold (pair
+    count ratio and base-pair F1).  With cpu, the oracle on two sequences of
+    each length (one core)."""
+    import torch
+
+    import synth
+
+    def pairs_of(part, off, lens):
+        out = []
+        for p in range(len(lens)):
+            a, n = int(off[p]), int(lens[p])
+            pp = part[a:a + n]
+            i = np.nonzero(pp > np.arange(n))[0]
+            out.append(set(zip(i.tolist(), pp[i].tolist())))
+        return out
+
+    rows = []
+    for length, n in FOLD_LENGTHS:
+        seq, off, lens = synth.rna_structured(n, length, seed=7)
+        seq_t = torch.from_numpy(seq).to(dev)
+        off_t = torch.from_numpy(off.view(np.int64)).to(dev)
+        len_t = torch.from_numpy(lens.view(np.int32)).to(dev)
+        out_t = torch.empty(n * F.FOLD_RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        part_t = torch.empty(len(seq), dtype=torch.int32, device=dev)
+        row = {"length": length, "sequences": n}
+        ref = None
+        for X in (None,) + FOLD_XS:
+            prm = F.make_fold_params(min_loop=3, xdrop=X, warmup=15, traceback=True)
+
+            def run():
+                rc = ctx.fold_batch_ptr(prm, n, seq_t.data_ptr(), off_t.data_ptr(),
+                                        len_t.data_ptr(), out_t.data_ptr(), part_t.data_ptr(),
+                                        stream=stream.cuda_stream)
+                if rc != 0:
+                    raise F.FiltrError(rc, F.last_error())
+
+            for _ in range(max(warmup, 1)):
+                run()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            for k in range(steps):
+                flush.fill_((k + 5) & 0xFF)
+                ev[k][0].record(stream)
+                run()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in ev)[steps // 2]
+            res = out_t.cpu().numpy().view(F.FOLD_RESULT_DTYPE).copy()
+            pairs = pairs_of(part_t.cpu().numpy(), off, lens)
+            key = "unpruned" if X is None else f"x{X}"
+            entry = {"ms": ms, "sequences_per_s": n / (ms * 1e-3),
+                     "cells": int(res["cells"].sum()), "mean_pairs": float(res["score"].mean()),
+                     "dropped": int((res["status"] != 0).sum())}
+            if ref is None:
+                ref = (res, pairs)
+            else:
+                f1 = []
+                for a, b in zip(ref[1], pairs):
+                    tp = len(a & b)
+                    f1.append(1.0 if not a and not b else 2 * tp / max(len(a) + len(b), 1))
+                entry.update(speedup=row["unpruned"]["ms"] / ms,
+                             cells_fraction=entry["cells"] / row["unpruned"]["cells"],
+                             pair_ratio=float(res["score"].sum() / max(ref[0]["score"].sum(), 1)),
+                             pair_f1=float(np.mean(f1)))
+            row[key] = entry
+        if cpu:
+            import oracle
+
+            t0 = time.perf_counter()
+            ores, _ = oracle.fold_batch(seq[: 2 * length], off[:2], lens[:2], nthreads=1,
+                                        min_loop=3)
+            row["oracle_ms_per_sequence_1core"] = (time.perf_counter() - t0) * 1e3 / 2
+            assert np.array_equal(ores["score"], ref[0]["score"][:2].astype(np.int64))
+        rows.append(row)
+    return {"call": "filtr_fold_batch, traceback on, min_loop 3, warm-up 15 spans",
+            "l2": "flushed between timed steps", "steps": steps, "rows": rows}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -577,6 +669,13 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     is_long = wl == "long-pair-1m"
     tb_on = bool(sc.get("traceback"))
+    if args.fold_only:
+        if rank == 0:
+            tab = fold_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
+                             cpu=not args.no_cpu_baseline)
+            print(json.dumps({"fold_table": tab}), flush=True)
+        ctx.close()
+        return
     if args.search_only:
         if rank == 0:
             tab = search_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
@@ -702,6 +801,9 @@ def main():
         if not args.no_search and wl == "protein-sw-100k":
             line["search"] = search_table(F, ctx, 3, 1, stream, flush, dev,
                                           cpu=not args.no_cpu_baseline)
+        if not args.no_fold and wl == "protein-sw-100k":
+            line["fold"] = fold_table(F, ctx, 3, 1, stream, flush, dev,
+                                      cpu=not args.no_cpu_baseline)
         if not args.no_serve and wl == "protein-sw-100k":
             line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
         if not args.no_cpu_baseline and not is_long:

@@ -332,6 +332,52 @@ filtr_status filtr_search_batch(filtr_ctx *ctx, const filtr_search_params *param
                                 const uint64_t *r_off, const uint32_t *r_len, filtr_result *out,
                                 uint32_t *cigar, uint64_t cigar_cap, void *stream);
 
+/* ---- RNA folding with X-drop transferred to it (Sec. 9.5) -----------------
+ * Table 1's Nussinov recurrence over the triangle 0 <= i <= j < n:
+ *   F(i,j) = max(F(i+1,j), F(i,j-1), F(i+1,j-1) + 1 if i pairs j,
+ *                max over i <= m < j of F(i,m) + F(m+1,j)),  F(i,i) = 0,
+ * the largest number of nested base pairs, swept span by span (k = j - i).
+ * Bases pair as A-U, C-G or G-U (codes A=0 C=1 G=2 U=3) with at least min_loop
+ * bases between them.  With use_xdrop, the X-drop rule of alignment is reused
+ * on the spans: after the first `warmup` spans (the paper uses 15) a cell is
+ * pruned when F < best(k-1) - X, best(k-1) the largest unpruned F of the span
+ * before, and span k covers the positions [lo - 1, hi] of the unpruned cells of
+ * span k-1; the sweep stops at the first span with nothing unpruned.  The result
+ * is F(0, n-1) (FILTR_ST_OK), or, when that cell was pruned or never reached,
+ * the best unpruned cell (FILTR_ST_DROPPED: largest F, then longest span, then
+ * smallest i) with its fold. */
+#define FILTR_FOLD_MAX_LEN 4096u
+typedef struct {
+  int32_t min_loop;   /* >= 0 */
+  int32_t use_xdrop;  /* 1: X-drop on the spans */
+  int32_t xdrop;      /* X >= 0 */
+  int32_t warmup;     /* spans <= warmup are never pruned; >= 0 */
+  int32_t traceback;  /* 1: write the fold to partner */
+} filtr_fold_params;
+
+typedef struct {
+  int32_t score;        /* base pairs: F of the end cell */
+  int32_t i_end, j_end; /* the end cell (0, n-1), or the best unpruned one when DROPPED */
+  int32_t status;       /* FILTR_ST_OK or FILTR_ST_DROPPED */
+  uint64_t cells;       /* cells evaluated, span 0 included (n(n+1)/2 unpruned) */
+} filtr_fold_result;    /* 24 bytes */
+
+/* Fold n_seqs RNAs.
+ *   seq / off / len : DEVICE, codes (one byte each, 0..3), uint64 starts, uint32
+ *                     lengths (<= FILTR_FOLD_MAX_LEN)
+ *   out             : DEVICE, n_seqs filtr_fold_result
+ *   partner         : DEVICE, int32 per base at the base's own offset (same
+ *                     layout as seq): its partner's index within the sequence,
+ *                     or -1 (required with traceback, else may be NULL)
+ * One synchronisation (codes and lengths); each sequence's triangle
+ * (n(n+1)/2 words) lives in the context's workspace, in waves of sequences that
+ * fit.  FILTR_ERR_INVALID for NULL pointers, negative parameters or a code >= 4;
+ * FILTR_ERR_UNSUPPORTED for a sequence over FILTR_FOLD_MAX_LEN; FILTR_ERR_NOMEM
+ * when one triangle does not fit the workspace. */
+filtr_status filtr_fold_batch(filtr_ctx *ctx, const filtr_fold_params *params, uint32_t n_seqs,
+                              const uint8_t *seq, const uint64_t *off, const uint32_t *len,
+                              filtr_fold_result *out, int32_t *partner, void *stream);
+
 /* ---- Captured batch pipeline (CUDA graph) --------------------------------
  * The batched path of filtr_align_batch for tiled batches (full matrix or
  * static band, no X-drop), captured once as a CUDA graph and replayed per batch

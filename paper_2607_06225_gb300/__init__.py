@@ -13,11 +13,12 @@ from ._lib import (ALPHA_DNA, ALPHA_PROTEIN, ERR_CIGAR_CAP, ERR_INVALID, ERR_NOM
                    LOCAL, OK, PREC_AUTO, PREC_I16X2, PREC_I32, PRUNE_BAND, PRUNE_BAND_LITERAL,
                    PRUNE_XDROP, PRUNE_ZDROP, RESULT_DTYPE, ST_DROPPED, ST_EMPTY, ST_OK, ST_TOO_WIDE,
                    ST_UNREACHABLE, TUNE_SHAPES, XDROP_INF, Context, FiltrError, Graph, Params,
-                   SearchParams, check, last_error, lib, make_params, make_search_params)
+                   FOLD_RESULT_DTYPE, FoldParams, SearchParams, check, last_error, lib,
+                   make_fold_params, make_params, make_search_params)
 
 __all__ = ["Context", "FiltrError", "Params", "make_params", "DeviceBatch", "align_batch",
            "align_batch_host", "align_long", "RESULT_DTYPE", "lib", "last_error", "SearchParams",
-           "make_search_params", "search_batch"]
+           "make_search_params", "search_batch", "FoldParams", "make_fold_params", "fold_batch"]
 
 
 class DeviceBatch:
@@ -97,6 +98,31 @@ def search_batch(ctx: Context, params: SearchParams, batch, stream=None,
     res = results_to_numpy(out_t, db.n)
     cig = cig_t.cpu().numpy().view(np.uint32).copy() if params.traceback else np.zeros(0, np.uint32)
     return res, cig, rc
+
+
+def fold_batch(ctx: Context, params: FoldParams, seq, off, lens, stream=None, device="cuda",
+               raise_on_error=True):
+    """Fold RNAs (host numpy codes, offsets, lengths) with filtr_fold_batch.
+    Returns (results structured array, partner int32 array in seq's layout,
+    status code)."""
+    import torch
+
+    n = int(len(lens))
+    seq_t = torch.from_numpy(np.ascontiguousarray(seq, dtype=np.uint8)
+                             if len(seq) else np.zeros(1, np.uint8)).to(device)
+    off_t = torch.from_numpy(np.ascontiguousarray(off, dtype=np.uint64).view(np.int64)).to(device)
+    len_t = torch.from_numpy(np.ascontiguousarray(lens, dtype=np.uint32).view(np.int32)).to(device)
+    out_t = torch.empty(max(n, 1) * FOLD_RESULT_DTYPE.itemsize, dtype=torch.uint8, device=device)
+    part_t = torch.full((max(int(len(seq)), 1),), -1, dtype=torch.int32, device=device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = ctx.fold_batch_ptr(params, n, seq_t.data_ptr(), off_t.data_ptr(), len_t.data_ptr(),
+                            out_t.data_ptr(), part_t.data_ptr() if params.traceback else None,
+                            stream=s.cuda_stream)
+    if rc != OK and raise_on_error:
+        check(rc, "filtr_fold_batch")
+    s.synchronize()
+    res = out_t[: n * FOLD_RESULT_DTYPE.itemsize].cpu().numpy().view(FOLD_RESULT_DTYPE).copy()
+    return res, part_t.cpu().numpy()[: int(len(seq))].copy(), rc
 
 
 def graph_align(graph: Graph, batch, stream=None, cigar_cap: int | None = None, device="cuda"):

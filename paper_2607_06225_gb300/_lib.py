@@ -63,6 +63,26 @@ def make_search_params(traceback=True, band=None, adapt=None, alphabet=0) -> Sea
     return p
 
 
+class FoldParams(C.Structure):
+    _fields_ = [("min_loop", C.c_int32), ("use_xdrop", C.c_int32), ("xdrop", C.c_int32),
+                ("warmup", C.c_int32), ("traceback", C.c_int32)]
+
+
+FOLD_RESULT_DTYPE = np.dtype([("score", np.int32), ("i_end", np.int32), ("j_end", np.int32),
+                              ("status", np.int32), ("cells", np.uint64)])
+
+
+def make_fold_params(min_loop=3, xdrop=None, warmup=15, traceback=True) -> FoldParams:
+    """filtr_fold_params: xdrop=None folds unpruned."""
+    p = FoldParams()
+    p.min_loop = int(min_loop)
+    p.use_xdrop = 0 if xdrop is None else 1
+    p.xdrop = 0 if xdrop is None else int(xdrop)
+    p.warmup = int(warmup)
+    p.traceback = 1 if traceback else 0
+    return p
+
+
 class Stats(C.Structure):
     _fields_ = [("ms_validate", C.c_double), ("ms_forward", C.c_double), ("ms_walk", C.c_double),
                 ("ms_place", C.c_double), ("ms_total", C.c_double), ("launches", C.c_uint32),
@@ -114,6 +134,9 @@ def lib():
         L.filtr_pack.argtypes = [_P, C.c_uint64, C.c_int32, _P, _P, _P]
         batch_args = [C.c_void_p, C.POINTER(Params), C.c_uint32, _P, _P, _P, _P, _P, _P, _P, _P,
                       C.c_uint64]
+        L.filtr_fold_batch.restype = i32
+        L.filtr_fold_batch.argtypes = [C.c_void_p, C.POINTER(FoldParams), C.c_uint32, _P, _P, _P,
+                                       _P, _P, C.c_void_p]
         L.filtr_search_batch.restype = i32
         L.filtr_search_batch.argtypes = [C.c_void_p, C.POINTER(SearchParams), C.c_uint32, _P, _P,
                                          _P, _P, _P, _P, _P, _P, C.c_uint64, C.c_void_p]
@@ -260,6 +283,11 @@ class Context:
         return lib().filtr_search_batch(self.handle, C.byref(params), int(n), q_seq, q_off, q_len,
                                         r_seq, r_off, r_len, out, cigar, int(cigar_cap),
                                         C.c_void_p(int(stream)) if stream else None)
+
+    def fold_batch_ptr(self, params: FoldParams, n: int, seq, off, lens, out, partner,
+                       stream: int = 0) -> int:
+        return lib().filtr_fold_batch(self.handle, C.byref(params), int(n), seq, off, lens, out,
+                                      partner, C.c_void_p(int(stream)) if stream else None)
 
     def align_batch_host_ptr(self, params: Params, n: int, q_seq, q_off, q_len, r_seq, r_off,
                              r_len, out, cigar, cigar_cap: int) -> int:

@@ -320,6 +320,35 @@ def edit_pairs(n: int, length: int, div: float, seed: int = 6) -> Batch:
                 dict(mode="global", affine=False, gap_open=0, gap_extend=1, traceback=False), seed)
 
 
+def rna_structured(n: int, length: int, seed: int = 7, stems: int | None = None):
+    """Synthetic RNAs for the folding transfer (Sec. 9.5's four RNA classes of
+    76-500 bases stand-in): uniform ACGU (codes A=0 C=1 G=2 U=3), then
+    `stems` hairpin stems planted -- a segment of 4-10 bases and, 4-40 bases
+    further on, its reverse complement -- so the folds have nested helices.
+    Returns (codes, offsets, lengths) of n sequences of `length` bases."""
+    rng = np.random.default_rng(seed)
+    comp = np.array([3, 2, 1, 0], np.uint8)  # A<->U, C<->G
+    if stems is None:
+        stems = max(1, length // 40)
+    seqs = []
+    for _ in range(n):
+        x = rng.integers(0, 4, size=length).astype(np.uint8)
+        for _s in range(stems):
+            L = int(rng.integers(4, 11))
+            loop = int(rng.integers(4, 41))
+            if 2 * L + loop > length:
+                continue
+            a = int(rng.integers(0, length - 2 * L - loop + 1))
+            b = a + L + loop
+            x[b:b + L] = comp[x[a:a + L][::-1]]
+        seqs.append(x)
+    lens = np.full(n, length, dtype=np.uint32)
+    off = np.zeros(n, dtype=np.uint64)
+    if n:
+        off[1:] = np.cumsum(lens[:-1].astype(np.uint64))
+    return (np.concatenate(seqs) if n else np.zeros(0, np.uint8)), off, lens
+
+
 def random_pairs(n: int, mmax: int, nmax: int, alphabet: int, seed: int, mmin: int = 0,
                  nmin: int = 0, related: float = 0.5) -> tuple[list, list]:
     """Small random pairs for parity tests: lengths uniform in [min, max]; with

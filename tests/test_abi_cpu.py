@@ -143,3 +143,12 @@ def test_search_rejects_on_host(L):
 def test_search_ring_hook_rejects_on_host(L):
     lib = L.lib()
     assert lib.filtr_test_set_search_ring(None, 256) == L.ERR_INVALID
+
+
+def test_fold_rejects_on_host(L):
+    lib = L.lib()
+    p = L.make_fold_params(xdrop=2)
+    assert (p.min_loop, p.use_xdrop, p.xdrop, p.warmup, p.traceback) == (3, 1, 2, 15, 1)
+    assert lib.filtr_fold_batch(None, C.byref(p), 1, None, None, None, None, None,
+                                None) == L.ERR_INVALID
+    assert L.FOLD_RESULT_DTYPE.itemsize == 24
