@@ -78,6 +78,8 @@ def parse():
                     help="skip the RNA folding X-drop transfer table")
     ap.add_argument("--fold-only", action="store_true",
                     help="run only the RNA folding table and print it")
+    ap.add_argument("--fold-lengths", default=None,
+                    help="folding table rows to run, 'length:sequences,...' (default: all four)")
     ap.add_argument("--search-cells", default=None,
                     help="table cells to run, 'length:divergence:pairs,...' (default: all nine)")
     ap.add_argument("--tune-save", default=None,
@@ -541,7 +543,7 @@ FOLD_LENGTHS = ((76, 2048), (120, 2048), (300, 1024), (500, 1024))
 FOLD_XS = (2, 8, 32)
 
 
-def fold_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True):
+def fold_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True, lengths=None):
     """Fold one batch of structured synthetic RNAs per length unpruned and
     under X-drop (15-span warm-up): CUDA events on the stream, L2 flushed
     between steps; cells evaluated and agreement with the unpruned fold (pair
@@ -561,7 +563,9 @@ def fold_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True):
         return out
 
     rows = []
-    for length, n in FOLD_LENGTHS:
+    todo = FOLD_LENGTHS if not lengths else [tuple(int(v) for v in item.split(":"))
+                                             for item in lengths.split(",")]
+    for length, n in todo:
         seq, off, lens = synth.rna_structured(n, length, seed=7)
         seq_t = torch.from_numpy(seq).to(dev)
         off_t = torch.from_numpy(off.view(np.int64)).to(dev)
@@ -672,7 +676,7 @@ def main():
     if args.fold_only:
         if rank == 0:
             tab = fold_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
-                             cpu=not args.no_cpu_baseline)
+                             cpu=not args.no_cpu_baseline, lengths=args.fold_lengths)
             print(json.dumps({"fold_table": tab}), flush=True)
         ctx.close()
         return
