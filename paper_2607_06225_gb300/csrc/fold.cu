@@ -96,9 +96,17 @@ __global__ void __launch_bounds__(FOLD_THREADS) k_fold(const FoldArgs a) {
             f = max(f, inner + 1);
           }
         }
-        if (sub < k) {  // F(i, i+t) + F(i+t+1, j), t = sub, sub + G, ...
-          // o1 -> F(i, i+t) in row t, o2 -> F(i+t+1, j) in row k-1-t; both step
-          // by whole rows: row_off(a + G) - row_off(a) = G n - G a - G(G-1)/2
+        // F(i, i+t) + F(i+t+1, j): o1 -> F(i, i+t) in row t, o2 -> F(i+t+1, j)
+        // in row k-1-t, both stepped by whole rows (row t holds n - t cells)
+        if (G == 1) {
+          int o1 = i, o2 = roff[k - 1] + i + 1;
+#pragma unroll 4
+          for (int t = 0; t < k; ++t) {
+            f = max(f, D[o1] + D[o2]);
+            o1 += n - t;
+            o2 -= n - k + 1 + t;
+          }
+        } else if (sub < k) {  // t = sub, sub + G, ...: row_off(a + G) - row_off(a) = G n - G a - G(G-1)/2
           const int gg = G * (G - 1) / 2;
           int o1 = roff[sub] + i, o2 = roff[k - 1 - sub] + i + sub + 1;
           for (int t = sub; t < k; t += G) {
