@@ -265,7 +265,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    batch = synth.protein_pairs(n=min(args.pairs, max(args.cpu_sample, 1)), seed=2)
+    # a bounded sample of the protein workload (--pairs 0 means the workload's own
+    # 100,000 pairs, of which the oracle times the first cpu_sample)
+    batch = synth.protein_pairs(n=min(args.pairs or 100_000, max(args.cpu_sample, 1)), seed=2)
     sc = dict(batch.scoring)
     times, cells = [], 0
     per_step = max(1, min(args.cpu_sample // max(args.steps + args.warmup, 1), batch.n))

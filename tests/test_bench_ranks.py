@@ -53,3 +53,25 @@ def test_single_process_passthrough():
     import bench
 
     assert bench.reduce_over_ranks(3.0, 7.0, None, None) == (3.0, 7.0)
+
+
+def test_reference_arm_prints_one_line():
+    """`bench.py --impl reference` (the oracle on a bounded sample of the protein
+    workload, host cores only) prints one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--cpu-sample", "12"], cwd=root, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "GCUPS"
+    for key in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "cpu_baseline", "e2e", "config"):
+        assert key in d, key
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
