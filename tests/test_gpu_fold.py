@@ -2,7 +2,7 @@
 the X-drop transfer of Sec. 9.5) against the oracle: score, end cell, status,
 cells and the fold, bit for bit, unpruned and under several thresholds and
 warm-ups, on random and structured RNAs of 0 to 500 bases (Sec. 9.5's range),
-plus the argument checks."""
+plus several table waves in a small workspace and the argument checks."""
 import numpy as np
 import pytest
 
@@ -93,3 +93,20 @@ def test_rejects(F, ctx):
     _, _, rc = F.fold_batch(ctx, F.make_fold_params(), big, off, np.array([5000], np.uint32),
                             raise_on_error=False)
     assert rc == F.ERR_UNSUPPORTED
+
+
+def test_table_waves(F):
+    """A workspace that holds a few hundred 300-base triangles at a time: the
+    call runs in several waves with the same results as one."""
+    seq, off, lens = synth.rna_structured(600, 300, seed=74)
+    small = F.Context(0, 40 << 20)  # about 0.18 MB of table per sequence
+    try:
+        res, part, rc = F.fold_batch(small, F.make_fold_params(xdrop=2), seq, off, lens)
+        assert rc == 0, F.last_error()
+        assert small.last_stats()["waves"] > 1
+    finally:
+        small.close()
+    ores, opart = oracle.fold_batch(seq, off, lens, xdrop=2)
+    assert np.array_equal(res["score"].astype(np.int64), ores["score"])
+    assert np.array_equal(res["cells"].astype(np.int64), ores["cells"])
+    assert np.array_equal(part, opart[: len(seq)])
