@@ -7,7 +7,11 @@
  * integer scores, under the pruning rules of Sec. 7 -- a static band
  * (Sec. 7.1 prune axis lo <= diag(i,j) <= hi) and X-drop (Sec. 5.2 conditional
  * definition with the diag_lo / diag_hi domain recurrences, Sec. 7.2) -- and
- * returns score, end coordinates and the traceback as a SAM/BAM CIGAR.
+ * returns score, end coordinates and the traceback as a SAM/BAM CIGAR.  Beside
+ * it: Table 1's own M/I/D gap form (FILTR_AFFINE_MID), a running-maximum X-drop
+ * threshold (FILTR_PRUNE_XDROP_RUNNING), edit distance by the search traversal
+ * of Sec. 6.3 with WFA-Adapt (filtr_search_batch), and Nussinov RNA folding with
+ * X-drop transferred to it (Sec. 9.5, filtr_fold_batch).
  *
  * Conventions shared by every entry point
  *   - q is the query (length M, rows i = 1..M), r the reference (length N,
@@ -33,7 +37,9 @@
  *     FILTR_ST_DROPPED with the best unpruned cell as its end.
  *   - Z-drop (Sec. 9.3): as X-drop, with a cell pruned when
  *     best(k-1) - H > xdrop + |(j - i) - d_best(k-1)|, d_best(k-1) the diagonal
- *     of antidiagonal k-1's best cell (largest H, then smallest i).
+ *     of antidiagonal k-1's best cell (largest H, then smallest i).  With
+ *     FILTR_PRUNE_XDROP_RUNNING, best(k-1) becomes the best of every antidiagonal
+ *     up to k-1 (and d_best the diagonal where it was first reached).
  *   - CIGAR ops are BAM uint32 words  (len << 4) | op  with op 7 '=', 8 'X',
  *     1 'I', 2 'D'.
  *   - Errors: every function returns a filtr_status; nothing aborts and no

@@ -1,5 +1,7 @@
-"""GB300 pairwise alignment (NW / SW, linear and affine gaps, band and X-drop
-pruning, CIGAR traceback) behind the C ABI in include/filtr.h.
+"""GB300 pairwise alignment (NW / SW, linear and affine gaps -- Gotoh H/E/F or
+Table 1's M/I/D --, band, X-drop and Z-drop pruning, CIGAR traceback), edit
+distance by the search traversal (with WFA-Adapt) and Nussinov RNA folding with
+X-drop, behind the C ABI in include/filtr.h.
 
 This package is the thin Python face of libfiltr.so: it marshals numpy / torch
 buffers into C-ABI calls.  PyTorch provides device memory and streams only.
