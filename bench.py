@@ -255,8 +255,16 @@ def cpu_baseline(batch, sc, npairs):
     res, _, _ = oracle.align_batch(sub, nthreads=nth, **sc)
     dt = time.perf_counter() - t
     cells = int(res["cells"].sum())
+    # the same oracle on one core, over a sample as many times smaller as there are cores
+    n1 = max(1, len(idx) // nth)
+    t1 = time.perf_counter()
+    r1, _, _ = oracle.align_batch(batch.subset(np.arange(n1)), nthreads=1, **sc)
+    dt1 = time.perf_counter() - t1
+    c1 = int(r1["cells"].sum())
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": nth, "kind": "oracle",
-            "sample": f"first {len(idx)} of the {batch.n} pairs ({cells} cells), {dt:.1f} s"}
+            "sample": f"first {len(idx)} of the {batch.n} pairs ({cells} cells), {dt:.1f} s",
+            "one_core": {"value": c1 / dt1 / 1e9, "unit": "GCUPS",
+                         "sample": f"first {n1} pairs ({c1} cells), {dt1:.1f} s"}}
 
 
 def run_reference(args):
