@@ -7,9 +7,12 @@ local alignment, score + end coordinates + CIGAR.  Metric: GCUPS (cells whose
 recurrence was evaluated / second), inputs resident in HBM.
 
 Also reported on the same JSON line: the same call through the host-buffer
-entry point (e2e), the plain one-launch-per-pair form on a sample, the
-roofline of the forward kernel against the measured integer throughput, the
-CPU oracle on a bounded sample, and SM clocks sampled during the timed region.
+entry point (e2e), the plain one-launch-per-pair form and the whole-GPU
+per-pair form (filtr_align_long) on samples, the roofline of the forward
+kernels against the measured integer throughput of their cell widths, the CPU
+oracle on a bounded sample (its results compared with the GPU's), SM clocks
+sampled during the timed region, and under "configs" the same record for the
+short-DNA, long-read and megabase-pair workloads.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -56,13 +59,17 @@ def parse():
                     choices=["protein-sw-100k", "short-dna-1k", "long-reads-10k", "long-pair-1m",
                              "long-reads-10k-zdrop"])
     ap.add_argument("--pairs", type=int, default=0, help="0: the workload's own size")
-    ap.add_argument("--plain-sample", type=int, default=3000)
+    ap.add_argument("--plain-sample", type=int, default=0,
+                    help="pairs of the plain per-pair sample (0: the workload's default)")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workspace-gb", type=float, default=64.0)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the sub-records of the other workloads (short DNA, long reads, "
+                         "the megabase pair) on the default protein run")
     ap.add_argument("--precision", default="auto", choices=["auto", "i32", "i16x2"],
                     help="cell width of the tiled kernels (results are identical)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -245,26 +252,74 @@ def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lane
             "budget_gb": budget_gb, "lanes": lanes}
 
 
-def cpu_baseline(batch, sc, npairs):
+def trimmed_mean(xs, drop=2):
+    """Mean after dropping the `drop` smallest and largest values (the paper's
+    protocol: 10 runs, the 2 fastest and 2 slowest dropped)."""
+    xs = sorted(xs)
+    if len(xs) > 2 * drop:
+        xs = xs[drop:len(xs) - drop]
+    return sum(xs) / len(xs)
+
+
+def cpu_baseline(batch, sc, res, cig_t, npairs, time_pairs, runs=10):
+    """The oracle on the GPU machine's host cores.  First a parity pass: the oracle
+    on the first `npairs` pairs, every field and CIGAR compared with the GPU
+    step's results for those pairs.  Then the timing: `runs` runs over the first
+    `time_pairs` pairs on all cores, and as many on one core over a sample as
+    many times smaller as there are cores; each figure is the trimmed mean
+    (runs >= 10: the 2 fastest and 2 slowest dropped)."""
     import oracle
 
-    idx = np.arange(min(npairs, batch.n))
-    sub = batch.subset(idx)
     nth = os.cpu_count() or 1
+    n = min(npairs, batch.n)
+    sub = batch.subset(np.arange(n))
     t = time.perf_counter()
-    res, _, _ = oracle.align_batch(sub, nthreads=nth, **sc)
-    dt = time.perf_counter() - t
-    cells = int(res["cells"].sum())
-    # the same oracle on one core, over a sample as many times smaller as there are cores
-    n1 = max(1, len(idx) // nth)
-    t1 = time.perf_counter()
-    r1, _, _ = oracle.align_batch(batch.subset(np.arange(n1)), nthreads=1, **sc)
-    dt1 = time.perf_counter() - t1
-    c1 = int(r1["cells"].sum())
-    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": nth, "kind": "oracle",
-            "sample": f"first {len(idx)} of the {batch.n} pairs ({cells} cells), {dt:.1f} s",
-            "one_core": {"value": c1 / dt1 / 1e9, "unit": "GCUPS",
-                         "sample": f"first {n1} pairs ({c1} cells), {dt1:.1f} s"}}
+    ores, oops, ooff = oracle.align_batch(sub, nthreads=nth, **sc)
+    dt_parity = time.perf_counter() - t
+    tb = bool(sc.get("traceback"))
+    fields = ("score", "q_end", "r_end", "status", "cells")
+    eq = np.ones(n, dtype=bool)
+    for f in fields:
+        eq &= res[f][:n].astype(np.int64) == ores[f].astype(np.int64)
+    cig_eq = None
+    if tb:
+        hi = int((res["cigar_off"][:n].astype(np.int64) + res["cigar_len"][:n]).max()) if n else 0
+        gc = cig_t[:hi].cpu().numpy().view(np.uint32) if hi else np.zeros(0, np.uint32)
+        cig_eq = 0
+        for p in range(n):
+            o, k = int(res["cigar_off"][p]), int(res["cigar_len"][p])
+            a = int(ooff[p])
+            ok = (k == int(ores["n_ops"][p]) and np.array_equal(gc[o:o + k], oops[a:a + k])
+                  and int(res["q_begin"][p]) == int(ores["q_begin"][p])
+                  and int(res["r_begin"][p]) == int(ores["r_begin"][p]))
+            eq[p] &= ok
+            cig_eq += int(ok)
+    parity = {"pairs": n, "equal": int(eq.sum()), "fields": list(fields) + (["cigar", "begin"] if tb else []),
+              "cigars_equal": cig_eq, "oracle_s": round(dt_parity, 2)}
+    tn = min(time_pairs, batch.n)
+    tsub = batch.subset(np.arange(tn))
+    times, cells = [], 0
+    for _ in range(runs):
+        t = time.perf_counter()
+        r, _, _ = oracle.align_batch(tsub, nthreads=nth, **sc)
+        times.append(time.perf_counter() - t)
+        cells = int(r["cells"].sum())
+    n1 = max(1, tn // nth)
+    s1 = batch.subset(np.arange(n1))
+    times1, c1 = [], 0
+    for _ in range(runs):
+        t = time.perf_counter()
+        r1, _, _ = oracle.align_batch(s1, nthreads=1, **sc)
+        times1.append(time.perf_counter() - t)
+        c1 = int(r1["cells"].sum())
+    tm, tm1 = trimmed_mean(times), trimmed_mean(times1)
+    proto = f"trimmed mean of {runs} runs (2 fastest and 2 slowest dropped)" if runs >= 10 else \
+        f"mean of {runs} run(s)"
+    return {"value": cells / tm / 1e9, "unit": "GCUPS", "cores": nth, "nproc": nth, "kind": "oracle",
+            "sample": f"first {tn} of the {batch.n} pairs ({cells} cells), {proto}, {tm:.2f} s per run",
+            "one_core": {"value": c1 / tm1 / 1e9, "unit": "GCUPS",
+                         "sample": f"first {n1} pairs ({c1} cells), {proto}, {tm1:.2f} s per run"},
+            "parity": parity}
 
 
 def run_reference(args):
@@ -637,6 +692,213 @@ def fold_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True, lengths=None
             "l2": "flushed between timed steps", "steps": steps, "rows": rows}
 
 
+def workload_batch(synth, wl, pairs, seed_off):
+    if wl == "protein-sw-100k":
+        return synth.protein_pairs(n=pairs or 100_000, seed=2 + seed_off)
+    if wl == "short-dna-1k":
+        return synth.short_dna_pairs(n=pairs or 1000, seed=1 + seed_off)
+    if wl in ("long-reads-10k", "long-reads-10k-zdrop"):
+        return synth.long_reads(n=pairs or 10_000, seed=3 + seed_off)
+    return synth.long_pair(seed=5 + seed_off)
+
+
+# per workload: pairs of the plain one-launch-per-pair sample, of the
+# whole-GPU-per-pair (filtr_align_long) sample, and of the oracle's parity /
+# timing samples (pairs, pairs timed, runs)
+PLAIN_SAMPLE = {"protein-sw-100k": 3000, "short-dna-1k": 1000, "long-reads-10k": 20,
+                "long-reads-10k-zdrop": 20}
+LONG_SAMPLE = {"protein-sw-100k": 300, "short-dna-1k": 300, "long-reads-10k": 4,
+               "long-reads-10k-zdrop": 4}
+CPU_SAMPLE = {"protein-sw-100k": (5000, 1000, 10), "short-dna-1k": (1000, 1000, 10),
+              "long-reads-10k": (160, 160, 1), "long-reads-10k-zdrop": (64, 64, 1)}
+
+
+def roofline_of(wl, cells, cells_packed, fwd_ms, probe, traffic_per_cell):
+    """ALU roofline of the forward kernels.  Work = cells x 9 integer operations
+    (an add and a max count as two).  Peak: the time the cells would take at
+    the measured rate of their cell width -- int32 cells at the two-pipe
+    add/max rate, int16x2 cells at the packed DPX add-max rate (two cells per
+    lane instruction, two operations each) -- so the fraction follows the mix."""
+    i32 = probe["int_ops"] if probe else None
+    pk = 2.0 * probe["viaddmax_s16x2_lanes"] if probe else None
+    achieved = cells * OPS_PER_CELL / (fwd_ms * 1e-3) / 1e12
+    peak = None
+    if i32:
+        t_min = (cells - cells_packed) * OPS_PER_CELL / i32 + cells_packed * OPS_PER_CELL / pk
+        peak = cells * OPS_PER_CELL / t_min / 1e12 if t_min > 0 else None
+    xd = wl in ("long-reads-10k", "long-pair-1m", "long-reads-10k-zdrop")
+    kern = "k_xdrop (antidiagonal sweep)" if xd else "k_full + k_pack (tiled forward, all waves)"
+    return {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": (achieved / peak) if peak else None, "ops_per_cell": OPS_PER_CELL,
+            "cells": {"i32": cells - cells_packed, "i16x2": cells_packed},
+            "peak_per_width": {"i32": i32 / 1e12 if i32 else None,
+                               "i16x2": pk / 1e12 if pk else None},
+            "forward_ms": fwd_ms, "forward_gcups": cells / (fwd_ms * 1e-3) / 1e9,
+            "traffic": (traffic_per_cell * cells) if traffic_per_cell else None,
+            "traffic_unit": "DRAM bytes per step (ncu dram__bytes_read+write per cell x cells)",
+            "algorithmic_bytes": 0.5 * cells,
+            "peak_source": "filtr_probe_int_peak: int32 add+max two-pipe rate; "
+                           "__viaddmax_s16x2 lane rate x 2 ops (measured on this GPU, 'of measured')",
+            "probe": probe}
+
+
+def plain_long_per_pair(F, ctx, params, batch, nsample, stream, dev, res):
+    """The whole-GPU-per-pair form: one filtr_align_long call (the intra-pair
+    kernel across every SM) per pair, on a sample; results must equal the
+    batched call's."""
+    import torch
+
+    ns = min(nsample, batch.n)
+    tot_ms, cells = 0.0, 0
+    cap = int(max(batch.q_len[:ns].max() + batch.r_len[:ns].max(), 1)) + 1
+    dout = torch.empty(F.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    dcig = torch.empty(cap, dtype=torch.int32, device=dev)
+    for p in range(ns):
+        q, r = batch.pair(p)
+        dq = torch.from_numpy(np.ascontiguousarray(q)).to(dev)
+        dr = torch.from_numpy(np.ascontiguousarray(r)).to(dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc = ctx.align_long_ptr(params, dq.data_ptr(), len(q), dr.data_ptr(), len(r), dout.data_ptr(),
+                                dcig.data_ptr(), cap, stream=stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+        got = F.results_to_numpy(dout, 1)[0]
+        for f in ("score", "q_end", "r_end", "status", "cells"):
+            assert int(got[f]) == int(res[p][f]), "filtr_align_long and the batched call differ"
+        tot_ms += a.elapsed_time(b)
+        cells += int(got["cells"])
+    return {"pairs": ns, "gcups": cells / (tot_ms * 1e-3) / 1e9, "ms_total": tot_ms,
+            "call": "filtr_align_long per pair (intra-pair kernel on every SM)"}
+
+
+def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev, rank, world, dist,
+                     probe):
+    """One workload: untimed setup and warm-up, `steps` timed steps (CUDA events,
+    L2 flushed between steps, clocks sampled), then on rank 0 the end-to-end
+    call through the host-buffer entry point, the plain forms and the roofline.
+    Returns (record, batch, scoring, results, cigar tensor)."""
+    import torch
+
+    seed_off = 1000 * rank
+    batch = workload_batch(synth, wl, args.pairs if wl == args.workload else 0, seed_off)
+    sc = dict(batch.scoring)
+    if wl == "long-reads-10k-zdrop":
+        sc.update(xdrop=None, zdrop=400)
+    prec = {"auto": F.PREC_AUTO, "i32": F.PREC_I32, "i16x2": F.PREC_I16X2}[args.precision]
+    params = F.make_params(batch.subst, **dict(sc, precision=prec))
+    db = F.DeviceBatch(batch, dev)
+    out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
+    is_long = wl == "long-pair-1m"
+    tb_on = bool(sc.get("traceback"))
+
+    def step():
+        if is_long:
+            rc = ctx.align_long_ptr(params, db.q_seq.data_ptr(), int(batch.q_len[0]),
+                                    db.r_seq.data_ptr(), int(batch.r_len[0]), out_t.data_ptr(),
+                                    cig_t.data_ptr(), db.cigar_upper, stream=stream.cuda_stream)
+        else:
+            rc = ctx.align_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(),
+                                     cig_t.data_ptr() if tb_on else None,
+                                     db.cigar_upper if tb_on else 0, stream=stream.cuda_stream)
+        if rc != 0:
+            raise F.FiltrError(rc, F.last_error())
+
+    tune = None
+    if not args.no_autotune and not sc.get("xdrop") and not sc.get("zdrop"):
+        # one-time setup, outside every timed region
+        if args.tune_load and wl == args.workload:
+            with open(args.tune_load) as f:
+                tune = json.load(f)
+            ctx.tune_apply(params, tune)
+        else:
+            tune = ctx.autotune(params)
+            if args.tune_save and wl == args.workload:
+                with open(args.tune_save, "w") as f:
+                    json.dump(tune, f)
+    ctx.set_timing(True)
+    for _ in range(max(warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    res = F.results_to_numpy(out_t, db.n)
+    cells = int(res["cells"].sum())
+    if wl in ("protein-sw-100k", "short-dna-1k"):
+        assert cells == batch.cells_full()
+
+    sampler = ClockSampler(dev.index or 0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    fwd_ms, walk_ms, launches, other_ms = [], [], [], {}
+    packed = cells_packed = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the events)
+        torch.cuda.nvtx.range_push("timed_step")  # lets a profiler select these launches
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+        torch.cuda.nvtx.range_pop()
+        st = ctx.last_stats()  # waits for the step; device-side phase times
+        fwd_ms.append(st["ms_forward"])
+        walk_ms.append(st["ms_walk"])
+        for key in ("ms_validate", "ms_place", "ms_total", "ms_host_wait", "ms_host_plan"):
+            other_ms.setdefault(key[3:], []).append(st[key])
+        launches.append(st["launches"])
+        packed = st.get("pairs_i16x2", 0)
+        cells_packed = st.get("cells_i16x2", 0)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    ms, total_cells = reduce_over_ranks(ms, float(cells), dist, dev)
+    value = total_cells / (ms * 1e-3) / 1e9
+    rec = None
+    if rank == 0:
+        plain = plain_long = None
+        if is_long:
+            e2e = long_pair_e2e(F, ctx, params, batch, steps, res, stream, dev)
+        else:
+            e2e = host_entry_e2e(F, ctx, params, batch, db, res, cells, steps, tb_on)
+            ns = args.plain_sample if wl == args.workload and args.plain_sample else PLAIN_SAMPLE[wl]
+            plain = plain_per_pair(F, ctx, params, batch, ns, stream, dev, tb_on)
+            plain_long = plain_long_per_pair(F, ctx, params, batch, LONG_SAMPLE[wl], stream, dev, res)
+        fwd = statistics.median(fwd_ms)
+        # the committed capture covers the tiled kernels on the protein workload only
+        traffic_per_cell = ncu_traffic() if wl == "protein-sw-100k" else None
+        roof = roofline_of(wl, cells, cells_packed if not is_long else 0, fwd, probe,
+                           traffic_per_cell)
+        rec = {
+            "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i32|i16x2 (exact integer)" if cells_packed else "i32",
+            "data": "synthetic",
+            "config": {"workload": wl, "pairs": batch.n, "cells_per_step": cells,
+                       "mode": WORKLOAD_DESC[wl],
+                       "precision": args.precision, "pairs_i16x2": packed,
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"replica x{world}"},
+            "plain_per_pair": plain,
+            "plain_long_per_pair": plain_long,
+            "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms,
+                          **{k: statistics.median(v) for k, v in other_ms.items()}},
+            "autotune_ns_per_warp_step": tune,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": int(statistics.median(launches)),
+            "clocks": clocks,
+            "wall_s_timed": wall,
+        }
+    return rec, batch, sc, res, cig_t, params, db, (out_t, cig_t)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -660,29 +922,9 @@ def main():
     dev = torch.device("cuda", local_rank)
     if not os.path.exists(F._lib.LIB_PATH):
         B.build()
-    # weak scaling: every rank aligns its own batch (independent problems)
-    wl = args.workload
-    seed_off = 1000 * rank
-    if wl == "protein-sw-100k":
-        batch = synth.protein_pairs(n=args.pairs or 100_000, seed=2 + seed_off)
-    elif wl == "short-dna-1k":
-        batch = synth.short_dna_pairs(n=args.pairs or 1000, seed=1 + seed_off)
-    elif wl in ("long-reads-10k", "long-reads-10k-zdrop"):
-        batch = synth.long_reads(n=args.pairs or 10_000, seed=3 + seed_off)
-    else:
-        batch = synth.long_pair(seed=5 + seed_off)
-    sc = dict(batch.scoring)
-    if wl == "long-reads-10k-zdrop":
-        sc.update(xdrop=None, zdrop=400)
-    prec = {"auto": F.PREC_AUTO, "i32": F.PREC_I32, "i16x2": F.PREC_I16X2}[args.precision]
-    params = F.make_params(batch.subst, **dict(sc, precision=prec))
     ctx = F.Context(local_rank, int(args.workspace_gb * (1 << 30)))
-    db = F.DeviceBatch(batch, dev)
-    out_t, cig_t = F.alloc_outputs(db.n, db.cigar_upper, dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
-    is_long = wl == "long-pair-1m"
-    tb_on = bool(sc.get("traceback"))
     if args.fold_only:
         if rank == 0:
             tab = fold_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
@@ -697,117 +939,14 @@ def main():
             print(json.dumps({"search_table": tab}), flush=True)
         ctx.close()
         return
-
-    def step():
-        if is_long:
-            rc = ctx.align_long_ptr(params, db.q_seq.data_ptr(), int(batch.q_len[0]),
-                                    db.r_seq.data_ptr(), int(batch.r_len[0]), out_t.data_ptr(),
-                                    cig_t.data_ptr(), db.cigar_upper, stream=stream.cuda_stream)
-        else:
-            rc = ctx.align_batch_ptr(params, db.n, *db.ptrs(), out_t.data_ptr(),
-                                     cig_t.data_ptr() if tb_on else None,
-                                     db.cigar_upper if tb_on else 0, stream=stream.cuda_stream)
-        if rc != 0:
-            raise F.FiltrError(rc, F.last_error())
-
-    tune = None
-    if not args.no_autotune and not sc.get("xdrop") and not sc.get("zdrop"):
-        # one-time setup, outside every timed region
-        if args.tune_load:
-            with open(args.tune_load) as f:
-                tune = json.load(f)
-            ctx.tune_apply(params, tune)
-        else:
-            tune = ctx.autotune(params)
-            if args.tune_save:
-                with open(args.tune_save, "w") as f:
-                    json.dump(tune, f)
-    ctx.set_timing(True)
-    for _ in range(max(args.warmup, 1)):
-        step()
-    torch.cuda.synchronize()
-    res = F.results_to_numpy(out_t, db.n)
-    cells = int(res["cells"].sum())
-    if wl in ("protein-sw-100k", "short-dna-1k"):
-        assert cells == batch.cells_full()
-
+    # weak scaling: every rank aligns its own batch (independent problems)
+    wl = args.workload
     probe = ctx.probe() if rank == 0 else None
-
-    sampler = ClockSampler(local_rank)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    fwd_ms, walk_ms, launches, other_ms = [], [], [], {}
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the events)
-        torch.cuda.nvtx.range_push("timed_step")  # lets a profiler select these launches
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-        torch.cuda.nvtx.range_pop()
-        st = ctx.last_stats()  # waits for the step; device-side phase times
-        fwd_ms.append(st["ms_forward"])
-        walk_ms.append(st["ms_walk"])
-        for key in ("ms_validate", "ms_place", "ms_total", "ms_host_wait", "ms_host_plan"):
-            other_ms.setdefault(key[3:], []).append(st[key])
-        launches.append(st["launches"])
-        packed = st.get("pairs_i16x2", 0)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    ms, total_cells = reduce_over_ranks(ms, float(cells), dist, dev)
-    value = total_cells / (ms * 1e-3) / 1e9
-
-    line = None
+    line, batch, sc, res, cig_t, params, db, outs = measure_workload(
+        F, ctx, synth, wl, args, args.steps, args.warmup, stream, flush, dev, rank, world, dist, probe)
+    tb_on = bool(sc.get("traceback"))
     if rank == 0:
-        if is_long:
-            e2e, plain = long_pair_e2e(F, ctx, params, batch, args.steps, res, stream, dev), None
-        else:
-            e2e = host_entry_e2e(F, ctx, params, batch, db, res, cells, args.steps, tb_on)
-            plain = plain_per_pair(F, ctx, params, batch, args.plain_sample, stream, dev, tb_on)
-        fwd = statistics.median(fwd_ms)
-        peak_ops = max(probe["viaddmax"], probe["int_ops"]) if probe else None
-        achieved = cells * OPS_PER_CELL / (fwd * 1e-3) / 1e12
-        # the committed capture covers the tiled kernels on this workload only
-        traffic_per_cell = ncu_traffic() if wl == "protein-sw-100k" else None
-        kern = "k_xdrop (antidiagonal sweep)" if wl in ("long-reads-10k", "long-pair-1m",
-                                                        "long-reads-10k-zdrop") else \
-            "k_full + k_pack (tiled forward, all waves)"
-        roof = {"bound": "alu", "kernel": kern, "achieved": achieved,
-                "peak": peak_ops / 1e12 if peak_ops else None, "unit": "Tops/s",
-                "frac": (achieved / (peak_ops / 1e12)) if peak_ops else None,
-                "ops_per_cell": OPS_PER_CELL,
-                "forward_ms": fwd, "forward_gcups": cells / (fwd * 1e-3) / 1e9,
-                "traffic": (traffic_per_cell * cells) if traffic_per_cell else None,
-                "traffic_unit": "DRAM bytes per step (ncu dram__bytes_read+write per cell x cells)",
-                "algorithmic_bytes": 0.5 * cells,
-                "peak_source": "measured int32 add-max throughput (filtr_probe_int_peak)",
-                "probe": probe}
-        line = {
-            "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
-            "data": "synthetic",
-            "config": {"workload": wl, "pairs": batch.n, "cells_per_step": cells,
-                       "mode": WORKLOAD_DESC[wl],
-                       "precision": args.precision, "pairs_i16x2": packed,
-                       "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": f"replica x{world}"},
-            "plain_per_pair": plain,
-            "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms,
-                          **{k: statistics.median(v) for k, v in other_ms.items()}},
-            "autotune_ns_per_warp_step": tune,
-            "roofline": roof,
-            "e2e": e2e,
-            "gpu_launches": int(statistics.median(launches)),
-            "clocks": clocks,
-            "wall_s_timed": wall,
-        }
+        cells = int(res["cells"].sum())
         if wl in ("protein-sw-100k", "short-dna-1k") and not args.no_graph:
             line["graph"] = graph_bench(F, ctx, params, batch, db, res, cells, args.steps,
                                         args.warmup, stream, flush, dev, tb_on,
@@ -820,8 +959,37 @@ def main():
                                       cpu=not args.no_cpu_baseline)
         if not args.no_serve and wl == "protein-sw-100k":
             line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
-        if not args.no_cpu_baseline and not is_long:
-            line["cpu_baseline"] = cpu_baseline(batch, sc, args.cpu_sample)
+        if not args.no_cpu_baseline and wl != "long-pair-1m":
+            npairs, tpairs, runs = CPU_SAMPLE[wl]
+            if args.cpu_sample != CPU_SAMPLE_PAIRS:
+                npairs = tpairs = args.cpu_sample
+            line["cpu_baseline"] = cpu_baseline(batch, sc, res, cig_t, npairs, tpairs, runs)
+    del db, outs, cig_t
+    torch.cuda.empty_cache()
+    # the other configurations, each timed the same way (a sub-record each)
+    if args.configs and wl == "protein-sw-100k":
+        subs = {}
+        for other in ("short-dna-1k", "long-reads-10k", "long-pair-1m"):
+            # enough steps for the clock sampler (200 ms period) to see the short workload
+            k_steps = {"long-pair-1m": 2, "long-reads-10k": 3, "short-dna-1k": 2000}[other]
+            rec, ob, osc, ores, ocig, _, odb, oouts = measure_workload(
+                F, ctx, synth, other, args, k_steps, 3, stream, flush, dev, rank, world, dist, probe)
+            if rank == 0:
+                if not args.no_cpu_baseline and other != "long-pair-1m":
+                    npairs, tpairs, runs = CPU_SAMPLE[other]
+                    rec["cpu_baseline"] = cpu_baseline(ob, osc, ores, ocig, npairs, tpairs, runs)
+                elif other == "long-pair-1m":
+                    rec["cpu_baseline"] = {
+                        "value": None, "kind": "oracle",
+                        "note": "not timed here: the oracle keeps every evaluated cell (848 M cells, "
+                                "about 35 GB) and takes about 40 s; its result is stored in "
+                                "tests/golden/long_pair_1mbp.json and the GPU test compares against it"}
+                subs[other] = rec
+            del odb, oouts, ocig
+            torch.cuda.empty_cache()
+        if rank == 0:
+            line["configs"] = subs
+    if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -219,18 +219,21 @@ filtr_status filtr_align_batch_plain(filtr_ctx *ctx, const filtr_params *params,
  * the library holds until the process exits.
  *   params        : traceback must be 0; full matrix or band (no X-drop)
  *   q_seq .. r_len: DEVICE, as filtr_align_batch;  out: DEVICE, n_pairs results
- *   max_query_len / max_ref_len: the longest query / reference of the batch;
- *                   the strip buffers are sized by max_ref_len, so the batch
- *                   runs on fewer warps as it grows, and it is rejected with
- *                   FILTR_ERR_UNSUPPORTED beyond 2,097,134 reference residues (or when
- *                   scores could reach 2^28); a pair longer than the limits it
- *                   was given gets status FILTR_ST_TOO_WIDE.
+ *   max_query_len / max_ref_len: the longest query / reference of the batch
+ *                   (both >= 1, else FILTR_ERR_INVALID); the strip buffers are
+ *                   sized by max_ref_len, so the batch runs on fewer warps as it
+ *                   grows, and it is rejected with FILTR_ERR_UNSUPPORTED beyond
+ *                   2,097,134 reference residues, at 2^30 query residues, or when
+ *                   scores could reach 2^28; a pair longer than the limits it
+ *                   was given gets status FILTR_ST_TOO_WIDE (the others are
+ *                   computed as usual).
  * Results equal filtr_align_batch's (score, end coordinates, status, cells;
  * q_begin / r_begin as without traceback).  The call validates residue codes
- * and waits for that check on `stream` (FILTR_ERR_INVALID for a bad code),
- * then returns with the alignment queued on `stream`.  The first call on a
- * device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
+ * and waits for that check on `stream` (FILTR_ERR_INVALID for a bad code):
+ * every call copies one word to the host and synchronises `stream`.  It then
+ * returns with the alignment queued on `stream`.  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
  * Every call shares the one array and clears its counters first: calls whose
  * work overlaps on the GPU (other streams, other host threads) race and must
  * be serialised by the caller. */
@@ -272,6 +275,7 @@ typedef struct {
   uint32_t device_plan; /* 1: the call was planned on the device, 0: on the host */
   double ms_host_wait;  /* host wall time blocked on the validation and length read-back */
   double ms_host_plan;  /* host wall time from the lengths' arrival to the plan's upload */
+  uint64_t cells_i16x2; /* of cells_planned, those of the pairs in the int16x2 tiled kernel */
 } filtr_stats;
 filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);

@@ -88,7 +88,8 @@ class Stats(C.Structure):
                 ("ms_place", C.c_double), ("ms_total", C.c_double), ("launches", C.c_uint32),
                 ("waves", C.c_uint32), ("cells_planned", C.c_uint64),
                 ("pairs_i16x2", C.c_uint32), ("device_plan", C.c_uint32),
-                ("ms_host_wait", C.c_double), ("ms_host_plan", C.c_double)]
+                ("ms_host_wait", C.c_double), ("ms_host_plan", C.c_double),
+                ("cells_i16x2", C.c_uint64)]
 
 
 # the eight tiled shapes in the order filtr_autotune reports them

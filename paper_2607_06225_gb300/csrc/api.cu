@@ -452,6 +452,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     if (n_main) P.waves.push_back(w);
     P.cigar_upper = dsum.cigar_upper;
     P.cells_estimate = dsum.cells;
+    P.cells_packed = dsum.cells_packed;
     P.xdrop_w0 = 1;
     ce = cudaMemsetAsync(d_counters, 0, n_counters * 4, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "clearing the work queues");
@@ -725,6 +726,7 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     }
   }
   ctx->last_cells_estimate = P.cells_estimate;
+  ctx->last_cells_packed = P.cells_packed;
   ctx->last_pairs_packed = 0;
   for (const Wave &w : P.waves)
     for (const Group &g : w.groups)
@@ -990,6 +992,7 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out) {
   out->waves = (uint32_t)c->last_waves;
   out->cells_planned = c->last_cells_estimate;
   out->pairs_i16x2 = c->last_pairs_packed;
+  out->cells_i16x2 = c->last_cells_packed;
   out->device_plan = c->last_dev_plan ? 1u : 0u;
   out->ms_host_wait = c->last_host_wait_ms;
   out->ms_host_plan = c->last_host_plan_ms;

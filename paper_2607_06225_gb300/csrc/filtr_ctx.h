@@ -29,6 +29,7 @@ struct Ctx {
   bool ensure_side(int n);
   std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
   uint64_t last_cells_estimate = 0;
+  uint64_t last_cells_packed = 0;
   uint32_t last_pairs_packed = 0;
   double last_host_wait_ms = 0, last_host_plan_ms = 0;
   Plan plan;                       // the last call's plan; its buffers are reused

@@ -366,6 +366,7 @@ static filtr_status fold_impl(Ctx *ctx, const filtr_fold_params *prm, uint32_t n
   ctx->last_waves = (int)waves.size();
   ctx->last_launches = launches;
   ctx->last_cells_estimate = 0;
+  ctx->last_cells_packed = 0;
   ctx->last_pairs_packed = 0;
   if (!ctx->done_ev) cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
   if (ctx->done_ev) cudaEventRecord(ctx->done_ev, st);

@@ -59,13 +59,13 @@ __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanA
   const PlanView V = plan_view(a);
   if (blockIdx.x * DEV_PLAN_BLOCK >= V.n) return;  // uniform over the block
   __shared__ uint32_t hist[PLAN_KEYS];
-  __shared__ unsigned long long part[4][DEV_PLAN_BLOCK / 32];
+  __shared__ unsigned long long part[5][DEV_PLAN_BLOCK / 32];
   __shared__ uint32_t pmax[2][DEV_PLAN_BLOCK / 32];
   for (int i = threadIdx.x; i < PLAN_KEYS; i += DEV_PLAN_BLOCK) hist[i] = 0;
   __syncthreads();
   const uint32_t p = blockIdx.x * DEV_PLAN_BLOCK + threadIdx.x;
-  // traceback words, cells, staging words, M + N
-  unsigned long long v[4] = {0ull, 0ull, 0ull, 0ull};
+  // traceback words, cells, staging words, M + N, cells of int16x2 shapes
+  unsigned long long v[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
   uint32_t mm = 0, mn = 0;
   if (p < V.n) {
     const uint32_t M = V.q_len[p], N = V.r_len[p];
@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanA
       const int k = choose_shape(a.tab, a.sp, M, N);
       if (a.sp.traceback) w = shape_tb_words(a.tab, k, M, N, a.sp);
       v[1] = cost;
+      v[4] = a.tab.packed[k] ? cost : 0ull;
       key = k * 64 + cost_bucket_desc(cost);
     }
     v[0] = w;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanA
   }
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 5; ++i) {
     unsigned long long x = v[i];
     for (int o = 16; o; o >>= 1) x += __shfl_down_sync(FULL_MASK, x, o);
     if (lane == 0) part[i][wp] = x;
@@ -102,17 +103,18 @@ __global__ void __launch_bounds__(DEV_PLAN_BLOCK) k_plan_classify(const DevPlanA
   }
   __syncthreads();
   DevPlanSummary &S = a.state->sum;
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < 5) {
     unsigned long long x = 0;
     for (int k = 0; k < DEV_PLAN_BLOCK / 32; ++k) x += part[threadIdx.x][k];
     if (threadIdx.x == 2) a.blk[blockIdx.x] = x;
     unsigned long long *dst = threadIdx.x == 0   ? &S.tb_words
                               : threadIdx.x == 1 ? &S.cells
                               : threadIdx.x == 2 ? &S.stage_words
-                                                 : &S.cigar_upper;
+                              : threadIdx.x == 3 ? &S.cigar_upper
+                                                 : &S.cells_packed;
     if (x) atomicAdd(dst, x);
-  } else if (threadIdx.x < 6) {
-    const int t = threadIdx.x - 4;
+  } else if (threadIdx.x < 7) {
+    const int t = threadIdx.x - 5;
     uint32_t x = 0;
     for (int k = 0; k < DEV_PLAN_BLOCK / 32; ++k) x = max(x, pmax[t][k]);
     atomicMax(t ? &S.max_n : &S.max_m, x);

@@ -179,6 +179,7 @@ filtr_status run_long(Ctx *c, const ScoreParams &sp, const filtr_params *params,
   }
   c->last_launches = launches;
   c->last_cells_estimate = band_cells(M, N, sp);
+  c->last_cells_packed = 0;
   c->last_waves = 1;
   if (!sync) return FILTR_OK;  // the result's status reports a timeout
   // the wait flag (and the CIGAR length) decide the status: synchronise once

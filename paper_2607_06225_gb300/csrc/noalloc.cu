@@ -89,11 +89,18 @@ filtr_status filtr_align_batch_noalloc(const filtr_params *params, uint32_t n_pa
   // the strip buffers must hold at least one CTA's warps
   const uint64_t per_warp = ((uint64_t)max_ref_len + 2) * sizeof(int2);
   const uint64_t max_warps = (NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / per_warp;
-  if (max_ref_len == 0 || max_query_len == 0 || max_warps < (uint64_t)FULL_WARPS ||
-      max_query_len >= (1u << 30)) {
-    set_error("max_ref_len %u / max_query_len %u exceed the fixed %zu-byte scratch "
-              "(longest reference: %zu)",
-              max_ref_len, max_query_len, NOALLOC_SCRATCH_BYTES,
+  if (max_ref_len == 0 || max_query_len == 0) {
+    set_error("filtr_align_batch_noalloc: max_query_len and max_ref_len must be >= 1");
+    return FILTR_ERR_INVALID;
+  }
+  if (max_query_len >= (1u << 30)) {
+    set_error("max_query_len %u: queries are limited to fewer than 2^30 residues", max_query_len);
+    return FILTR_ERR_UNSUPPORTED;
+  }
+  if (max_warps < (uint64_t)FULL_WARPS) {
+    set_error("max_ref_len %u: the strip buffers of the fixed %zu-byte scratch hold references "
+              "of at most %zu residues",
+              max_ref_len, NOALLOC_SCRATCH_BYTES,
               (size_t)((NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER) / (FULL_WARPS * sizeof(int2)) - 2));
     return FILTR_ERR_UNSUPPORTED;
   }

@@ -92,6 +92,7 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->max_n = P->max_m = 0;
   P->cigar_upper = 0;
   P->cells_estimate = 0;
+  P->cells_packed = 0;
 
   // per pair: kernel shape key, cost bucket, traceback words (flat arrays)
   // shape keys: 0..3 the int32 tiled kernel with R = 32, 24, 16, 8; 4..7 the
@@ -110,7 +111,7 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->xdrop_w0 = xw;
   uint32_t live = 0;
   // running totals in locals: the byte stores below may alias *P
-  uint64_t max_n = 0, max_m = 0, cigar_upper = 0, stage_words = 0, cells = 0;
+  uint64_t max_n = 0, max_m = 0, cigar_upper = 0, stage_words = 0, cells = 0, cells_packed = 0;
   uint64_t *stage_off = P->stage_off.data();
   for (uint32_t p = 0; p < n; ++p) {
     const uint32_t M = in.q_len[p], N = in.r_len[p];
@@ -137,6 +138,7 @@ bool make_plan(const PlanInput &in, Plan *P) {
     } else {
       const int k = choose_shape(tab, sp, M, N);
       shape[p] = (uint8_t)k;
+      if (tab.packed[k]) cells_packed += cost;
       if (sp.traceback) w = shape_tb_words(tab, k, M, N, sp);
     }
     if (sp.traceback && w > in.tb_budget_words) {
@@ -154,6 +156,7 @@ bool make_plan(const PlanInput &in, Plan *P) {
   P->cigar_upper = cigar_upper;
   P->stage_words = stage_words;
   P->cells_estimate = cells;
+  P->cells_packed = cells_packed;
 
   // counting sort of pair ids, most expensive bucket first
   uint32_t start[64] = {};

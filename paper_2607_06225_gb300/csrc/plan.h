@@ -34,6 +34,7 @@ struct Plan {
   uint64_t cigar_upper = 0;       // sum over pairs of M + N: no CIGAR can be longer
   int xdrop_w0 = 1;               // group width X-drop / Z-drop pairs first run at
   uint64_t cells_estimate = 0;
+  uint64_t cells_packed = 0;  // of which in pairs given an int16x2 shape
   // per-pair scratch of make_plan, kept with the plan so that a context that
   // plans batch after batch reuses its pages
   std::vector<uint8_t> s_bucket, s_shape;
@@ -86,6 +87,7 @@ struct DevPlanSummary {
   unsigned long long cells;         // cells of the non-empty pairs
   unsigned long long stage_words;   // sum of M + N + 1 (traceback on)
   unsigned long long cigar_upper;   // sum of M + N
+  unsigned long long cells_packed;  // cells of the pairs given an int16x2 shape
 };
 
 // Zeroed before each call.  The host reads back bad[] and sum with one copy.

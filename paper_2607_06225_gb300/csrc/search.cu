@@ -7,10 +7,11 @@
 // (mismatch, a step down from diagonal d+1, a step right from diagonal d-1),
 // each term only when its predecessor was reached and the move stays inside the
 // matrix; extend() follows matches.  Lane l of the warp takes the diagonals
-// lo + l, lo + l + 32, ...; the three terms are three coalesced loads of the
-// previous wavefront.  Both sequences are staged in shared memory, so a match
-// run compares four residues per step (two aligned words each side and a funnel
-// shift).  The domain grows by one diagonal on each side per score, clipped to
+// lo + l, lo + l + 32, ...; each lane loads its diagonal of the previous
+// wavefront once and takes the neighbours d - 1 and d + 1 by warp shuffles
+// (a chunk's edge lanes from the neighbouring chunk or one extra load).  Both
+// sequences are staged in shared memory, so a match run compares four residues
+// per step (two aligned words each side and a funnel shift).  The domain grows by one diagonal on each side per score, clipped to
 // the matrix and the band; WFA-Adapt (Sec. 7.2, 9.3) moves its bounds inwards
 // past unreached diagonals and those whose remaining distance max(M - i, N - j)
 // exceeds the wavefront's smallest by more than max_dist, from the first
@@ -754,6 +755,7 @@ static filtr_status search_impl(Ctx *ctx, const filtr_search_params *prm, uint32
   }
   ctx->last_launches = launches;
   ctx->last_cells_estimate = 0;
+  ctx->last_cells_packed = 0;
   ctx->last_pairs_packed = 0;
   if (!ctx->done_ev) cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
   if (ctx->done_ev) cudaEventRecord(ctx->done_ev, st);

@@ -219,8 +219,11 @@ def protein_pairs(n: int = 100_000, lmin: int = 100, lmax: int = 1000, seed: int
 
 
 def long_reads(n: int = 10_000, lmin: int = 10_000, lmax: int = 50_000, seed: int = 3,
-               band: int = 256, xdrop: int = 400) -> Batch:
+               band: int = 256, xdrop: int = 400, idx=None) -> Batch:
     """Banded global alignment of simulated long reads.
+
+    `idx` (optional) selects pairs of the n-pair workload: the batch then holds
+    exactly those pairs, identical to the same rows of the full batch.
 
     Reference uniform ACGT of length U[lmin, lmax].  Query: per reference base an
     insertion event with probability 0.06*0.7, a deletion event 0.03*0.7, a
@@ -231,9 +234,12 @@ def long_reads(n: int = 10_000, lmin: int = 10_000, lmax: int = 50_000, seed: in
     rng = np.random.default_rng(seed)
     lens = rng.integers(lmin, lmax + 1, size=n)
     qs, rs = [], []
-    for p in range(n):
-        r = rng.integers(0, DNA, size=int(lens[p])).astype(np.uint8)
-        q = mutate(rng, r, 0.01, 0.06 * 0.7, 0.03 * 0.7, 0.7)
+    for p in (range(n) if idx is None else idx):
+        # each pair draws from its own stream, so a sample of the workload can be
+        # regenerated without the rest of it
+        prng = np.random.default_rng((seed, int(p)))
+        r = prng.integers(0, DNA, size=int(lens[p])).astype(np.uint8)
+        q = mutate(prng, r, 0.01, 0.06 * 0.7, 0.03 * 0.7, 0.7)
         qs.append(q)
         rs.append(r)
     return pack(qs, rs, DNA, dna_subst(2, -4),

@@ -98,3 +98,44 @@ def test_poll_and_errors(F):
         srv.submit(p, bad, q)
     srv.close()
     ctx.close()
+
+
+def test_large_request_route_and_budget_refusal(F):
+    """A request above 2^26 cells (a 8200 x 8300 protein pair, local, traceback)
+    runs alone on the intra-pair kernel and equals the oracle; a request whose
+    traceback exceeds a lane's share of the budget is refused with
+    FILTR_ERR_BUSY at submission, and the server keeps serving afterwards."""
+    from paper_2607_06225_gb300._lib import ERR_BUSY
+
+    psub = synth.protein_subst(np.random.default_rng(2))
+    p = F.make_params(psub, **KINDS["sw_protein"])
+    rng = np.random.default_rng(44)
+    r = rng.integers(0, 20, 8300).astype(np.uint8)
+    q = np.concatenate([rng.integers(0, 20, 3000).astype(np.uint8), r[2000:7200]])
+    assert q.shape[0] * r.shape[0] > 1 << 26
+    ctx = F.Context(0, 1 << 28)
+    srv = F.Server(ctx, 2 << 30, max_inflight=2)
+    try:
+        t = srv.submit(p, q, r)
+        res, cig, _ = srv.wait(t)
+        o = oracle.align(q, r, psub, **KINDS["sw_protein"])
+        for f in ("score", "q_begin", "q_end", "r_begin", "r_end", "status", "cells"):
+            assert int(res[f]) == int(o[f]), f
+        assert np.array_equal(cig, o["cigar"])
+    finally:
+        srv.close()
+    # 192 MB over two lanes: 16 MB of I/O buffer and 80 MB of workspace a lane,
+    # of which a micro-batch may use 64 MB -- less than the traceback alone of a
+    # 12000 x 12000 pair (half a byte per cell, about 72 MB)
+    srv = F.Server(ctx, 192 << 20, max_inflight=2)
+    try:
+        big = rng.integers(0, 20, 12000).astype(np.uint8)
+        with pytest.raises(F.FiltrError) as ei:
+            srv.submit(p, big, big)
+        assert ei.value.code == ERR_BUSY
+        small = rng.integers(0, 20, 400).astype(np.uint8)
+        res, cig, _ = srv.wait(srv.submit(p, small, small))
+        assert int(res["score"]) == int(sum(int(psub[c, c]) for c in small))
+    finally:
+        srv.close()
+        ctx.close()
