@@ -59,6 +59,12 @@ def parse():
                     choices=["protein-sw-100k", "short-dna-1k", "long-reads-10k", "long-pair-1m",
                              "long-reads-10k-zdrop"])
     ap.add_argument("--pairs", type=int, default=0, help="0: the workload's own size")
+    ap.add_argument("--lmin", type=int, default=0,
+                    help="long-read workload: shortest reference (0: 10,000; profiling cases)")
+    ap.add_argument("--lmax", type=int, default=0,
+                    help="long-read workload: longest reference (0: 50,000; profiling cases)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain per-pair forms (profiling runs)")
     ap.add_argument("--plain-sample", type=int, default=0,
                     help="pairs of the plain per-pair sample (0: the workload's default)")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
@@ -692,13 +698,14 @@ def fold_table(F, ctx, steps, warmup, stream, flush, dev, cpu=True, lengths=None
             "l2": "flushed between timed steps", "steps": steps, "rows": rows}
 
 
-def workload_batch(synth, wl, pairs, seed_off):
+def workload_batch(synth, wl, pairs, seed_off, lmin=0, lmax=0):
     if wl == "protein-sw-100k":
         return synth.protein_pairs(n=pairs or 100_000, seed=2 + seed_off)
     if wl == "short-dna-1k":
         return synth.short_dna_pairs(n=pairs or 1000, seed=1 + seed_off)
     if wl in ("long-reads-10k", "long-reads-10k-zdrop"):
-        return synth.long_reads(n=pairs or 10_000, seed=3 + seed_off)
+        return synth.long_reads(n=pairs or 10_000, lmin=lmin or 10_000, lmax=lmax or 50_000,
+                                seed=3 + seed_off)
     return synth.long_pair(seed=5 + seed_off)
 
 
@@ -784,7 +791,9 @@ def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev,
     import torch
 
     seed_off = 1000 * rank
-    batch = workload_batch(synth, wl, args.pairs if wl == args.workload else 0, seed_off)
+    own = wl == args.workload
+    batch = workload_batch(synth, wl, args.pairs if own else 0, seed_off,
+                           args.lmin if own else 0, args.lmax if own else 0)
     sc = dict(batch.scoring)
     if wl == "long-reads-10k-zdrop":
         sc.update(xdrop=None, zdrop=400)
@@ -866,9 +875,11 @@ def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev,
             e2e = long_pair_e2e(F, ctx, params, batch, steps, res, stream, dev)
         else:
             e2e = host_entry_e2e(F, ctx, params, batch, db, res, cells, steps, tb_on)
-            ns = args.plain_sample if wl == args.workload and args.plain_sample else PLAIN_SAMPLE[wl]
-            plain = plain_per_pair(F, ctx, params, batch, ns, stream, dev, tb_on)
-            plain_long = plain_long_per_pair(F, ctx, params, batch, LONG_SAMPLE[wl], stream, dev, res)
+            if not args.no_plain:
+                ns = args.plain_sample if wl == args.workload and args.plain_sample else PLAIN_SAMPLE[wl]
+                plain = plain_per_pair(F, ctx, params, batch, ns, stream, dev, tb_on)
+                plain_long = plain_long_per_pair(F, ctx, params, batch, LONG_SAMPLE[wl], stream, dev,
+                                                 res)
         fwd = statistics.median(fwd_ms)
         # the committed capture covers the tiled kernels on the protein workload only
         traffic_per_cell = ncu_traffic() if wl == "protein-sw-100k" else None

@@ -276,6 +276,8 @@ typedef struct {
   double ms_host_wait;  /* host wall time blocked on the validation and length read-back */
   double ms_host_plan;  /* host wall time from the lengths' arrival to the plan's upload */
   uint64_t cells_i16x2; /* of cells_planned, those of the pairs in the int16x2 tiled kernel */
+  uint32_t pairs_xd16;  /* X-drop / Z-drop pairs that ran in the int16x2 antidiagonal sweep */
+  uint32_t pairs_xd16_rerun; /* of which, pairs that left its 16-bit range and were rerun in int32 */
 } filtr_stats;
 filtr_status filtr_ctx_set_timing(filtr_ctx *ctx, int enable);
 filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out);

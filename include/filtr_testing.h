@@ -48,6 +48,14 @@ filtr_status filtr_test_set_device_plan(filtr_ctx *ctx, int32_t mode);
  * depend on it; it trades shared memory (occupancy) against load latency. */
 filtr_status filtr_test_set_search_ring(filtr_ctx *ctx, int32_t entries);
 
+/* Cell width of the antidiagonal (X-drop / Z-drop) sweep: 0 the default (two
+ * cells per register for affine pairs whose threshold leaves room, int32
+ * otherwise), 1 int32 always, 2 two cells per register with the base score
+ * never moved, so pairs whose scores drift more than about 16,000 from where
+ * they started leave the 16-bit range and are rerun in int32
+ * (filtr_stats.pairs_xd16_rerun counts them).  Results do not depend on it. */
+filtr_status filtr_test_set_packed_sweep(filtr_ctx *ctx, int32_t mode);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,7 +89,8 @@ class Stats(C.Structure):
                 ("waves", C.c_uint32), ("cells_planned", C.c_uint64),
                 ("pairs_i16x2", C.c_uint32), ("device_plan", C.c_uint32),
                 ("ms_host_wait", C.c_double), ("ms_host_plan", C.c_double),
-                ("cells_i16x2", C.c_uint64)]
+                ("cells_i16x2", C.c_uint64), ("pairs_xd16", C.c_uint32),
+                ("pairs_xd16_rerun", C.c_uint32)]
 
 
 # the eight tiled shapes in the order filtr_autotune reports them
@@ -176,6 +177,8 @@ def lib():
         L.filtr_test_set_device_plan.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_test_set_search_ring.restype = i32
         L.filtr_test_set_search_ring.argtypes = [C.c_void_p, C.c_int32]
+        L.filtr_test_set_packed_sweep.restype = i32
+        L.filtr_test_set_packed_sweep.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_graph_create.restype = i32
         L.filtr_graph_create.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32,
                                          C.c_size_t, C.POINTER(C.c_void_p)]

@@ -121,6 +121,14 @@ filtr_status to_score_params(const filtr_params *p, ScoreParams *sp) {
     sp->smin = std::min(sp->smin, (int32_t)p->subst[t]);
     sp->smax = std::max(sp->smax, (int32_t)p->subst[t]);
   }
+  // one match score and one mismatch score (DNA +2 / -4): the packed sweep
+  // then scores two cells by comparing codes instead of looking them up
+  sp->uni = 1;
+  sp->uni_match = p->subst[0];
+  sp->uni_mismatch = p->alphabet > 1 ? p->subst[1] : 0;
+  for (int a = 0; a < p->alphabet; ++a)
+    for (int b = 0; b < p->alphabet; ++b)
+      if (p->subst[a * p->alphabet + b] != (a == b ? sp->uni_match : sp->uni_mismatch)) sp->uni = 0;
   return FILTR_OK;
 }
 
@@ -248,6 +256,9 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     set_error("cigar is NULL but cigar_cap > 0");
     return FILTR_ERR_INVALID;
   }
+  // X-drop / Z-drop pairs take the packed sweep when their threshold leaves
+  // room in 15 bits (those that leave the range anyway are rerun in int32)
+  sp.xd16 = (ctx->xd16_mode != 1 && xd16_eligible(sp)) ? 1 : 0;
   cudaError_t ce = cudaSetDevice(ctx->device);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
   if (ctx->done_ev) {
@@ -272,7 +283,8 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   uint32_t *d_counters = c.take<uint32_t>(n_counters);
   uint64_t *d_total = c.take<uint64_t>(4);
   uint32_t *d_ovf = c.take<uint32_t>(n);
-  uint32_t *d_novf = c.take<uint32_t>(4);
+  uint32_t *d_novf = c.take<uint32_t>(8);  // [0] window overflows, [4] packed-range overflows
+  uint32_t *d_ovf16 = sp.xd16 ? c.take<uint32_t>(n) : nullptr;
   uint32_t *d_rerun = c.take<uint32_t>(n);
   // The device planner serves tiled batches (not X-drop, not one launch per
   // pair) once planning on the host would cost more than the read-back: when
@@ -509,6 +521,9 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   fa.max_n = 0;
   fa.max_m = 0;
   fa.ck = nullptr;
+  fa.ovf16 = d_ovf16;
+  fa.n_ovf16 = d_novf + 4;
+  fa.x16_rebase = ctx->xd16_mode == 2 ? 0 : X16_REBASE;
   WalkArgs wa;
   wa.b = b;
   wa.sp = sp;
@@ -585,18 +600,26 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     ++launches;
     return ce == cudaSuccess;
   };
-  auto read_overflow = [&](std::vector<uint32_t> *list) -> bool {
+  // pairs that outgrew their window (list) and, from the packed sweep, pairs
+  // that left its 16-bit range (list16); both counters come back in one copy
+  auto read_overflow = [&](std::vector<uint32_t> *list, std::vector<uint32_t> *list16) -> bool {
     uint32_t *h = reinterpret_cast<uint32_t *>(ctx->h_stage);
-    ce = cudaMemcpyAsync(h, d_novf, 4, cudaMemcpyDeviceToHost, st);
+    ce = cudaMemcpyAsync(h, d_novf, 32, cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return false;
-    const uint32_t k = h[0];
+    const uint32_t k = h[0], k16 = fa.sp.xd16 ? h[4] : 0;
     list->clear();
     if (k) {
       ce = cudaMemcpyAsync(h, d_ovf, k * 4ull, cudaMemcpyDeviceToHost, st);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
       if (ce != cudaSuccess) return false;
       list->assign(h, h + k);
+    }
+    if (k16) {
+      ce = cudaMemcpyAsync(h, d_ovf16, k16 * 4ull, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) return false;
+      list16->insert(list16->end(), h, h + k16);
     }
     return true;
   };
@@ -610,13 +633,13 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     ++launches;
     return ce == cudaSuccess;
   };
-  std::vector<uint32_t> pending;
+  std::vector<uint32_t> pending, pending16;
   for (const Wave &w : P.waves) {
     bool has_xd = false;
     ctx->span_begin(Ctx::PH_FORWARD, st);
     for (const Group &g : w.groups) has_xd |= g.family == FAM_XDROP;
     if (has_xd) {
-      ce = cudaMemsetAsync(d_novf, 0, 4, st);
+      ce = cudaMemsetAsync(d_novf, 0, 32, st);
       if (ce != cudaSuccess) return cuda_fail(ce, "overflow reset");
     }
     if (n_conc) {  // fork: each shape on its own side stream and strip region; join on st
@@ -644,17 +667,16 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     }
     ctx->span_end(st);
     std::vector<uint32_t> ovf;
-    if (has_xd && !read_overflow(&ovf)) return cuda_fail(ce, "reading the overflow list");
+    if (has_xd && !read_overflow(&ovf, &pending16)) return cuda_fail(ce, "reading the overflow list");
     if (!walk(d_order + w.walk_begin, w.walk_end - w.walk_begin)) return cuda_fail(ce, "walk launch");
     pending.insert(pending.end(), ovf.begin(), ovf.end());
   }
-  static const int kWider[] = {2, 4, 8, 16, 32};
-  for (int wi = 0; wi < 5 && !pending.empty(); ++wi) {
-    const int W = kWider[wi];
-    if (W <= P.xdrop_w0) continue;
-    // rerun the pairs that outgrew their window, in sub-waves that fit the budget
-    std::vector<uint32_t> todo;
-    todo.swap(pending);
+  const uint32_t n_xd16 = fa.sp.xd16 ? n_main : 0;
+  uint32_t n_xd16_rerun = 0;
+  // rerun `todo` at group width W, in sub-waves that fit the traceback budget;
+  // pairs that outgrow the window again join `pending`, pairs that leave the
+  // packed range join `pending16`
+  auto rerun = [&](std::vector<uint32_t> &todo, int W) -> bool {
     size_t i0 = 0;
     while (i0 < todo.size()) {
       size_t i1 = i0;
@@ -680,17 +702,38 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
       ce = cudaMemcpyAsync(d_rerun, h, cnt * 4ull, cudaMemcpyHostToDevice, st);
       if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(d_tbl, h + n * 4ull, n * sizeof(TbLayout), cudaMemcpyHostToDevice, st);
-      if (ce == cudaSuccess) ce = cudaMemsetAsync(d_novf, 0, 4, st);
-      if (ce != cudaSuccess) return cuda_fail(ce, "rerun upload");
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(d_novf, 0, 32, st);
+      if (ce != cudaSuccess) return false;
       ctx->span_begin(Ctx::PH_FORWARD, st);
-      if (!run_group(d_rerun, cnt, FAM_XDROP, 8, W, st, grid_max)) return cuda_fail(ce, "rerun launch");
+      if (!run_group(d_rerun, cnt, FAM_XDROP, 8, W, st, grid_max)) return false;
       ctx->span_end(st);
       std::vector<uint32_t> ovf;
-      if (!read_overflow(&ovf)) return cuda_fail(ce, "reading the overflow list");
-      if (!walk(d_rerun, cnt)) return cuda_fail(ce, "walk launch");
+      if (!read_overflow(&ovf, &pending16)) return false;
+      if (!walk(d_rerun, cnt)) return false;
       pending.insert(pending.end(), ovf.begin(), ovf.end());
       i0 = i1;
     }
+    return true;
+  };
+  static const int kWider[] = {2, 4, 8, 16, 32};
+  auto ladder = [&](int w_done) -> bool {  // rerun `pending` ever wider, above w_done warps
+    for (int wi = 0; wi < 5 && !pending.empty(); ++wi) {
+      const int W = kWider[wi];
+      if (W <= w_done) continue;
+      std::vector<uint32_t> todo;
+      todo.swap(pending);
+      if (!rerun(todo, W)) return false;
+    }
+    return true;
+  };
+  if (!ladder(P.xdrop_w0)) return cuda_fail(ce, "rerun");
+  if (!pending16.empty()) {  // pairs that left the packed range: the int32 sweep
+    std::vector<uint32_t> todo;
+    todo.swap(pending16);
+    n_xd16_rerun = (uint32_t)todo.size();
+    fa.sp.xd16 = 0;
+    const int w0 = std::max(1, (int)P.xdrop_w0);
+    if (!rerun(todo, w0) || !ladder(w0)) return cuda_fail(ce, "int32 rerun");
   }
   if (n_trivial) {
     ce = launch_trivial(b, sp, d_order + n_main, n_trivial, out, d_fwd, st);
@@ -727,6 +770,8 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   }
   ctx->last_cells_estimate = P.cells_estimate;
   ctx->last_cells_packed = P.cells_packed;
+  ctx->last_xd16 = n_xd16;
+  ctx->last_xd16_rerun = n_xd16_rerun;
   ctx->last_pairs_packed = 0;
   for (const Wave &w : P.waves)
     for (const Group &g : w.groups)
@@ -993,6 +1038,8 @@ filtr_status filtr_ctx_last_stats(filtr_ctx *ctx, filtr_stats *out) {
   out->cells_planned = c->last_cells_estimate;
   out->pairs_i16x2 = c->last_pairs_packed;
   out->cells_i16x2 = c->last_cells_packed;
+  out->pairs_xd16 = c->last_xd16;
+  out->pairs_xd16_rerun = c->last_xd16_rerun;
   out->device_plan = c->last_dev_plan ? 1u : 0u;
   out->ms_host_wait = c->last_host_wait_ms;
   out->ms_host_plan = c->last_host_plan_ms;

@@ -30,6 +30,8 @@ struct Ctx {
   std::map<std::tuple<int, int, int, int, int, int>, int> occ_cache;
   uint64_t last_cells_estimate = 0;
   uint64_t last_cells_packed = 0;
+  uint32_t last_xd16 = 0, last_xd16_rerun = 0;
+  int xd16_mode = 0;  // packed antidiagonal sweep: 0 when eligible, 1 never, 2 without moving the base
   uint32_t last_pairs_packed = 0;
   double last_host_wait_ms = 0, last_host_plan_ms = 0;
   Plan plan;                       // the last call's plan; its buffers are reused

@@ -118,8 +118,22 @@ struct ScoreParams {
   int32_t traceback;
   int32_t precision;           // FILTR_PREC_*
   int32_t smin, smax;          // smallest / largest substitution score
+  int32_t uni, uni_match, uni_mismatch;  // 1: one score on the diagonal, one off it
+  int32_t xd16;                // 1: the antidiagonal sweep runs two cells per register
   int8_t subst[MAX_ALPHA * MAX_ALPHA];
 };
+
+// The packed (int16x2) antidiagonal sweep takes affine H/E/F pairs whose X-drop
+// or Z-drop threshold leaves room in 15 bits around the running best; a pair
+// whose values nevertheless leave the range stops with this internal status
+// and is rerun by the int32 sweep.
+constexpr int X16_MAX_DROP = 8000;
+constexpr int X16_OVERFLOW = 64;
+constexpr int X16_REBASE = 4096;  // distance of the best from the packed centre that moves the base
+inline bool xd16_eligible(const ScoreParams &sp) {
+  return sp.use_xdrop && sp.affine && !sp.mid && sp.xdrop < X16_MAX_DROP && sp.o + sp.e <= 1000 &&
+         sp.smax <= 127 && sp.smin >= -128 && sp.precision != FILTR_PREC_I32;
+}
 
 // Score range of a batch whose longest query / reference are max_m / max_n:
 // |H| stays below 2^28 so that NEG arithmetic never meets finite scores, and
@@ -207,6 +221,11 @@ struct FullArgs {
   uint32_t max_n;          // 0, or the longest reference the strip buffers hold
   uint32_t max_m;          // 0, or the longest query accepted
   const struct XdCkpt *ck; // X-drop kernel: checkpoint mode (nullptr = normal)
+  // packed X-drop sweep: pairs that left the 16-bit range (rerun in int32),
+  // and the base move distance (<= 0: never, a test hook)
+  uint32_t *ovf16 = nullptr;
+  uint32_t *n_ovf16 = nullptr;
+  int x16_rebase = X16_REBASE;
   // captured pipeline (tiled kernels only): b and out come from gd, and the
   // launch takes order[begin, begin + count[gshape]) with begin the pairs of
   // the shapes before gshape in the device plan's summary

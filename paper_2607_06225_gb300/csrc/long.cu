@@ -285,6 +285,7 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   fa.strip_stride = 0;
   fa.max_n = 0;
   fa.max_m = 0;
+  fa.x16_rebase = c->xd16_mode == 2 ? 0 : X16_REBASE;
   // forward: every segment is offered to each width in turn; the narrowest
   // window that holds it does the work, the other launches return at once
   uint32_t launches = 0;
@@ -307,6 +308,11 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward sweep");
   const FwdOut f = *hf;
   c->last_launches = launches;
+  if (hflags[0] == 3) {  // the packed sweep left its 16-bit range: the whole pair in int32
+    ScoreParams s32 = sp;
+    s32.xd16 = 0;
+    return run_xdrop_ckpt(c, s32, params, q, M, r, N, out, cigar, cap, st, C);
+  }
   if (single && hflags[0] == 2) {  // the pool ran out: recompute the segments instead
     const bool saved = c->ckpt_recompute;
     c->ckpt_recompute = true;
@@ -461,6 +467,7 @@ filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const 
   }
   rc = validate_seq(c, q, M, r, N, sp.alphabet, st);
   if (rc != FILTR_OK) return rc;
+  sp.xd16 = (c->xd16_mode != 1 && xd16_eligible(sp)) ? 1 : 0;
   if (sp.use_xdrop && M && N &&
       (c->ckpt_interval > 0 || (int64_t)M + N > XD_SEGMENTED_SWEEP ||
        4 * xd_tb_words(M, N, 32, 8) > c->ws_bytes / 2)) {  // the widest traceback would not fit
@@ -523,6 +530,15 @@ filtr_status filtr_test_set_device_plan(filtr_ctx *ctx, int32_t mode) {
     return FILTR_ERR_INVALID;
   }
   reinterpret_cast<Ctx *>(ctx)->dev_plan_mode = mode;
+  return FILTR_OK;
+}
+
+filtr_status filtr_test_set_packed_sweep(filtr_ctx *ctx, int32_t mode) {
+  if (!ctx || mode < 0 || mode > 2) {
+    set_error("filtr_test_set_packed_sweep: bad arguments");
+    return FILTR_ERR_INVALID;
+  }
+  reinterpret_cast<Ctx *>(ctx)->xd16_mode = mode;
   return FILTR_OK;
 }
 
