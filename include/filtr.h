@@ -485,10 +485,12 @@ filtr_status filtr_probe_int_peak(filtr_ctx *ctx, double out[5]);
 /* ---- serving: continuous batching of single-pair requests ------------------
  * Requests are copied into resident device buffers, admitted while their
  * device memory (sequences + DP workspace + traceback bytes) fits mem_budget,
- * grouped by kind into micro-batches and launched on up to max_inflight
- * streams; a micro-batch launches as soon as a stream is free, so requests
- * that arrive while others run overlap with them on the device.  A worker
- * thread owned by the server does all device work. */
+ * grouped by kind and cost class (cells within a factor of 4) into
+ * micro-batches and launched on up to max_inflight streams; a micro-batch
+ * launches as soon as a stream is free, so requests that arrive while others
+ * run overlap with them on the device.  A request above 2^22 cells runs alone,
+ * on the intra-pair kernel when it is not X-drop.  A worker thread owned by the
+ * server does all device work. */
 filtr_status filtr_serve_create(filtr_ctx *ctx, size_t mem_budget, uint32_t max_inflight,
                                 filtr_server **out);
 /* Queue one pair (HOST pointers, copied before returning).  FILTR_ERR_BUSY if the

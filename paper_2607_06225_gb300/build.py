@@ -15,6 +15,8 @@ OUT = os.path.join(HERE, "libfiltr.so")
 OBJ = os.path.join(ROOT, "_build", "obj")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
+# extra nvcc flags for experiments (e.g. -D overrides of kernel tuning macros)
+NVCC_FLAGS += os.environ.get("FILTR_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:

@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
   const int M = (int)a.b.q_len[p], N = (int)a.b.r_len[p];
   const uint32_t *base = a.tb + L.off;
   const int32_t *ck = reinterpret_cast<const int32_t *>(base);
-  const uint32_t *tbw = base + ((int64_t)M + N + 1);
+  const uint32_t *tbw = base + xd_origin_words(M, N);
   const int wpk = xd_words_per_k(L.warps, L.R);
   WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,

@@ -139,8 +139,11 @@ struct X16Knobs {
   int rebase;  // distance of the best from C0 that moves the base; <= 0: never
 };
 
+#ifndef FILTR_X16_MINB
+#define FILTR_X16_MINB 1
+#endif
 template <int W, bool LOCAL, bool TB, bool ZD>
-__global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
+__global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB : 1)
     k_xdrop16(const FullArgs a, uint32_t *overflow, uint32_t *n_overflow, X16Knobs kn) {
   constexpr int S = X16_S;
   constexpr int WIN = W * 32 * S;
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
         tbp = ck->pool + rsv;
       } else {
         ckp = reinterpret_cast<int32_t *>(a.tb + a.tbl[p].off);
-        tbp = a.tb + a.tbl[p].off + (uint64_t)(M + N + 1);
+        tbp = a.tb + a.tbl[p].off + (uint64_t)xd_origin_words(M, N);
       }
     }
 
@@ -288,6 +291,12 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
       }
     }
     int brun = best;  // running best (FILTR_PRUNE_XDROP_RUNNING); best is antidiagonal k-1's
+    // the best cell is the result of local alignments; Z-drop needs each
+    // antidiagonal's best diagonal.  A global X-drop pair reports its best
+    // cell only when it is dropped, which it then takes from the int32 rerun,
+    // so its sweep keeps neither.
+    const bool track = (LOCAL || ZD) && ckmode != 2;
+    const bool need_bs = ZD || track;
     bool ended = false;
     if (W > 1) {
       const int b0 = (k_first - 1) & 1;
@@ -319,7 +328,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
     uint32_t nextc = 0;  // the code entering the window at the next antidiagonal
     // reductions of the last antidiagonal masked (consumed one antidiagonal later)
     bool pending = false;
-    int pmax = 0, plo = INT_MAX, phi = INT_MIN, pbs = -1, pk_ = 0, pc = 0;
+    int pmax = 0, plo = INT_MAX, phi = INT_MIN, pbs = -1;  // of antidiagonal k - 1, origin c
     int k = k_first;
 
     // consume the reductions of antidiagonal kk (origin ckk): best, live range,
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
       if (glo == INT_MAX) return false;
       const int gv = gmax - X16_C0 + base;
       const int jj = ckk + gbs, ii = kk - jj;
-      if (gv > bv || (gv == bv && (ii < bi || (ii == bi && jj < bj)))) {
+      if (track && (gv > bv || (gv == bv && (ii < bi || (ii == bi && jj < bj))))) {
         bv = gv;
         bi = ii;
         bj = jj;
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
         if (lane == 31) nxH2 = (W > 1 && warp < W - 1) ? sh.first[buf][warp < W - 1 ? warp + 1 : 0].H2 : 0u;
       }
       // ---- raw cells of k ------------------------------------------------------
-      const uint32_t Z2 = x16_splat(min(max(X16_C0 - base, 0), 0x7fff));
+      const uint32_t Z2 = LOCAL ? x16_splat(min(max(X16_C0 - base, 0), 0x7fff)) : 0u;
       uint32_t Hr[X16_P], Er[X16_P], Fr[X16_P];
       uint32_t nib = 0;
       if (delta == 1) {
@@ -430,7 +439,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
       if (pending) {
         int gmax = pmax, glo = plo, ghi = phi, gbs = pbs;
         if (W > 1) {
-          const int nb = pk_ & 1;
+          const int nb = (k - 1) & 1;
           const int v0 = lane < W ? sh.red[nb][lane][0] : INT_MIN;
           gmax = __reduce_max_sync(X16_FULL, v0);
           glo = __reduce_min_sync(X16_FULL, lane < W ? sh.red[nb][lane][1] : INT_MAX);
@@ -438,7 +447,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
           gbs = __reduce_max_sync(X16_FULL, (lane < W && v0 == gmax) ? sh.red[nb][lane][3] : -1);
         }
         pending = false;
-        if (!consume(pk_, pc, gmax, glo, ghi, gbs)) {  // nothing alive on k - 1: the sweep ends there
+        if (!consume(k - 1, c, gmax, glo, ghi, gbs)) {  // nothing alive on k - 1: the sweep ends there
           ended = true;
           break;
         }
@@ -504,8 +513,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
         if (vB >= 0 && vA < S) dom = (0xffu << max(vA, 0)) & (0xffu >> (S - 1 - min(vB, S - 1))) & 0xffu;
         const uint32_t dsp = (dom & 0xfu) | ((dom & 0xf0u) << 12);
         const int zx = ZD ? 2 * (cn + base_slot) - k - dbest : 0;
-        uint32_t af[X16_P];
-        uint32_t t2 = 0;
+        uint32_t t2 = 0, amw = 0;
 #pragma unroll
         for (int r = 0; r < X16_P; ++r) {
           uint32_t th2;
@@ -516,28 +524,37 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
           } else {
             th2 = x16_splat(thr);
           }
-          const uint32_t al = x16_ge(Hr[r], th2);
-          const uint32_t m = x16_halfmask(al) & x16_halfmask(dsp << (15 - r));
-          af[r] = al;
+          // halves outside the candidate range get an unreachable threshold
+          const uint32_t dm = x16_halfmask(dsp << (15 - r));
+          th2 = (th2 & dm) | (0x7fff7fffu & ~dm);
+          const uint32_t m = x16_halfmask(x16_ge(Hr[r], th2));
           H2[r] = H1[r];
           H1[r] = Hr[r] & m;
           E1[r] = Er[r] & m;
           F1[r] = Fr[r] & m;
           t2 = __vimax_s16x2_relu(t2, H1[r]);
+          amw |= m & (0x10001u << r);  // live slots: bit r (low half), bit 16 + r (high half)
         }
-        const uint32_t am = x16_gather(af[0], af[1], af[2], af[3]) & dom;
+        const uint32_t am = (amw & 0xfu) | ((amw >> 12) & 0xf0u);
         const int tmax = max(x16_lo(t2), x16_hi(t2));
-        // the largest live slot holding the thread's maximum (smallest i)
-        const uint32_t tm2 = x16_splat(tmax);
-        const uint32_t bm = x16_gather(x16_ge(H1[0], tm2), x16_ge(H1[1], tm2), x16_ge(H1[2], tm2),
-                                       x16_ge(H1[3], tm2)) & am;
         const int tl = am ? __ffs(am) - 1 : -1;
         const int th = am ? 31 - __clz(am) : -1;
-        const int ts = bm ? 31 - __clz(bm) : -1;
+        // the largest live slot holding the thread's maximum (smallest i)
+        int ts = -1;
+        if (need_bs) {
+          const uint32_t tm2 = x16_splat(tmax);
+          uint32_t bmw = 0;
+#pragma unroll
+          for (int r = 0; r < X16_P; ++r) bmw |= x16_halfmask(x16_ge(H1[r], tm2)) & (0x10001u << r);
+          const uint32_t bm = ((bmw & 0xfu) | ((bmw >> 12) & 0xf0u)) & am;
+          ts = bm ? 31 - __clz(bm) : -1;
+        }
         // ---- traceback word and origin of k -----------------------------------------
         if (TB) {
           const int64_t row = (ckmode >= 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
-          if (dom) tbp[row * (WIN / 8) + tid] = nib;
+          // only the 32-byte sectors (8 threads) holding a slot of the range
+          const unsigned act = __ballot_sync(X16_FULL, dom != 0);
+          if ((act >> (lane & 24)) & 0xffu) tbp[row * (WIN / 8) + tid] = nib;
           if (tid == 0) ckp[row] = cn;
         }
         {
@@ -559,13 +576,11 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
         const int wmax = __reduce_max_sync(X16_FULL, am ? tmax : 0);
         const int wlo = __reduce_min_sync(X16_FULL, am ? base_slot + tl : INT_MAX);
         const int whi = __reduce_max_sync(X16_FULL, am ? base_slot + th : INT_MIN);
-        const int wbs = __reduce_max_sync(X16_FULL, (am && tmax == wmax) ? base_slot + ts : -1);
+        const int wbs = need_bs ? __reduce_max_sync(X16_FULL, (am && tmax == wmax) ? base_slot + ts : -1) : 0;
         pmax = wmax;
         plo = wlo;
         phi = whi;
         pbs = wbs;
-        pk_ = k;
-        pc = cn;
         pending = true;
         if (W > 1) {
           const int nb = k & 1;
@@ -587,7 +602,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
     if (pending) {  // the last antidiagonal's reductions
       int gmax = pmax, glo = plo, ghi = phi, gbs = pbs;
       if (W > 1) {
-        const int nb = pk_ & 1;
+        const int nb = (k - 1) & 1;
         const int v0 = lane < W ? sh.red[nb][lane][0] : INT_MIN;
         gmax = __reduce_max_sync(X16_FULL, v0);
         glo = __reduce_min_sync(X16_FULL, lane < W ? sh.red[nb][lane][1] : INT_MAX);
@@ -595,9 +610,11 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32)
         gbs = __reduce_max_sync(X16_FULL, (lane < W && v0 == gmax) ? sh.red[nb][lane][3] : -1);
       }
       pending = false;
-      if (!consume(pk_, pc, gmax, glo, ghi, gbs)) ended = true;
+      if (!consume(k - 1, c, gmax, glo, ghi, gbs)) ended = true;
     }
     if (status == FILTR_ST_OK && k > k_last && k_last == M + N) ended = true;
+    // a dropped global pair without its best cell: the int32 sweep finds it
+    if (!LOCAL && !track && ckmode != 2 && status == FILTR_ST_OK && ended && !corner) status = X16_OVERFLOW;
     if (ckmode == 3 && status == FILTR_ST_TOO_WIDE && W < XD_MAX_WARPS) break;
     if (ckmode >= 2 && status == X16_OVERFLOW) {  // the whole pair goes to the int32 sweep
       if (tid == 0 && ckmode == 3) ck->flags[0] = 3;

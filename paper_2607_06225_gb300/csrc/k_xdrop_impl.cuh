@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         tbp = ck->pool + rsv;
       } else {
         ckp = reinterpret_cast<int32_t *>(a.tb + a.tbl[p].off);
-        tbp = a.tb + a.tbl[p].off + (uint64_t)(M + N + 1);
+        tbp = a.tb + a.tbl[p].off + (uint64_t)xd_origin_words(M, N);
       }
     }
 
@@ -415,8 +415,11 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32) k_xdrop(const FullArgs 
         if (MIDF) G1[s] = Gn[s];
       }
       if (TB) {
+        // only the 32-byte sectors (8 threads) of the row that hold a slot of
+        // the candidate range: the walk reads no other
         const int64_t row = (ckmode >= 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
-        tbp[row * (WIN / 8) + tid] = nibs;
+        const unsigned act = __ballot_sync(FULLMASK, vB >= 0 && vA < XS);
+        if ((act >> (lane & 24)) & 0xffu) tbp[row * (WIN / 8) + tid] = nibs;
         if (tid == 0) ckp[row] = cn;
       }
       // this thread's best cell on k (largest slot among equal maxima = smallest i)

@@ -1,8 +1,9 @@
 // k_xdrop_layout.h -- traceback layout of the antidiagonal (X-drop) kernel.
 //
 // Per pair: (M + N + 1) int32 window origins c_k (the column j of slot 0 on
-// antidiagonal k), then for every antidiagonal k a window of WPK words holding
-// one 4-bit nibble per slot (slot p <-> cell (k - c_k - p, c_k + p)).
+// antidiagonal k), padded to a multiple of 8 words, then for every antidiagonal
+// k a window of WPK words holding one 4-bit nibble per slot (slot p <-> cell
+// (k - c_k - p, c_k + p)).
 #pragma once
 
 #include "filtr_internal.h"
@@ -11,8 +12,12 @@ namespace filtr {
 
 FILTR_HD int xd_window_slots(int warps, int S) { return warps * 32 * S; }
 FILTR_HD int xd_words_per_k(int warps, int S) { return xd_window_slots(warps, S) / 8; }
+// the origins, padded to whole 32-byte sectors so that every antidiagonal's
+// row of words starts on a sector (a kernel may then skip the sectors of a
+// row that hold no live slot without partial-sector writes)
+FILTR_HD int64_t xd_origin_words(int64_t M, int64_t N) { return (M + N + 1 + 7) & ~(int64_t)7; }
 FILTR_HD uint64_t xd_tb_words(int64_t M, int64_t N, int warps, int S) {
-  return (uint64_t)(M + N + 1) * (uint64_t)(1 + xd_words_per_k(warps, S));
+  return (uint64_t)xd_origin_words(M, N) + (uint64_t)(M + N + 1) * (uint64_t)xd_words_per_k(warps, S);
 }
 
 // Checkpointed sweep of one long pair (filtr_align_long).  The antidiagonals
@@ -70,7 +75,7 @@ struct XdGeom {
 __device__ __forceinline__ void xd_geom_init(XdGeom &g, const uint32_t *base, int64_t M, int64_t N,
                                              const TbLayout &L) {
   g.ck = reinterpret_cast<const int32_t *>(base);
-  g.tb = base + (M + N + 1);
+  g.tb = base + xd_origin_words(M, N);
   g.wpk = xd_words_per_k(L.warps, L.R);
 }
 

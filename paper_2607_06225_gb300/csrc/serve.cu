@@ -43,7 +43,8 @@ struct Req {
   uint64_t bytes = 0;   // lane memory this request needs
   uint64_t io = 0;      // of which in the lane's I/O buffer
   uint64_t cells = 0;
-  bool big = false;     // cost class
+  bool big = false;     // runs alone (on the intra-pair kernel unless X-drop)
+  int cls = 0;          // cost class: requests batch only within a factor of 4 in cells
   uint64_t t_submit = 0, t_launch = 0, t_done = 0;
   int state = 0;        // 0 queued, 1 running, 2 done
   filtr_status err = FILTR_OK;
@@ -63,7 +64,20 @@ struct Lane {
   uint64_t cig_cap = 0;
 };
 
-constexpr uint64_t BIG_CELLS = 1ull << 26;  // pairs above this are batched only with each other
+// A request above BIG_CELLS runs alone: one warp would take it tens of
+// milliseconds (every request of its micro-batch would wait that long), while
+// the intra-pair kernel spreads its row strips over as many warps.
+constexpr uint64_t BIG_CELLS = 1ull << 22;
+// Micro-batches hold requests of one cost class (cells within a factor of 4),
+// so a short request never waits for a long one launched with it.
+inline int cost_class(uint64_t cells) {
+  int b = 0;
+  while (cells >= 4 && b < 31) {
+    cells >>= 2;
+    ++b;
+  }
+  return b;
+}
 
 }  // namespace
 
@@ -103,7 +117,7 @@ uint64_t request_bytes(const ScoreParams &sp, uint32_t M, uint32_t N) {
 }
 
 bool same_params(const Req *a, const Req *b) {
-  return memcmp(&a->sp, &b->sp, sizeof(ScoreParams)) == 0 && a->big == b->big;
+  return memcmp(&a->sp, &b->sp, sizeof(ScoreParams)) == 0 && a->big == b->big && a->cls == b->cls;
 }
 
 // Launch one micro-batch on a free lane (called with the server lock released).
@@ -162,7 +176,7 @@ filtr_status launch_batch(Server *S, Lane &L) {
   filtr_result *dres = reinterpret_cast<filtr_result *>(L.d_io + o_res);
   uint32_t *dcig = reinterpret_cast<uint32_t *>(L.d_io + o_cig);
   filtr_status rc;
-  if (n == 1 && B[0]->big && !B[0]->sp.use_xdrop && B[0]->q.size() > 512 && !B[0]->r.empty()) {
+  if (n == 1 && B[0]->big && !B[0]->sp.use_xdrop && B[0]->q.size() > 1024 && !B[0]->r.empty()) {
     // a large request: every SM on it (intra-pair strips) instead of one warp
     rc = long_pair_async(L.ctx, B[0]->sp, &B[0]->p, b.q_seq, (uint32_t)B[0]->q.size(), b.r_seq,
                          (uint32_t)B[0]->r.size(), dres, B[0]->sp.traceback ? dcig : nullptr,
@@ -399,6 +413,7 @@ filtr_status filtr_serve_submit(filtr_server *srv, const filtr_params *params, c
   R->io = 256 * 8 + 2ull * (M + N) + 4ull * (M + N + 1) + 64;
   R->cells = band_cells(M, N, R->sp);
   R->big = R->cells > BIG_CELLS;
+  R->cls = cost_class(R->cells);
   std::lock_guard<std::mutex> lk(S->mu);
   if (R->bytes > S->lane_capacity || R->io > S->lane_io || S->queue.size() >= S->max_queue ||
       S->stop) {

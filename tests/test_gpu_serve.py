@@ -101,7 +101,7 @@ def test_poll_and_errors(F):
 
 
 def test_large_request_route_and_budget_refusal(F):
-    """A request above 2^26 cells (a 8200 x 8300 protein pair, local, traceback)
+    """A request above 2^22 cells (a 8200 x 8300 protein pair, local, traceback)
     runs alone on the intra-pair kernel and equals the oracle; a request whose
     traceback exceeds a lane's share of the budget is refused with
     FILTR_ERR_BUSY at submission, and the server keeps serving afterwards."""
@@ -112,7 +112,7 @@ def test_large_request_route_and_budget_refusal(F):
     rng = np.random.default_rng(44)
     r = rng.integers(0, 20, 8300).astype(np.uint8)
     q = np.concatenate([rng.integers(0, 20, 3000).astype(np.uint8), r[2000:7200]])
-    assert q.shape[0] * r.shape[0] > 1 << 26
+    assert q.shape[0] * r.shape[0] > 1 << 22
     ctx = F.Context(0, 1 << 28)
     srv = F.Server(ctx, 2 << 30, max_inflight=2)
     try:
