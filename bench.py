@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-lanes", type=int, default=8, help="concurrent serving lanes")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving measurement and print it")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="skip the sub-records of the other workloads (short DNA, long reads, "
                          "the megabase pair) on the default protein run")
@@ -239,6 +242,9 @@ def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lane
             cells += int(res["cells"])
         return time.perf_counter() - t0, lat, cells
 
+    def pct(x, q):
+        return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
     burst, _ = synth.serve_mix(400, rate_hz=1e9, seed=seed + 100)
     wall, _, cells = run(burst, paced=False)
     capacity = cells / wall  # cells per second for this mix
@@ -248,11 +254,16 @@ def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lane
     reqs, _ = synth.serve_mix(n, rate_hz=rate, seed=seed)
     wall, lat, cells = run(reqs, paced=True)
     srv.close()
+    per_kind = {}
+    for kind in SERVE_KINDS:
+        lk = [x for x, rq in zip(lat, reqs) if rq.kind == kind]
+        per_kind[kind] = {"requests": len(lk), "p50_ms": pct(lk, 50), "p99_ms": pct(lk, 99)}
     lat = np.array(lat)
     return {"requests": n, "offered_rate_hz": rate, "load_frac_of_capacity": load_frac,
             "offered_gcups": rate * mean_cells / 1e9, "capacity_gcups": capacity / 1e9,
             "achieved_gcups": cells / wall / 1e9, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "per_kind": per_kind,
             "mix": "40% SW protein / 40% band-256 NW DNA / 20% X-drop-400 DNA, log-normal lengths "
                    "(median 2000, sigma 1, clipped 100-100000), traceback on",
             "budget_gb": budget_gb, "lanes": lanes}
@@ -943,6 +954,12 @@ def main():
             print(json.dumps({"fold_table": tab}), flush=True)
         ctx.close()
         return
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0,
+                                                     args.serve_lanes)}), flush=True)
+        ctx.close()
+        return
     if args.search_only:
         if rank == 0:
             tab = search_table(F, ctx, args.steps, args.warmup, stream, flush, dev,
@@ -969,7 +986,8 @@ def main():
             line["fold"] = fold_table(F, ctx, 3, 1, stream, flush, dev,
                                       cpu=not args.no_cpu_baseline)
         if not args.no_serve and wl == "protein-sw-100k":
-            line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0, 4)
+            line["serving"] = serve_bench(F, ctx, args.serve_seconds, args.serve_load, 40.0,
+                                          args.serve_lanes)
         if not args.no_cpu_baseline and wl != "long-pair-1m":
             npairs, tpairs, runs = CPU_SAMPLE[wl]
             if args.cpu_sample != CPU_SAMPLE_PAIRS:

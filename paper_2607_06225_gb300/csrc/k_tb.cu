@@ -256,12 +256,19 @@ struct WalkCore {
   bool mid = false;  // Table 1's M/I/D: a gap that opened leaves through a diagonal step (state 3)
 };
 
+// Residue codes of the walk's diagonal steps: straight from the sequences, or
+// from codes a warp cached with the traceback bits.
+struct GlobalCodes {
+  __device__ int q(const WalkCore &w, int i) const { return w.q[i - 1]; }
+  __device__ int r(const WalkCore &w, int j) const { return w.r[j - 1]; }
+};
+
 // Walks until the alignment's start is reached (returns true), or until the
 // current cell's antidiagonal is <= k_stop or < k_low (returns false, state
 // kept); the steps are those of k_walk.
-template <class Bits>
+template <class Bits, class Codes = GlobalCodes>
 __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t k_stop,
-                                         int64_t k_low) {
+                                         int64_t k_low, const Codes &codes = Codes{}) {
   for (;;) {
     if (w.state == 0) {
       if ((w.i == 0 && w.j == 0) || (w.local && w.v == 0)) return true;
@@ -286,7 +293,7 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
       } else if (nib & TB_PE) {
         w.state = 1;
       } else {
-        const int qc = w.q[w.i - 1], rc = w.r[w.j - 1];
+        const int qc = codes.q(w, w.i), rc = codes.r(w, w.j);
         w.em.put(qc == rc ? OP_EQ : OP_X, 1);
         w.v -= w.subst[qc * w.A + rc];
         --w.i;
@@ -324,7 +331,7 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
       --w.i;
     } else {  // state 3: the gap opened from M here, so this cell is a diagonal step
       if (w.i == 0 && w.j == 0) return true;
-      const int qc = w.q[w.i - 1], rc = w.r[w.j - 1];
+      const int qc = codes.q(w, w.i), rc = codes.r(w, w.j);
       w.em.put(qc == rc ? OP_EQ : OP_X, 1);
       w.v -= w.subst[qc * w.A + rc];
       --w.i;
@@ -337,6 +344,16 @@ __device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t 
 struct XdCache {
   uint32_t w[32 * XW];
   int32_t c[32], b[32];
+  // the 32 query / reference codes below the window's first cell (i0, j0):
+  // qc[x] = q[i0 - 1 - x], rc[x] = r[j0 - 1 - x] (a walk inside the window
+  // steps diagonally only from cells with i > i0 - 32, j > j0 - 32)
+  uint8_t qc[32], rc[32];
+  int32_t i0, j0;
+};
+struct XdCacheCodes {
+  const XdCache *C;
+  __device__ int q(const WalkCore &, int i) const { return C->qc[C->i0 - i]; }
+  __device__ int r(const WalkCore &, int j) const { return C->rc[C->j0 - j]; }
 };
 
 // Where antidiagonal k's window origin and traceback row live.
@@ -359,18 +376,27 @@ struct XdPoolRows {  // single-pass segmented sweep: segment s = (k - 1) / C
   const int32_t *seg_w;
   int C;
   __device__ void at(int64_t k, int &c, const uint32_t *&row, int &w) const {
-    const int64_t s = (k - 1) / C, i = k - 1 - s * C;
+    const int km = (int)(k - 1);  // antidiagonals stay below 2^31
+    const int s = km / C, i = km - s * C;
     w = xd_words_per_k(__ldg(seg_w + s), 8);
-    c = __ldg(seg_ck_all + s * C + i);
-    row = pool + __ldg(seg_off + s) + i * w;
+    c = __ldg(seg_ck_all + (int64_t)s * C + i);
+    row = pool + __ldg(seg_off + s) + (int64_t)i * w;
   }
 };
 
-// All lanes: cache antidiagonals k0 - lane (those > k_min) around column j0.
+// All lanes: cache antidiagonals k0 - lane (those > k_min) around column j0,
+// and the residue codes the walk reads below (i0, j0).
 template <class Rows>
 __device__ __forceinline__ void xd_fill(XdCache &C, const Rows &rows, int64_t k0, int j0,
-                                        int64_t k_min) {
+                                        int64_t k_min, const WalkCore &w) {
   const int lane = threadIdx.x & 31;
+  const int i0 = (int)(k0 - j0);
+  C.qc[lane] = (i0 - 1 - lane >= 0) ? w.q[i0 - 1 - lane] : 0;
+  C.rc[lane] = (j0 - 1 - lane >= 0) ? w.r[j0 - 1 - lane] : 0;
+  if (lane == 0) {
+    C.i0 = i0;
+    C.j0 = j0;
+  }
   const int64_t kk = k0 - lane;
   if (kk > k_min) {
     int c, wpk;
@@ -400,6 +426,9 @@ struct XdCacheBits {
 // One warp per pair of a batched X-drop call (4 pairs per 128-thread block).
 __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
   __shared__ XdCache cache[4];
+  __shared__ int8_t s_sub[MAX_ALPHA * MAX_ALPHA];
+  for (int x = threadIdx.x; x < a.sp.alphabet * a.sp.alphabet; x += blockDim.x) s_sub[x] = a.sp.subst[x];
+  __syncthreads();
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t t = blockIdx.x * 4 + wib;
   if (t >= a.n_order) return;
@@ -415,7 +444,7 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
   const int32_t *ck = reinterpret_cast<const int32_t *>(base);
   const uint32_t *tbw = base + xd_origin_words(M, N);
   const int wpk = xd_words_per_k(L.warps, L.R);
-  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
+  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], s_sub, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
              Emitter{a.stage + a.stage_off[p], 0, -1, 0}, a.sp.mid != 0};
   XdCache &C = cache[wib];
@@ -424,8 +453,8 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
     const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
     if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
     const int64_t k0 = (int64_t)i0 + j0;
-    xd_fill(C, XdRows{ck, tbw, wpk, 0}, k0, j0, 0);
-    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31);
+    xd_fill(C, XdRows{ck, tbw, wpk, 0}, k0, j0, 0, w);
+    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31, XdCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {
@@ -525,12 +554,15 @@ __global__ void __launch_bounds__(128) k_walk_tw(const WalkArgs a) {
 __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int32_t *seg_ck,
                             int k_start, int wpk, WalkState *ws) {
   __shared__ XdCache C;
+  __shared__ int8_t s_sub[MAX_ALPHA * MAX_ALPHA];
+  for (int x = threadIdx.x; x < a.sp.alphabet * a.sp.alphabet; x += blockDim.x) s_sub[x] = a.sp.subst[x];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const WalkState st = *ws;
   if (st.done) return;
   const uint32_t p = a.order[0];
-  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
+  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], s_sub, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, st.i, st.j, st.v, st.state,
              Emitter{a.stage + a.stage_off[p], st.n, st.cur, st.run}, a.sp.mid != 0};
   bool done = false;
@@ -539,8 +571,8 @@ __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int3
     const bool d = __shfl_sync(0xffffffffu, (int)done, 0) != 0;
     const int64_t k0 = (int64_t)i0 + j0;
     if (d || k0 <= k_start) break;
-    xd_fill(C, XdRows{seg_ck, seg_tb, wpk, (int64_t)k_start + 1}, k0, j0, k_start);
-    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, k_start, k0 - 31);
+    xd_fill(C, XdRows{seg_ck, seg_tb, wpk, (int64_t)k_start + 1}, k0, j0, k_start, w);
+    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, k_start, k0 - 31, XdCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {
@@ -567,6 +599,9 @@ __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int3
 // The whole traceback of a single-pass segmented sweep; one warp.
 __global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
   __shared__ XdCache C;
+  __shared__ int8_t s_sub[MAX_ALPHA * MAX_ALPHA];
+  for (int x = threadIdx.x; x < a.sp.alphabet * a.sp.alphabet; x += blockDim.x) s_sub[x] = a.sp.subst[x];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const uint32_t p = a.order[0];
@@ -575,7 +610,7 @@ __global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
     if (lane == 0) a.out[p].cigar_len = 0;
     return;
   }
-  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], a.sp.subst, a.sp.alphabet,
+  WalkCore w{a.b.q_seq + a.b.q_off[p], a.b.r_seq + a.b.r_off[p], s_sub, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
              Emitter{a.stage + a.stage_off[p], 0, -1, 0}, a.sp.mid != 0};
   bool done = false;
@@ -583,8 +618,8 @@ __global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
     const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
     if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
     const int64_t k0 = (int64_t)i0 + j0;
-    xd_fill(C, rows, k0, j0, 0);
-    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31);
+    xd_fill(C, rows, k0, j0, 0, w);
+    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31, XdCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {

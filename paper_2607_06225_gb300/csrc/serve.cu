@@ -1,16 +1,16 @@
 // serve.cu -- continuous batching of single-pair requests (filtr_serve_*).
 //
-// A worker thread owns `lanes`: each lane is a context (own workspace and
-// stream), a device I/O buffer and pinned host staging.  Submitted requests
-// (host copies, codes checked on submit) wait in a FIFO queue.  Whenever a
-// lane is free, the worker forms a micro-batch from the oldest request and the
-// following queued requests with identical parameters and a similar cost
-// class, as far as the lane's memory allows (sequences + results + CIGAR +
-// traceback + staging bytes), copies it in, launches the batched alignment on
-// the lane's stream and records an event.  Lanes run concurrently, so requests
-// that arrive while others are on the GPU start as soon as a lane frees up and
-// overlap with them on the device.  Completion is found by polling the lanes'
-// events; results move to per-ticket host storage and waiters are woken.
+// The server owns `lanes`: each lane is a context (own workspace and stream),
+// a device I/O buffer, pinned host staging and a host thread.  Submitted
+// requests (host copies, codes checked on submit) wait in a FIFO queue.
+// Whenever a lane is free, its thread forms a micro-batch from the oldest
+// request and the following queued requests with identical parameters and the
+// same cost class, as far as the lane's memory allows (sequences + results +
+// CIGAR + traceback + staging bytes), copies it in, launches the batched
+// alignment on the lane's stream and waits for its event.  Lanes run
+// concurrently, so requests that arrive while others are on the GPU start as
+// soon as a lane frees up and overlap with them on the device; results move to
+// per-ticket host storage and waiters are woken.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -85,7 +85,7 @@ struct Server {
   Ctx *parent = nullptr;
   size_t budget = 0;
   std::vector<Lane> lanes;
-  std::thread worker;
+  std::vector<std::thread> workers;  // one per lane
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Req *> queue;
@@ -213,85 +213,64 @@ void finish_batch(Lane &L, uint64_t t) {
   L.busy = false;
 }
 
-void worker_main(Server *S) {
+// One host thread per lane: it takes the next micro-batch from the shared
+// queue when its lane is free, launches it and waits for it.  A batch whose
+// host code must wait for the device (the X-drop sweep reads back the pairs
+// that outgrew their window) then holds up only its own lane.
+void lane_main(Server *S, Lane *Lp) {
+  Lane &L = *Lp;
   cudaSetDevice(S->parent->device);
   std::unique_lock<std::mutex> lk(S->mu);
-  while (true) {
-    // completions
-    bool any_busy = false, finished = false;
-    for (Lane &L : S->lanes) {
-      if (!L.busy) continue;
-      const cudaError_t q = cudaEventQuery(L.done);
-      if (q == cudaSuccess) {
-        finish_batch(L, now_ns());
-        finished = true;
-      } else if (q != cudaErrorNotReady) {
-        S->fatal = FILTR_ERR_CUDA;
-        S->fatal_msg = cudaGetErrorString(q);
-        for (Req *r : L.batch) {
-          r->err = FILTR_ERR_CUDA;
-          r->state = 2;
-          r->t_done = now_ns();
-        }
-        L.batch.clear();
-        L.busy = false;
-        finished = true;
+  for (;;) {
+    S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+    if (S->stop) break;
+    Req *head = S->queue.front();
+    uint64_t used = 0, used_io = 0;
+    std::vector<Req *> pick;
+    for (auto it = S->queue.begin(); it != S->queue.end();) {
+      Req *r = *it;
+      if (same_params(head, r) &&
+          (pick.empty() || (used + r->bytes <= S->lane_capacity && used_io + r->io <= S->lane_io)) &&
+          pick.size() < 65536) {
+        used += r->bytes;
+        used_io += r->io;
+        pick.push_back(r);
+        it = S->queue.erase(it);
+        if (r->big) break;  // big requests run alone
       } else {
-        any_busy = true;
+        ++it;
       }
     }
-    if (finished) S->cv_done.notify_all();
-    if (S->stop && !any_busy) break;
-    // launches
-    bool launched = false;
-    for (Lane &L : S->lanes) {
-      if (L.busy || S->queue.empty() || S->stop) continue;
-      Req *head = S->queue.front();
-      uint64_t used = 0, used_io = 0;
-      std::vector<Req *> pick;
-      for (auto it = S->queue.begin(); it != S->queue.end();) {
-        Req *r = *it;
-        if (same_params(head, r) &&
-            (pick.empty() ||
-             (used + r->bytes <= S->lane_capacity && used_io + r->io <= S->lane_io)) &&
-            pick.size() < 65536) {
-          used += r->bytes;
-          used_io += r->io;
-          pick.push_back(r);
-          it = S->queue.erase(it);
-          if (r->big) break;  // big requests run alone
-        } else {
-          ++it;
-        }
-      }
-      const uint64_t t = now_ns();
-      for (Req *r : pick) {
-        r->state = 1;
-        r->t_launch = t;
-      }
-      L.batch = pick;
-      L.busy = true;
-      lk.unlock();
-      const filtr_status rc = launch_batch(S, L);
-      lk.lock();
-      if (rc != FILTR_OK) {
-        for (Req *r : L.batch) {
-          r->err = rc;
-          r->state = 2;
-          r->t_done = now_ns();
-        }
-        L.batch.clear();
-        L.busy = false;
-        S->cv_done.notify_all();
-      }
-      launched = true;
+    const uint64_t t = now_ns();
+    for (Req *r : pick) {
+      r->state = 1;
+      r->t_launch = t;
     }
-    if (!launched) {
-      if (any_busy)
-        S->cv_work.wait_for(lk, std::chrono::microseconds(50));
-      else
-        S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+    L.batch = pick;
+    L.busy = true;
+    if (!S->queue.empty()) S->cv_work.notify_one();  // another lane may take the rest
+    lk.unlock();
+    filtr_status rc = launch_batch(S, L);
+    cudaError_t e = cudaSuccess;
+    if (rc == FILTR_OK) e = cudaEventSynchronize(L.done);
+    lk.lock();
+    if (rc == FILTR_OK && e == cudaSuccess) {
+      finish_batch(L, now_ns());
+    } else {
+      if (rc == FILTR_OK) {
+        rc = FILTR_ERR_CUDA;
+        S->fatal = FILTR_ERR_CUDA;
+        S->fatal_msg = cudaGetErrorString(e);
+      }
+      for (Req *r : L.batch) {
+        r->err = rc;
+        r->state = 2;
+        r->t_done = now_ns();
+      }
+      L.batch.clear();
+      L.busy = false;
     }
+    S->cv_done.notify_all();
   }
 }
 
@@ -373,7 +352,7 @@ filtr_status filtr_serve_create(filtr_ctx *ctx, size_t mem_budget, uint32_t max_
     }
     L.io_bytes = io;
   }
-  S->worker = std::thread(worker_main, S);
+  for (Lane &L : S->lanes) S->workers.emplace_back(lane_main, S, &L);
   *out = reinterpret_cast<filtr_server *>(S);
   return FILTR_OK;
 }
@@ -479,7 +458,8 @@ filtr_status filtr_serve_destroy(filtr_server *srv) {
     S->queue.clear();
   }
   S->cv_work.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  for (std::thread &w : S->workers)
+    if (w.joinable()) w.join();
   for (auto &kv : S->table) delete kv.second;
   for (Lane &L : S->lanes) {
     if (L.ctx) ctx_delete(L.ctx);
