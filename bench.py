@@ -852,6 +852,7 @@ def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev,
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     fwd_ms, walk_ms, launches, other_ms = [], [], [], {}
     packed = cells_packed = 0
+    xd16 = (0, 0)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -872,6 +873,7 @@ def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev,
         launches.append(st["launches"])
         packed = st.get("pairs_i16x2", 0)
         cells_packed = st.get("cells_i16x2", 0)
+        xd16 = (st.get("pairs_xd16", 0), st.get("pairs_xd16_rerun", 0))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
@@ -905,10 +907,12 @@ def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev,
             "config": {"workload": wl, "pairs": batch.n, "cells_per_step": cells,
                        "mode": WORKLOAD_DESC[wl],
                        "precision": args.precision, "pairs_i16x2": packed,
+                       "pairs_sweep_i16x2": xd16[0], "pairs_sweep_rerun_i32": xd16[1],
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replica x{world}"},
             "plain_per_pair": plain,
             "plain_long_per_pair": plain_long,
+            "step_ms": step_ms,
             "phases_ms": {"forward": fwd, "walk": statistics.median(walk_ms), "step": ms,
                           **{k: statistics.median(v) for k, v in other_ms.items()}},
             "autotune_ns_per_warp_step": tune,

@@ -149,11 +149,14 @@ filtr_status filtr_params_check(const filtr_params *params);
 filtr_status filtr_ctx_create(int device, size_t workspace_bytes, filtr_ctx **out);
 filtr_status filtr_ctx_destroy(filtr_ctx *ctx);
 
-/* Pack step: validate n residue codes at `codes` (DEVICE) against `alphabet`
- * and write them packed at `packed` (DEVICE, ceil(n*bits/32) uint32 words,
- * bits = 2 for DNA, 8 for protein; residue t sits at bits [bits*(t % per_word), ...)
- * of word t / per_word).  *bad_out (DEVICE, one uint32) receives the number of
- * invalid codes.  Stream ordered; no synchronisation. */
+/* Pack step (Sec. 2's residue alphabets): validate n residue codes at `codes`
+ * (DEVICE, 16-byte aligned: each thread reads 16 codes with one vector load)
+ * against `alphabet` and write them packed at `packed` (DEVICE, 4-byte aligned,
+ * ceil(n*bits/32) uint32 words, bits = 2 for DNA, 8 for protein; residue t
+ * sits at bits [bits*(t % per_word), ...) of word t / per_word; a DNA code
+ * keeps its two low bits).  *bad_out (DEVICE, one uint32, not cleared here)
+ * gains the number of codes >= alphabet.  Stream ordered; no synchronisation.
+ * FILTR_ERR_INVALID for a bad alphabet, a NULL or misaligned pointer. */
 filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint32_t *packed,
                         uint32_t *bad_out, void *stream);
 

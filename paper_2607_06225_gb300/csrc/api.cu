@@ -904,6 +904,14 @@ filtr_status filtr_pack(const uint8_t *codes, uint64_t n, int32_t alphabet, uint
     set_error("NULL pointer");
     return FILTR_ERR_INVALID;
   }
+  if (reinterpret_cast<uintptr_t>(codes) & 15u) {
+    set_error("filtr_pack: codes must start on a 16-byte boundary (they are read 16 at a time)");
+    return FILTR_ERR_INVALID;
+  }
+  if (reinterpret_cast<uintptr_t>(packed) & 3u) {
+    set_error("filtr_pack: packed must start on a 4-byte boundary");
+    return FILTR_ERR_INVALID;
+  }
   cudaError_t e = launch_pack(codes, n, alphabet, packed, bad_out, (cudaStream_t)stream);
   return e == cudaSuccess ? FILTR_OK : cuda_fail(e, "pack launch");
 }

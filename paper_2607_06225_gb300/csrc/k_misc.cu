@@ -95,23 +95,56 @@ __global__ void k_validate_pairs(const BatchDev b0, uint32_t n, int alphabet, ui
 }
 
 // DNA: 16 codes of 2 bits per word; protein: 4 codes of 8 bits per word.
+// 16 codes per thread from one 16-byte load: DNA packs them into one word
+// (2 bits each), protein copies them as four words (8 bits each); codes at or
+// above the alphabet are counted.  `codes` must be 16-byte aligned; the last
+// partial group of 16 is read byte by byte.
 __global__ void k_pack(const uint8_t *codes, uint64_t n, int alphabet, uint32_t *packed,
                        uint32_t *bad) {
-  const int per = (alphabet <= 4) ? 16 : 4, bits = (alphabet <= 4) ? 2 : 8;
-  const uint64_t words = (n + per - 1) / per;
+  const bool dna = alphabet <= 4;
+  const uint32_t lim = (uint32_t)alphabet - 1u;
+  const uint32_t limv = lim * 0x01010101u;
+  const uint64_t groups = (n + 15) / 16;
   uint32_t cnt = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < words; w += stride) {
-    uint32_t v = 0;
-    for (int k = 0; k < per; ++k) {
-      const uint64_t x = w * per + k;
-      if (x < n) {
-        const uint32_t c = codes[x];
-        cnt += c >= (uint32_t)alphabet;
-        v |= (c & ((1u << bits) - 1)) << (bits * k);
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < groups; g += stride) {
+    uint32_t x[4];
+    if (g * 16 + 16 <= n) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(codes) + g);
+      x[0] = v.x;
+      x[1] = v.y;
+      x[2] = v.z;
+      x[3] = v.w;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cnt += __popc(__vcmpgtu4(x[k], limv)) >> 3;
+    } else {  // the tail: bytes past n count as code 0
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t w = 0;
+        for (int b = 0; b < 4; ++b) {
+          const uint64_t t = g * 16 + 4 * k + b;
+          const uint32_t c = t < n ? codes[t] : 0u;
+          cnt += c > lim;
+          w |= (c & 0xffu) << (8 * b);
+        }
+        x[k] = w;
       }
     }
-    packed[w] = v;
+    if (dna) {  // four bytes -> 8 bits: code b at bits 2b
+      uint32_t out = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t t = x[k] & 0x03030303u;
+        t = (t | (t >> 6)) & 0x000f000fu;
+        t = (t | (t >> 12)) & 0xffu;
+        out |= t << (8 * k);
+      }
+      packed[g] = out;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (g * 4 + k < (n + 3) / 4) packed[g * 4 + k] = x[k];
+    }
   }
   for (int off = 16; off; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(bad, cnt);
@@ -217,9 +250,8 @@ cudaError_t launch_validate_pairs(const BatchDev &b, uint32_t n, int alphabet, u
 cudaError_t launch_pack(const uint8_t *codes, uint64_t n, int alphabet, uint32_t *packed,
                         uint32_t *bad, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int per = (alphabet <= 4) ? 16 : 4;
-  uint64_t words = (n + per - 1) / per;
-  unsigned blocks = (unsigned)((words + 255) / 256);
+  const uint64_t groups = (n + 15) / 16;
+  unsigned blocks = (unsigned)((groups + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   k_pack<<<blocks, 256, 0, s>>>(codes, n, alphabet, packed, bad);
   return cudaGetLastError();

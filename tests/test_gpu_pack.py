@@ -6,7 +6,8 @@ kernel; the stats report how many did.  Sizes cover the packed staircase's
 edge-only strips (N < 64: every step masked), one and several strips of
 512 and 1024 rows with ragged tails, rows past M in either half of a lane's
 registers, one-residue sequences, and pairs whose bound does not fit (they run
-in int32 and give identical results)."""
+in int32 and give identical results).  Also the residue packer (filtr_pack,
+16 codes per vector load) against a host packer."""
 import numpy as np
 import pytest
 
@@ -225,3 +226,48 @@ def test_each_packed_height(F, R, mode):
         run_checked(F, c, b, sc, expect_packed=b.n)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("alphabet", [4, 20])
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 1000, 65536 + 7])
+def test_filtr_pack_against_host_packer(F, alphabet, n):
+    """filtr_pack (one 16-byte load per thread) against a numpy packer: DNA two
+    bits per code (code t at bits 2*(t % 16) of word t / 16), protein one byte
+    per code; codes >= alphabet are counted (and packed by their low bits)."""
+    import ctypes as C
+
+    import torch
+
+    rng = np.random.default_rng(n + alphabet)
+    codes = rng.integers(0, alphabet, size=n).astype(np.uint8)
+    bad_at = rng.choice(n, size=min(n, 5), replace=False) if n else []
+    for t in bad_at:
+        codes[t] = alphabet + int(rng.integers(0, 50))
+    bits, per = (2, 16) if alphabet == 4 else (8, 4)
+    words = (n * bits + 31) // 32
+    want = np.zeros(max(words, 1), dtype=np.uint64)
+    for t in range(n):
+        want[t // per] |= (int(codes[t]) & ((1 << bits) - 1)) << (bits * (t % per))
+    d_codes = torch.from_numpy(codes if n else np.zeros(1, np.uint8)).cuda()
+    d_packed = torch.zeros(max(words, 1), dtype=torch.int32, device="cuda")
+    d_bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = F.lib().filtr_pack(C.c_void_p(d_codes.data_ptr()), n, alphabet, C.c_void_p(d_packed.data_ptr()),
+                            C.c_void_p(d_bad.data_ptr()), None)
+    torch.cuda.synchronize()
+    assert rc == 0, F.last_error()
+    got = d_packed.cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(got[:words], want[:words])
+    assert int(d_bad.item()) == len(bad_at)
+
+
+def test_filtr_pack_rejects_misaligned_codes(F):
+    import ctypes as C
+
+    import torch
+
+    d = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(8, dtype=torch.int32, device="cuda")
+    bad = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = F.lib().filtr_pack(C.c_void_p(d.data_ptr() + 1), 32, 4, C.c_void_p(out.data_ptr()),
+                            C.c_void_p(bad.data_ptr()), None)
+    assert rc == F.ERR_INVALID
