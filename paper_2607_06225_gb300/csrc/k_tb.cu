@@ -263,81 +263,156 @@ struct GlobalCodes {
   __device__ int r(const WalkCore &w, int j) const { return w.r[j - 1]; }
 };
 
-// Walks until the alignment's start is reached (returns true), or until the
-// current cell's antidiagonal is <= k_stop or < k_low (returns false, state
-// kept); the steps are those of k_walk.
+// One step of the walk (those of k_walk): 1 when the alignment's start is
+// reached, 2 when the current cell's antidiagonal is <= k_stop or < k_low or
+// its bits are not cached (state kept), else 0.
 template <class Bits, class Codes = GlobalCodes>
-__device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t k_stop,
-                                         int64_t k_low, const Codes &codes = Codes{}) {
-  for (;;) {
-    if (w.state == 0) {
-      if ((w.i == 0 && w.j == 0) || (w.local && w.v == 0)) return true;
-      if (w.i == 0) {
-        w.em.put(OP_D, (uint32_t)w.j);
-        w.j = 0;
-        return true;
-      }
-      if (w.j == 0) {
-        w.em.put(OP_I, (uint32_t)w.i);
-        w.i = 0;
-        return true;
-      }
+__device__ __forceinline__ int walk_step(WalkCore &w, const Bits &bits, int64_t k_stop, int64_t k_low,
+                                         const Codes &codes = Codes{}) {
+  if (w.state == 0) {
+    if ((w.i == 0 && w.j == 0) || (w.local && w.v == 0)) return 1;
+    if (w.i == 0) {
+      w.em.put(OP_D, (uint32_t)w.j);
+      w.j = 0;
+      return 1;
     }
-    const int64_t k = (int64_t)w.i + w.j;
-    if (k <= k_stop || k < k_low) return false;
-    if (w.state == 0) {
-      const uint32_t nib = bits(w.i, w.j);
-      if (nib > 15u) return false;  // not cached: the warp refills around (i, j)
-      if (nib & TB_PF) {
-        w.state = 2;
-      } else if (nib & TB_PE) {
-        w.state = 1;
-      } else {
-        const int qc = codes.q(w, w.i), rc = codes.r(w, w.j);
-        w.em.put(qc == rc ? OP_EQ : OP_X, 1);
-        w.v -= w.subst[qc * w.A + rc];
-        --w.i;
-        --w.j;
-      }
-    } else if (w.state == 1) {
-      if (w.j == 0) {
-        w.state = 0;
-        continue;
-      }
-      const uint32_t nib = bits(w.i, w.j);
-      if (nib > 15u) return false;
-      w.em.put(OP_D, 1);
-      if (nib & TB_EEXT) {
-        w.v += w.e;
-      } else {
-        w.v += w.oe;
-        w.state = w.mid ? 3 : 0;
-      }
-      --w.j;
-    } else if (w.state == 2) {
-      if (w.i == 0) {
-        w.state = 0;
-        continue;
-      }
-      const uint32_t nib = bits(w.i, w.j);
-      if (nib > 15u) return false;
-      w.em.put(OP_I, 1);
-      if (nib & TB_FEXT) {
-        w.v += w.e;
-      } else {
-        w.v += w.oe;
-        w.state = w.mid ? 3 : 0;
-      }
-      --w.i;
-    } else {  // state 3: the gap opened from M here, so this cell is a diagonal step
-      if (w.i == 0 && w.j == 0) return true;
+    if (w.j == 0) {
+      w.em.put(OP_I, (uint32_t)w.i);
+      w.i = 0;
+      return 1;
+    }
+  }
+  const int64_t k = (int64_t)w.i + w.j;
+  if (k <= k_stop || k < k_low) return 2;
+  if (w.state == 0) {
+    const uint32_t nib = bits(w.i, w.j);
+    if (nib > 15u) return 2;  // not cached: the warp refills around (i, j)
+    if (nib & TB_PF) {
+      w.state = 2;
+    } else if (nib & TB_PE) {
+      w.state = 1;
+    } else {
       const int qc = codes.q(w, w.i), rc = codes.r(w, w.j);
       w.em.put(qc == rc ? OP_EQ : OP_X, 1);
       w.v -= w.subst[qc * w.A + rc];
       --w.i;
       --w.j;
-      w.state = 0;
     }
+  } else if (w.state == 1) {
+    if (w.j == 0) {
+      w.state = 0;
+      return 0;
+    }
+    const uint32_t nib = bits(w.i, w.j);
+    if (nib > 15u) return 2;
+    w.em.put(OP_D, 1);
+    if (nib & TB_EEXT) {
+      w.v += w.e;
+    } else {
+      w.v += w.oe;
+      w.state = w.mid ? 3 : 0;
+    }
+    --w.j;
+  } else if (w.state == 2) {
+    if (w.i == 0) {
+      w.state = 0;
+      return 0;
+    }
+    const uint32_t nib = bits(w.i, w.j);
+    if (nib > 15u) return 2;
+    w.em.put(OP_I, 1);
+    if (nib & TB_FEXT) {
+      w.v += w.e;
+    } else {
+      w.v += w.oe;
+      w.state = w.mid ? 3 : 0;
+    }
+    --w.i;
+  } else {  // state 3: the gap opened from M here, so this cell is a diagonal step
+    if (w.i == 0 && w.j == 0) return 1;
+    const int qc = codes.q(w, w.i), rc = codes.r(w, w.j);
+    w.em.put(qc == rc ? OP_EQ : OP_X, 1);
+    w.v -= w.subst[qc * w.A + rc];
+    --w.i;
+    --w.j;
+    w.state = 0;
+  }
+  return 0;
+}
+
+// Walks until the alignment's start is reached (returns true), or until the
+// current cell's antidiagonal is <= k_stop or < k_low (returns false, state
+// kept): the steps of k_walk, one walk_step at a time.
+template <class Bits, class Codes = GlobalCodes>
+__device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t k_stop,
+                                         int64_t k_low, const Codes &codes = Codes{}) {
+  for (;;) {
+    const int r = walk_step(w, bits, k_stop, k_low, codes);
+    if (r == 1) return true;
+    if (r == 2) return false;
+  }
+}
+
+// The same walk with the whole warp (every lane calls it; w is lane 0's).  A
+// run of diagonal steps (matches and mismatches, H taken from the diagonal) is
+// taken in one go: lane d looks at the cell d steps down the diagonal, a ballot
+// finds where the run ends (a gap, row or column 0, the window's edge, or for
+// local alignments the first cell of value 0), a warp scan gives the value
+// change, and lane 0 emits the run's '=' / 'X' ops.  Lane 0 walks the other
+// steps alone.
+template <class Bits, class Codes>
+__device__ __forceinline__ bool walk_coop(WalkCore &w, const Bits &bits, int64_t k_stop,
+                                          int64_t k_low, const Codes &codes) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const int i = __shfl_sync(FULL, w.i, 0), j = __shfl_sync(FULL, w.j, 0);
+    const int v = __shfl_sync(FULL, w.v, 0), st = __shfl_sync(FULL, w.state, 0);
+    if (st == 0) {
+      const int ii = i - lane, jj = j - lane;
+      const int64_t kk = (int64_t)ii + jj;
+      bool ok = ii >= 1 && jj >= 1 && kk > k_stop && kk >= k_low;
+      int qc = 0, rc = 1, sc = 0;
+      if (ok) {
+        ok = (bits(ii, jj) & (TB_PE | TB_PF)) == 0u;
+        qc = codes.q(w, ii);
+        rc = codes.r(w, jj);
+        sc = w.subst[qc * w.A + rc];
+      }
+      int pre = sc;  // inclusive scan of the scores down the diagonal
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, pre, o);
+        if (lane >= o) pre += t;
+      }
+      if (w.local && v - (pre - sc) == 0) ok = false;  // the value at cell d
+      const unsigned okm = __ballot_sync(FULL, ok);
+      const int L = (okm == FULL) ? 32 : __ffs(~okm) - 1;
+      if (L > 0) {
+        const unsigned eqm = __ballot_sync(FULL, qc == rc);
+        const int dv = __shfl_sync(FULL, pre, L - 1);
+        if (lane == 0) {
+          int d = 0;
+          while (d < L) {
+            const unsigned rest = eqm >> d;
+            const bool eq = (rest & 1u) != 0u;
+            const unsigned stop = eq ? ~rest : rest;
+            const int len = min(stop ? __ffs(stop) - 1 : 32 - d, L - d);
+            w.em.put(eq ? OP_EQ : OP_X, (uint32_t)len);
+            d += len;
+          }
+          w.v -= dv;
+          w.i -= L;
+          w.j -= L;
+        }
+        continue;
+      }
+    }
+    int r = 0;
+    if (lane == 0) r = walk_step(w, bits, k_stop, k_low, codes);
+    r = __shfl_sync(FULL, r, 0);
+    if (r == 1) return true;
+    if (r == 2) return false;
   }
 }
 
@@ -454,7 +529,7 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
     if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
     const int64_t k0 = (int64_t)i0 + j0;
     xd_fill(C, XdRows{ck, tbw, wpk, 0}, k0, j0, 0, w);
-    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31, XdCacheCodes{&C});
+    done = walk_coop(w, XdCacheBits{&C, k0}, -1, k0 - 31, XdCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {
@@ -572,7 +647,7 @@ __global__ void k_walk_segw(const WalkArgs a, const uint32_t *seg_tb, const int3
     const int64_t k0 = (int64_t)i0 + j0;
     if (d || k0 <= k_start) break;
     xd_fill(C, XdRows{seg_ck, seg_tb, wpk, (int64_t)k_start + 1}, k0, j0, k_start, w);
-    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, k_start, k0 - 31, XdCacheCodes{&C});
+    done = walk_coop(w, XdCacheBits{&C, k0}, k_start, k0 - 31, XdCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {
@@ -619,7 +694,7 @@ __global__ void k_walk_poolw(const WalkArgs a, const XdPoolRows rows) {
     if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
     const int64_t k0 = (int64_t)i0 + j0;
     xd_fill(C, rows, k0, j0, 0, w);
-    if (lane == 0) done = walk_run(w, XdCacheBits{&C, k0}, -1, k0 - 31, XdCacheCodes{&C});
+    done = walk_coop(w, XdCacheBits{&C, k0}, -1, k0 - 31, XdCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {
