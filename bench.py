@@ -828,7 +828,7 @@ def measure_workload(F, ctx, synth, wl, args, steps, warmup, stream, flush, dev,
             raise F.FiltrError(rc, F.last_error())
 
     tune = None
-    if not args.no_autotune and not sc.get("xdrop") and not sc.get("zdrop"):
+    if not args.no_autotune:
         # one-time setup, outside every timed region
         if args.tune_load and wl == args.workload:
             with open(args.tune_load) as f:

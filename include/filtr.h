@@ -453,10 +453,21 @@ filtr_status filtr_graph_destroy(filtr_graph *graph);
  *        R = 32, 30, 28, ..., 10, 8; ns_per_warp_step is 0 for shapes not
  *        timed (not allowed for these parameters, or too large for the
  *        workspace); entries past n_shapes are 0.
+ * With X-drop / Z-drop parameters it tunes the antidiagonal sweep instead:
+ * the int16x2 and int32 sweeps at a first group width of one and of two warps
+ * each run a batch of related pairs (2048-residue random references, queries
+ * with 5% substitutions, 2% insertions, 2% deletions) filling the device twice,
+ * and the context keeps, for this recurrence kind (mode, alphabet, traceback,
+ * band, Z-drop, running threshold), the candidate with the smallest time per
+ * evaluated cell among those that finished at least 99% of the pairs without
+ * outgrowing their window; later calls start X-drop pairs at that width and
+ * cell width (the int16x2 sweep still only where the threshold leaves room).
+ * The report then lists n_shapes = 4 candidates: rows_per_lane = the first
+ * group width in warps (1, 1, 2, 2), packed = 1 for the int16x2 sweep (1, 0,
+ * 1, 0), ns_per_warp_step = nanoseconds per evaluated cell (0: not run).
  * Synchronous (waits for the context's previous call); uses the workspace.
- * Errors: FILTR_ERR_INVALID (NULL ctx, bad params, X-drop parameters, which
- * use the antidiagonal kernel only), FILTR_ERR_NOMEM (the workspace holds no
- * calibration batch), FILTR_ERR_CUDA. */
+ * Errors: FILTR_ERR_INVALID (NULL ctx, bad params), FILTR_ERR_NOMEM (the
+ * workspace holds no calibration batch), FILTR_ERR_CUDA. */
 #define FILTR_TUNE_MAX_SHAPES 24
 typedef struct {
   int32_t n_shapes;
@@ -472,9 +483,11 @@ filtr_status filtr_autotune(filtr_ctx *ctx, const filtr_params *params, filtr_tu
  * and a profiled run plans exactly as an unprofiled one did.  Shapes whose
  * ns_per_warp_step is 0 keep the built-in cost scaled to the given ones.
  * Host only: launches nothing, does not wait for the GPU.
- * Errors: FILTR_ERR_INVALID (NULL ctx or report, bad params, X-drop
- * parameters, a shape list other than the one filtr_autotune reports, in its
- * order, a negative or non-finite cost, or no positive cost). */
+ * With X-drop / Z-drop parameters the report is a sweep report (4 candidates
+ * as filtr_autotune lists them) and the fastest timed candidate is installed.
+ * Errors: FILTR_ERR_INVALID (NULL ctx or report, bad params, a shape or
+ * candidate list other than the one filtr_autotune reports, in its order, a
+ * negative or non-finite cost, or no positive cost). */
 filtr_status filtr_tune_apply(filtr_ctx *ctx, const filtr_params *params,
                               const filtr_tune_report *report);
 

@@ -19,6 +19,7 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_CIGAR_CAP, ERR_UNSU
 GLOBAL, LOCAL = 0, 1
 ALPHA_DNA, ALPHA_PROTEIN = 4, 20
 PRUNE_BAND, PRUNE_XDROP, PRUNE_BAND_LITERAL, PRUNE_ZDROP, PRUNE_XDROP_RUNNING = 1, 2, 4, 8, 16
+AFFINE_MID = 2  # FILTR_AFFINE_MID: Table 1's M/I/D form
 PREC_AUTO, PREC_I32, PREC_I16X2 = 0, 1, 2
 XDROP_INF = 0x7FFFFFFF
 ST_OK, ST_DROPPED, ST_UNREACHABLE, ST_EMPTY, ST_TOO_WIDE = 0, 1, 2, 3, 4
@@ -97,6 +98,8 @@ class Stats(C.Structure):
 TUNE_SHAPES = [("i32", 32), ("i32", 24), ("i32", 16), ("i32", 8)] + [
     ("i16x2", R) for R in range(32, 7, -2)]
 TUNE_MAX_SHAPES = 24
+# the antidiagonal sweep's candidates (X-drop / Z-drop parameters), in report order
+TUNE_SWEEP = [("i16x2", 1), ("i32", 1), ("i16x2", 2), ("i32", 2)]
 
 
 class TuneReport(C.Structure):
@@ -223,7 +226,7 @@ def make_params(subst, mode="global", affine=True, gap_open=0, gap_extend=1, ban
     p = Params()
     p.mode = LOCAL if mode in ("local", LOCAL) else GLOBAL
     p.alphabet = int(s.shape[0])
-    p.affine = (2 if mid else 1) if affine else 0  # 2: FILTR_AFFINE_MID
+    p.affine = (AFFINE_MID if mid else 1) if affine else 0
     p.gap_open = int(gap_open)
     p.gap_extend = int(gap_extend)
     p.subst = s.ctypes.data_as(C.POINTER(C.c_int8))
@@ -314,20 +317,34 @@ class Context:
 
     def autotune(self, params) -> dict:
         """Time the tiled kernel shapes for this recurrence kind (filtr_autotune);
-        returns {"i32 R=32": ns per warp step, ...} for the shapes timed."""
+        returns {"i32 R=32": ns per warp step, ...} for the shapes timed, or for
+        X-drop / Z-drop parameters {"sweep i16x2 W=1": ns per cell, ...} for the
+        sweep candidates timed."""
         rep = TuneReport()
         check(lib().filtr_autotune(self.handle, C.byref(params), C.byref(rep)), "filtr_autotune")
+        sweep = bool(params.prune & (PRUNE_XDROP | PRUNE_ZDROP)) or params.affine == AFFINE_MID
         out = {}
         for k in range(rep.n_shapes):
             if rep.ns_per_warp_step[k] > 0:
                 kind = "i16x2" if rep.packed[k] else "i32"
-                out[f"{kind} R={rep.rows_per_lane[k]}"] = rep.ns_per_warp_step[k]
+                key = (f"sweep {kind} W={rep.rows_per_lane[k]}" if sweep
+                       else f"{kind} R={rep.rows_per_lane[k]}")
+                out[key] = rep.ns_per_warp_step[k]
         return out
 
     def tune_apply(self, params, table: dict):
         """Install costs from an earlier autotune() table (filtr_tune_apply);
         shapes missing from the table keep the scaled built-in cost."""
         rep = TuneReport()
+        if params.prune & (PRUNE_XDROP | PRUNE_ZDROP) or params.affine == AFFINE_MID:
+            rep.n_shapes = len(TUNE_SWEEP)
+            for k, (kind, W) in enumerate(TUNE_SWEEP):
+                rep.rows_per_lane[k] = W
+                rep.packed[k] = 1 if kind == "i16x2" else 0
+                rep.ns_per_warp_step[k] = float(table.get(f"sweep {kind} W={W}", 0.0))
+            check(lib().filtr_tune_apply(self.handle, C.byref(params), C.byref(rep)),
+                  "filtr_tune_apply")
+            return
         rep.n_shapes = len(TUNE_SHAPES)
         for k, (kind, R) in enumerate(TUNE_SHAPES):
             rep.rows_per_lane[k] = R

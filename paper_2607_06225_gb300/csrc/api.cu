@@ -258,7 +258,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
   }
   // X-drop / Z-drop pairs take the packed sweep when their threshold leaves
   // room in 15 bits (those that leave the range anyway are rerun in int32)
-  sp.xd16 = (ctx->xd16_mode != 1 && xd16_eligible(sp)) ? 1 : 0;
+  const Ctx::SweepChoice *swc = sp.use_xdrop ? ctx->sweep_choice(sp) : nullptr;
+  sp.xd16 = (ctx->xd16_mode != 1 && xd16_eligible(sp) && (!swc || swc->packed || ctx->xd16_mode == 2))
+                ? 1
+                : 0;
   cudaError_t ce = cudaSetDevice(ctx->device);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaSetDevice");
   if (ctx->done_ev) {
@@ -482,7 +485,10 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     n_conc = 0;
     ctx->h_ql.assign(h_ql, h_ql + n);  // the staging area is reused for the plan upload
     ctx->h_rl.assign(h_rl, h_rl + n);
-    PlanInput in{&sp, n, ctx->h_ql.data(), ctx->h_rl.data(), tb_budget, 8, ctx->xdrop_warps0};
+    // first group width of X-drop pairs: the test hook's, the tuned one, or the
+    // planner's estimate from the expected live width
+    const int w0 = ctx->xdrop_warps0 > 0 ? ctx->xdrop_warps0 : (swc ? swc->warps : 0);
+    PlanInput in{&sp, n, ctx->h_ql.data(), ctx->h_rl.data(), tb_budget, 8, w0};
     in.shape_cost = costs;
     if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
     n_main = (uint32_t)P.order.size();

@@ -59,6 +59,20 @@ struct Ctx {
   std::vector<Span> spans;
 
   // measured shape costs (filtr_autotune), per recurrence kind
+  // the antidiagonal sweep's tuned choice (filtr_autotune with X-drop / Z-drop
+  // parameters): cell width and first group width, per recurrence kind
+  struct SweepChoice {
+    int packed, warps;
+  };
+  using SweepKey = std::tuple<int, int, int, int, int, int>;  // mode, alphabet, traceback, band, zdrop, running
+  std::map<SweepKey, SweepChoice> sweep_tuned;
+  static SweepKey sweep_key(const ScoreParams &sp) {
+    return SweepKey(sp.mode, sp.alphabet, sp.traceback, sp.use_band, sp.zdrop, sp.xrun);
+  }
+  const SweepChoice *sweep_choice(const ScoreParams &sp) const {
+    auto it = sweep_tuned.find(sweep_key(sp));
+    return it == sweep_tuned.end() ? nullptr : &it->second;
+  }
   using TuneKey = std::tuple<int, int, int, int, int>;  // mode, affine, traceback, alphabet, band
   std::map<TuneKey, std::vector<ShapeCost>> tuned;
   static TuneKey tune_key(const ScoreParams &sp) {

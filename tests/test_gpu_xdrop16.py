@@ -151,3 +151,37 @@ def test_long_pair_segmented(F, ctx, interval, recompute, mode):
     for f in ("score", "q_end", "r_end", "status", "cells"):
         assert int(res[f]) == int(o[f]), (f, int(res[f]), int(o[f]))
     assert np.array_equal(cig, o["cigar"])
+
+
+def test_sweep_autotune_and_apply(F):
+    """filtr_autotune with X-drop parameters times the int16x2 and int32 sweeps at
+    a first width of one and two warps and keeps the fastest; filtr_tune_apply
+    installs a saved choice.  Results never change: every choice equals the
+    oracle; a table with only int32 candidates runs no pair packed."""
+    b = synth.long_reads(n=40, lmin=2000, lmax=4000, seed=61)
+    sc = dict(b.scoring)
+    params = F.make_params(b.subst, **sc)
+    ores, oops, ooff = oracle_batch(b, sc)
+    c = F.Context(0, 4 << 30)
+    try:
+        table = c.autotune(params)
+        assert set(table) <= {"sweep i16x2 W=1", "sweep i32 W=1", "sweep i16x2 W=2", "sweep i32 W=2"}
+        assert "sweep i16x2 W=1" in table and "sweep i32 W=1" in table
+        assert all(v > 0 for v in table.values())
+        c.set_timing(True)
+        res, cig, rc = F.align_batch(c, params, b)
+        assert rc == 0, F.last_error()
+        compare(b, sc, res, cig, ores, oops, ooff, label="tuned sweep")
+        only32 = {k: v for k, v in table.items() if "i32" in k}
+        c.tune_apply(params, only32)
+        res, cig, rc = F.align_batch(c, params, b)
+        assert rc == 0, F.last_error()
+        assert c.last_stats()["pairs_xd16"] == 0
+        compare(b, sc, res, cig, ores, oops, ooff, label="int32 sweep by tune table")
+        c.tune_apply(params, {"sweep i16x2 W=2": 1.0})
+        res, cig, rc = F.align_batch(c, params, b)
+        assert rc == 0, F.last_error()
+        assert c.last_stats()["pairs_xd16"] == b.n
+        compare(b, sc, res, cig, ores, oops, ooff, label="packed sweep at two warps by tune table")
+    finally:
+        c.close()
