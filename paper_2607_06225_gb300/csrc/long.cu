@@ -311,8 +311,13 @@ filtr_status run_xdrop_ckpt(Ctx *c, const ScoreParams &sp, const filtr_params *p
   if (hflags[0] == 3) {  // the packed sweep left its 16-bit range: the whole pair in int32
     ScoreParams s32 = sp;
     s32.xd16 = 0;
-    return run_xdrop_ckpt(c, s32, params, q, M, r, N, out, cigar, cap, st, C);
+    const filtr_status rc = run_xdrop_ckpt(c, s32, params, q, M, r, N, out, cigar, cap, st, C);
+    c->last_xd16 = 1;
+    c->last_xd16_rerun = 1;
+    return rc;
   }
+  c->last_xd16 = sp.xd16 ? 1u : 0u;
+  c->last_xd16_rerun = 0;
   if (single && hflags[0] == 2) {  // the pool ran out: recompute the segments instead
     const bool saved = c->ckpt_recompute;
     c->ckpt_recompute = true;
