@@ -69,7 +69,9 @@ def parse():
                     help="pairs of the plain per-pair sample (0: the workload's default)")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE_PAIRS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workspace-gb", type=float, default=64.0)
+    # 96 GB: the long-read workload's traceback (10,000 reads x (M + N + 1) rows of
+    # 128 bytes, about 77 GB) fits one wave; the protein workload needs about 20 GB
+    ap.add_argument("--workspace-gb", type=float, default=96.0)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--no-serve", action="store_true")
