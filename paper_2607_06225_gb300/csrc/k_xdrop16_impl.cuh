@@ -96,8 +96,12 @@ __device__ __forceinline__ void x16_cells(const uint32_t (&H1)[X16_P], const uin
                                           uint32_t nxF1, uint32_t nxH2, const uint32_t (&s2)[X16_P],
                                           uint32_t NOE2, uint32_t NE2, uint32_t Z2, uint32_t (&Hr)[X16_P],
                                           uint32_t (&Er)[X16_P], uint32_t (&Fr)[X16_P], uint32_t &nib) {
+  uint32_t fl[X16_P][4];  // traceback flags of each register: F extended, E extended, F > max(D, E), E > D
+  uint32_t acc = 0;
 #pragma unroll
-  for (int r = 0; r < X16_P; ++r) {
+  for (int rr = 0; rr < X16_P; ++rr) {
+    // registers in the order 0, 2, 1, 3: the flags of r and r + 2 pack together
+    const int r = (rr & 1) * 2 + (rr >> 1);
     // left (slot - 1 + delta) and up (slot + delta) on k-1, diagonal on k-2
     const uint32_t Hl = DELTA ? H1[r] : (r ? H1[r ? r - 1 : 0] : x16_down0(H1[3], pvH1));
     const uint32_t El = DELTA ? E1[r] : (r ? E1[r ? r - 1 : 0] : x16_down0(E1[3], pvE1));
@@ -121,16 +125,30 @@ __device__ __forceinline__ void x16_cells(const uint32_t (&H1)[X16_P], const uin
     Er[r] = E;
     Fr[r] = F;
     if (TB) {
-      // nibble bits: 3 E > D, 2 F > max(D, E), 1 E extended, 0 F extended; the
-      // flag of slot r (bit 15) goes to bit 28 - 4r + c, that of slot r + 4
-      // (bit 31) to bit 12 - 4r + c: one rotation by 4r + 19 - c
-      const uint32_t f3 = x16_gt(E, D), f2 = x16_gt(F, DE), f1 = x16_gt(E, Hol), f0 = x16_gt(F, Hou);
-      nib |= __funnelshift_r(f3, f3, 4 * r + 16) & ((1u << (31 - 4 * r)) | (1u << (15 - 4 * r)));
-      nib |= __funnelshift_r(f2, f2, 4 * r + 17) & ((1u << (30 - 4 * r)) | (1u << (14 - 4 * r)));
-      nib |= __funnelshift_r(f1, f1, 4 * r + 18) & ((1u << (29 - 4 * r)) | (1u << (13 - 4 * r)));
-      nib |= __funnelshift_r(f0, f0, 4 * r + 19) & ((1u << (28 - 4 * r)) | (1u << (12 - 4 * r)));
+      // nibble bits c: 3 E > D, 2 F > max(D, E), 1 E extended, 0 F extended.
+      // The flag of slot r (bit 15 of its difference) belongs at bit
+      // 28 - 4r + c of the word, that of slot r + 4 (bit 31) at 12 - 4r + c.
+      // Registers r and r + 2 place a flag 8 bits apart, so one byte permute
+      // takes the four sign bits of flag c of both registers as 0x00 / 0xff
+      // bytes (255 x flag) in the order of their target bits, and a
+      // multiply-add by 2^(4 - 4r + c) on the FMA pipe adds 255 x those bits to
+      // a sum.  The sum is 255 x the word; 255 is odd, so one multiply by its
+      // inverse mod 2^32 gives the word.
+      fl[r][3] = x16_gt(E, D);
+      fl[r][2] = x16_gt(F, DE);
+      fl[r][1] = x16_gt(E, Hol);
+      fl[r][0] = x16_gt(F, Hou);
+      if (r >= 2) {
+#pragma unroll
+        for (int c = 3; c >= 0; --c) {
+          uint32_t pk;
+          asm("prmt.b32 %0, %1, %2, 0xD9FB;" : "=r"(pk) : "r"(fl[r][c]), "r"(fl[r - 2][c]));
+          asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(acc) : "r"(pk), "r"(1u << (4 - 4 * (r - 2) + c)), "r"(acc));
+        }
+      }
     }
   }
+  if (TB) nib = acc * 0xfefefeffu;  // 255^-1 mod 2^32
 }
 
 // runtime knobs of the packed sweep (a test hook can switch rebasing off, so
