@@ -542,10 +542,8 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
           } else {
             th2 = x16_splat(thr);
           }
-          // halves outside the candidate range get an unreachable threshold
-          const uint32_t dm = x16_halfmask(dsp << (15 - r));
-          th2 = (th2 & dm) | (0x7fff7fffu & ~dm);
-          const uint32_t m = x16_halfmask(x16_ge(Hr[r], th2));
+          // [H >= threshold] per half, kept only inside the candidate range
+          const uint32_t m = x16_halfmask(x16_ge(Hr[r], th2) & (dsp << (15 - r)));
           H2[r] = H1[r];
           H1[r] = Hr[r] & m;
           E1[r] = Er[r] & m;
