@@ -34,6 +34,7 @@
 // flight while the raw cells of k are computed, and are consumed only to mask
 // them.  The window may trail the left end by a slot; a pair whose range
 // outgrows it is rerun wider (status TOO_WIDE), as in the int32 sweep.
+#include <algorithm>
 #include <climits>
 
 #pragma once
@@ -160,7 +161,8 @@ struct X16Knobs {
 #ifndef FILTR_X16_MINB
 #define FILTR_X16_MINB 1
 #endif
-template <int W, bool LOCAL, bool TB, bool ZD>
+// UNI: one match and one mismatch score (codes compared), else a score table
+template <int W, bool LOCAL, bool TB, bool ZD, bool UNI>
 __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB : 1)
     k_xdrop16(const FullArgs a, uint32_t *overflow, uint32_t *n_overflow, X16Knobs kn) {
   constexpr int S = X16_S;
@@ -184,7 +186,6 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
   // and the lowest threshold that keeps every relevant value above the floor
   const int pceil = 0x7fff - 4 * smax - 2 * oe - 8;
   const int pfloor = 2 * smax + 2 * oe + 8;
-  const bool uni = a.sp.uni != 0;
   const uint32_t MA2 = x16_splat(a.sp.uni_match), MI2 = x16_splat(a.sp.uni_mismatch);
   const uint32_t NOE2 = x16_splat(-oe), NE2 = x16_splat(-e);
 
@@ -274,8 +275,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
     int cornerH = INT_MIN;
     if (TB && tid == 0 && ckmode == 0) ckp[0] = 0;
     int k_first = 1, k_last = M + N;
+    int row0 = 0;  // traceback row of antidiagonal k: k - row0
     if (ckmode >= 2) {
       k_first = ck->k_start + 1;
+      row0 = k_first;
       k_last = min(ck->k_end, M + N);
       if (ck->k_start > 0) {
         const int32_t *rec = ck->buf + (int64_t)seg * xd_ckpt_stride();
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       }
       // ---- substitution scores of the eight cells --------------------------------
       uint32_t s2[X16_P];
-      if (uni) {
+      if (UNI) {
 #pragma unroll
         for (int r = 0; r < X16_P; ++r) {
           const uint32_t ne = x16_halfmask((qh[r] ^ rh[r]) + 0x7fff7fffu);  // codes differ
@@ -516,14 +519,12 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       thr = min(thr, 0x7fff);
       {  // the next antidiagonal's origin (a lower bound of its range's left end) and code
         const int cnx = min(range_lo(k + 1, lo - 2), cn + 1);
-        if (k < k_last) {
-          if (cnx - cn == 1) {
-            const int j = cnx + base_slot + S - 1;
-            nextc = (j >= 1 && j <= N) ? rs[j - 1] : 0u;
-          } else {
-            const int i = k + 1 - cnx - base_slot;
-            nextc = (i >= 1 && i <= M) ? q[i - 1] : 0u;
-          }
+        if (k < k_last) {  // a reference code if the origin moves, else a query code
+          const bool mvx = cnx - cn == 1;
+          const int j = cnx + base_slot + S - 1, i = k + 1 - cnx - base_slot;
+          const bool ok = mvx ? (j >= 1 && j <= N) : (i >= 1 && i <= M);
+          const uint8_t *src = mvx ? rs + (j - 1) : q + (i - 1);
+          nextc = ok ? *src : 0u;
         }
         // ---- prune k --------------------------------------------------------------
         const int vA = jA - cn - base_slot, vB = jB - cn - base_slot;
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         }
         // ---- traceback word and origin of k -----------------------------------------
         if (TB) {
-          const int64_t row = (ckmode >= 2) ? (int64_t)(k - ck->k_start - 1) : (int64_t)k;
+          const int64_t row = (int64_t)(k - row0);
           // only the 32-byte sectors (8 threads) holding a slot of the range
           const unsigned act = __ballot_sync(X16_FULL, dom != 0);
           if ((act >> (lane & 24)) & 0xffu) tbp[row * (WIN / 8) + tid] = nib;
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         }
         {
           const int a0 = max(jA, 1), b0 = min(jB, k - 1);
-          if (b0 >= a0) cells += (uint64_t)(b0 - a0 + 1);
+          cells += (uint64_t)max(b0 - a0 + 1, 0);
         }
         if (k == M + N) {  // the corner is the single cell of antidiagonal M + N
           const int pcn = N - cn - base_slot;
@@ -765,7 +766,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
 template <int W, bool LOCAL, bool TB, bool ZD>
 cudaError_t x16_launch(const FullArgs &a, int grid, uint32_t *ovf, uint32_t *novf, X16Knobs kn,
                        cudaStream_t s) {
-  k_xdrop16<W, LOCAL, TB, ZD><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf, kn);
+  if (a.sp.uni)
+    k_xdrop16<W, LOCAL, TB, ZD, true><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf, kn);
+  else
+    k_xdrop16<W, LOCAL, TB, ZD, false><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf, kn);
   return cudaGetLastError();
 }
 
@@ -781,9 +785,10 @@ cudaError_t x16_dispatch(const FullArgs &a, int grid, uint32_t *ovf, uint32_t *n
 
 template <int W, bool LOCAL, bool TB, bool ZD>
 int x16_occ() {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_xdrop16<W, LOCAL, TB, ZD>, W == 1 ? 128 : W * 32, 0);
-  return nb;
+  int nb = 0, nb2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_xdrop16<W, LOCAL, TB, ZD, true>, W == 1 ? 128 : W * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_xdrop16<W, LOCAL, TB, ZD, false>, W == 1 ? 128 : W * 32, 0);
+  return std::min(nb, nb2);
 }
 
 template <int W, bool ZD>
