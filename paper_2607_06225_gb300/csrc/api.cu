@@ -599,8 +599,8 @@ filtr_status align_batch_impl(Ctx *ctx, const filtr_params *params, uint32_t n,
     fa.order = d_ord;
     fa.n_order = cnt;
     fa.counter = d_counters + (counter_i++ % n_counters);
-    const int ppc = xd_pairs_per_cta(W);
-    const int bps = std::max(1, xd_max_blocks_per_sm(W, sp));
+    const int ppc = xd_pairs_per_cta(W, fa.sp);
+    const int bps = std::max(1, xd_max_blocks_per_sm(W, fa.sp));
     int grid = (int)std::min<int64_t>((int64_t)ctx->sms * bps, (cnt + ppc - 1) / ppc);
     ce = launch_xdrop(fa, W, std::max(grid, 1), d_ovf, d_novf, st);
     ++launches;

@@ -292,7 +292,7 @@ inline int pack_smem_bytes(int R, int alphabet) {
 }
 cudaError_t launch_xdrop(const FullArgs &a, int W, int grid, uint32_t *overflow,
                          uint32_t *n_overflow, cudaStream_t s);
-int xd_pairs_per_cta(int W);
+int xd_pairs_per_cta(int W, const ScoreParams &sp);
 struct WalkState;
 cudaError_t launch_walk_segment(const WalkArgs &a, const uint32_t *seg_tb, const int32_t *seg_ck,
                                 int k_start, int wpk, WalkState *st, cudaStream_t s);

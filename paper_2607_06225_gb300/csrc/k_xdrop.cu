@@ -18,7 +18,9 @@ cudaError_t launch_xdrop16_z(const FullArgs &a, int W, int grid, uint32_t *overf
 int xdrop16_x_blocks_per_sm(int W, const ScoreParams &sp);
 int xdrop16_z_blocks_per_sm(int W, const ScoreParams &sp);
 
-int xd_pairs_per_cta(int W) { return W == 1 ? 4 : 1; }
+// one-warp groups run four to a block: the int32 sweep at W = 1, the packed
+// sweep at W = 1 and W = 2 (16 slots per thread)
+int xd_pairs_per_cta(int W, const ScoreParams &sp) { return (W == 1 || (W == 2 && sp.xd16)) ? 4 : 1; }
 
 int xd_max_blocks_per_sm(int W, const ScoreParams &sp) {
   if (sp.xd16) return sp.zdrop ? xdrop16_z_blocks_per_sm(W, sp) : xdrop16_x_blocks_per_sm(W, sp);

@@ -24,7 +24,12 @@
 // halves, and only registers 0 and 3 take a byte permute with the edge value
 // of the next / previous thread.  Traceback nibbles are the int32 sweep's
 // (slot s in bits 4(7-s)..4(7-s)+3 of the thread's word), so every walk reads
-// both kernels' output alike.
+// both kernels' output alike.  A one-warp group can also hold 16 slots per
+// thread (G = 2, a 512-slot window): registers 4g .. 4g+3 then hold slots
+// 8g .. 8g+7 as above, each group of four registers behaving like one 8-slot
+// thread (its own traceback word, its neighbour views across the group edge
+// taken from the other group), so the window's rows and checkpoint records are
+// those of two warps of 8-slot threads.
 //
 // Schedule.  Pruning antidiagonal k needs best(k-1) and the live range
 // [lo(k-1), hi(k-1)]; the raw update of k needs only the pruned values of k-1
@@ -46,8 +51,6 @@ namespace filtr {
 namespace {
 
 constexpr unsigned X16_FULL = 0xffffffffu;
-constexpr int X16_S = 8;     // slots per thread
-constexpr int X16_P = 4;     // packed registers per state array
 constexpr int X16_C0 = 16384;
 
 struct alignas(16) Edge16 {
@@ -89,32 +92,52 @@ __device__ __forceinline__ uint32_t x16_gather(uint32_t f0, uint32_t f1, uint32_
 __device__ __forceinline__ int x16_lo(uint32_t x) { return (int)(int16_t)(x & 0xffffu); }
 __device__ __forceinline__ int x16_hi(uint32_t x) { return (int)(int16_t)(x >> 16); }
 
-// the raw update of the eight cells of one thread on one antidiagonal
-template <bool LOCAL, bool TB, int DELTA, int DOFF>
-__device__ __forceinline__ void x16_cells(const uint32_t (&H1)[X16_P], const uint32_t (&E1)[X16_P],
-                                          const uint32_t (&F1)[X16_P], const uint32_t (&H2)[X16_P],
+// register view of the slots one below for register (g, 0) of a thread with G
+// groups: the low half is slot 8g - 1 (the high half of group g - 1's register
+// 3, or of the previous thread's last register, pv), the high half slot 8g + 3
+template <int G>
+__device__ __forceinline__ uint32_t x16_down_g(const uint32_t (&X)[4 * G], int g, uint32_t pv) {
+  return x16_down0(X[4 * g + 3], g ? X[g ? 4 * g - 1 : 0] : pv);
+}
+// register view of the slots one above for register (g, 3): slot 8g + 4 (high
+// half of register (g, 0)) and slot 8g + 8 (low half of group g + 1's register
+// 0, or of the next thread's first register, nx)
+template <int G>
+__device__ __forceinline__ uint32_t x16_up_g(const uint32_t (&X)[4 * G], int g, uint32_t nx) {
+  return x16_up3(X[4 * g], g < G - 1 ? X[g < G - 1 ? 4 * g + 4 : 0] : nx);
+}
+
+// the raw update of the 8G cells of one thread on one antidiagonal.  Register
+// 4g + r holds slot 8g + r (low half) and slot 8g + r + 4 (high half), so each
+// group of four registers is laid out as a thread of eight slots, and its
+// traceback flags form word g of the thread (nib[g]).
+template <int G, bool LOCAL, bool TB, int DELTA, int DOFF>
+__device__ __forceinline__ void x16_cells(const uint32_t (&H1)[4 * G], const uint32_t (&E1)[4 * G],
+                                          const uint32_t (&F1)[4 * G], const uint32_t (&H2)[4 * G],
                                           uint32_t pvH1, uint32_t pvE1, uint32_t pvH2, uint32_t nxH1,
-                                          uint32_t nxF1, uint32_t nxH2, const uint32_t (&s2)[X16_P],
-                                          uint32_t NOE2, uint32_t NE2, uint32_t Z2, uint32_t (&Hr)[X16_P],
-                                          uint32_t (&Er)[X16_P], uint32_t (&Fr)[X16_P], uint32_t &nib) {
-  uint32_t fl[X16_P][4];  // traceback flags of each register: F extended, E extended, F > max(D, E), E > D
+                                          uint32_t nxF1, uint32_t nxH2, const uint32_t (&s2)[4 * G],
+                                          uint32_t NOE2, uint32_t NE2, uint32_t Z2, uint32_t (&Hr)[4 * G],
+                                          uint32_t (&Er)[4 * G], uint32_t (&Fr)[4 * G], uint32_t (&nib)[G]) {
+  uint32_t fl[4 * G][4];  // traceback flags of each register: F extended, E extended, F > max(D, E), E > D
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
   uint32_t acc = 0;
 #pragma unroll
-  for (int rr = 0; rr < X16_P; ++rr) {
+  for (int rr = 0; rr < 4; ++rr) {
     // registers in the order 0, 2, 1, 3: the flags of r and r + 2 pack together
-    const int r = (rr & 1) * 2 + (rr >> 1);
+    const int rq = (rr & 1) * 2 + (rr >> 1), r = 4 * g + rq;
     // left (slot - 1 + delta) and up (slot + delta) on k-1, diagonal on k-2
-    const uint32_t Hl = DELTA ? H1[r] : (r ? H1[r ? r - 1 : 0] : x16_down0(H1[3], pvH1));
-    const uint32_t El = DELTA ? E1[r] : (r ? E1[r ? r - 1 : 0] : x16_down0(E1[3], pvE1));
-    const uint32_t Hu = DELTA ? (r < 3 ? H1[r < 3 ? r + 1 : 3] : x16_up3(H1[0], nxH1)) : H1[r];
-    const uint32_t Fu = DELTA ? (r < 3 ? F1[r < 3 ? r + 1 : 3] : x16_up3(F1[0], nxF1)) : F1[r];
+    const uint32_t Hl = DELTA ? H1[r] : (rq ? H1[rq ? r - 1 : 0] : x16_down_g<G>(H1, g, pvH1));
+    const uint32_t El = DELTA ? E1[r] : (rq ? E1[rq ? r - 1 : 0] : x16_down_g<G>(E1, g, pvE1));
+    const uint32_t Hu = DELTA ? (rq < 3 ? H1[rq < 3 ? r + 1 : 0] : x16_up_g<G>(H1, g, nxH1)) : H1[r];
+    const uint32_t Fu = DELTA ? (rq < 3 ? F1[rq < 3 ? r + 1 : 0] : x16_up_g<G>(F1, g, nxF1)) : F1[r];
     uint32_t Hd;
     if (DOFF == 0)
       Hd = H2[r];
     else if (DOFF < 0)
-      Hd = r ? H2[r ? r - 1 : 0] : x16_down0(H2[3], pvH2);
+      Hd = rq ? H2[rq ? r - 1 : 0] : x16_down_g<G>(H2, g, pvH2);
     else
-      Hd = r < 3 ? H2[r < 3 ? r + 1 : 3] : x16_up3(H2[0], nxH2);
+      Hd = rq < 3 ? H2[rq < 3 ? r + 1 : 0] : x16_up_g<G>(H2, g, nxH2);
     const uint32_t D = __viaddmax_s16x2_relu(Hd, s2[r], 0u);
     const uint32_t Hol = __viaddmax_s16x2_relu(Hl, NOE2, 0u);
     const uint32_t E = __viaddmax_s16x2(El, NE2, Hol);
@@ -139,17 +162,18 @@ __device__ __forceinline__ void x16_cells(const uint32_t (&H1)[X16_P], const uin
       fl[r][2] = x16_gt(F, DE);
       fl[r][1] = x16_gt(E, Hol);
       fl[r][0] = x16_gt(F, Hou);
-      if (r >= 2) {
+      if (rq >= 2) {
 #pragma unroll
         for (int c = 3; c >= 0; --c) {
           uint32_t pk;
           asm("prmt.b32 %0, %1, %2, 0xD9FB;" : "=r"(pk) : "r"(fl[r][c]), "r"(fl[r - 2][c]));
-          asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(acc) : "r"(pk), "r"(1u << (4 - 4 * (r - 2) + c)), "r"(acc));
+          asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(acc) : "r"(pk), "r"(1u << (4 - 4 * (rq - 2) + c)), "r"(acc));
         }
       }
     }
   }
-  if (TB) nib = acc * 0xfefefeffu;  // 255^-1 mod 2^32
+  if (TB) nib[g] = acc * 0xfefefeffu;  // 255^-1 mod 2^32
+  }
 }
 
 // runtime knobs of the packed sweep (a test hook can switch rebasing off, so
@@ -162,10 +186,15 @@ struct X16Knobs {
 #define FILTR_X16_MINB 1
 #endif
 // UNI: one match and one mismatch score (codes compared), else a score table
-template <int W, bool LOCAL, bool TB, bool ZD, bool UNI>
-__global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB : 1)
+// G: groups of four registers (eight slots) per thread -- 1, or 2 for a one-warp
+// group holding a 512-slot window (W = 1 only)
+template <int W, int G, bool LOCAL, bool TB, bool ZD, bool UNI>
+// (16-slot threads: at most 168 registers, three blocks of four groups per SM)
+__global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? (G == 2 ? 3 : FILTR_X16_MINB) : 1)
     k_xdrop16(const FullArgs a, uint32_t *overflow, uint32_t *n_overflow, X16Knobs kn) {
-  constexpr int S = X16_S;
+  static_assert(G == 1 || (G == 2 && W == 1), "16 slots per thread in one-warp groups only");
+  constexpr int S = 8 * G, P = 4 * G;
+  constexpr int WCODE = W * G;  // the group width the host and the walks know: slots / 256
   constexpr int WIN = W * 32 * S;
   constexpr int GROUPS = (W == 1) ? 4 : 1;
   __shared__ X16Shared<W> shm[GROUPS];
@@ -261,9 +290,9 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
     }
 
     // ---- antidiagonal 0 (or the checkpoint resumed) ----------------------------
-    uint32_t H1[X16_P], E1[X16_P], F1[X16_P], H2[X16_P];
+    uint32_t H1[P], E1[P], F1[P], H2[P];
 #pragma unroll
-    for (int r = 0; r < X16_P; ++r) H1[r] = E1[r] = F1[r] = H2[r] = 0u;
+    for (int r = 0; r < P; ++r) H1[r] = E1[r] = F1[r] = H2[r] = 0u;
     int base = 0;  // real value of packed C0
     if (tid == 0) H1[0] = (uint32_t)X16_C0;  // H(0, 0) = 0
     int c = 0, dprev = 0;
@@ -290,18 +319,20 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         dbest = rec[XCK_DBEST];
         base = rec[XCK_BEST];
         const int wwin = rec[XCK_WIN];
-        const int32_t *mine = rec + XCK_HDR + tid * (4 * S);
         auto pk = [&](int v) -> uint32_t {  // real -> packed (minus infinity and far below: 0)
           const int x = v - base + X16_C0;
           return (v <= NEG_HALF || x <= 0) ? 0u : (uint32_t)min(x, 0x7fff);
         };
+        // records hold eight-slot threads: group g of this thread is record thread tid * G + g
 #pragma unroll
-        for (int r = 0; r < X16_P; ++r) {
-          const bool inl = base_slot + r < wwin, inh = base_slot + r + 4 < wwin;
-          H1[r] = (inl ? pk(mine[r]) : 0u) | ((inh ? pk(mine[r + 4]) : 0u) << 16);
-          E1[r] = (inl ? pk(mine[S + r]) : 0u) | ((inh ? pk(mine[S + r + 4]) : 0u) << 16);
-          F1[r] = (inl ? pk(mine[2 * S + r]) : 0u) | ((inh ? pk(mine[2 * S + r + 4]) : 0u) << 16);
-          H2[r] = (inl ? pk(mine[3 * S + r]) : 0u) | ((inh ? pk(mine[3 * S + r + 4]) : 0u) << 16);
+        for (int r = 0; r < P; ++r) {
+          const int g = r >> 2, rq = r & 3;
+          const int32_t *mine = rec + XCK_HDR + (tid * G + g) * 32;
+          const bool inl = base_slot + 8 * g + rq < wwin, inh = base_slot + 8 * g + rq + 4 < wwin;
+          H1[r] = (inl ? pk(mine[rq]) : 0u) | ((inh ? pk(mine[rq + 4]) : 0u) << 16);
+          E1[r] = (inl ? pk(mine[8 + rq]) : 0u) | ((inh ? pk(mine[8 + rq + 4]) : 0u) << 16);
+          F1[r] = (inl ? pk(mine[16 + rq]) : 0u) | ((inh ? pk(mine[16 + rq + 4]) : 0u) << 16);
+          H2[r] = (inl ? pk(mine[24 + rq]) : 0u) | ((inh ? pk(mine[24 + rq + 4]) : 0u) << 16);
         }
         if (ckmode == 3) {
           bv = rec[XCK_BV];
@@ -322,7 +353,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
     if (W > 1) {
       const int b0 = (k_first - 1) & 1;
       if (lane == 0) sh.first[b0][warp] = Edge16{H1[0], E1[0], F1[0], H2[0]};
-      if (lane == 31) sh.last[b0][warp] = Edge16{H1[3], E1[3], F1[3], H2[3]};
+      if (lane == 31) sh.last[b0][warp] = Edge16{H1[P - 1], E1[P - 1], F1[P - 1], H2[P - 1]};
       __syncthreads();
     }
     // window origin and codes of k_first: the exact left end of its range
@@ -330,13 +361,13 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       return max(max(0, kk - M), (kk + max(dl, band_lo) + 1) >> 1);
     };
     int cn = min(range_lo(k_first, lo - 1), c + 1);
-    uint32_t qh[X16_P], rh[X16_P];  // residue codes, low half slot r, high half slot r + 4
+    uint32_t qh[P], rh[P];  // residue codes of register (g, r): slots 8g + r and 8g + r + 4
 #pragma unroll
-    for (int r = 0; r < X16_P; ++r) {
+    for (int r = 0; r < P; ++r) {
       uint32_t qv = 0, rv = 0;
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
-        const int pp = base_slot + r + 4 * hh;
+        const int pp = base_slot + 8 * (r >> 2) + (r & 3) + 4 * hh;
         const int j = cn + pp, i = k_first - j;
         const uint32_t qc = (i >= 1 && i <= M) ? q[i - 1] : 0u;
         const uint32_t rc = (j >= 1 && j <= N) ? rs[j - 1] : 0u;
@@ -378,31 +409,41 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       const int delta = cn - c;
       // ---- codes at the new origin --------------------------------------------
       if (k != k_first) {
-        if (delta == 1) {  // reference codes move down one slot, the new one enters slot 7
-          const uint32_t t = (rh[0] >> 16) | (nextc << 16);
-          rh[0] = rh[1];
-          rh[1] = rh[2];
-          rh[2] = rh[3];
-          rh[3] = t;
+        if (delta == 1) {  // reference codes move down one slot, the new one enters slot S - 1
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            // slot 8g + 8 enters group g from the next group (or is the new code)
+            const uint32_t in = g < G - 1 ? (rh[g < G - 1 ? 4 * g + 4 : 0] & 0xffffu) : nextc;
+            const uint32_t t = (rh[4 * g] >> 16) | (in << 16);
+            rh[4 * g] = rh[4 * g + 1];
+            rh[4 * g + 1] = rh[4 * g + 2];
+            rh[4 * g + 2] = rh[4 * g + 3];
+            rh[4 * g + 3] = t;
+          }
         } else {  // query codes move up one slot, the new one enters slot 0
-          const uint32_t t = nextc | (qh[3] << 16);
-          qh[3] = qh[2];
-          qh[2] = qh[1];
-          qh[1] = qh[0];
-          qh[0] = t;
+#pragma unroll
+          for (int g = G - 1; g >= 0; --g) {
+            // slot 8g - 1 enters group g from the group before (or is the new code)
+            const uint32_t in = g ? (qh[g ? 4 * g - 1 : 0] >> 16) : nextc;
+            const uint32_t t = in | (qh[4 * g + 3] << 16);
+            qh[4 * g + 3] = qh[4 * g + 2];
+            qh[4 * g + 2] = qh[4 * g + 1];
+            qh[4 * g + 1] = qh[4 * g];
+            qh[4 * g] = t;
+          }
         }
       }
       // ---- substitution scores of the eight cells --------------------------------
-      uint32_t s2[X16_P];
+      uint32_t s2[P];
       if (UNI) {
 #pragma unroll
-        for (int r = 0; r < X16_P; ++r) {
+        for (int r = 0; r < P; ++r) {
           const uint32_t ne = x16_halfmask((qh[r] ^ rh[r]) + 0x7fff7fffu);  // codes differ
           s2[r] = (ne & MI2) | (~ne & MA2);
         }
       } else {
 #pragma unroll
-        for (int r = 0; r < X16_P; ++r) {
+        for (int r = 0; r < P; ++r) {
           const uint32_t idx = qh[r] * (uint32_t)A + rh[r];
           const int slo = s_sub[idx & 0xffffu], shi = s_sub[idx >> 16];
           s2[r] = ((uint32_t)slo & 0xffffu) | ((uint32_t)shi << 16);
@@ -413,8 +454,8 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       uint32_t pvH1 = 0, pvE1 = 0, pvH2 = 0, nxH1 = 0, nxF1 = 0, nxH2 = 0;
       const int doff = delta + dprev - 1;
       if (delta == 0) {
-        pvH1 = __shfl_up_sync(X16_FULL, H1[3], 1);
-        pvE1 = __shfl_up_sync(X16_FULL, E1[3], 1);
+        pvH1 = __shfl_up_sync(X16_FULL, H1[P - 1], 1);
+        pvE1 = __shfl_up_sync(X16_FULL, E1[P - 1], 1);
         if (lane == 0) {
           const bool in = W > 1 && warp > 0;
           pvH1 = in ? sh.last[buf][in ? warp - 1 : 0].H1 : 0u;
@@ -430,7 +471,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         }
       }
       if (doff < 0) {
-        pvH2 = __shfl_up_sync(X16_FULL, H2[3], 1);
+        pvH2 = __shfl_up_sync(X16_FULL, H2[P - 1], 1);
         if (lane == 0) pvH2 = (W > 1 && warp > 0) ? sh.last[buf][warp > 0 ? warp - 1 : 0].H2 : 0u;
       } else if (doff > 0) {
         nxH2 = __shfl_down_sync(X16_FULL, H2[0], 1);
@@ -438,21 +479,21 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       }
       // ---- raw cells of k ------------------------------------------------------
       const uint32_t Z2 = LOCAL ? x16_splat(min(max(X16_C0 - base, 0), 0x7fff)) : 0u;
-      uint32_t Hr[X16_P], Er[X16_P], Fr[X16_P];
-      uint32_t nib = 0;
+      uint32_t Hr[P], Er[P], Fr[P];
+      uint32_t nib[G];
       if (delta == 1) {
         if (doff == 0)
-          x16_cells<LOCAL, TB, 1, 0>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2, Hr,
+          x16_cells<G, LOCAL, TB, 1, 0>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2, Hr,
                                      Er, Fr, nib);
         else
-          x16_cells<LOCAL, TB, 1, 1>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2, Hr,
+          x16_cells<G, LOCAL, TB, 1, 1>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2, Hr,
                                      Er, Fr, nib);
       } else {
         if (doff == 0)
-          x16_cells<LOCAL, TB, 0, 0>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2, Hr,
+          x16_cells<G, LOCAL, TB, 0, 0>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2, Hr,
                                      Er, Fr, nib);
         else
-          x16_cells<LOCAL, TB, 0, -1>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2,
+          x16_cells<G, LOCAL, TB, 0, -1>(H1, E1, F1, H2, pvH1, pvE1, pvH2, nxH1, nxF1, nxH2, s2, NOE2, NE2, Z2,
                                       Hr, Er, Fr, nib);
       }
 
@@ -479,7 +520,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
           base += sft;
           const uint32_t d2 = x16_splat(-sft);
 #pragma unroll
-          for (int r = 0; r < X16_P; ++r) {
+          for (int r = 0; r < P; ++r) {
             H1[r] = __viaddmax_s16x2_relu(H1[r], d2, 0u);
             E1[r] = __viaddmax_s16x2_relu(E1[r], d2, 0u);
             F1[r] = __viaddmax_s16x2_relu(F1[r], d2, 0u);
@@ -528,31 +569,38 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         }
         // ---- prune k --------------------------------------------------------------
         const int vA = jA - cn - base_slot, vB = jB - cn - base_slot;
-        uint32_t dom = 0;
-        if (vB >= 0 && vA < S) dom = (0xffu << max(vA, 0)) & (0xffu >> (S - 1 - min(vB, S - 1))) & 0xffu;
-        const uint32_t dsp = (dom & 0xfu) | ((dom & 0xf0u) << 12);
+        constexpr uint32_t SFULL = (1u << S) - 1u;
+        uint32_t dom = 0;  // bit s: slot s of the thread is in the candidate range
+        if (vB >= 0 && vA < S) dom = (SFULL << max(vA, 0)) & (SFULL >> (S - 1 - min(vB, S - 1))) & SFULL;
         const int zx = ZD ? 2 * (cn + base_slot) - k - dbest : 0;
-        uint32_t t2 = 0, amw = 0;
+        uint32_t t2 = 0, am = 0;
 #pragma unroll
-        for (int r = 0; r < X16_P; ++r) {
-          uint32_t th2;
-          if (ZD) {
-            const int tl = min(max(thr - abs(zx + 2 * r), 1), 0x7fff);
-            const int tu = min(max(thr - abs(zx + 2 * r + 8), 1), 0x7fff);
-            th2 = (uint32_t)tl | ((uint32_t)tu << 16);
-          } else {
-            th2 = x16_splat(thr);
+        for (int g = 0; g < G; ++g) {
+          // the group's range bits: slot 8g + r at bit r, slot 8g + r + 4 at bit 16 + r
+          const uint32_t dsp = ((dom >> (8 * g)) & 0xfu) | (((dom >> (8 * g + 4)) & 0xfu) << 16);
+          uint32_t amw = 0;
+#pragma unroll
+          for (int rq = 0; rq < 4; ++rq) {
+            const int r = 4 * g + rq;
+            uint32_t th2;
+            if (ZD) {
+              const int tl = min(max(thr - abs(zx + 2 * (8 * g + rq)), 1), 0x7fff);
+              const int tu = min(max(thr - abs(zx + 2 * (8 * g + rq) + 8), 1), 0x7fff);
+              th2 = (uint32_t)tl | ((uint32_t)tu << 16);
+            } else {
+              th2 = x16_splat(thr);
+            }
+            // [H >= threshold] per half, kept only inside the candidate range
+            const uint32_t m = x16_halfmask(x16_ge(Hr[r], th2) & (dsp << (15 - rq)));
+            H2[r] = H1[r];
+            H1[r] = Hr[r] & m;
+            E1[r] = Er[r] & m;
+            F1[r] = Fr[r] & m;
+            t2 = __vimax_s16x2_relu(t2, H1[r]);
+            amw |= m & (0x10001u << rq);  // live slots: bit rq (low half), bit 16 + rq (high half)
           }
-          // [H >= threshold] per half, kept only inside the candidate range
-          const uint32_t m = x16_halfmask(x16_ge(Hr[r], th2) & (dsp << (15 - r)));
-          H2[r] = H1[r];
-          H1[r] = Hr[r] & m;
-          E1[r] = Er[r] & m;
-          F1[r] = Fr[r] & m;
-          t2 = __vimax_s16x2_relu(t2, H1[r]);
-          amw |= m & (0x10001u << r);  // live slots: bit r (low half), bit 16 + r (high half)
+          am |= ((amw & 0xfu) | ((amw >> 12) & 0xf0u)) << (8 * g);
         }
-        const uint32_t am = (amw & 0xfu) | ((amw >> 12) & 0xf0u);
         const int tmax = max(x16_lo(t2), x16_hi(t2));
         const int tl = am ? __ffs(am) - 1 : -1;
         const int th = am ? 31 - __clz(am) : -1;
@@ -560,18 +608,28 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         int ts = -1;
         if (need_bs) {
           const uint32_t tm2 = x16_splat(tmax);
-          uint32_t bmw = 0;
+          uint32_t bm = 0;
 #pragma unroll
-          for (int r = 0; r < X16_P; ++r) bmw |= x16_halfmask(x16_ge(H1[r], tm2)) & (0x10001u << r);
-          const uint32_t bm = ((bmw & 0xfu) | ((bmw >> 12) & 0xf0u)) & am;
+          for (int g = 0; g < G; ++g) {
+            uint32_t bmw = 0;
+#pragma unroll
+            for (int rq = 0; rq < 4; ++rq)
+              bmw |= x16_halfmask(x16_ge(H1[4 * g + rq], tm2)) & (0x10001u << rq);
+            bm |= ((bmw & 0xfu) | ((bmw >> 12) & 0xf0u)) << (8 * g);
+          }
+          bm &= am;
           ts = bm ? 31 - __clz(bm) : -1;
         }
         // ---- traceback word and origin of k -----------------------------------------
         if (TB) {
           const int64_t row = (int64_t)(k - row0);
-          // only the 32-byte sectors (8 threads) holding a slot of the range
+          // only the 32-byte sectors (8 / G threads) holding a slot of the range
+          constexpr int TPS = 8 / G;
           const unsigned act = __ballot_sync(X16_FULL, dom != 0);
-          if ((act >> (lane & 24)) & 0xffu) tbp[row * (WIN / 8) + tid] = nib;
+          if ((act >> (lane & (32 - TPS))) & ((1u << TPS) - 1u)) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) tbp[row * (WIN / 8) + G * tid + g] = nib[g];
+          }
           if (tid == 0) ckp[row] = cn;
         }
         {
@@ -581,11 +639,12 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         if (k == M + N) {  // the corner is the single cell of antidiagonal M + N
           const int pcn = N - cn - base_slot;
           if (pcn >= 0 && pcn < S) {
+            // slot pcn: register 4 (pcn / 8) + pcn % 4, high half when pcn % 8 >= 4
             uint32_t hv = 0;
 #pragma unroll
-            for (int r = 0; r < X16_P; ++r)
-              if ((pcn & 3) == r) hv = H1[r];
-            const int v = (pcn < 4) ? (int)(hv & 0xffffu) : (int)(hv >> 16);
+            for (int r = 0; r < P; ++r)
+              if (4 * (pcn >> 3) + (pcn & 3) == r) hv = H1[r];
+            const int v = ((pcn & 7) < 4) ? (int)(hv & 0xffffu) : (int)(hv >> 16);
             cornerH = v ? v - X16_C0 + base : NEG;
           }
         }
@@ -608,7 +667,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
             sh.red[nb][warp][3] = wbs;
             sh.first[nb][warp] = Edge16{H1[0], E1[0], F1[0], H2[0]};
           }
-          if (lane == 31) sh.last[nb][warp] = Edge16{H1[3], E1[3], F1[3], H2[3]};
+          if (lane == 31) sh.last[nb][warp] = Edge16{H1[P - 1], E1[P - 1], F1[P - 1], H2[P - 1]};
           __syncthreads();
         }
         c = cn;
@@ -632,7 +691,7 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
     if (status == FILTR_ST_OK && k > k_last && k_last == M + N) ended = true;
     // a dropped global pair without its best cell: the int32 sweep finds it
     if (!LOCAL && !track && ckmode != 2 && status == FILTR_ST_OK && ended && !corner) status = X16_OVERFLOW;
-    if (ckmode == 3 && status == FILTR_ST_TOO_WIDE && W < XD_MAX_WARPS) break;
+    if (ckmode == 3 && status == FILTR_ST_TOO_WIDE && WCODE < XD_MAX_WARPS) break;
     if (ckmode >= 2 && status == X16_OVERFLOW) {  // the whole pair goes to the int32 sweep
       if (tid == 0 && ckmode == 3) ck->flags[0] = 3;
       break;
@@ -655,9 +714,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       int32_t *rec = ck->buf + (int64_t)(ck->k_end / ck->C) * xd_ckpt_stride();
       int used = 0;
 #pragma unroll
-      for (int r = 0; r < X16_P; ++r) {
-        if ((H1[r] | E1[r] | F1[r] | H2[r]) & 0xffffu) used = max(used, base_slot + r + 1);
-        if ((H1[r] | E1[r] | F1[r] | H2[r]) >> 16) used = max(used, base_slot + r + 5);
+      for (int r = 0; r < P; ++r) {
+        const int sl = base_slot + 8 * (r >> 2) + (r & 3);  // slot of the low half
+        if ((H1[r] | E1[r] | F1[r] | H2[r]) & 0xffffu) used = max(used, sl + 1);
+        if ((H1[r] | E1[r] | F1[r] | H2[r]) >> 16) used = max(used, sl + 5);
       }
       used = __reduce_max_sync(X16_FULL, used);
       if (W > 1) {
@@ -670,16 +730,17 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         const int v = hh ? (int)(x >> 16) : (int)(x & 0xffffu);
         return v ? v - X16_C0 + base : NEG;
       };
-      int32_t *mine = rec + XCK_HDR + tid * (4 * S);
+      // eight-slot record threads: group g of this thread is record thread tid * G + g
 #pragma unroll
-      for (int r = 0; r < X16_P; ++r) {
+      for (int r = 0; r < P; ++r) {
+        int32_t *mine = rec + XCK_HDR + (tid * G + (r >> 2)) * 32;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const int s = r + 4 * hh;
+          const int s = (r & 3) + 4 * hh;
           mine[s] = rv(H1[r], hh);
-          mine[S + s] = rv(E1[r], hh);
-          mine[2 * S + s] = rv(F1[r], hh);
-          mine[3 * S + s] = rv(H2[r], hh);
+          mine[8 + s] = rv(E1[r], hh);
+          mine[16 + s] = rv(F1[r], hh);
+          mine[24 + s] = rv(H2[r], hh);
         }
       }
       if (tid == 0) {
@@ -698,9 +759,9 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
         rec[XCK_CELLS_HI] = (int32_t)(uint32_t)(cells >> 32);
         if (TB) {
           ck->seg_off[seg] = rsv;
-          ck->seg_w[seg] = W;
+          ck->seg_w[seg] = WCODE;
         }
-        ck->flags[1 + seg] = W;
+        ck->flags[1 + seg] = WCODE;
       }
       gsync();
       continue;
@@ -709,10 +770,10 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
       if (ckmode == 3) {
         if (TB && status != FILTR_ST_TOO_WIDE) {
           ck->seg_off[seg] = rsv;
-          ck->seg_w[seg] = W;
+          ck->seg_w[seg] = WCODE;
         }
         ck->flags[0] = 1;
-        if (status != FILTR_ST_TOO_WIDE) ck->flags[1 + seg] = W;
+        if (status != FILTR_ST_TOO_WIDE) ck->flags[1 + seg] = WCODE;
       }
       int score = 0, ei = 0, ej = 0;
       if (status == FILTR_ST_TOO_WIDE) {
@@ -763,51 +824,62 @@ __global__ void __launch_bounds__(W == 1 ? 128 : W * 32, W == 1 ? FILTR_X16_MINB
   }
 }
 
-template <int W, bool LOCAL, bool TB, bool ZD>
+// Group widths: W = 1 (256 slots) runs one warp per pair (8 slots per thread,
+// four pairs per 128-thread block).  W = 2 (512 slots) runs one warp of 16-slot
+// threads for batched pairs, where the bookkeeping done once per warp and the
+// absence of block barriers pay, and two warps of 8-slot threads for the
+// segments of one long pair (a.ck), where the shorter chain of two half-loaded
+// warps gives the lower latency per antidiagonal.  The traceback rows and the
+// checkpoint records of W = 2 are the same in either form: thread t of the
+// one-warp group writes words 2t and 2t + 1.  W >= 4 runs W warps of 8-slot
+// threads.
+template <int KW, int G, bool LOCAL, bool TB, bool ZD>
 cudaError_t x16_launch(const FullArgs &a, int grid, uint32_t *ovf, uint32_t *novf, X16Knobs kn,
                        cudaStream_t s) {
   if (a.sp.uni)
-    k_xdrop16<W, LOCAL, TB, ZD, true><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf, kn);
+    k_xdrop16<KW, G, LOCAL, TB, ZD, true><<<grid, KW == 1 ? 128 : KW * 32, 0, s>>>(a, ovf, novf, kn);
   else
-    k_xdrop16<W, LOCAL, TB, ZD, false><<<grid, W == 1 ? 128 : W * 32, 0, s>>>(a, ovf, novf, kn);
+    k_xdrop16<KW, G, LOCAL, TB, ZD, false><<<grid, KW == 1 ? 128 : KW * 32, 0, s>>>(a, ovf, novf, kn);
   return cudaGetLastError();
 }
 
-template <int W, bool ZD>
+template <int KW, int G, bool ZD>
 cudaError_t x16_dispatch(const FullArgs &a, int grid, uint32_t *ovf, uint32_t *novf, X16Knobs kn,
                          cudaStream_t s) {
   const bool L = a.sp.mode == FILTR_LOCAL, T = a.sp.traceback != 0;
-  if (L) return T ? x16_launch<W, true, true, ZD>(a, grid, ovf, novf, kn, s)
-                  : x16_launch<W, true, false, ZD>(a, grid, ovf, novf, kn, s);
-  return T ? x16_launch<W, false, true, ZD>(a, grid, ovf, novf, kn, s)
-           : x16_launch<W, false, false, ZD>(a, grid, ovf, novf, kn, s);
+  if (L) return T ? x16_launch<KW, G, true, true, ZD>(a, grid, ovf, novf, kn, s)
+                  : x16_launch<KW, G, true, false, ZD>(a, grid, ovf, novf, kn, s);
+  return T ? x16_launch<KW, G, false, true, ZD>(a, grid, ovf, novf, kn, s)
+           : x16_launch<KW, G, false, false, ZD>(a, grid, ovf, novf, kn, s);
 }
 
-template <int W, bool LOCAL, bool TB, bool ZD>
+template <int KW, int G, bool LOCAL, bool TB, bool ZD>
 int x16_occ() {
   int nb = 0, nb2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_xdrop16<W, LOCAL, TB, ZD, true>, W == 1 ? 128 : W * 32, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_xdrop16<W, LOCAL, TB, ZD, false>, W == 1 ? 128 : W * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_xdrop16<KW, G, LOCAL, TB, ZD, true>, KW == 1 ? 128 : KW * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_xdrop16<KW, G, LOCAL, TB, ZD, false>, KW == 1 ? 128 : KW * 32,
+                                                0);
   return std::min(nb, nb2);
 }
 
-template <int W, bool ZD>
+template <int KW, int G, bool ZD>
 int x16_occ_w(const ScoreParams &sp) {
   const bool L = sp.mode == FILTR_LOCAL, T = sp.traceback != 0;
-  if (L) return T ? x16_occ<W, true, true, ZD>() : x16_occ<W, true, false, ZD>();
-  return T ? x16_occ<W, false, true, ZD>() : x16_occ<W, false, false, ZD>();
+  if (L) return T ? x16_occ<KW, G, true, true, ZD>() : x16_occ<KW, G, true, false, ZD>();
+  return T ? x16_occ<KW, G, false, true, ZD>() : x16_occ<KW, G, false, false, ZD>();
 }
 
 template <bool ZD>
 cudaError_t x16_launch_any(const FullArgs &a, int W, int grid, uint32_t *ovf, uint32_t *novf, X16Knobs kn,
                            cudaStream_t s) {
   switch (W) {
-    case 1: return x16_dispatch<1, ZD>(a, grid, ovf, novf, kn, s);
-    case 2: return x16_dispatch<2, ZD>(a, grid, ovf, novf, kn, s);
-    case 4: return x16_dispatch<4, ZD>(a, grid, ovf, novf, kn, s);
-    case 8: return x16_dispatch<8, ZD>(a, grid, ovf, novf, kn, s);
-    case 16: return x16_dispatch<16, ZD>(a, grid, ovf, novf, kn, s);
-    case 32: return x16_dispatch<32, ZD>(a, grid, ovf, novf, kn, s);
+    case 1: return x16_dispatch<1, 1, ZD>(a, grid, ovf, novf, kn, s);
+    case 2: return a.ck ? x16_dispatch<2, 1, ZD>(a, grid, ovf, novf, kn, s)
+                        : x16_dispatch<1, 2, ZD>(a, grid, ovf, novf, kn, s);
+    case 4: return x16_dispatch<4, 1, ZD>(a, grid, ovf, novf, kn, s);
+    case 8: return x16_dispatch<8, 1, ZD>(a, grid, ovf, novf, kn, s);
+    case 16: return x16_dispatch<16, 1, ZD>(a, grid, ovf, novf, kn, s);
+    case 32: return x16_dispatch<32, 1, ZD>(a, grid, ovf, novf, kn, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -815,12 +887,12 @@ cudaError_t x16_launch_any(const FullArgs &a, int W, int grid, uint32_t *ovf, ui
 template <bool ZD>
 int x16_occ_any(int W, const ScoreParams &sp) {
   switch (W) {
-    case 1: return x16_occ_w<1, ZD>(sp);
-    case 2: return x16_occ_w<2, ZD>(sp);
-    case 4: return x16_occ_w<4, ZD>(sp);
-    case 8: return x16_occ_w<8, ZD>(sp);
-    case 16: return x16_occ_w<16, ZD>(sp);
-    case 32: return x16_occ_w<32, ZD>(sp);
+    case 1: return x16_occ_w<1, 1, ZD>(sp);
+    case 2: return x16_occ_w<1, 2, ZD>(sp);
+    case 4: return x16_occ_w<4, 1, ZD>(sp);
+    case 8: return x16_occ_w<8, 1, ZD>(sp);
+    case 16: return x16_occ_w<16, 1, ZD>(sp);
+    case 32: return x16_occ_w<32, 1, ZD>(sp);
     default: return 0;
   }
 }

@@ -171,7 +171,7 @@ double time_sweep(Ctx *c, const ScoreParams &sp0, int W, bool packed, cudaStream
   ScoreParams sp = sp0;
   sp.xd16 = packed ? 1 : 0;
   if (packed && !xd16_eligible(sp0)) return -1.0;
-  const int ppc = xd_pairs_per_cta(W);
+  const int ppc = xd_pairs_per_cta(W, sp);
   const int bps = std::max(1, xd_max_blocks_per_sm(W, sp));
   const int grid = c->sms * bps;
   // the reference and the query of every pair, generated once on the host

@@ -86,6 +86,33 @@ def test_packed_equals_oracle_and_int32(F, ctx, case, tb):
         assert np.array_equal(cig[:used], c32[:used])
 
 
+WIDE = [dict(mode="global", xdrop=40), dict(mode="local", xdrop=60), dict(mode="global", zdrop=30),
+        dict(mode="local", zdrop=50), dict(mode="global", xdrop=60, band=16),
+        dict(mode="global", zdrop=25, xdrop_running=True)]
+
+
+@pytest.mark.parametrize("case", WIDE, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+@pytest.mark.parametrize("width", [2, 4])
+def test_packed_first_width(F, ctx, case, width):
+    """The packed sweep started at a 512-slot window (one warp of 16-slot
+    threads) or at 1024 slots (four warps of 8-slot threads): the same results
+    and CIGARs as the oracle and as the default first width."""
+    b = mixed(2000 + len(str(case)), n=60)
+    sc = dict(affine=True, gap_open=4, gap_extend=2, traceback=True, **case)
+    ref, rcig, _ = run(F, ctx, b, sc)
+    assert F.lib().filtr_test_set_first_width(ctx.handle, width) == 0
+    try:
+        res, cig, st = run(F, ctx, b, sc)
+    finally:
+        F.lib().filtr_test_set_first_width(ctx.handle, 0)
+    assert st["pairs_xd16"] > 0
+    ores, oops, ooff = oracle_batch(b, sc)
+    compare(b, sc, res, cig, ores, oops, ooff, label=f"first width {width} {case}")
+    assert np.array_equal(res, ref)
+    used = int((res["cigar_off"] + res["cigar_len"]).max())
+    assert np.array_equal(cig[:used], rcig[:used])
+
+
 def test_protein_scores_by_table(F, ctx):
     """A 20x20 matrix (scores looked up per cell pair, not by code comparison)."""
     P = synth.protein_pairs(n=60, lmin=30, lmax=600, seed=23)
