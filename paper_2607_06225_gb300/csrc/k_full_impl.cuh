@@ -162,7 +162,7 @@ template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 cudaError_t launch_t(const FullArgs &a, int grid, cudaStream_t s) {
   auto k = k_full<R, LOCAL, AFFINE, TB, BAND, GR>;
   const int smem = full_smem_bytes(R, a.sp.alphabet);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = smem_limit_once<k_full<R, LOCAL, AFFINE, TB, BAND, GR>>(full_smem_bytes(R, MAX_ALPHA));
   if (e != cudaSuccess) return e;
   k<<<grid, FULL_WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
@@ -171,8 +171,7 @@ cudaError_t launch_t(const FullArgs &a, int grid, cudaStream_t s) {
 template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 int occ_t(int smem) {
   int nb = 0;
-  cudaFuncSetAttribute(k_full<R, LOCAL, AFFINE, TB, BAND, GR>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  smem_limit_once<k_full<R, LOCAL, AFFINE, TB, BAND, GR>>(full_smem_bytes(R, MAX_ALPHA));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_full<R, LOCAL, AFFINE, TB, BAND, GR>,
                                                 FULL_WARPS * 32, smem);
   return nb;
