@@ -21,6 +21,12 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+# The serving measurement runs many streams at once: with CUDA's lazy module
+# loading, the first launch of each kernel waits for the device's running work
+# and stalls every batch in flight on the other streams (a 124 ms banded pair
+# held seven small requests up to 72 ms each).  Load every kernel up front.
+os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
 import statistics
 import subprocess
 import sys
@@ -217,10 +223,16 @@ def reduce_over_ranks(ms: float, cells: float, dist, device) -> tuple:
     return float(t.item()), float(c.item())
 
 
+# a fixed request rate, so that latencies compare across builds whose
+# capacities (and so whose relative load) differ
+SERVE_FIXED_RATE_HZ = 900.0
+
+
 def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lanes: int, seed: int = 4):
     """Serving mix at a fixed offered load: first the burst capacity of the mix
     (every request submitted at once), then Poisson arrivals at `load_frac` of
-    that capacity for `seconds`; latency = completion - submission."""
+    that capacity for `seconds`; latency = completion - submission.  A second
+    run at SERVE_FIXED_RATE_HZ gives the latencies at one absolute rate."""
     import synth
 
     srv = F.Server(ctx, int(budget_gb * (1 << 30)), max_inflight=lanes)
@@ -264,6 +276,10 @@ def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lane
     reqs, _ = synth.serve_mix(n, rate_hz=rate, seed=seed)
     refused["n"] = 0
     wall, lat, cells, done = run(reqs, paced=True)
+    refused_main = refused["n"]
+    fixed_reqs, _ = synth.serve_mix(max(50, int(SERVE_FIXED_RATE_HZ * seconds)), rate_hz=SERVE_FIXED_RATE_HZ,
+                                    seed=seed)
+    _, flat, _, _ = run(fixed_reqs, paced=True)
     srv.close()
     per_kind = {}
     for kind in SERVE_KINDS:
@@ -275,7 +291,10 @@ def serve_bench(F, ctx, seconds: float, load_frac: float, budget_gb: float, lane
             "achieved_gcups": cells / wall / 1e9, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
             "per_kind": per_kind,
-            "refused": refused["n"],
+            "fixed_rate": {"offered_rate_hz": SERVE_FIXED_RATE_HZ, "requests": len(flat),
+                           "p50_ms": pct(flat, 50), "p99_ms": pct(flat, 99),
+                           "refused": refused["n"] - refused_main},
+            "refused": refused_main,
             "refused_note": "requests over a lane's share of the budget (budget / lanes) get "
                             "FILTR_ERR_BUSY at submission and are not in the latencies",
             "mix": "40% SW protein / 40% band-256 NW DNA / 20% X-drop-400 DNA, log-normal lengths "

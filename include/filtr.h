@@ -505,8 +505,12 @@ filtr_status filtr_probe_int_peak(filtr_ctx *ctx, double out[5]);
  * micro-batches and launched on up to max_inflight streams; a micro-batch
  * launches as soon as a stream is free, so requests that arrive while others
  * run overlap with them on the device.  A request above 2^22 cells runs alone,
- * on the intra-pair kernel when it is not X-drop.  A worker thread owned by the
- * server does all device work. */
+ * on the intra-pair kernel when it is not X-drop.  Each stream has a host
+ * thread owned by the server, which launches its micro-batches and waits for
+ * them.  Load the library's kernels eagerly in a serving process
+ * (CUDA_MODULE_LOADING=EAGER in the environment before CUDA starts): with lazy
+ * loading, the first launch of each kernel waits for the device's running work,
+ * and the batches already in flight on the other streams wait with it. */
 filtr_status filtr_serve_create(filtr_ctx *ctx, size_t mem_budget, uint32_t max_inflight,
                                 filtr_server **out);
 /* Queue one pair (HOST pointers, copied before returning).  FILTR_ERR_BUSY if the
