@@ -454,7 +454,9 @@ filtr_status filtr_graph_destroy(filtr_graph *graph);
  *        timed (not allowed for these parameters, or too large for the
  *        workspace); entries past n_shapes are 0.
  * With X-drop / Z-drop parameters it tunes the antidiagonal sweep instead:
- * the int16x2 and int32 sweeps at a first group width of one and of two warps
+ * the int16x2 and int32 sweeps at a first group width of 1 and of 2 (windows of
+ * 256 and 512 slots; a width-2 window of the int16x2 sweep is one warp of
+ * 16-slot threads, of the int32 sweep two warps)
  * each run a batch of related pairs (2048-residue random references, queries
  * with 5% substitutions, 2% insertions, 2% deletions) filling the device twice,
  * and the context keeps, for this recurrence kind (mode, alphabet, traceback,

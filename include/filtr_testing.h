@@ -30,9 +30,10 @@ filtr_status filtr_test_set_checkpoint(filtr_ctx *ctx, int32_t interval);
  * without traceback, then each segment recomputed backwards and walked. */
 filtr_status filtr_test_force_recompute(filtr_ctx *ctx, int32_t on);
 
-/* Group width (1, 2, 4, 8, 16 or 32 warps) at which filtr_align_batch first
- * runs X-drop / Z-drop pairs (those that outgrow it are rerun wider); 0
- * restores the default.  Results do not depend on it. */
+/* Group width W (1, 2, 4, 8, 16 or 32: a window of 256 W slots, run by W warps,
+ * except that the int16x2 sweep runs W = 2 as one warp of 16-slot threads) at
+ * which filtr_align_batch first runs X-drop / Z-drop pairs (those that outgrow
+ * it are rerun wider); 0 restores the default.  Results do not depend on it. */
 filtr_status filtr_test_set_first_width(filtr_ctx *ctx, int32_t warps);
 
 /* Which planner filtr_align_batch uses for tiled batches: 0 the default (the

@@ -12,7 +12,7 @@
 // changes speed only.
 //
 // With X-drop / Z-drop parameters it tunes the antidiagonal sweep instead: the
-// int16x2 and int32 sweeps at a first group width of one and two warps each run
+// int16x2 and int32 sweeps at a first group width of 1 and 2 (256 and 512 slots) each run
 // a batch of related pairs (2048-residue random references, queries with 5%
 // substitutions, 2% insertions and 2% deletions) that fills the device twice,
 // and the context keeps the width and cell width with the smallest time per
