@@ -5,8 +5,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <atomic>
-
 #include <string>
 #include <vector>
 
@@ -289,21 +287,6 @@ int pack_odd_blocks_per_sm(int R, const ScoreParams &sp);
 // them when FullArgs::gd is set)
 int full_graph_blocks_per_sm(int R, const ScoreParams &sp);
 int pack_graph_blocks_per_sm(int R, const ScoreParams &sp);
-// Raise kernel K's dynamic shared memory limit to `bytes` once per device
-// (devices 0-31), so that launches need no attribute call of their own: the
-// attribute call takes driver locks every lane's host thread would contend on.
-template <auto K>
-inline cudaError_t smem_limit_once(int bytes) {
-  static std::atomic<uint32_t> done{0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const uint32_t bit = 1u << (dev & 31);
-  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
-  return e;
-}
 inline int pack_smem_bytes(int R, int alphabet) {
   return 512 + FULL_WARPS * alphabet * pack_prof_stride(R);
 }

@@ -162,7 +162,7 @@ template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 cudaError_t launch_t(const FullArgs &a, int grid, cudaStream_t s) {
   auto k = k_full<R, LOCAL, AFFINE, TB, BAND, GR>;
   const int smem = full_smem_bytes(R, a.sp.alphabet);
-  cudaError_t e = smem_limit_once<k_full<R, LOCAL, AFFINE, TB, BAND, GR>>(full_smem_bytes(R, MAX_ALPHA));
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, FULL_WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
@@ -171,7 +171,8 @@ cudaError_t launch_t(const FullArgs &a, int grid, cudaStream_t s) {
 template <int R, bool LOCAL, bool AFFINE, bool TB, bool BAND, bool GR>
 int occ_t(int smem) {
   int nb = 0;
-  smem_limit_once<k_full<R, LOCAL, AFFINE, TB, BAND, GR>>(full_smem_bytes(R, MAX_ALPHA));
+  cudaFuncSetAttribute(k_full<R, LOCAL, AFFINE, TB, BAND, GR>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_full<R, LOCAL, AFFINE, TB, BAND, GR>,
                                                 FULL_WARPS * 32, smem);
   return nb;

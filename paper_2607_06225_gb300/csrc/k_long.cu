@@ -219,7 +219,7 @@ cudaError_t coop(const LongArgs &a, int grid, cudaStream_t s) {
   constexpr int R = 16;
   auto k = k_long<R, LOCAL, AFFINE, TB, BAND>;
   const int smem = full_smem_bytes(R, a.sp.alphabet);
-  cudaError_t e = smem_limit_once<k_long<R, LOCAL, AFFINE, TB, BAND>>(full_smem_bytes(R, MAX_ALPHA));
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   LongArgs copy = a;
   void *args[] = {&copy};
@@ -231,7 +231,7 @@ int occ_long() {
   constexpr int R = 16;
   int nb = 0;
   auto k = k_long<R, LOCAL, AFFINE, TB, BAND>;
-  smem_limit_once<k_long<R, LOCAL, AFFINE, TB, BAND>>(full_smem_bytes(R, MAX_ALPHA));
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, full_smem_bytes(R, 20));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, FULL_WARPS * 32, full_smem_bytes(R, 20));
   return nb;
 }

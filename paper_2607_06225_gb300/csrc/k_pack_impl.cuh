@@ -466,7 +466,7 @@ template <int R, bool LOCAL, bool AFFINE, bool TB, bool GR>
 cudaError_t launch_pt(const FullArgs &a, int grid, cudaStream_t s) {
   auto k = k_pack<R, LOCAL, AFFINE, TB, GR>;
   const int smem = pack_smem_bytes(R, a.sp.alphabet);
-  cudaError_t e = smem_limit_once<k_pack<R, LOCAL, AFFINE, TB, GR>>(pack_smem_bytes(R, MAX_ALPHA));
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, FULL_WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
@@ -475,7 +475,8 @@ cudaError_t launch_pt(const FullArgs &a, int grid, cudaStream_t s) {
 template <int R, bool LOCAL, bool AFFINE, bool TB, bool GR>
 int occ_pt(int smem) {
   int nb = 0;
-  smem_limit_once<k_pack<R, LOCAL, AFFINE, TB, GR>>(pack_smem_bytes(R, MAX_ALPHA));
+  cudaFuncSetAttribute(k_pack<R, LOCAL, AFFINE, TB, GR>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pack<R, LOCAL, AFFINE, TB, GR>,
                                                 FULL_WARPS * 32, smem);
   return nb;
