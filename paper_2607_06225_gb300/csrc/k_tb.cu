@@ -38,6 +38,35 @@ __device__ __forceinline__ void geom_seek(FullGeom &g, int s) {
   }
 }
 
+// A cursor past the last strip of an M x N int32 tile (strips of 32 * R rows):
+// base = the words of every strip, so the first seek moves it down to the strip
+// that holds the row asked for.
+__device__ __forceinline__ void geom_init(FullGeom &g, int R, int M, int N, const ScoreParams &sp) {
+  g.R = R;
+  g.HS = 32 * R;
+  g.M = M;
+  g.N = N;
+  g.band = sp.use_band != 0;
+  band_limits(M, N, sp.band, sp.band_literal, &g.lo, &g.hi);
+  if (!g.band) {
+    g.lo = -(int64_t)M - 1;
+    g.hi = (int64_t)N + 1;
+  }
+  const int nstrips = (M + g.HS - 1) / g.HS;
+  g.base = 0;
+  g.s = nstrips;
+  g.jlo = 1;
+  g.nsteps = 0;
+  for (int s = 0; s < nstrips; ++s) {
+    int64_t jl, jh;
+    strip_cols((int64_t)s * g.HS, g.HS, M, N, g.band, g.lo, g.hi, &jl, &jh);
+    g.base += strip_tb_words(jl, jh, g.R);
+  }
+}
+
+// Choice bits of cell (i, j) of an int32 tile (banded or not).  The cursor g
+// only moves up, so successive calls on one cursor must ask for rows that do
+// not increase.
 __device__ __forceinline__ uint32_t full_bits(const uint32_t *tb, FullGeom &g, int i, int j) {
   const int s = (i - 1) / g.HS;
   geom_seek(g, s);
@@ -122,27 +151,7 @@ __device__ __forceinline__ void walk_thread(const WalkArgs &a, const BatchDev &b
   XdGeom xg;
   PackGeom pg{L.R, (int64_t)pack_strip_tb_words(1, N, L.R)};
   if (L.family == FAM_FULL && L.valid) {
-    g.R = L.R;
-    g.HS = 32 * L.R;
-    g.M = M;
-    g.N = N;
-    g.band = a.sp.use_band != 0;
-    band_limits(M, N, a.sp.band, a.sp.band_literal, &g.lo, &g.hi);
-    if (!g.band) {
-      g.lo = -(int64_t)M - 1;
-      g.hi = (int64_t)N + 1;
-    }
-    // start at the strip holding the last row, base = sum of earlier strips
-    const int nstrips = (M + g.HS - 1) / g.HS;
-    g.base = 0;
-    g.s = nstrips;
-    g.jlo = 1;
-    g.nsteps = 0;
-    for (int s = 0; s < nstrips; ++s) {
-      int64_t jl, jh;
-      strip_cols((int64_t)s * g.HS, g.HS, M, N, g.band, g.lo, g.hi, &jl, &jh);
-      g.base += strip_tb_words(jl, jh, g.R);
-    }
+    geom_init(g, L.R, M, N, a.sp);
   } else if (L.family == FAM_XDROP && L.valid) {
     xd_geom_init(xg, tb, M, N, L);
   }
@@ -549,11 +558,30 @@ __global__ void __launch_bounds__(128) k_walk_xdw(const WalkArgs a) {
 // mismatches follow the diagonal, a gap the row or the column, so lane 0 walks
 // from the cache until the path leaves all three lines (a gap's start or end),
 // and the warp refills there: about two refills per gap instead of a load per
-// step.  Banded int32 pairs (strip offsets that depend on the band) are walked
-// by lane 0 alone.
+// step.  Runs of diagonal steps along the cached diagonal are taken by the
+// whole warp (walk_coop), with the 32 codes below (i0, j0) cached beside the
+// bits.  In a banded int32 tile the strips' offsets depend on the band, so
+// every lane keeps two strip cursors: one for row i0 and one for row i0 - d.
+// Both rows never increase from one refill to the next, and a cursor only
+// moves up.
 
 struct TileCache {
   uint8_t d[32], row[32], col[32];
+  // qc[x] = q[i0 - 1 - x], rc[x] = r[j0 - 1 - x]: the codes of the diagonal
+  // line's cells (and of the row's and the column's)
+  uint8_t qc[32], rc[32];
+  int32_t i0, j0;
+};
+struct TileCacheCodes {  // cached codes; cells further from (i0, j0) read the sequences
+  const TileCache *C;
+  __device__ int q(const WalkCore &w, int i) const {
+    const int x = C->i0 - i;
+    return x < 32 ? C->qc[x] : w.q[i - 1];
+  }
+  __device__ int r(const WalkCore &w, int j) const {
+    const int x = C->j0 - j;
+    return x < 32 ? C->rc[x] : w.r[j - 1];
+  }
 };
 
 struct TileCacheBits {
@@ -570,6 +598,9 @@ struct TileCacheBits {
 
 __global__ void __launch_bounds__(128) k_walk_tw(const WalkArgs a) {
   __shared__ TileCache cache[4];
+  __shared__ int8_t s_sub[MAX_ALPHA * MAX_ALPHA];
+  for (int x = threadIdx.x; x < a.sp.alphabet * a.sp.alphabet; x += blockDim.x) s_sub[x] = a.sp.subst[x];
+  __syncthreads();
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t t = blockIdx.x * 4 + wib;
   const GraphDesc *gd = a.gd;  // captured pipeline: batch, outputs and count from here
@@ -580,10 +611,11 @@ __global__ void __launch_bounds__(128) k_walk_tw(const WalkArgs a) {
   const uint32_t p = a.order[t];
   const TbLayout L = a.tbl[p];
   const bool pk = L.family == FAM_PACK;
-  if (!L.valid || !(pk || (L.family == FAM_FULL && !a.sp.use_band))) {
-    if (lane == 0) walk_thread(a, b, out, p);  // empty pairs, banded int32 tiles
+  if (!L.valid || !(pk || L.family == FAM_FULL)) {
+    if (lane == 0) walk_thread(a, b, out, p);  // empty pairs
     return;
   }
+  const bool fb = !pk && a.sp.use_band;
   const FwdOut f = a.fwd[p];
   if (f.status != FILTR_ST_OK && f.status != FILTR_ST_DROPPED) {
     if (lane == 0) out[p].cigar_len = 0;
@@ -592,25 +624,38 @@ __global__ void __launch_bounds__(128) k_walk_tw(const WalkArgs a) {
   const int N = (int)b.r_len[p];
   const uint32_t *tb = a.tb + L.off;
   const PackGeom pg{L.R, (int64_t)pack_strip_tb_words(1, N, L.R)};
-  WalkCore w{b.q_seq + b.q_off[p], b.r_seq + b.r_off[p], a.sp.subst, a.sp.alphabet,
+  WalkCore w{b.q_seq + b.q_off[p], b.r_seq + b.r_off[p], s_sub, a.sp.alphabet,
              a.sp.e, a.sp.o + a.sp.e, a.sp.mode == FILTR_LOCAL, f.end_i, f.end_j, f.score, 0,
              Emitter{a.stage + a.stage_off[p], 0, -1, 0}, a.sp.mid != 0};
   TileCache &C = cache[wib];
   bool done = false;
-  auto cell = [&](int ii, int jj) -> uint8_t {
+  FullGeom g_row, g_lane;  // banded int32 tiles: cursors for rows i0 and i0 - lane
+  if (fb) {
+    geom_init(g_row, L.R, (int)b.q_len[p], N, a.sp);
+    g_lane = g_row;
+  }
+  auto cell = [&](FullGeom &g, int ii, int jj) -> uint8_t {
     if (ii < 1 || jj < 1) return 0;
-    return (uint8_t)(pk ? pack_bits(tb, pg, ii, jj) : full_bits_unbanded(tb, L.R, N, ii, jj));
+    if (pk) return (uint8_t)pack_bits(tb, pg, ii, jj);
+    if (fb) return (uint8_t)full_bits(tb, g, ii, jj);
+    return (uint8_t)full_bits_unbanded(tb, L.R, N, ii, jj);
   };
   for (;;) {
     const int i0 = __shfl_sync(0xffffffffu, w.i, 0), j0 = __shfl_sync(0xffffffffu, w.j, 0);
     if (__shfl_sync(0xffffffffu, (int)done, 0)) break;
-    const uint8_t cd = cell(i0 - lane, j0 - lane), cr = cell(i0, j0 - lane),
-                  cc = cell(i0 - lane, j0);
+    const uint8_t cr = cell(g_row, i0, j0 - lane), cd = cell(g_lane, i0 - lane, j0 - lane),
+                  cc = cell(g_lane, i0 - lane, j0);
     C.d[lane] = cd;
     C.row[lane] = cr;
     C.col[lane] = cc;
+    C.qc[lane] = (i0 - 1 - lane >= 0) ? w.q[i0 - 1 - lane] : 0;
+    C.rc[lane] = (j0 - 1 - lane >= 0) ? w.r[j0 - 1 - lane] : 0;
+    if (lane == 0) {
+      C.i0 = i0;
+      C.j0 = j0;
+    }
     __syncwarp();
-    if (lane == 0) done = walk_run(w, TileCacheBits{&C, i0, j0}, -1, INT64_MIN);
+    done = walk_coop(w, TileCacheBits{&C, i0, j0}, -1, INT64_MIN, TileCacheCodes{&C});
     __syncwarp();
   }
   if (lane == 0) {
