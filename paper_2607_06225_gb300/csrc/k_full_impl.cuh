@@ -20,6 +20,7 @@ namespace {
 struct WarpIO {
   int2 *buf;
   __device__ bool wait(int) { return true; }
+  static constexpr bool FETCH = false;
   __device__ int2 in(int j) { return buf[j]; }
   __device__ void out(int j, int H, int F) { buf[j] = make_int2(H, F); }
   __device__ void done_col(int, int, int) {}

@@ -36,6 +36,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 struct RingIO {
+  static constexpr bool FETCH = true;
   int2 *ring;
   uint32_t stride;
   unsigned long long *prog;
@@ -77,6 +78,15 @@ struct RingIO {
     return ok != 0;
   }
   __device__ int2 in(int j) { return __ldcg(ring + (size_t)((s - 1) % nw) * stride + (j - prev_jlo)); }
+  // After wait(j): the published columns j .. min(ready, jmax, j + 31), lane x
+  // loading column j + x.  The warp barrier orders the other lanes' loads after
+  // lane 0's acquire.
+  __device__ int fetch(int j, int jmax, int2 &v) {
+    __syncwarp();
+    const int n = min(min(ready, jmax) - j + 1, 32), x = threadIdx.x & 31;
+    if (x < n) v = __ldcg(ring + (size_t)((s - 1) % nw) * stride + (j + x - prev_jlo));
+    return n;
+  }
   __device__ void out(int j, int H, int F) {
     __stcg(ring + (size_t)(s % nw) * stride + (j - jlo), make_int2(H, F));
   }

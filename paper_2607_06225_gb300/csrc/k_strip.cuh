@@ -127,6 +127,12 @@ struct LaneBest {
 //   bool wait(int j)          -- before lane 0 reads column j of the strip
 //                                above; false aborts the strip (timeout)
 //   int2 in(int j)            -- lane 0 only: (H, F) of the strip above
+//   FETCH                     -- constexpr bool: lane 0's input row is
+//                                fetched ahead with fetch() instead of in()
+//   int fetch(int j, int jmax, int2 &v) -- (FETCH only) after wait(j): lane x
+//                                loads (H, F) of column j + x of the strip
+//                                above for the n columns (1 <= n <= 32, up to
+//                                jmax) known to be ready; returns n
 //   void out(int j, int H, int F) -- lane 31 only: this strip's bottom row
 //   void done_col(int j, int jlo, int jhi) -- lane 31 only, after out(j)
 // prev_jlo / prev_jhi: the strip above's columns (empty for s == 0).
@@ -197,6 +203,13 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
 
   const int nsteps = (jhi - jlo + 1) + 31;
   int upH = NEG, upF = NEG, prevIn = dtop;
+  // lane 0's input row, fetched ahead (IO::FETCH): lane x of pv holds column
+  // pbase + x of the strip above (x < pn), so a step waits on a load once per
+  // fetch.  A strip that follows the strip above closely (one long pair) would
+  // otherwise wait on a load every step; with many warps per SM (batched
+  // pairs) the loads' latency is hidden anyway, and the registers cost more.
+  int2 pv = make_int2(NEG, NEG);
+  int pbase = 0, pn = 0;
   int rc_next = P.r[jlo - 1];
   // Best cell (local), without a per-step scan: each cell's key is
   // H * 32 + (31 - its row in the lane), so the largest key is the largest H
@@ -210,8 +223,20 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
   for (int t = 0; t < nsteps; ++t) {
     const int j = jlo + t - lane;
     const int j0 = jlo + t;  // lane 0's column
-    if (s > 0 && j0 <= jhi && j0 >= prev_jlo && j0 <= prev_jhi) {
-      if (!io.wait(j0)) return false;
+    const bool need = s > 0 && j0 <= jhi && j0 >= prev_jlo && j0 <= prev_jhi;  // warp-uniform
+    int2 vin = make_int2(NEG, NEG);
+    if constexpr (IO::FETCH) {
+      if (need) {
+        if (j0 >= pbase + pn) {
+          if (!io.wait(j0)) return false;
+          pn = io.fetch(j0, prev_jhi, pv);
+          pbase = j0;
+        }
+        vin.x = __shfl_sync(STRIP_FULLMASK, pv.x, j0 - pbase);
+        vin.y = AFFINE ? __shfl_sync(STRIP_FULLMASK, pv.y, j0 - pbase) : NEG;
+      }
+    } else {
+      if (need && !io.wait(j0)) return false;
     }
     int inH = __shfl_up_sync(STRIP_FULLMASK, upH, 1);
     int inF = AFFINE ? __shfl_up_sync(STRIP_FULLMASK, upF, 1) : NEG;
@@ -219,10 +244,10 @@ __device__ __forceinline__ bool strip_pass(const StripPair &P, int s, int jlo, i
       if (s == 0) {
         inH = (!BAND || j <= hi) ? (LOCAL ? 0 : -(o + j * e)) : NEG;
         inF = NEG;
-      } else if (j >= prev_jlo && j <= prev_jhi) {
-        const int2 v = io.in(j);
-        inH = v.x;
-        inF = v.y;
+      } else if (need) {
+        if constexpr (!IO::FETCH) vin = io.in(j);
+        inH = vin.x;
+        inF = vin.y;
       } else {
         inH = NEG;
         inF = NEG;
