@@ -14,7 +14,7 @@ extern "C" {
  * strip never publishing its progress, so every later strip's bounded wait runs
  * out after timeout_ns nanoseconds.  Returns FILTR_ERR_TIMEOUT when the
  * timeout path works (every warp stopped and the context stays usable);
- * M must exceed one strip (512 rows). */
+ * M must exceed 512 rows (at least two strips). */
 filtr_status filtr_test_long_timeout(filtr_ctx *ctx, const filtr_params *params, const uint8_t *q,
                                      uint32_t M, const uint8_t *r, uint32_t N,
                                      uint64_t timeout_ns);

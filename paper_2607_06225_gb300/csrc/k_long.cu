@@ -90,9 +90,10 @@ struct RingIO {
   __device__ void out(int j, int H, int F) {
     __stcg(ring + (size_t)(s % nw) * stride + (j - jlo), make_int2(H, F));
   }
+  // Lane 31 writes the ring and publishes: its release store orders its own
+  // ring writes before the progress word, so no separate fence is needed.
   __device__ void done_col(int j, int jlo, int jhi) {
     if ((((j - jlo) & 15) == 15 || j == jhi) && !(withhold && s == 0)) {
-      __threadfence();
       st_release(prog + s % nw, ((unsigned long long)s << 32) | (unsigned)j);
     }
   }
@@ -226,7 +227,7 @@ __global__ void k_long_finish(const LongArgs a, int nw, uint64_t cells, filtr_re
 
 template <bool LOCAL, bool AFFINE, bool TB, bool BAND>
 cudaError_t coop(const LongArgs &a, int grid, cudaStream_t s) {
-  constexpr int R = 16;
+  constexpr int R = LONG_R;
   auto k = k_long<R, LOCAL, AFFINE, TB, BAND>;
   const int smem = full_smem_bytes(R, a.sp.alphabet);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -238,7 +239,7 @@ cudaError_t coop(const LongArgs &a, int grid, cudaStream_t s) {
 
 template <bool LOCAL, bool AFFINE, bool TB, bool BAND>
 int occ_long() {
-  constexpr int R = 16;
+  constexpr int R = LONG_R;
   int nb = 0;
   auto k = k_long<R, LOCAL, AFFINE, TB, BAND>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, full_smem_bytes(R, 20));

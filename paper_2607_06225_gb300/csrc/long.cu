@@ -59,7 +59,7 @@ filtr_status run_long(Ctx *c, const ScoreParams &sp, const filtr_params *params,
                       uint32_t M, const uint8_t *r, uint32_t N, filtr_result *out, uint32_t *cigar,
                       uint64_t cap, cudaStream_t st, int withhold, unsigned long long timeout_ns,
                       bool sync = true) {
-  constexpr int R = 16, HS = 32 * R;
+  constexpr int R = LONG_R, HS = 32 * R;
   int64_t lo = -(int64_t)M - 1, hi = (int64_t)N + 1;
   if (sp.use_band) {
     band_limits(M, N, sp.band, sp.band_literal, &lo, &hi);
