@@ -253,9 +253,11 @@ filtr_status filtr_align_batch_noalloc(const filtr_params *params, uint32_t n_pa
  * X-drop pairs run as one antidiagonal sweep with checkpointed traceback: every
  * `C`-th antidiagonal's state is kept, and the backward pass recomputes one
  * segment at a time, so the traceback memory is bounded by the workspace.
- * Band / full-matrix pairs split the query into row strips, one per CTA, which
- * hand their boundary rows down through global memory with release/acquire
- * flags; every wait is bounded and a timeout returns FILTR_ERR_TIMEOUT. */
+ * Band / full-matrix pairs split the query into row strips of 256 rows, one
+ * warp per strip at a time, which hand their bottom rows down through global
+ * memory with release/acquire progress words; every wait is bounded and a
+ * timeout returns FILTR_ERR_TIMEOUT.  Pairs with M <= 512 or M * N < 2^22
+ * run as a one-pair batch instead. */
 filtr_status filtr_align_long(filtr_ctx *ctx, const filtr_params *params, const uint8_t *q,
                               uint32_t M, const uint8_t *r, uint32_t N, filtr_result *out,
                               uint32_t *cigar, uint64_t cigar_cap, void *stream);
