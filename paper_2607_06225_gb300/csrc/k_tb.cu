@@ -822,8 +822,8 @@ cudaError_t launch_walk(const WalkArgs &a, cudaStream_t s) {
   // A warp per pair keeps more loads in flight for each pair but issues the
   // serial walk as a whole warp's instructions: for one or a few pairs (plain
   // per-pair calls, a long pair) it is the faster form; with thousands of pairs
-  // a thread per pair (32 pairs per instruction stream) is (2.3 ms against
-  // 5.2 ms for the 100,000-pair protein batch).
+  // a thread per pair (32 pairs per instruction stream) is (2.5 ms against
+  // 3.4 ms for the 100,000-pair protein batch).
   if (a.n_order <= 256)
     k_walk_tw<<<(a.n_order + 3) / 4, 128, 0, s>>>(a);
   else
