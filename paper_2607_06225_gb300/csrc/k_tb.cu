@@ -265,19 +265,13 @@ struct WalkCore {
   bool mid = false;  // Table 1's M/I/D: a gap that opened leaves through a diagonal step (state 3)
 };
 
-// Residue codes of the walk's diagonal steps: straight from the sequences, or
-// from codes a warp cached with the traceback bits.
-struct GlobalCodes {
-  __device__ int q(const WalkCore &w, int i) const { return w.q[i - 1]; }
-  __device__ int r(const WalkCore &w, int j) const { return w.r[j - 1]; }
-};
-
 // One step of the walk (those of k_walk): 1 when the alignment's start is
 // reached, 2 when the current cell's antidiagonal is <= k_stop or < k_low or
-// its bits are not cached (state kept), else 0.
-template <class Bits, class Codes = GlobalCodes>
+// its bits are not cached (state kept), else 0.  Codes gives the residue codes
+// of the diagonal steps (cached by the warp beside the bits).
+template <class Bits, class Codes>
 __device__ __forceinline__ int walk_step(WalkCore &w, const Bits &bits, int64_t k_stop, int64_t k_low,
-                                         const Codes &codes = Codes{}) {
+                                         const Codes &codes) {
   if (w.state == 0) {
     if ((w.i == 0 && w.j == 0) || (w.local && w.v == 0)) return 1;
     if (w.i == 0) {
@@ -350,19 +344,9 @@ __device__ __forceinline__ int walk_step(WalkCore &w, const Bits &bits, int64_t 
 }
 
 // Walks until the alignment's start is reached (returns true), or until the
-// current cell's antidiagonal is <= k_stop or < k_low (returns false, state
-// kept): the steps of k_walk, one walk_step at a time.
-template <class Bits, class Codes = GlobalCodes>
-__device__ __forceinline__ bool walk_run(WalkCore &w, const Bits &bits, int64_t k_stop,
-                                         int64_t k_low, const Codes &codes = Codes{}) {
-  for (;;) {
-    const int r = walk_step(w, bits, k_stop, k_low, codes);
-    if (r == 1) return true;
-    if (r == 2) return false;
-  }
-}
-
-// The same walk with the whole warp (every lane calls it; w is lane 0's).  A
+// current cell's antidiagonal is <= k_stop or < k_low or its bits are not
+// cached (returns false, state kept), with the whole warp (every lane calls
+// it; w is lane 0's).  A
 // run of diagonal steps (matches and mismatches, H taken from the diagonal) is
 // taken in one go: lane d looks at the cell d steps down the diagonal, a ballot
 // finds where the run ends (a gap, row or column 0, the window's edge, or for
