@@ -75,6 +75,20 @@ def test_banded_long(F, ctx, literal):
                                          band=64, band_literal=literal, traceback=True))
 
 
+def test_banded_long_local(F, ctx):
+    """A local alignment inside a long banded pair: a 12 kbp core at 3/1/1%
+    sub/ins/del between random flanks, band 64 around the core's diagonal.  The
+    best cell is reduced over every strip's warps, and the warp walk stops at the
+    first H of 0 inside the banded tile."""
+    rng = np.random.default_rng(21)
+    core = rng.integers(0, 4, 12000).astype(np.uint8)
+    flank = lambda n: rng.integers(0, 4, n).astype(np.uint8)
+    r = np.concatenate([flank(1500), core, flank(800)])
+    q = np.concatenate([flank(1500), synth.mutate(rng, core, 0.03, 0.01, 0.01, 0.7), flank(900)])
+    check_pair(F, ctx, q, r, DNA_S, dict(mode="local", affine=True, gap_open=4, gap_extend=2,
+                                         band=64, traceback=True))
+
+
 def test_xdrop_long_scaled(F, ctx):
     """The megabase workload's shape at 30 kbp: 1% divergence plus a 300-base
     random insertion, X-drop 200."""
