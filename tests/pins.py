@@ -89,6 +89,47 @@ def brute_local(q, r, S, o, e):
     return best
 
 
+def path_in_band(path, i0, j0, lo, hi) -> bool:
+    """Whether every cell a path visits from (i0, j0), its first cell included,
+    lies on a diagonal d = j - i with lo <= d <= hi (Sec. 7.1's static band)."""
+    i, j = i0, j0
+    if not lo <= j - i <= hi:
+        return False
+    for mv in path:
+        if mv != "V":
+            j += 1
+        if mv != "H":
+            i += 1
+        if not lo <= j - i <= hi:
+            return False
+    return True
+
+
+def brute_global_band(q, r, S, o, e, lo, hi):
+    """Best score over the paths (0,0) -> (M,N) that stay inside the band, or
+    None when no path does."""
+    scores = [path_score(p, q, r, S, o, e) for p in all_paths(len(q), len(r))
+              if path_in_band(p, 0, 0, lo, hi)]
+    return max(scores) if scores else None
+
+
+def brute_local_band(q, r, S, o, e, lo, hi):
+    """Best score over every path between two cells (i0, j0) <= (i1, j1) that
+    stays inside the band, or 0 (the empty alignment)."""
+    best = 0
+    M, N = len(q), len(r)
+    for i0 in range(M + 1):
+        for i1 in range(i0, M + 1):
+            for j0 in range(N + 1):
+                for j1 in range(j0, N + 1):
+                    if i1 - i0 == 0 and j1 - j0 == 0:
+                        continue
+                    for p in all_paths(i1 - i0, j1 - j0):
+                        if path_in_band(p, i0, j0, lo, hi):
+                            best = max(best, path_score(p, q[i0:i1], r[j0:j1], S, o, e))
+    return best
+
+
 def levenshtein(a, b) -> int:
     """Textbook two-row edit distance (unit substitution / insertion / deletion)."""
     prev = list(range(len(b) + 1))

@@ -2,8 +2,8 @@
 the pin suite (test_oracle_pins.py) rejects every one of them: a transposed
 operand, a dropped term, a wrong sign, each tie-break flipped, the X-drop rule
 and domain altered, the Z-drop distance term dropped, signed or anchored, its
-best-diagonal tie flipped, the band edge shifted, the CIGAR op table swapped and
-the cell counter widened."""
+best-diagonal tie flipped, the band edge shifted, a neighbour outside the domain
+read as zero, the CIGAR op table swapped and the cell counter widened."""
 import os
 import shutil
 import subprocess
@@ -42,6 +42,8 @@ MUTANTS = {
     "mid_F_opens_from_H": ("out->F = (mid ? u->M : u->H) - o - e;", "out->F = u->H - o - e;"),
     "mid_walk_skips_forced_diagonal": ("if (!ch.e_ext) state = after_open;",
                                        "if (!ch.e_ext) state = 0;"),
+    "missing_left_neighbour_as_zero": ("if (l && (mid ? l->vM : l->vH)) {\n      out->E = (mid ? l->M : l->H) - o - e;",
+                                       "if (!l || (mid ? l->vM : l->vH)) {\n      out->E = (l ? (mid ? l->M : l->H) : 0) - o - e;"),
     "cells_count_boundary": ("      if (i >= 1 && j >= 1) ++*cells;\n      if (alive)",
                              "      ++*cells;\n      if (alive)"),
 }

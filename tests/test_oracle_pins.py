@@ -7,6 +7,7 @@ fix, none of which is the oracle restating itself.
   * self-alignment scores the sum of the diagonal substitution scores;
   * a band at least as wide as the matrix reproduces the unpruned run; the
     banded domain in (k, m) coordinates matches the closed form of Sec. 7.1;
+    a banded score is the best path that stays inside the band (brute force);
   * X-drop with X = infinity reproduces the unpruned run;
   * row-major and antidiagonal evaluation agree in every output (Sec. 6:
     ordering rewrites preserve values and traceback);
@@ -21,7 +22,8 @@ import numpy as np
 import pytest
 
 import oracle
-from pins import (brute_global, brute_global_mid, brute_local, brute_local_mid, cigar_from_str,
+from pins import (brute_global, brute_global_band, brute_global_mid, brute_local, brute_local_band,
+                  brute_local_mid, cigar_from_str,
                   levenshtein, mid_ok, rescore_cigar)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -142,6 +144,56 @@ def test_band_closed_form(oracle_lib):
                            band_literal=True)
         assert res["cells"] == sum(1 for (i, j) in want if i >= 1 and j >= 1)
         assert res["status"] == (0 if abs(N - M) <= B else 2)
+
+
+@pytest.mark.parametrize("affine,o", [(True, 4), (False, 0)])
+@pytest.mark.parametrize("mode", ["global", "local"])
+def test_band_brute_force(mode, affine, o, oracle_lib):
+    """Sec. 7.1: a banded alignment scores the best path (in local mode, the best
+    path between any two cells, or 0) whose every cell lies inside the band --
+    brute force over every path of tiny pairs, literal and widened bands.  A
+    global pair whose band holds no path from (0,0) to (M,N) is unreachable."""
+    rng = np.random.default_rng(31 if affine else 32)
+    seen_unreachable = seen_clipped = False
+    for t in range(48):
+        M, N = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+        r = rng.integers(0, 4, size=N).astype(np.uint8)
+        if t % 3 == 1:  # a related pair: substitutions of the reference, then cut to M
+            q = np.where(rng.random(max(M, N)) < 0.2, rng.integers(0, 4, size=max(M, N)),
+                         np.resize(r, max(M, N)))[:M].astype(np.uint8)
+        elif t % 3 == 2:  # the reference behind 1-2 extra residues: its diagonal is -s
+            s = int(rng.integers(1, 3))
+            q = np.concatenate([rng.integers(0, 4, size=s), r])[:max(M, s + 1)].astype(np.uint8)
+            M = len(q)
+        else:
+            q = rng.integers(0, 4, size=M).astype(np.uint8)
+        B = int(rng.integers(0, 3))
+        for literal in (False, True):
+            if literal:
+                lo, hi = -B, B
+            else:  # widened to hold both corners
+                lo, hi = min(0, N - M) - B, max(0, N - M) + B
+            res = oracle.align(q, r, DNA_S, mode=mode, affine=affine, gap_open=o, gap_extend=2,
+                               band=B, band_literal=literal)
+            unbanded = oracle.align(q, r, DNA_S, mode=mode, affine=affine, gap_open=o,
+                                    gap_extend=2)
+            if mode == "global":
+                want = brute_global_band(q, r, DNA_S, o, 2, lo, hi)
+                if want is None:
+                    seen_unreachable = True
+                    assert res["status"] == 2
+                    continue
+                assert res["status"] == 0 and res["score"] == want
+            else:
+                want = brute_local_band(q, r, DNA_S, o, 2, lo, hi)
+                assert res["score"] == want
+                if want == 0:
+                    continue
+            seen_clipped |= want < unbanded["score"]
+            _check_cigar(res, q, r, DNA_S, o, 2)
+    assert seen_clipped  # some band cut off the unbanded optimum
+    if mode == "global":
+        assert seen_unreachable  # some literal band missed the far corner
 
 
 def test_widened_band_holds_both_corners(oracle_lib):
