@@ -1,17 +1,18 @@
 // k_long.cu -- one long pair with every SM on it (full matrix or static band).
 //
-// The query is cut into row strips of 32*R rows (k_strip.cuh).  All warps of a
-// cooperatively launched grid (so every warp is resident) take strips
-// round-robin: warp w handles strips w, w + NW, w + 2NW, ...  Strip s needs the
-// bottom row of strip s-1, which is being computed at the same time by another
-// warp: lane 31 of strip s-1 writes (H, F) per column into a ring slot and,
-// every 16 columns, publishes a 64-bit progress word (strip << 32 | column)
-// with a release store (slots are indexed from the strip's first column, so a
-// banded pair needs only band-wide slots); lane 0 of strip s waits with acquire
-// loads until the
-// column it needs is published.  A ring of NW slots suffices: strip s-1+NW
-// reuses strip s-1's slot, and it cannot reach column c before strip s has
-// read column c (the chain s, s+1, ..., s-2+NW must each pass c first).
+// The query is cut into row strips of 32*R rows (k_strip.cuh, R = LONG_R).
+// All warps of a cooperatively launched grid (so every warp is resident) take
+// strips round-robin: warp w handles strips w, w + NW, w + 2NW, ...  Strip s
+// needs the bottom row of strip s-1, which is being computed at the same time
+// by another warp: lane 31 of strip s-1 writes (H, F) per column into a ring
+// slot and, every 16 columns, publishes a 64-bit progress word (strip << 32 |
+// column) with a release store (slots are indexed from the strip's first
+// column, so a banded pair needs only band-wide slots); lane 0 of strip s
+// waits with acquire loads until the column it needs is published, and the
+// warp then fetches every published column it can use (up to 32) at once.  A
+// ring of NW slots suffices: strip s-1+NW reuses strip s-1's slot, and it
+// cannot reach column c before strip s has read column c (the chain s, s+1,
+// ..., s-2+NW must each pass c first; a fetch reads a column before its use).
 // No cycle of waits exists (every wait is on a smaller strip number), and
 // every wait is bounded by a timeout on %globaltimer, after which the kernel
 // sets an error flag, every warp stops at its next wait, and the host returns
