@@ -57,6 +57,30 @@ filtr_status filtr_test_set_search_ring(filtr_ctx *ctx, int32_t entries);
  * (filtr_stats.pairs_xd16_rerun counts them).  Results do not depend on it. */
 filtr_status filtr_test_set_packed_sweep(filtr_ctx *ctx, int32_t mode);
 
+/* Run filtr_align_batch's host planner, with no device and the default shape
+ * costs, on n pairs of lengths q_len[p] x r_len[p] (HOST arrays) under params.
+ * Each wave's traceback may use tb_budget_words 32-bit words.  Outputs are HOST
+ * arrays the caller allocates:
+ *   order[n]       : the planned pairs in launch order (waves, then the groups
+ *                    of one kernel shape inside a wave, each cost-descending),
+ *                    then the pairs with nothing to evaluate;
+ *   wave[n]        : per pair id, its wave (UINT32_MAX: nothing to evaluate);
+ *   tb_off[n], tb_words[n] : per pair id, its traceback area inside its wave's
+ *                    (words; 0 with traceback off);
+ *   kernel[n]      : per pair id, family << 16 | R << 8 | warps (family 0 the
+ *                    int32 tile, 1 the antidiagonal sweep, 3 the int16x2 tile;
+ *                    R rows per lane of a tile or slots per lane of the sweep;
+ *                    warps the sweep's first group width);
+ *   wave_info[3n]  : per wave, its traceback words, then the first and one past
+ *                    the last position of its pairs in order;
+ *   counts[3]      : planned pairs, waves, pairs with nothing to evaluate.
+ * FILTR_ERR_NOMEM when one pair's traceback exceeds tb_budget_words;
+ * FILTR_ERR_INVALID for bad parameters or NULL arrays. */
+filtr_status filtr_test_plan_host(const filtr_params *params, uint32_t n, const uint32_t *q_len,
+                                  const uint32_t *r_len, uint64_t tb_budget_words, uint32_t *order,
+                                  uint32_t *wave, uint64_t *tb_off, uint64_t *tb_words,
+                                  uint32_t *kernel, uint64_t *wave_info, uint32_t *counts);
+
 #ifdef __cplusplus
 }
 #endif

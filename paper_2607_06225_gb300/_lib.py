@@ -182,6 +182,9 @@ def lib():
         L.filtr_test_set_search_ring.argtypes = [C.c_void_p, C.c_int32]
         L.filtr_test_set_packed_sweep.restype = i32
         L.filtr_test_set_packed_sweep.argtypes = [C.c_void_p, C.c_int32]
+        L.filtr_test_plan_host.restype = i32
+        L.filtr_test_plan_host.argtypes = [C.POINTER(Params), C.c_uint32, _P, _P, C.c_uint64, _P, _P,
+                                           _P, _P, _P, _P, _P]
         L.filtr_graph_create.restype = i32
         L.filtr_graph_create.argtypes = [C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32,
                                          C.c_size_t, C.POINTER(C.c_void_p)]

@@ -11,6 +11,7 @@
 #include <string>
 #include <tuple>
 
+#include "../../include/filtr_testing.h"
 #include "filtr_ctx.h"
 #include "k_xdrop_layout.h"
 #include "plan.h"
@@ -802,6 +803,49 @@ const char *filtr_version(void) { return "filtr-gb300 0.1 (sm_103a)"; }
 filtr_status filtr_params_check(const filtr_params *params) {
   ScoreParams sp;
   return to_score_params(params, &sp);
+}
+
+filtr_status filtr_test_plan_host(const filtr_params *params, uint32_t n, const uint32_t *q_len,
+                                  const uint32_t *r_len, uint64_t tb_budget_words, uint32_t *order,
+                                  uint32_t *wave, uint64_t *tb_off, uint64_t *tb_words,
+                                  uint32_t *kernel, uint64_t *wave_info, uint32_t *counts) {
+  ScoreParams sp;
+  filtr_status rc = to_score_params(params, &sp);
+  if (rc != FILTR_OK) return rc;
+  if (!counts || (n && (!q_len || !r_len || !order || !wave || !tb_off || !tb_words || !kernel ||
+                        !wave_info))) {
+    set_error("filtr_test_plan_host: NULL argument");
+    return FILTR_ERR_INVALID;
+  }
+  PlanInput in{&sp, n, q_len, r_len, tb_budget_words, 8, 0};
+  Plan P;
+  if (!make_plan(in, &P)) return FILTR_ERR_NOMEM;
+  const uint32_t nm = (uint32_t)P.order.size(), nt = (uint32_t)P.trivial.size();
+  for (uint32_t t = 0; t < nm; ++t) order[t] = P.order[t];
+  for (uint32_t t = 0; t < nt; ++t) order[nm + t] = P.trivial[t];
+  for (uint32_t p = 0; p < n; ++p) {
+    wave[p] = UINT32_MAX;
+    tb_off[p] = tb_words[p] = 0;
+    kernel[p] = 0;
+  }
+  for (size_t w = 0; w < P.waves.size(); ++w) {
+    const Wave &W = P.waves[w];
+    wave_info[3 * w] = W.tb_words;
+    wave_info[3 * w + 1] = W.walk_begin;
+    wave_info[3 * w + 2] = W.walk_end;
+    for (const Group &g : W.groups)
+      for (uint32_t t = g.begin; t < g.end; ++t) {
+        const uint32_t p = P.order[t];
+        wave[p] = (uint32_t)w;
+        kernel[p] = (uint32_t)g.family << 16 | (uint32_t)g.R << 8 | g.warps;
+        tb_off[p] = P.tbl[p].off;
+        tb_words[p] = sp.traceback ? P.s_words[p] : 0;
+      }
+  }
+  counts[0] = nm;
+  counts[1] = (uint32_t)P.waves.size();
+  counts[2] = nt;
+  return FILTR_OK;
 }
 
 filtr_status filtr_ctx_create(int device, size_t workspace_bytes, filtr_ctx **out) {
